@@ -1,0 +1,143 @@
+/*
+ * xpcs.h -- C ABI of the GB300 (sm_103a) library for XPCS two-time correlation on raw
+ * photon-count frames and on SVD-compressed frames, after arXiv 2407.20356,
+ * "Homomorphic data compression for real time photon correlation analysis".
+ *
+ * Conventions for every entry point:
+ *  - Pointers are DEVICE pointers (memory of the context's GPU) unless the parameter
+ *    name ends in `_host`, in which case they are host pointers.
+ *  - The caller owns every data buffer.  The library owns the opaque handles it creates
+ *    (context, ring plan, basis, stream) and frees them in the matching destroy/close.
+ *  - Matrices are dense row-major.  X is T x M (frame t, pixel p), one frame per row.
+ *  - Work is enqueued on the context's CUDA stream.  Unless the context is in
+ *    asynchronous mode (xpcs_set_async), each call waits for its work and returns any
+ *    error it raised; in asynchronous mode errors surface at xpcs_synchronize().
+ *  - Functions return an xpcs_status; nothing throws or aborts across the ABI.  The text
+ *    of the last error of a context is available from xpcs_last_error().
+ *  - Two-time outputs C are n_q x T x T float32 with only the upper triangle
+ *    (t2 >= t1) written; the lower triangle is left untouched.  Undefined pairs (a ring
+ *    sum <= 0) are NaN.  g2 and count arrays are n_q x T, indexed by lag tau = 0..T-1;
+ *    g2 is NaN where count is 0.
+ */
+#ifndef XPCS_GB300_H
+#define XPCS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum xpcs_status {
+  XPCS_OK = 0,
+  XPCS_EINVAL = 1,   /* bad argument, shape or handle */
+  XPCS_ENOMEM = 2,   /* device allocation failed or the HBM budget would be exceeded */
+  XPCS_ECUDA = 3,    /* a CUDA runtime/driver/library call failed */
+  XPCS_ETIMEOUT = 4, /* a bounded device-side wait expired; the context stays usable */
+  XPCS_EBUSY = 5,    /* the request does not fit the HBM budget now; retry later */
+  XPCS_ERANGE = 6,   /* input outside the exact range of the requested path */
+  XPCS_ENOTSUP = 7   /* shape or option not supported by this build */
+} xpcs_status;
+
+typedef enum xpcs_dtype { XPCS_U8 = 0, XPCS_U16 = 1 } xpcs_dtype;
+
+/* Arithmetic of the compressed two-time Gram (tensor cores, f32 accumulation). */
+typedef enum xpcs_precision {
+  XPCS_PREC_FP16 = 0,  /* coefficients in f16 (unit roundoff 2^-11) */
+  XPCS_PREC_BF16 = 1,  /* coefficients in bf16 (unit roundoff 2^-8) */
+  XPCS_PREC_BF16X3 = 2 /* hi/lo bf16 split, three products: about 2^-16 */
+} xpcs_precision;
+
+typedef struct xpcs_ctx xpcs_ctx;
+typedef struct xpcs_rings xpcs_rings;
+typedef struct xpcs_basis xpcs_basis;
+
+/* ------------------------------------------------------------------ context */
+
+/* Library version (major*10000 + minor*100 + patch). */
+int xpcs_version(void);
+
+/* Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t, or NULL
+ * for a stream the library creates).  `hbm_budget_bytes` caps the device memory the
+ * library itself allocates (scratch and handles); 0 means no cap. */
+xpcs_status xpcs_create(int device, size_t hbm_budget_bytes, void* cuda_stream, xpcs_ctx** out);
+xpcs_status xpcs_destroy(xpcs_ctx* ctx);
+/* Text of the last error of this context ("" if none).  Valid until the next call. */
+const char* xpcs_last_error(const xpcs_ctx* ctx);
+/* async != 0: calls return once their work is enqueued; errors surface at synchronize. */
+xpcs_status xpcs_set_async(xpcs_ctx* ctx, int async);
+/* Wait for all enqueued work and report any device-side error. */
+xpcs_status xpcs_synchronize(xpcs_ctx* ctx);
+/* Bytes the library currently holds on the device for this context and its handles. */
+size_t xpcs_device_bytes(const xpcs_ctx* ctx);
+
+/* ------------------------------------------------------------------ q-rings (Sec. 2.2)
+ * A ring plan fixes which pixels form each q-ring: qmap[p] in [0, n_q) is the ring of
+ * pixel p, -1 leaves the pixel out (the q-subsets of Sec. 2.2).  `qmap` is a device
+ * int32 array of length M, read once; the plan keeps its own copy. */
+xpcs_status xpcs_rings_create(xpcs_ctx* ctx, const int32_t* qmap, int64_t M, int n_q, xpcs_rings** out);
+xpcs_status xpcs_rings_destroy(xpcs_rings* rings);
+/* M_q, the pixel count of every ring (host array of n_q). */
+xpcs_status xpcs_rings_sizes(const xpcs_rings* rings, int64_t* Mq_host);
+
+/* Ring sums S_q(t) = sum over p in ring q of X[t][p] (M_q times the pixel average in the
+ * denominator of Eq. 1).  X: T x M counts of `dtype`.  S_out: n_q x T int64. */
+xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X, xpcs_dtype dtype, int64_t T,
+                           int64_t* S_out);
+
+/* ------------------------------------------------------------------ raw path (Eq. 1, 2)
+ * Exact two-time correlation of raw counts, per ring:
+ *   N_q = X_q X_q^T (Eq. 2 on the ring's pixels), C_q = M_q N_q / (S_q(t1) S_q(t2)) (Eq. 1),
+ *   g2_q(tau) = mean over t of C_q(t, t+tau) over defined pairs.
+ * The integer Gram is computed exactly on the tensor cores (bf16 operands, f32
+ * accumulation kept below 2^24); counts above 256, or a ring whose largest per-frame
+ * sum of squared counts reaches 2^24, return XPCS_ERANGE.
+ * Outputs (all nullable): C_out n_q x T x T f32 (upper triangle), N_out n_q x T x T
+ * int64 (upper triangle), g2_out n_q x T f64, count_out n_q x T int64. */
+xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X, xpcs_dtype dtype, int64_t T,
+                             float* C_out, int64_t* N_out, double* g2_out, int64_t* count_out);
+
+/* ------------------------------------------------------------------ basis (Eq. 3-6)
+ * Fit the encoding matrix V_K (M x k) on n_fit frames F (T x M layout, n_fit rows):
+ * rows are divided by their Frobenius norm (Sec. 2.1), the n_fit x n_fit Gram is
+ * eigendecomposed in FP64, and V_K = F^T U_k Sigma_k^-1 keeps the k largest singular
+ * values (Eq. 6).  Ring factors G_q = B_q^T B_q and s_q = B_q^T 1 are formed in FP64.
+ * sigma_host (nullable): all n_fit singular values, descending.  k above the numerical
+ * rank returns XPCS_EINVAL. */
+xpcs_status xpcs_fit_basis(xpcs_ctx* ctx, const xpcs_rings* rings, const void* F, xpcs_dtype dtype, int64_t n_fit,
+                           int k, xpcs_basis** out, double* sigma_host);
+/* Use an external encoding matrix (the paper's option of a basis fit on other data):
+ * B_host is M x k FP64 row-major. */
+xpcs_status xpcs_basis_import(xpcs_ctx* ctx, const xpcs_rings* rings, const double* B_host, int k,
+                              xpcs_basis** out);
+/* Copy basis data to the host (each pointer nullable): B M x k, G n_q x k x k, s n_q x k. */
+xpcs_status xpcs_basis_export(xpcs_ctx* ctx, const xpcs_basis* basis, double* B_host, double* G_host,
+                              double* s_host);
+xpcs_status xpcs_basis_rank(const xpcs_basis* basis, int* k);
+xpcs_status xpcs_basis_destroy(xpcs_basis* basis);
+
+/* ------------------------------------------------------------------ encode (Eq. 7)
+ * Coefficients Y_K = X V_K: A_out is T x k float32.  X: T x M counts (M a multiple of 8
+ * for u16, 16 for u8).  Tensor cores: counts as bf16 (exact up to 256, else
+ * XPCS_ERANGE), V_K as a hi/lo bf16 pair, f32 accumulation. */
+xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* basis, const void* X, xpcs_dtype dtype, int64_t T,
+                        float* A_out);
+
+/* ------------------------------------------------------------------ compressed path (Eq. 8-10)
+ * Two-time correlation from coefficients only (no decompression):
+ *   N~_q = A G_q A^T, S~_q(t) = a_t s_q, C~_q = M_q N~_q / (S~_q(t1) S~_q(t2)),
+ * g2 as for the raw path.  A: T x k float32 (from xpcs_encode or the caller).
+ * Outputs nullable as for xpcs_twotime_raw. */
+xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T, xpcs_precision prec,
+                         float* C_out, double* g2_out, int64_t* count_out);
+
+/* ------------------------------------------------------------------ g2 over a stored C
+ * g2_q(tau) = mean over t of C[q][t][t+tau], NaN entries skipped, from the upper
+ * triangle of C (n_q x T x T float32).  g2_out n_q x T f64, count_out nullable. */
+xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out, int64_t* count_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XPCS_GB300_H */

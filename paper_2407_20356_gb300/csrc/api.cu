@@ -1,0 +1,734 @@
+// C ABI of the library: contexts, ring plans, bases and the offline correlation paths.
+#include <cudaTypedefs.h>
+#include <cusolverDn.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace xpcs;
+
+// ====================================================================== handles
+
+struct xpcs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  size_t held = 0;
+  bool async = false;
+  std::string err;
+  int num_sms = 0;
+  uint32_t* d_status = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_cap = 0;
+  cusolverDnHandle_t solver = nullptr;
+};
+
+struct xpcs_rings {
+  xpcs_ctx* ctx = nullptr;
+  int64_t M = 0;
+  int n_q = 0;
+  int64_t Mp = 0;                 // ring-sorted row length, each ring padded to 64
+  std::vector<int64_t> Mq;        // pixels per ring
+  std::vector<int> off;           // start of each ring's segment (multiple of 64)
+  std::vector<int> chunks;        // 64-wide chunks per ring segment (>= 1)
+  int* d_qmap = nullptr;
+  int* d_perm = nullptr;          // [Mp] pixel at each sorted position, -1 for padding
+  int* d_pos_ring = nullptr;      // [Mp] ring of each sorted position, -1 for padding
+  int* d_off = nullptr;
+  int* d_chunks = nullptr;
+  long long* d_Mq = nullptr;
+  size_t bytes = 0;
+};
+
+struct xpcs_basis {
+  xpcs_ctx* ctx = nullptr;
+  const xpcs_rings* rings = nullptr;
+  int k = 0;
+  int64_t M_pad = 0;
+  double* d_B = nullptr;          // M x k
+  double* d_G = nullptr;          // n_q x k x k
+  double* d_s = nullptr;          // n_q x k
+  float* d_G32 = nullptr;         // n_q x k x k
+  __nv_bfloat16* d_Bcat = nullptr;  // 2k x M_pad
+  size_t bytes = 0;
+};
+
+// ====================================================================== helpers
+
+namespace {
+
+xpcs_status fail(xpcs_ctx* ctx, xpcs_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+#define XPCS_CUDA(ctx, call)                                                                               \
+  do {                                                                                                     \
+    cudaError_t e_ = (call);                                                                               \
+    if (e_ != cudaSuccess)                                                                                 \
+      return fail((ctx), XPCS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+#define XPCS_TRY(expr)                      \
+  do {                                      \
+    xpcs_status s_ = (expr);                \
+    if (s_ != XPCS_OK) return s_;           \
+  } while (0)
+
+xpcs_status dev_alloc(xpcs_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return XPCS_OK;
+  if (ctx->budget && ctx->held + bytes > ctx->budget)
+    return fail(ctx, XPCS_ENOMEM, "device memory budget exceeded (" + std::to_string(ctx->held + bytes) + " > " +
+                                      std::to_string(ctx->budget) + " bytes)");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, XPCS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->held += bytes;
+  return XPCS_OK;
+}
+
+void dev_free(xpcs_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->held -= std::min(ctx->held, bytes);
+}
+
+// Scratch: one growing device buffer per context, carved per call.
+struct Carve {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+xpcs_status ensure_scratch(xpcs_ctx* ctx, size_t need) {
+  if (need <= ctx->scratch_cap) return XPCS_OK;
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  dev_free(ctx, ctx->scratch, ctx->scratch_cap);
+  ctx->scratch = nullptr;
+  ctx->scratch_cap = 0;
+  const size_t cap = need + need / 8;
+  void* p = nullptr;
+  XPCS_TRY(dev_alloc(ctx, &p, cap));
+  ctx->scratch = p;
+  ctx->scratch_cap = cap;
+  return XPCS_OK;
+}
+
+// Wait for the context's work (unless asynchronous) and map the device status word.
+xpcs_status finish(xpcs_ctx* ctx) {
+  if (ctx->async) return XPCS_OK;
+  return xpcs_synchronize(ctx);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// 2-D tiled map of a row-major [rows][cols] matrix of 16-bit (or 8-bit) elements,
+// box = box_cols x box_rows, with the given swizzle.
+xpcs_status make_map(xpcs_ctx* ctx, CUtensorMap* map, const void* base, CUtensorMapDataType dt, int elem_bytes,
+                     uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw) {
+  auto fn = get_encode_fn();
+  if (!fn) return fail(ctx, XPCS_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((cols * elem_bytes) & 15))
+    return fail(ctx, XPCS_ENOTSUP, "tensor map needs 16-byte aligned base and row pitch");
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * (uint64_t)elem_bytes};
+  cuuint32_t box[2] = {box_cols, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, XPCS_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return XPCS_OK;
+}
+
+// Work items of the two-time kernel: (q, delta, I0, I1), tiles (I, I+delta) of one tile
+// diagonal, CH tiles per item; ordered ring by ring, chunk by chunk, delta ascending.
+std::vector<int4> make_items(int n_q, int nT, int CH) {
+  std::vector<int4> items;
+  for (int q = 0; q < n_q; ++q)
+    for (int c = 0; c * CH < nT; ++c)
+      for (int d = 0; d < nT; ++d) {
+        const int I0 = c * CH, I1 = std::min(c * CH + CH, nT - d);
+        if (I0 < I1) items.push_back(make_int4(q, d, I0, I1));
+      }
+  return items;
+}
+
+}  // namespace
+
+// ====================================================================== context
+
+extern "C" int xpcs_version(void) { return 100; }
+
+extern "C" xpcs_status xpcs_create(int device, size_t hbm_budget_bytes, void* cuda_stream, xpcs_ctx** out) {
+  if (!out) return XPCS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return XPCS_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return XPCS_ECUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return XPCS_ECUDA;
+  if (prop.major * 10 + prop.minor < 100) return XPCS_ENOTSUP;
+  auto* ctx = new xpcs_ctx();
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  ctx->num_sms = prop.multiProcessorCount;
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return XPCS_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  void* st = nullptr;
+  if (dev_alloc(ctx, &st, 256) != XPCS_OK || cudaMemset(st, 0, 256) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return XPCS_ENOMEM;
+  }
+  ctx->d_status = static_cast<uint32_t*>(st);
+  *out = ctx;
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_destroy(xpcs_ctx* ctx) {
+  if (!ctx) return XPCS_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, ctx->scratch, ctx->scratch_cap);
+  dev_free(ctx, ctx->d_status, 256);
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return XPCS_OK;
+}
+
+extern "C" const char* xpcs_last_error(const xpcs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" xpcs_status xpcs_set_async(xpcs_ctx* ctx, int async) {
+  if (!ctx) return XPCS_EINVAL;
+  ctx->async = async != 0;
+  return XPCS_OK;
+}
+
+extern "C" size_t xpcs_device_bytes(const xpcs_ctx* ctx) { return ctx ? ctx->held : 0; }
+
+extern "C" xpcs_status xpcs_synchronize(xpcs_ctx* ctx) {
+  if (!ctx) return XPCS_EINVAL;
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  uint32_t st = 0;
+  XPCS_CUDA(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st != XPCS_DEV_OK) {
+    XPCS_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
+    if (st == XPCS_DEV_TIMEOUT) return fail(ctx, XPCS_ETIMEOUT, "a bounded device wait expired");
+    if (st == XPCS_DEV_RANGE)
+      return fail(ctx, XPCS_ERANGE,
+                  "counts outside the exact range (a count above 256, or a ring whose per-frame sum of squared "
+                  "counts reaches 2^24)");
+    return fail(ctx, XPCS_ECUDA, "device status " + std::to_string(st));
+  }
+  return XPCS_OK;
+}
+
+// ====================================================================== rings
+
+extern "C" xpcs_status xpcs_rings_create(xpcs_ctx* ctx, const int32_t* qmap, int64_t M, int n_q, xpcs_rings** out) {
+  if (!ctx || !qmap || !out || M <= 0 || n_q <= 0 || n_q > 1024) return fail(ctx, XPCS_EINVAL, "bad ring plan args");
+  *out = nullptr;
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  std::vector<int32_t> h(M);
+  XPCS_CUDA(ctx, cudaMemcpyAsync(h.data(), qmap, M * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  auto* r = new xpcs_rings();
+  r->ctx = ctx;
+  r->M = M;
+  r->n_q = n_q;
+  r->Mq.assign(n_q, 0);
+  for (int64_t p = 0; p < M; ++p) {
+    if (h[p] >= n_q || h[p] < -1) {
+      delete r;
+      return fail(ctx, XPCS_EINVAL, "qmap label outside [-1, n_q)");
+    }
+    if (h[p] >= 0) r->Mq[h[p]]++;
+  }
+  r->off.resize(n_q);
+  r->chunks.resize(n_q);
+  int64_t o = 0;
+  for (int q = 0; q < n_q; ++q) {
+    r->off[q] = (int)o;
+    const int64_t ch = std::max<int64_t>(1, (r->Mq[q] + KCH - 1) / KCH);
+    r->chunks[q] = (int)ch;
+    o += ch * KCH;
+  }
+  if (o > (int64_t)INT32_MAX / 2) {
+    delete r;
+    return fail(ctx, XPCS_ENOTSUP, "detector too large");
+  }
+  r->Mp = o;
+  std::vector<int> perm(r->Mp, -1), pos(r->Mp, -1), fill(n_q, 0);
+  for (int64_t p = 0; p < M; ++p) {
+    const int q = h[p];
+    if (q < 0) continue;
+    const int at = r->off[q] + fill[q]++;
+    perm[at] = (int)p;
+    pos[at] = q;
+  }
+  std::vector<long long> mq(r->Mq.begin(), r->Mq.end());
+  const size_t bytes = M * 4 + 2 * r->Mp * 4 + 2 * n_q * 4 + n_q * 8;
+  xpcs_status s = XPCS_OK;
+  void* p[6] = {};
+  const size_t sz[6] = {(size_t)M * 4, (size_t)r->Mp * 4, (size_t)r->Mp * 4, (size_t)n_q * 4, (size_t)n_q * 4,
+                        (size_t)n_q * 8};
+  for (int i = 0; i < 6 && s == XPCS_OK; ++i) s = dev_alloc(ctx, &p[i], sz[i]);
+  if (s != XPCS_OK) {
+    for (int i = 0; i < 6; ++i) dev_free(ctx, p[i], sz[i]);
+    delete r;
+    return s;
+  }
+  r->d_qmap = (int*)p[0];
+  r->d_perm = (int*)p[1];
+  r->d_pos_ring = (int*)p[2];
+  r->d_off = (int*)p[3];
+  r->d_chunks = (int*)p[4];
+  r->d_Mq = (long long*)p[5];
+  r->bytes = bytes;
+  cudaError_t e = cudaMemcpy(r->d_qmap, h.data(), sz[0], cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(r->d_perm, perm.data(), sz[1], cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(r->d_pos_ring, pos.data(), sz[2], cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(r->d_off, r->off.data(), sz[3], cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(r->d_chunks, r->chunks.data(), sz[4], cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(r->d_Mq, mq.data(), sz[5], cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    xpcs_rings_destroy(r);
+    return fail(ctx, XPCS_ECUDA, std::string("ring plan upload: ") + cudaGetErrorString(e));
+  }
+  *out = r;
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_rings_destroy(xpcs_rings* r) {
+  if (!r) return XPCS_EINVAL;
+  xpcs_ctx* ctx = r->ctx;
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, r->d_qmap, (size_t)r->M * 4);
+  dev_free(ctx, r->d_perm, (size_t)r->Mp * 4);
+  dev_free(ctx, r->d_pos_ring, (size_t)r->Mp * 4);
+  dev_free(ctx, r->d_off, (size_t)r->n_q * 4);
+  dev_free(ctx, r->d_chunks, (size_t)r->n_q * 4);
+  dev_free(ctx, r->d_Mq, (size_t)r->n_q * 8);
+  delete r;
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_rings_sizes(const xpcs_rings* r, int64_t* Mq_host) {
+  if (!r || !Mq_host) return XPCS_EINVAL;
+  for (int q = 0; q < r->n_q; ++q) Mq_host[q] = r->Mq[q];
+  return XPCS_OK;
+}
+
+// ====================================================================== raw path
+
+namespace {
+
+struct RawBuffers {
+  __nv_bfloat16* Xp;
+  long long* S;
+  unsigned long long* sq;
+  float* r;
+  uint8_t* blk_bad;
+  float* partials;
+  uint32_t* vbits;
+  long long* count;
+  int4* items;
+};
+
+// Ingest (ring-sorted bf16 copy + ring sums) and the per-frame factors of Eq. 1.
+xpcs_status raw_ingest(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_dtype dtype, int64_t T, int T_pad,
+                       int nT, bool want_xp, long long* S, RawBuffers& b) {
+  XPCS_CUDA(ctx, cudaMemsetAsync(b.sq, 0, R->n_q * sizeof(unsigned long long), ctx->stream));
+  RawIngestParams ip{};
+  ip.X = X;
+  ip.dtype = dtype;
+  ip.T = T;
+  ip.M = R->M;
+  ip.T_pad = T_pad;
+  ip.Mp = R->Mp;
+  ip.perm = R->d_perm;
+  ip.pos_ring = R->d_pos_ring;
+  ip.n_q = R->n_q;
+  ip.Xp = want_xp ? b.Xp : nullptr;
+  ip.S = S;
+  ip.sq = b.sq;
+  ip.status = ctx->d_status;
+  XPCS_CUDA(ctx, launch_raw_ingest(ip, ctx->stream));
+  return XPCS_OK;
+}
+
+}  // namespace
+
+extern "C" xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_dtype dtype,
+                                      int64_t T, int64_t* S_out) {
+  if (!ctx || !R || !X || !S_out || T <= 0 || R->ctx != ctx) return fail(ctx, XPCS_EINVAL, "bad ring_sums args");
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  Carve c;
+  c.take<unsigned long long>(R->n_q);
+  XPCS_TRY(ensure_scratch(ctx, c.off));
+  c = Carve{0, static_cast<char*>(ctx->scratch)};
+  RawBuffers b{};
+  b.sq = c.take<unsigned long long>(R->n_q);
+  // ring sums only: the ingest kernel covers exactly T frames
+  RawIngestParams ip{};
+  XPCS_CUDA(ctx, cudaMemsetAsync(b.sq, 0, R->n_q * sizeof(unsigned long long), ctx->stream));
+  ip.X = X;
+  ip.dtype = dtype;
+  ip.T = T;
+  ip.M = R->M;
+  ip.T_pad = (int)T;
+  ip.Mp = R->Mp;
+  ip.perm = R->d_perm;
+  ip.pos_ring = R->d_pos_ring;
+  ip.n_q = R->n_q;
+  ip.Xp = nullptr;
+  ip.S = reinterpret_cast<long long*>(S_out);
+  ip.sq = b.sq;
+  ip.status = ctx->d_status;
+  XPCS_CUDA(ctx, launch_raw_ingest(ip, ctx->stream));
+  return finish(ctx);
+}
+
+namespace {
+
+// Shared tail of both two-time paths: the Gram launch, pair counts and g2.
+xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap& tmR, GramParams gp, int n_q,
+                        int64_t T, int T_pad, int nT, int maxC, const std::vector<int4>& items, int4* d_items,
+                        uint32_t* vbits, long long* count, double* g2_out) {
+  XPCS_CUDA(ctx, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  gp.items = d_items;
+  gp.n_items = (int)items.size();
+  const int grid = std::min<int>(gp.n_items, ctx->num_sms);
+  XPCS_CUDA(ctx, launch_gram(tmL, tmR, gp, grid, ctx->stream));
+  if (count) {
+    XPCS_CUDA(ctx, launch_counts(gp.r, n_q, T, T_pad, vbits, T_pad / 32, count, ctx->stream));
+    if (g2_out)
+      XPCS_CUDA(ctx, launch_g2_finalize(gp.partials, count, n_q, T, nT, maxC, gp.CH, g2_out, ctx->stream));
+  }
+  return XPCS_OK;
+}
+
+}  // namespace
+
+extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_dtype dtype,
+                                        int64_t T, float* C_out, int64_t* N_out, double* g2_out, int64_t* count_out) {
+  if (!ctx || !R || !X || T <= 0 || R->ctx != ctx || (dtype != XPCS_U8 && dtype != XPCS_U16))
+    return fail(ctx, XPCS_EINVAL, "bad twotime_raw args");
+  if (T > (1 << 24)) return fail(ctx, XPCS_ENOTSUP, "T too large");
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int n_q = R->n_q;
+  const int nT = (int)((T + TILE - 1) / TILE);
+  const int T_pad = nT * TILE;
+  const int CH = CHUNK_TILES;
+  const int maxC = (nT + CH - 1) / CH;
+  const bool want_g2 = g2_out != nullptr;
+  const bool want_cnt = want_g2 || count_out;
+  const std::vector<int4> items = make_items(n_q, nT, CH);
+  auto layout = [&](Carve& c, RawBuffers& b) {
+    b.Xp = c.take<__nv_bfloat16>((size_t)T_pad * R->Mp);
+    b.S = c.take<long long>((size_t)n_q * T);
+    b.sq = c.take<unsigned long long>(n_q);
+    b.r = c.take<float>((size_t)n_q * T_pad);
+    b.blk_bad = c.take<uint8_t>((size_t)n_q * nT);
+    b.partials = want_g2 ? c.take<float>((size_t)n_q * nT * maxC * DIAG_SLOTS) : nullptr;
+    b.vbits = c.take<uint32_t>((size_t)n_q * (T_pad / 32));
+    b.count = (want_cnt && !count_out) ? c.take<long long>((size_t)n_q * T) : nullptr;
+    b.items = c.take<int4>(items.size());
+  };
+  RawBuffers b{};
+  Carve c0;
+  layout(c0, b);
+  XPCS_TRY(ensure_scratch(ctx, c0.off));
+  Carve c1{0, static_cast<char*>(ctx->scratch)};
+  layout(c1, b);
+  if (count_out) b.count = reinterpret_cast<long long*>(count_out);
+  XPCS_TRY(raw_ingest(ctx, R, X, dtype, T, T_pad, nT, true, b.S, b));
+  XPCS_CUDA(ctx, launch_raw_scales(b.S, R->d_Mq, n_q, T, T_pad, nT, b.sq, b.r, b.blk_bad, ctx->d_status,
+                                   ctx->stream));
+  CUtensorMap tm;
+  XPCS_TRY(make_map(ctx, &tm, b.Xp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, R->Mp, T_pad, KCH, TILE,
+                    CU_TENSOR_MAP_SWIZZLE_128B));
+  GramParams gp{};
+  gp.T = (int)T;
+  gp.nT = nT;
+  gp.T_pad = T_pad;
+  gp.maxC = maxC;
+  gp.CH = CH;
+  gp.k_off = R->d_off;
+  gp.k_chunks = R->d_chunks;
+  gp.ring_rows = 0;
+  gp.fmt = 1;
+  gp.raw = 1;
+  gp.r = b.r;
+  gp.blk_bad = b.blk_bad;
+  gp.C = C_out;
+  gp.Nout = reinterpret_cast<long long*>(N_out);
+  gp.partials = b.partials;
+  gp.status = ctx->d_status;
+  XPCS_TRY(run_twotime(ctx, tm, tm, gp, n_q, T, T_pad, nT, maxC, items, b.items, b.vbits,
+                       want_cnt ? b.count : nullptr, g2_out));
+  return finish(ctx);
+}
+
+// ====================================================================== basis
+
+namespace {
+
+xpcs_status basis_alloc(xpcs_ctx* ctx, const xpcs_rings* R, int k, xpcs_basis** out) {
+  auto* B = new xpcs_basis();
+  B->ctx = ctx;
+  B->rings = R;
+  B->k = k;
+  B->M_pad = (R->M + 63) / 64 * 64;
+  const int n_q = R->n_q;
+  const size_t szs[5] = {(size_t)R->M * k * 8, (size_t)n_q * k * k * 8, (size_t)n_q * k * 8,
+                         (size_t)n_q * k * k * 4, (size_t)2 * k * B->M_pad * 2};
+  void* p[5] = {};
+  xpcs_status s = XPCS_OK;
+  for (int i = 0; i < 5 && s == XPCS_OK; ++i) s = dev_alloc(ctx, &p[i], szs[i]);
+  if (s != XPCS_OK) {
+    for (int i = 0; i < 5; ++i) dev_free(ctx, p[i], szs[i]);
+    delete B;
+    return s;
+  }
+  B->d_B = (double*)p[0];
+  B->d_G = (double*)p[1];
+  B->d_s = (double*)p[2];
+  B->d_G32 = (float*)p[3];
+  B->d_Bcat = (__nv_bfloat16*)p[4];
+  B->bytes = szs[0] + szs[1] + szs[2] + szs[3] + szs[4];
+  *out = B;
+  return XPCS_OK;
+}
+
+// Ring factors G_q = B_q^T B_q, s_q = B_q^T 1 (FP64) and the bf16 encode operand.
+xpcs_status basis_finish(xpcs_ctx* ctx, xpcs_basis* B) {
+  const xpcs_rings* R = B->rings;
+  const int n_q = R->n_q, k = B->k;
+  int64_t maxMq = 1;
+  for (auto m : R->Mq) maxMq = std::max(maxMq, m);
+  const int n_split = (int)std::max<int64_t>(1, std::min<int64_t>(16, maxMq / 4096));
+  Carve c0;
+  c0.take<double>((size_t)n_q * n_split * k * k);
+  c0.take<double>((size_t)n_q * n_split * k);
+  XPCS_TRY(ensure_scratch(ctx, c0.off));
+  Carve c{0, static_cast<char*>(ctx->scratch)};
+  double* Gpart = c.take<double>((size_t)n_q * n_split * k * k);
+  double* spart = c.take<double>((size_t)n_q * n_split * k);
+  XPCS_CUDA(ctx, launch_ring_factors2(B->d_B, k, R->d_perm, R->d_off, R->d_Mq, n_q, n_split, Gpart, spart,
+                                      ctx->stream));
+  XPCS_CUDA(ctx, launch_ring_factors_reduce(Gpart, spart, n_split, n_q, k, B->d_G, B->d_s, B->d_G32, ctx->stream));
+  XPCS_CUDA(ctx, launch_basis_pack(B->d_B, R->M, B->M_pad, k, B->d_Bcat, ctx->stream));
+  return XPCS_OK;
+}
+
+}  // namespace
+
+extern "C" xpcs_status xpcs_basis_import(xpcs_ctx* ctx, const xpcs_rings* R, const double* B_host, int k,
+                                         xpcs_basis** out) {
+  if (!ctx || !R || !B_host || !out || k <= 0 || k > 256 || R->ctx != ctx)
+    return fail(ctx, XPCS_EINVAL, "bad basis_import args");
+  *out = nullptr;
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  xpcs_basis* B = nullptr;
+  XPCS_TRY(basis_alloc(ctx, R, k, &B));
+  cudaError_t e = cudaMemcpy(B->d_B, B_host, (size_t)R->M * k * 8, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    xpcs_basis_destroy(B);
+    return fail(ctx, XPCS_ECUDA, std::string("basis upload: ") + cudaGetErrorString(e));
+  }
+  xpcs_status s = basis_finish(ctx, B);
+  if (s == XPCS_OK) s = xpcs_synchronize(ctx);
+  if (s != XPCS_OK) {
+    xpcs_basis_destroy(B);
+    return s;
+  }
+  *out = B;
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_basis_export(xpcs_ctx* ctx, const xpcs_basis* B, double* B_host, double* G_host,
+                                         double* s_host) {
+  if (!ctx || !B || B->ctx != ctx) return fail(ctx, XPCS_EINVAL, "bad basis_export args");
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int n_q = B->rings->n_q, k = B->k;
+  if (B_host) XPCS_CUDA(ctx, cudaMemcpy(B_host, B->d_B, (size_t)B->rings->M * k * 8, cudaMemcpyDeviceToHost));
+  if (G_host) XPCS_CUDA(ctx, cudaMemcpy(G_host, B->d_G, (size_t)n_q * k * k * 8, cudaMemcpyDeviceToHost));
+  if (s_host) XPCS_CUDA(ctx, cudaMemcpy(s_host, B->d_s, (size_t)n_q * k * 8, cudaMemcpyDeviceToHost));
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_basis_rank(const xpcs_basis* B, int* k) {
+  if (!B || !k) return XPCS_EINVAL;
+  *k = B->k;
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_basis_destroy(xpcs_basis* B) {
+  if (!B) return XPCS_EINVAL;
+  xpcs_ctx* ctx = B->ctx;
+  cudaStreamSynchronize(ctx->stream);
+  const int n_q = B->rings->n_q, k = B->k;
+  dev_free(ctx, B->d_B, (size_t)B->rings->M * k * 8);
+  dev_free(ctx, B->d_G, (size_t)n_q * k * k * 8);
+  dev_free(ctx, B->d_s, (size_t)n_q * k * 8);
+  dev_free(ctx, B->d_G32, (size_t)n_q * k * k * 4);
+  dev_free(ctx, B->d_Bcat, (size_t)2 * k * B->M_pad * 2);
+  delete B;
+  return XPCS_OK;
+}
+
+// ====================================================================== compressed path
+
+extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const float* A, int64_t T,
+                                    xpcs_precision prec, float* C_out, double* g2_out, int64_t* count_out) {
+  if (!ctx || !B || !A || T <= 0 || B->ctx != ctx || (int)prec < 0 || (int)prec > 2)
+    return fail(ctx, XPCS_EINVAL, "bad twotime args");
+  if (T > (1 << 24)) return fail(ctx, XPCS_ENOTSUP, "T too large");
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int n_q = B->rings->n_q, k = B->k;
+  const int nT = (int)((T + TILE - 1) / TILE);
+  const int T_pad = nT * TILE;
+  const int CH = CHUNK_TILES;
+  const int maxC = (nT + CH - 1) / CH;
+  const int nseg = prec == XPCS_PREC_BF16X3 ? 3 : 1;
+  const int Kc = (nseg * k + KCH - 1) / KCH * KCH;
+  const bool want_g2 = g2_out != nullptr;
+  const bool want_cnt = want_g2 || count_out;
+  const std::vector<int4> items = make_items(n_q, nT, CH);
+  struct Bufs {
+    uint16_t *L, *R;
+    float* r;
+    uint8_t* blk_bad;
+    float* partials;
+    uint32_t* vbits;
+    long long* count;
+    int4* items;
+    int *koff, *kch;
+  } b{};
+  auto layout = [&](Carve& c) {
+    b.L = c.take<uint16_t>((size_t)n_q * T_pad * Kc);
+    b.R = c.take<uint16_t>((size_t)n_q * T_pad * Kc);
+    b.r = c.take<float>((size_t)n_q * T_pad);
+    b.blk_bad = c.take<uint8_t>((size_t)n_q * nT);
+    b.partials = want_g2 ? c.take<float>((size_t)n_q * nT * maxC * DIAG_SLOTS) : nullptr;
+    b.vbits = c.take<uint32_t>((size_t)n_q * (T_pad / 32));
+    b.count = (want_cnt && !count_out) ? c.take<long long>((size_t)n_q * T) : nullptr;
+    b.items = c.take<int4>(items.size());
+    b.koff = c.take<int>(n_q);
+    b.kch = c.take<int>(n_q);
+  };
+  Carve c0;
+  layout(c0);
+  XPCS_TRY(ensure_scratch(ctx, c0.off));
+  Carve c1{0, static_cast<char*>(ctx->scratch)};
+  layout(c1);
+  if (count_out) b.count = reinterpret_cast<long long*>(count_out);
+  std::vector<int> koff(n_q, 0), kch(n_q, Kc / KCH);
+  XPCS_CUDA(ctx, cudaMemcpyAsync(b.koff, koff.data(), n_q * 4, cudaMemcpyHostToDevice, ctx->stream));
+  XPCS_CUDA(ctx, cudaMemcpyAsync(b.kch, kch.data(), n_q * 4, cudaMemcpyHostToDevice, ctx->stream));
+  PrepParams pp{};
+  pp.A = A;
+  pp.T = T;
+  pp.k = k;
+  pp.n_q = n_q;
+  pp.T_pad = T_pad;
+  pp.nT = nT;
+  pp.G32 = B->d_G32;
+  pp.s64 = B->d_s;
+  pp.Mq = B->rings->d_Mq;
+  pp.prec = prec;
+  pp.Kc = Kc;
+  pp.L = b.L;
+  pp.R = b.R;
+  pp.r = b.r;
+  pp.blk_bad = b.blk_bad;
+  pp.St = nullptr;
+  XPCS_CUDA(ctx, launch_prep_compressed(pp, ctx->stream));
+  const CUtensorMapDataType dt =
+      prec == XPCS_PREC_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUtensorMap tmL, tmR;
+  XPCS_TRY(make_map(ctx, &tmL, b.L, dt, 2, Kc, (uint64_t)n_q * T_pad, KCH, TILE, CU_TENSOR_MAP_SWIZZLE_128B));
+  XPCS_TRY(make_map(ctx, &tmR, b.R, dt, 2, Kc, (uint64_t)n_q * T_pad, KCH, TILE, CU_TENSOR_MAP_SWIZZLE_128B));
+  GramParams gp{};
+  gp.T = (int)T;
+  gp.nT = nT;
+  gp.T_pad = T_pad;
+  gp.maxC = maxC;
+  gp.CH = CH;
+  gp.k_off = b.koff;
+  gp.k_chunks = b.kch;
+  gp.ring_rows = T_pad;
+  gp.fmt = prec == XPCS_PREC_FP16 ? 0 : 1;
+  gp.raw = 0;
+  gp.r = b.r;
+  gp.blk_bad = b.blk_bad;
+  gp.C = C_out;
+  gp.Nout = nullptr;
+  gp.partials = b.partials;
+  gp.status = ctx->d_status;
+  XPCS_TRY(run_twotime(ctx, tmL, tmR, gp, n_q, T, T_pad, nT, maxC, items, b.items, b.vbits,
+                       want_cnt ? b.count : nullptr, g2_out));
+  return finish(ctx);
+}
+
+// ====================================================================== g2 over stored C
+
+extern "C" xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out,
+                               int64_t* count_out) {
+  if (!ctx || !C || !g2_out || n_q <= 0 || T <= 0) return fail(ctx, XPCS_EINVAL, "bad g2 args");
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t lag_blocks = (T + TILE - 1) / TILE;
+  const int64_t blocks = lag_blocks * n_q;
+  const int target = 8 * ctx->num_sms;
+  const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, (target + blocks - 1) / blocks));
+  Carve c0;
+  c0.take<double>((size_t)splits * n_q * T);
+  c0.take<long long>((size_t)splits * n_q * T);
+  XPCS_TRY(ensure_scratch(ctx, c0.off));
+  Carve c{0, static_cast<char*>(ctx->scratch)};
+  double* part = c.take<double>((size_t)splits * n_q * T);
+  long long* cpart = c.take<long long>((size_t)splits * n_q * T);
+  XPCS_CUDA(ctx, launch_g2_from_C(C, n_q, T, part, splits, cpart, ctx->stream));
+  XPCS_CUDA(ctx, launch_g2_from_C_reduce(part, cpart, n_q, T, splits, g2_out,
+                                         reinterpret_cast<long long*>(count_out), ctx->stream));
+  return finish(ctx);
+}

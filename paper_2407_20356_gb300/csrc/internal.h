@@ -1,0 +1,139 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/xpcs.h"
+
+namespace xpcs {
+
+// status-word codes written by kernels (the host maps them to xpcs_status)
+enum : uint32_t {
+  XPCS_DEV_OK = 0,
+  XPCS_DEV_TIMEOUT = 1,  // a bounded wait expired
+  XPCS_DEV_RANGE = 2,    // input outside the exact range of the chosen path
+};
+
+constexpr int TILE = 128;        // frames per tile side
+constexpr int KCH = 64;          // 16-bit K elements per pipeline chunk (128 bytes)
+constexpr int DIAG_SLOTS = 256;  // local diagonal slots per (ring, tile-diagonal, chunk)
+constexpr int CHUNK_TILES = 8;   // tiles per work item along a tile diagonal
+
+// ------------------------------------------------------------------ Gram kernel
+
+struct GramParams {
+  int T;                   // frames
+  int nT;                  // ceil(T / 128)
+  int T_pad;               // nT * 128, rows per ring in r[] (and per ring block of operands)
+  int maxC;                // chunk slots per (ring, tile diagonal)
+  int CH;                  // tiles per chunk
+  int n_items;
+  const int4* items;       // (q, delta, I0, I1)
+  const int* k_off;        // per ring: K offset (elements) into the operand matrices
+  const int* k_chunks;     // per ring: number of 64-wide K chunks, >= 1
+  int ring_rows;           // operand row offset between rings (0 when rings share rows)
+  int fmt;                 // 0 = f16, 1 = bf16
+  int raw;                 // 1: C = acc * r(t1) * r(t2); 0: operands already scaled
+  const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined
+  const uint8_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
+  float* C;                // nullable [n_q][T][T]
+  long long* Nout;         // nullable, raw only [n_q][T][T]
+  float* partials;         // nullable [n_q][nT][maxC][256]
+  uint32_t* status;
+};
+
+cudaError_t launch_gram(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
+                        cudaStream_t st);
+int gram_smem_bytes();
+
+// ------------------------------------------------------------------ ingest / prep / g2
+
+struct RawIngestParams {
+  const void* X;           // [T][M] u8 or u16
+  int dtype;               // 0 u8, 1 u16
+  long long T, M;
+  int T_pad;
+  long long Mp;            // permuted row length (elements)
+  const int* perm;         // [Mp] source pixel or -1
+  const int* pos_ring;     // [Mp] ring of position or -1
+  int n_q;
+  __nv_bfloat16* Xp;       // [T_pad][Mp] (nullable when only sums are wanted)
+  long long* S;            // [n_q][T]
+  unsigned long long* sq;  // [n_q] max over frames of sum of squares (atomicMax)
+  uint32_t* status;
+};
+cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st);
+
+// r[q][t] = sqrt(Mq)/S (raw int64 sums) and block flags
+// (also flags XPCS_DEV_RANGE when a ring's max sum of squares reaches 2^24)
+cudaError_t launch_raw_scales(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
+                              const unsigned long long* sq, float* r, uint8_t* blk_bad, uint32_t* status,
+                              cudaStream_t st);
+
+struct PrepParams {
+  const float* A;          // [T][k]
+  long long T;
+  int k;
+  int n_q;
+  int T_pad, nT;
+  const float* G32;        // [n_q][k][k]
+  const double* s64;       // [n_q][k]
+  const long long* Mq;     // [n_q]
+  int prec;                // xpcs_precision
+  int Kc;                  // operand row length (elements, multiple of 64)
+  void* L;                 // [n_q][T_pad][Kc] 16-bit
+  void* R;                 // [n_q][T_pad][Kc] 16-bit
+  float* r;                // [n_q][T_pad]
+  uint8_t* blk_bad;        // [n_q][nT]
+  double* St;              // nullable [n_q][T] compressed ring sums
+};
+cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st);
+
+cudaError_t launch_counts(const float* r, int n_q, long long T, int T_pad, uint32_t* vbits, int words,
+                          long long* count, cudaStream_t st);
+cudaError_t launch_g2_finalize(const float* partials, const long long* count, int n_q, long long T, int nT,
+                               int maxC, int CH, double* g2, cudaStream_t st);
+cudaError_t launch_g2_from_C(const float* C, int n_q, long long T, double* partial, int row_splits,
+                             long long* cnt_partial, cudaStream_t st);
+cudaError_t launch_g2_from_C_reduce(const double* partial, const long long* cnt_partial, int n_q, long long T,
+                                    int row_splits, double* g2, long long* count, cudaStream_t st);
+
+// ------------------------------------------------------------------ encode
+
+struct EncodeParams {
+  long long T, M;
+  int k;
+  int dtype;             // 0 u8, 1 u16
+  int n_split;           // pixel splits
+  long long px_per_split;  // multiple of 64
+  float* partials;       // [n_split][T_pad][k]
+  int T_pad;
+  uint32_t* status;
+};
+cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const EncodeParams& p, int grid,
+                          cudaStream_t st);
+int encode_smem_bytes(int k);
+cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float* A,
+                                 cudaStream_t st);
+
+// ------------------------------------------------------------------ basis
+
+cudaError_t launch_gram_normalise(const long long* N, int n, double* Gf, double* nrm, cudaStream_t st);
+cudaError_t launch_basis_z(const double* U, const double* lam, const double* nrm, int n, int k, double* Z,
+                           cudaStream_t st);
+cudaError_t launch_basis_build(const void* F, int dtype, int n, long long M, const double* Z, int k, double* B,
+                               cudaStream_t st);
+cudaError_t launch_basis_sign(double* B, long long M, int k, cudaStream_t st);
+cudaError_t launch_ring_factors2(const double* B, int k, const int* perm, const int* off, const long long* Mq,
+                                 int n_q, int n_split, double* Gpart, double* spart, cudaStream_t st);
+cudaError_t launch_ring_factors_reduce(const double* Gpart, const double* spart, int n_chunks, int n_q, int k,
+                                       double* G, double* s, float* G32, cudaStream_t st);
+cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, __nv_bfloat16* Bcat,
+                              cudaStream_t st);
+
+}  // namespace xpcs

@@ -1,0 +1,382 @@
+// Ingest, per-frame normalisation factors, operand preparation, pair counts and the g2
+// reductions (sm_103a).
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace xpcs {
+
+namespace {
+
+constexpr int MAX_RINGS_SMEM = 1024;
+
+// ---------------------------------------------------------------- raw ingest (ring sums)
+// One CTA per (padded) frame.  Gathers the frame's pixels into ring-sorted order as bf16
+// (exact for counts <= 256), accumulates S_q(t) = sum of counts and sum of squares per
+// ring (Eq. 1 denominators and the exactness bound of the f32 Gram).
+__global__ void raw_ingest_kernel(const RawIngestParams p) {
+  __shared__ unsigned long long ssum[MAX_RINGS_SMEM];
+  __shared__ unsigned long long ssq[MAX_RINGS_SMEM];
+  const long long t = blockIdx.x;
+  for (int q = threadIdx.x; q < p.n_q; q += blockDim.x) {
+    ssum[q] = 0;
+    ssq[q] = 0;
+  }
+  __syncthreads();
+  const bool live = t < p.T;
+  bool too_big = false;
+  for (long long o = threadIdx.x; o < p.Mp; o += blockDim.x) {
+    unsigned x = 0;
+    const int src = p.perm[o];
+    if (live && src >= 0) {
+      x = p.dtype == 0 ? (unsigned)static_cast<const uint8_t*>(p.X)[t * p.M + src]
+                       : (unsigned)static_cast<const uint16_t*>(p.X)[t * p.M + src];
+    }
+    if (x > 256u) too_big = true;
+    if (p.Xp) p.Xp[t * p.Mp + o] = __float2bfloat16_rn((float)x);
+    if (x) {
+      const int q = p.pos_ring[o];
+      atomicAdd(&ssum[q], (unsigned long long)x);
+      atomicAdd(&ssq[q], (unsigned long long)x * x);
+    }
+  }
+  if (too_big && p.Xp) set_status(p.status, XPCS_DEV_RANGE);
+  __syncthreads();
+  if (live) {
+    for (int q = threadIdx.x; q < p.n_q; q += blockDim.x) {
+      p.S[(size_t)q * p.T + t] = (long long)ssum[q];
+      atomicMax(&p.sq[q], ssq[q]);
+    }
+  }
+}
+
+// r[q][t] = sqrt(M_q) / S_q(t) for defined frames, 0 otherwise; blk_bad marks tiles with
+// an undefined frame inside the series.
+__global__ void raw_scales_kernel(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
+                                  const unsigned long long* sq, float* r, uint8_t* blk_bad, uint32_t* status) {
+  const int q = blockIdx.y, I = blockIdx.x;
+  if (I == 0 && threadIdx.x == 0 && sq && sq[q] >= (1ull << 24)) set_status(status, XPCS_DEV_RANGE);
+  const long long t = (long long)I * TILE + threadIdx.x;
+  float v = 0.f;
+  bool bad = false;
+  if (t < T) {
+    const long long s = S[(size_t)q * T + t];
+    if (s > 0)
+      v = (float)(sqrt((double)Mq[q]) / (double)s);
+    else
+      bad = true;
+  }
+  r[(size_t)q * T_pad + t] = v;
+  const int any = __syncthreads_or(bad);
+  if (threadIdx.x == 0) blk_bad[(size_t)q * nT + I] = (uint8_t)any;
+}
+
+// ---------------------------------------------------------------- compressed preparation
+// Ring sums of the decompressed frames S~_q(t) = a_t . s_q (FP64), r = sqrt(M_q)/S~.
+__global__ void comp_scales_kernel(const PrepParams p) {
+  const int q = blockIdx.y, I = blockIdx.x;
+  const long long t = (long long)I * TILE + threadIdx.x;
+  float v = 0.f;
+  bool bad = false;
+  if (t < p.T) {
+    const float* a = p.A + t * p.k;
+    const double* s = p.s64 + (size_t)q * p.k;
+    double acc = 0.0;
+    for (int c = 0; c < p.k; ++c) acc += (double)a[c] * s[c];
+    if (p.St) p.St[(size_t)q * p.T + t] = acc;
+    if (acc > 0.0)
+      v = (float)(sqrt((double)p.Mq[q]) / acc);
+    else
+      bad = true;
+  }
+  p.r[(size_t)q * p.T_pad + t] = v;
+  const int any = __syncthreads_or(bad);
+  if (threadIdx.x == 0) p.blk_bad[(size_t)q * p.nT + I] = (uint8_t)any;
+}
+
+template <typename T16>
+XPCS_DEV T16 to16(float x);
+template <>
+XPCS_DEV __half to16<__half>(float x) { return __float2half_rn(x); }
+template <>
+XPCS_DEV __nv_bfloat16 to16<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+constexpr int PREP_FRAMES = 64;
+constexpr int PREP_COLS = 32;
+
+// Operand rows for one ring and 64 frames: L = r * (a G_q), R = r * a, in the requested
+// 16-bit format.  BF16X3 stores [hi | hi | lo] for L and [hi | lo | hi] for R so one
+// K-concatenated product gives hi*hi + hi*lo + lo*hi.
+template <typename T16, bool SPLIT>
+__global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) {
+  extern __shared__ float sm[];
+  const int k = p.k;
+  const int lda = k + 1;
+  float* As = sm;                          // [64][k+1]
+  float* Gs = sm + PREP_FRAMES * lda;      // [k][32]
+  const int q = blockIdx.y;
+  const long long t0 = (long long)blockIdx.x * PREP_FRAMES;
+  const float* rq = p.r + (size_t)q * p.T_pad;
+  for (int i = threadIdx.x; i < PREP_FRAMES * k; i += blockDim.x) {
+    const int f = i / k, c = i % k;
+    const long long t = t0 + f;
+    As[f * lda + c] = (t < p.T) ? p.A[t * k + c] * rq[t] : 0.f;
+  }
+  T16* L = static_cast<T16*>(p.L) + ((size_t)q * p.T_pad + t0) * p.Kc;
+  T16* R = static_cast<T16*>(p.R) + ((size_t)q * p.T_pad + t0) * p.Kc;
+  const int f = threadIdx.x % PREP_FRAMES;
+  const int g = threadIdx.x / PREP_FRAMES;  // 0..3 -> 8 columns each
+  const float* Gq = p.G32 + (size_t)q * k * k;
+  const int nseg = SPLIT ? 3 : 1;
+  for (int j0 = 0; j0 < k; j0 += PREP_COLS) {
+    const int nc = min(PREP_COLS, k - j0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < k * PREP_COLS; i += blockDim.x) {
+      const int c = i / PREP_COLS, j = i % PREP_COLS;
+      Gs[i] = (j < nc) ? Gq[(size_t)c * k + j0 + j] : 0.f;
+    }
+    __syncthreads();
+    float w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) w[u] = 0.f;
+    const float* arow = As + f * lda;
+    for (int c = 0; c < k; ++c) {
+      const float a = arow[c];
+      const float* gr = Gs + c * PREP_COLS + 8 * g;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) w[u] = fmaf(a, gr[u], w[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + 8 * g + u;
+      if (8 * g + u >= nc) break;
+      const float av = arow[j];
+      T16* lrow = L + (size_t)f * p.Kc;
+      T16* rrow = R + (size_t)f * p.Kc;
+      if (!SPLIT) {
+        lrow[j] = to16<T16>(w[u]);
+        rrow[j] = to16<T16>(av);
+      } else {
+        const T16 wh = to16<T16>(w[u]);
+        const T16 wl = to16<T16>(w[u] - (float)wh);
+        const T16 ah = to16<T16>(av);
+        const T16 al = to16<T16>(av - (float)ah);
+        lrow[j] = wh;
+        lrow[k + j] = wh;
+        lrow[2 * k + j] = wl;
+        rrow[j] = ah;
+        rrow[k + j] = al;
+        rrow[2 * k + j] = ah;
+      }
+    }
+  }
+  // zero the K padding
+  const int used = nseg * k;
+  const int pad = p.Kc - used;
+  if (pad > 0) {
+    for (int i = threadIdx.x; i < PREP_FRAMES * pad; i += blockDim.x) {
+      const int ff = i / pad, c = used + i % pad;
+      L[(size_t)ff * p.Kc + c] = to16<T16>(0.f);
+      R[(size_t)ff * p.Kc + c] = to16<T16>(0.f);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- pair counts
+__global__ void vbits_kernel(const float* r, int n_q, int T_pad, int words, uint32_t* vbits) {
+  const long long gw = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (gw >= (long long)n_q * words) return;
+  const int q = (int)(gw / words), w = (int)(gw % words);
+  const long long t = (long long)w * 32 + lane;
+  const bool v = (t < T_pad) && r[(size_t)q * T_pad + t] > 0.f;
+  const uint32_t m = __ballot_sync(0xffffffffu, v);
+  if (lane == 0) vbits[(size_t)q * words + w] = m;
+}
+
+// count_q(tau) = number of t with frames t and t+tau both defined.
+__global__ void counts_kernel(const uint32_t* vbits, int n_q, long long T, int words, long long* count) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)n_q * T) return;
+  const int q = (int)(gid / T);
+  const long long tau = gid % T;
+  const uint32_t* v = vbits + (size_t)q * words;
+  const int ws = (int)(tau >> 5), s = (int)(tau & 31);
+  long long c = 0;
+  for (int w = 0; w + ws < words; ++w) {
+    const uint32_t a = v[w + ws];
+    const uint32_t b = (w + ws + 1 < words) ? v[w + ws + 1] : 0u;
+    const uint32_t sh = s ? ((a >> s) | (b << (32 - s))) : a;
+    c += __popc(v[w] & sh);
+  }
+  count[gid] = c;
+}
+
+// g2_q(tau) from the per-(ring, tile diagonal, chunk) diagonal partial sums.
+__global__ void g2_finalize_kernel(const float* partials, const long long* count, int n_q, long long T, int nT,
+                                   int maxC, int CH, double* g2) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)n_q * T) return;
+  const int q = (int)(gid / T);
+  const long long tau = gid % T;
+  const int d1 = (int)(tau / TILE), e1 = (int)(tau % TILE);
+  double sum = 0.0;
+  {
+    const int nC = (nT - d1 + CH - 1) / CH;
+    const float* base = partials + ((size_t)q * nT + d1) * maxC * DIAG_SLOTS;
+    for (int c = 0; c < nC; ++c) sum += (double)base[(size_t)c * DIAG_SLOTS + TILE + e1];
+  }
+  const int d2 = d1 + 1;
+  if (d2 < nT) {
+    const int nC = (nT - d2 + CH - 1) / CH;
+    const float* base = partials + ((size_t)q * nT + d2) * maxC * DIAG_SLOTS;
+    for (int c = 0; c < nC; ++c) sum += (double)base[(size_t)c * DIAG_SLOTS + e1];
+  }
+  const long long n = count[gid];
+  g2[gid] = n > 0 ? sum / (double)n : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// ---------------------------------------------------------------- g2 over a stored C
+// Grid (lag blocks of 128, rings, row splits); 8 warps.  Lane l of every warp owns lags
+// L0 + l + 32 m (m = 0..3); the warp walks rows t, reading C[t][t + lag] as 128-byte
+// coalesced segments.  Undefined (NaN) entries are skipped and counted out.
+constexpr int G2C_WARPS = 8;
+__global__ void __launch_bounds__(256) g2_from_C_kernel(const float* __restrict__ C, int n_q, long long T,
+                                                        double* partial, long long* cnt_partial, int row_splits) {
+  __shared__ float ssum[G2C_WARPS][TILE];
+  __shared__ int scnt[G2C_WARPS][TILE];
+  const long long L0 = (long long)blockIdx.x * TILE;
+  const int q = blockIdx.y, split = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long nrows = T - L0;
+  const long long per = (nrows + row_splits - 1) / row_splits;
+  const long long r0 = (long long)split * per;
+  const long long r1 = min(nrows, r0 + per);
+  float s[4] = {0.f, 0.f, 0.f, 0.f};
+  int c[4] = {0, 0, 0, 0};
+  const float* Cq = C + (size_t)q * T * T;
+  for (long long t = r0 + warp; t < r1; t += G2C_WARPS) {
+    const float* row = Cq + (size_t)t * T + t + L0;
+    const long long lim = T - t - L0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int l = lane + 32 * m;
+      if (l < lim) {
+        const float v = __ldcs(row + l);
+        if (v == v) {
+          s[m] += v;
+          c[m] += 1;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    ssum[warp][lane + 32 * m] = s[m];
+    scnt[warp][lane + 32 * m] = c[m];
+  }
+  __syncthreads();
+  if (threadIdx.x < TILE) {
+    double a = 0.0;
+    long long n = 0;
+#pragma unroll
+    for (int w = 0; w < G2C_WARPS; ++w) {
+      a += (double)ssum[w][threadIdx.x];
+      n += scnt[w][threadIdx.x];
+    }
+    const long long tau = L0 + threadIdx.x;
+    if (tau < T) {
+      const size_t o = ((size_t)split * n_q + q) * T + tau;
+      partial[o] = a;
+      cnt_partial[o] = n;
+    }
+  }
+}
+
+__global__ void g2_from_C_reduce_kernel(const double* partial, const long long* cnt_partial, int n_q, long long T,
+                                        int row_splits, double* g2, long long* count) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)n_q * T) return;
+  double a = 0.0;
+  long long n = 0;
+  for (int s = 0; s < row_splits; ++s) {
+    a += partial[(size_t)s * n_q * T + gid];
+    n += cnt_partial[(size_t)s * n_q * T + gid];
+  }
+  g2[gid] = n > 0 ? a / (double)n : __longlong_as_double(0x7ff8000000000000ll);
+  if (count) count[gid] = n;
+}
+
+}  // namespace
+
+cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st) {
+  if (p.n_q > MAX_RINGS_SMEM) return cudaErrorInvalidValue;
+  raw_ingest_kernel<<<p.T_pad, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raw_scales(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
+                              const unsigned long long* sq, float* r, uint8_t* blk_bad, uint32_t* status,
+                              cudaStream_t st) {
+  raw_scales_kernel<<<dim3(nT, n_q), TILE, 0, st>>>(S, Mq, n_q, T, T_pad, nT, sq, r, blk_bad, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st) {
+  comp_scales_kernel<<<dim3(p.nT, p.n_q), TILE, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int smem = (PREP_FRAMES * (p.k + 1) + p.k * PREP_COLS) * (int)sizeof(float);
+  const dim3 grid(p.T_pad / PREP_FRAMES, p.n_q);
+#define XPCS_PREP_LAUNCH(T16, SPLIT)                                                                  \
+  do {                                                                                                \
+    e = cudaFuncSetAttribute(comp_operands_kernel<T16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             smem);                                                                   \
+    if (e != cudaSuccess) return e;                                                                   \
+    comp_operands_kernel<T16, SPLIT><<<grid, 256, smem, st>>>(p);                                     \
+  } while (0)
+  if (p.prec == XPCS_PREC_FP16)
+    XPCS_PREP_LAUNCH(__half, false);
+  else if (p.prec == XPCS_PREC_BF16)
+    XPCS_PREP_LAUNCH(__nv_bfloat16, false);
+  else
+    XPCS_PREP_LAUNCH(__nv_bfloat16, true);
+#undef XPCS_PREP_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counts(const float* r, int n_q, long long T, int T_pad, uint32_t* vbits, int words,
+                          long long* count, cudaStream_t st) {
+  const long long nw = (long long)n_q * words;
+  vbits_kernel<<<(unsigned)((nw + 7) / 8), 256, 0, st>>>(r, n_q, T_pad, words, vbits);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)n_q * T;
+  counts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vbits, n_q, T, words, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g2_finalize(const float* partials, const long long* count, int n_q, long long T, int nT,
+                               int maxC, int CH, double* g2, cudaStream_t st) {
+  const long long n = (long long)n_q * T;
+  g2_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, count, n_q, T, nT, maxC, CH, g2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g2_from_C(const float* C, int n_q, long long T, double* partial, int row_splits,
+                             long long* cnt_partial, cudaStream_t st) {
+  const dim3 grid((unsigned)((T + TILE - 1) / TILE), n_q, row_splits);
+  g2_from_C_kernel<<<grid, 256, 0, st>>>(C, n_q, T, partial, cnt_partial, row_splits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g2_from_C_reduce(const double* partial, const long long* cnt_partial, int n_q, long long T,
+                                    int row_splits, double* g2, long long* count, cudaStream_t st) {
+  const long long n = (long long)n_q * T;
+  g2_from_C_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, cnt_partial, n_q, T, row_splits,
+                                                                       g2, count);
+  return cudaGetLastError();
+}
+
+}  // namespace xpcs

@@ -1,0 +1,221 @@
+"""ctypes binding of libxpcs.so: the C ABI of include/xpcs.h, name for name.
+
+Argument marshalling only.  Device buffers may be passed as torch CUDA tensors or raw
+integer device addresses; host buffers as numpy arrays.  Every step of the computation
+runs in the library's CUDA kernels; there is no fallback of any kind: if the library is
+missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libxpcs.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with paper_2407_20356_gb300._build.build_library() "
+        "(or __graft_entry__.build()); this package has no CPU fallback")
+_lib = C.CDLL(LIB_PATH)
+
+XPCS_OK, XPCS_EINVAL, XPCS_ENOMEM, XPCS_ECUDA, XPCS_ETIMEOUT, XPCS_EBUSY, XPCS_ERANGE, XPCS_ENOTSUP = range(8)
+STATUS_NAMES = ["XPCS_OK", "XPCS_EINVAL", "XPCS_ENOMEM", "XPCS_ECUDA", "XPCS_ETIMEOUT", "XPCS_EBUSY",
+                "XPCS_ERANGE", "XPCS_ENOTSUP"]
+XPCS_U8, XPCS_U16 = 0, 1
+XPCS_PREC_FP16, XPCS_PREC_BF16, XPCS_PREC_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp16": XPCS_PREC_FP16, "bf16": XPCS_PREC_BF16, "bf16x3": XPCS_PREC_BF16X3}
+
+vp = C.c_void_p
+i64 = C.c_int64
+_SIGS = {
+    "xpcs_version": (C.c_int, []),
+    "xpcs_create": (C.c_int, [C.c_int, C.c_size_t, vp, C.POINTER(vp)]),
+    "xpcs_destroy": (C.c_int, [vp]),
+    "xpcs_last_error": (C.c_char_p, [vp]),
+    "xpcs_set_async": (C.c_int, [vp, C.c_int]),
+    "xpcs_synchronize": (C.c_int, [vp]),
+    "xpcs_device_bytes": (C.c_size_t, [vp]),
+    "xpcs_rings_create": (C.c_int, [vp, vp, i64, C.c_int, C.POINTER(vp)]),
+    "xpcs_rings_destroy": (C.c_int, [vp]),
+    "xpcs_rings_sizes": (C.c_int, [vp, vp]),
+    "xpcs_ring_sums": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
+    "xpcs_twotime_raw": (C.c_int, [vp, vp, vp, C.c_int, i64, vp, vp, vp, vp]),
+    "xpcs_fit_basis": (C.c_int, [vp, vp, vp, C.c_int, i64, C.c_int, C.POINTER(vp), vp]),
+    "xpcs_basis_import": (C.c_int, [vp, vp, vp, C.c_int, C.POINTER(vp)]),
+    "xpcs_basis_export": (C.c_int, [vp, vp, vp, vp, vp]),
+    "xpcs_basis_rank": (C.c_int, [vp, C.POINTER(C.c_int)]),
+    "xpcs_basis_destroy": (C.c_int, [vp]),
+    "xpcs_encode": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
+    "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
+    "xpcs_g2": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
+}
+
+
+def declared_symbols():
+    """Names of the entry points this binding declares."""
+    return list(_SIGS)
+
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class XpcsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _ptr(x):
+    """Device or host address of a tensor/array/int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _dtype_code(x):
+    s = str(getattr(x, "dtype", x))
+    if "uint8" in s:
+        return XPCS_U8
+    if "uint16" in s:
+        return XPCS_U16
+    raise TypeError(f"counts must be uint8 or uint16, got {s}")
+
+
+class Context:
+    """An xpcs_ctx: device, CUDA stream, device-memory budget."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, stream=None):
+        h = vp()
+        st = _lib.xpcs_create(device, hbm_budget, stream, C.byref(h))
+        if st != XPCS_OK:
+            raise XpcsError(st, "xpcs_create failed")
+        self.h = h
+
+    def check(self, st):
+        if st != XPCS_OK:
+            raise XpcsError(st, _lib.xpcs_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            _lib.xpcs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_async(self, on: bool):
+        self.check(_lib.xpcs_set_async(self.h, 1 if on else 0))
+
+    def synchronize(self):
+        self.check(_lib.xpcs_synchronize(self.h))
+
+    def device_bytes(self) -> int:
+        return int(_lib.xpcs_device_bytes(self.h))
+
+
+class Rings:
+    def __init__(self, ctx: Context, qmap, M: int, n_q: int):
+        h = vp()
+        ctx.check(_lib.xpcs_rings_create(ctx.h, _ptr(qmap), M, n_q, C.byref(h)))
+        self.ctx, self.h, self.M, self.n_q = ctx, h, M, n_q
+
+    def sizes(self) -> np.ndarray:
+        out = np.zeros(self.n_q, dtype=np.int64)
+        self.ctx.check(_lib.xpcs_rings_sizes(self.h, out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.h:
+            _lib.xpcs_rings_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Basis:
+    def __init__(self, ctx: Context, rings: Rings, h, k: int):
+        self.ctx, self.rings, self.h, self.k = ctx, rings, h, k
+
+    def export(self):
+        M, n_q, k = self.rings.M, self.rings.n_q, self.k
+        B = np.empty((M, k))
+        G = np.empty((n_q, k, k))
+        s = np.empty((n_q, k))
+        self.ctx.check(_lib.xpcs_basis_export(self.ctx.h, self.h, B.ctypes.data, G.ctypes.data, s.ctypes.data))
+        return B, G, s
+
+    def close(self):
+        if self.h:
+            _lib.xpcs_basis_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def xpcs_version() -> int:
+    return int(_lib.xpcs_version())
+
+
+def xpcs_rings_create(ctx: Context, qmap, M: int, n_q: int) -> Rings:
+    return Rings(ctx, qmap, M, n_q)
+
+
+def xpcs_ring_sums(ctx: Context, rings: Rings, X, T: int, S_out, dtype=None):
+    ctx.check(_lib.xpcs_ring_sums(ctx.h, rings.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(S_out)))
+
+
+def xpcs_twotime_raw(ctx: Context, rings: Rings, X, T: int, C_out=None, N_out=None, g2_out=None, count_out=None,
+                     dtype=None):
+    ctx.check(_lib.xpcs_twotime_raw(ctx.h, rings.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(C_out),
+                                    _ptr(N_out), _ptr(g2_out), _ptr(count_out)))
+
+
+def xpcs_fit_basis(ctx: Context, rings: Rings, F, n_fit: int, k: int, sigma_host=None, dtype=None) -> Basis:
+    h = vp()
+    ctx.check(_lib.xpcs_fit_basis(ctx.h, rings.h, _ptr(F), _dtype_code(dtype or F), n_fit, k, C.byref(h),
+                                  _ptr(sigma_host)))
+    return Basis(ctx, rings, h, k)
+
+
+def xpcs_basis_import(ctx: Context, rings: Rings, B_host: np.ndarray) -> Basis:
+    B_host = np.ascontiguousarray(B_host, dtype=np.float64)
+    assert B_host.shape[0] == rings.M
+    h = vp()
+    ctx.check(_lib.xpcs_basis_import(ctx.h, rings.h, B_host.ctypes.data, B_host.shape[1], C.byref(h)))
+    return Basis(ctx, rings, h, B_host.shape[1])
+
+
+def xpcs_encode(ctx: Context, basis: Basis, X, T: int, A_out, dtype=None):
+    ctx.check(_lib.xpcs_encode(ctx.h, basis.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(A_out)))
+
+
+def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None, g2_out=None, count_out=None):
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    ctx.check(_lib.xpcs_twotime(ctx.h, basis.h, _ptr(A), T, p, _ptr(C_out), _ptr(g2_out), _ptr(count_out)))
+
+
+def xpcs_g2(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
+    ctx.check(_lib.xpcs_g2(ctx.h, _ptr(C_in), n_q, T, _ptr(g2_out), _ptr(count_out)))

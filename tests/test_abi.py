@@ -1,0 +1,45 @@
+"""The C-ABI library loads and exports every entry point include/xpcs.h declares.
+
+CPU-only: loads the shared library and resolves symbols; no compute call is made.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "xpcs.h")
+LIB = os.path.join(ROOT, "paper_2407_20356_gb300", "lib", "libxpcs.so")
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(xpcs_[a-z0-9_]+)\s*\(", src)))
+
+
+def _ensure_built():
+    if not os.path.exists(LIB):
+        from paper_2407_20356_gb300 import _build
+
+        _build.build_library()
+
+
+def test_library_exports_every_declared_symbol():
+    _ensure_built()
+    names = header_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(LIB)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (xpcs_[a-z0-9_]+)\b", out))
+    assert set(names) <= exported, set(names) - exported
+
+
+def test_binding_declares_the_header_functions():
+    _ensure_built()
+    from paper_2407_20356_gb300 import xpcs
+
+    assert sorted(xpcs.declared_symbols()) == header_functions()
+    assert xpcs.xpcs_version() >= 100

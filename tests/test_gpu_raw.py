@@ -1,0 +1,121 @@
+"""GPU parity of the raw exact path (Eq. 1-2, ring g2) against the CPU oracle.
+
+Integer Grams and ring sums must be bit-exact; C (float32) within 1e-6 relative per
+element (three float32 roundings of an exact integer ratio); g2 within 2e-6 relative;
+pair counts exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import ring_qmap, speckle_counts
+from tests.gpu_util import run_raw, torch_cuda, upper
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2407_20356_gb300 import xpcs
+
+    return xpcs
+
+
+@pytest.fixture(scope="module")
+def ctx(X):
+    return X.Context(0)
+
+
+def _check_raw(X, ctx, frames, qmap, n_q):
+    out = run_raw(X, ctx, frames, qmap, n_q)
+    Cref, Nref, Sref, Mq = O.raw_twotime(frames, qmap, n_q)
+    assert np.array_equal(upper(out["N"]), upper(Nref)), "integer Gram not bit-exact"
+    Cu, Cr = upper(out["C"]), upper(Cref)
+    np.testing.assert_array_equal(np.isnan(Cu), np.isnan(Cr))
+    ok = ~np.isnan(Cr)
+    np.testing.assert_allclose(Cu[ok], Cr[ok], rtol=1e-6, atol=0)
+    for q in range(n_q):
+        g_ref, c_ref = O.g2_from_twotime(Cref[q])
+        np.testing.assert_array_equal(out["count"][q], c_ref)
+        g = out["g2"][q]
+        np.testing.assert_array_equal(np.isnan(g), np.isnan(g_ref))
+        okg = ~np.isnan(g_ref)
+        np.testing.assert_allclose(g[okg], g_ref[okg], rtol=2e-6, atol=0)
+    return out
+
+
+def test_raw_64x64_T500_eight_rings(X, ctx):
+    # 64x64 detector, T = 500 frames, 8 equal-width rings, uint8 counts of mean 0.1
+    frames = speckle_counts(64, 64, 500, 0.1, 1e-3, 20356001, np.uint8)
+    _check_raw(X, ctx, frames, ring_qmap(64, 64, 8), 8)
+
+
+@pytest.mark.parametrize("T", [1, 7, 128, 129, 300])
+def test_raw_ragged_frame_counts(X, ctx, T):
+    frames = speckle_counts(24, 40, T, 0.8, 2e-3, 11 + T, np.uint8)
+    _check_raw(X, ctx, frames, ring_qmap(24, 40, 5), 5)
+
+
+def test_raw_uint16_dark_frames_and_empty_ring(X, ctx):
+    rng = np.random.default_rng(3)
+    T, H, W, n_q = 260, 16, 48, 6
+    frames = speckle_counts(H, W, T, 0.3, 3e-3, 5, np.uint16)
+    frames[[0, 5, 130, 259]] = 0  # undefined frames: NaN pairs, excluded from g2
+    qmap = ring_qmap(H, W, n_q)
+    qmap[qmap == 4] = -1  # ring 4 is empty
+    qmap[rng.random(qmap.size) < 0.1] = -1  # scattered unused pixels
+    out = _check_raw(X, ctx, frames, qmap, n_q)
+    assert np.all(out["count"][4] == 0) and np.all(np.isnan(out["g2"][4]))
+
+
+def test_raw_large_counts_near_exact_limit(X, ctx):
+    # counts up to 256 stay exact in bf16; the f32 accumulation stays exact below 2^24
+    rng = np.random.default_rng(8)
+    T, M, n_q = 150, 256, 2
+    frames = rng.integers(0, 257, size=(T, M)).astype(np.uint16)
+    qmap = (np.arange(M) % n_q).astype(np.int32)  # 128 px per ring: sum of squares < 2^24
+    _check_raw(X, ctx, frames, qmap, n_q)
+
+
+def test_raw_rejects_counts_above_exact_range(X, ctx):
+    torch, dev = torch_cuda()
+    frames = np.zeros((10, 64), dtype=np.uint16)
+    frames[3, 5] = 300
+    qmap = np.zeros(64, dtype=np.int32)
+    with pytest.raises(X.XpcsError) as e:
+        run_raw(X, ctx, frames, qmap, 1)
+    assert e.value.status == X.XPCS_ERANGE
+    # the context stays usable
+    ok = speckle_counts(8, 8, 20, 1.0, 1e-3, 1, np.uint8)
+    _check_raw(X, ctx, ok, ring_qmap(8, 8, 2), 2)
+
+
+def test_ring_sums_exact(X, ctx):
+    torch, dev = torch_cuda()
+    frames = speckle_counts(32, 32, 77, 2.0, 1e-3, 9, np.uint16)
+    qmap = ring_qmap(32, 32, 7)
+    rings = X.Rings(ctx, torch.from_numpy(qmap).to(dev), 32 * 32, 7)
+    S = torch.empty((7, 77), dtype=torch.int64, device=dev)
+    X.xpcs_ring_sums(ctx, rings, torch.from_numpy(frames).to(dev), 77, S)
+    assert np.array_equal(S.cpu().numpy(), O.ring_sums(frames, qmap, 7))
+    assert np.array_equal(rings.sizes(), O.ring_sizes(qmap, 7))
+
+
+def test_g2_over_stored_twotime(X, ctx):
+    torch, dev = torch_cuda()
+    frames = speckle_counts(32, 32, 333, 0.4, 1e-3, 21, np.uint8)
+    frames[[2, 40]] = 0
+    qmap = ring_qmap(32, 32, 3)
+    out = run_raw(X, ctx, frames, qmap, 3, want_N=False)
+    C = torch.from_numpy(out["C"]).to(dev)
+    g2 = torch.empty((3, 333), dtype=torch.float64, device=dev)
+    cnt = torch.empty((3, 333), dtype=torch.int64, device=dev)
+    X.xpcs_g2(ctx, C, 3, 333, g2, cnt)
+    for q in range(3):
+        Cq = out["C"][q].astype(np.float64)
+        Cq = np.triu(Cq) + np.triu(Cq, 1).T  # the oracle reads a full matrix
+        g_ref, c_ref = O.g2_from_twotime(Cq)
+        np.testing.assert_array_equal(cnt[q].cpu().numpy(), c_ref)
+        g = g2[q].cpu().numpy()
+        ok = ~np.isnan(g_ref)
+        np.testing.assert_allclose(g[ok], g_ref[ok], rtol=1e-6)
