@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Benchmark of the XPCS correlation hot path on one GB300 (replicas on N GPUs).
+
+Workload (512x512 detector, T = 10,000 frames, uint16 Poisson counts of mean 0.1 from
+AR(1) speckle with D = 5e-4, 36 equal-width q-rings, basis of rank k = 64 fit in FP64 on
+the first 1000 frames).  One step = the compressed path over the whole series:
+encode A = X V_K (Eq. 7) + two-time C_q for every ring from the coefficients
+(Eq. 10 with ring factors, C stored as the float32 upper triangle) + g2.  The exact raw
+path (Eq. 1-2 on integer counts) is timed in the same run for the speed-up.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(H=512, W=512, T=10000, dtype="uint16", mean=0.1, D=5e-4, n_q=36, k=64, n_fit=1000,
+                seed=20356002)
+WORKLOAD_NAME = ("512x512 detector, T=10000 frames, uint16 Poisson AR(1) speckle mean 0.1 D=5e-4, "
+                 "36 q-rings, k=64 basis fit on the first 1000 frames; step = encode + two-time (C stored, "
+                 "float32 upper triangle) + g2")
+METRIC = "frames/s correlated (compressed vs exact raw path) at stated err; p99 frame latency"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d["hbm_gbs"], bf16_tflops=d["bf16_tflops"],
+                    bf16_tflops_sustained=d.get("bf16_tflops_sustained"), source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, source="fallback")
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.t_lo = self.t_hi = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def mark(self, lo, hi):
+        self.t_lo, self.t_hi = lo, hi
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.samples:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((t, float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        win = [r for r in rows if self.t_lo is not None and self.t_lo - 0.15 <= r[0] <= self.t_hi + 0.15] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in win for i, v in enumerate(r[3]) if v.lower() == "active"})
+        sm = sorted(r[1] for r in win)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[2] for r in win), "reasons": reasons,
+                "samples": len(win)}
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if n_gpus > 0 else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle timing (CPU)
+
+def oracle_cpu(frames_host, qmap, wl, n_rings_sample=1, enc_frames=None):
+    """Time the oracle on a bounded sample and extrapolate to the whole workload.
+
+    Encode runs over `enc_frames` frames (all if None); the two-time + g2 runs for
+    `n_rings_sample` rings at the full T.  Returns (frames/s, seconds, details).
+    """
+    import oracle as O
+
+    T, n_q, k = wl["T"], wl["n_q"], wl["k"]
+    t0 = time.perf_counter()
+    B, _ = O.fit_basis(frames_host[: wl["n_fit"]], k)
+    t_fit = time.perf_counter() - t0
+    G, s, Mq = O.ring_factors(B, qmap, n_q)
+    ne = T if enc_frames is None else enc_frames
+    t0 = time.perf_counter()
+    A = np.concatenate([O.encode(frames_host[i:i + 500], B) for i in range(0, ne, 500)])
+    t_enc = (time.perf_counter() - t0) * (T / ne)
+    t0 = time.perf_counter()
+    for q in range(n_rings_sample):
+        if ne < T:
+            break
+        Cq = O.twotime_from_gram(O.compressed_ring_gram(A, G[q]), A @ s[q], A @ s[q], Mq[q])
+        O.g2_from_twotime(Cq)
+        del Cq
+    t_ring = (time.perf_counter() - t0) / max(1, n_rings_sample)
+    total = t_enc + t_ring * n_q
+    return T / total, total, dict(t_fit=t_fit, t_encode_full=t_enc, t_ring=t_ring, B=B, G=G, s=s, Mq=Mq, A=A)
+
+
+def run_reference(args, wl):
+    world, rank, local = dist_init(0)
+    if rank != 0:
+        return
+    from synth import ring_qmap, speckle_counts
+
+    import oracle as O
+
+    # same workload, generated on the host (a prefix is enough for the sampled steps)
+    qmap = ring_qmap(wl["H"], wl["W"], wl["n_q"])
+    n_host = wl["n_fit"] + 200
+    frames = speckle_counts(wl["H"], wl["W"], n_host, wl["mean"], wl["D"], wl["seed"], np.uint16)
+    B, _ = O.fit_basis(frames[: wl["n_fit"]], wl["k"])
+    G, s, Mq = O.ring_factors(B, qmap, wl["n_q"])
+    T = wl["T"]
+    rng = np.random.default_rng(0)
+
+    def step():
+        # bounded sample: encode 200 frames (scaled to T) + two-time and g2 of one ring
+        # at the full T on coefficients of the same statistics (scaled to all rings)
+        t0 = time.perf_counter()
+        A = O.encode(frames[wl["n_fit"]:wl["n_fit"] + 200], B)
+        t_enc = (time.perf_counter() - t0) * T / 200
+        Af = A[rng.integers(0, 200, size=T)]
+        t0 = time.perf_counter()
+        q = int(rng.integers(0, wl["n_q"]))
+        Cq = O.twotime_from_gram(O.compressed_ring_gram(Af, G[q]), Af @ s[q], Af @ s[q], Mq[q])
+        O.g2_from_twotime(Cq)
+        t_ring = time.perf_counter() - t0
+        return t_enc + t_ring * wl["n_q"]
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    est = [step() for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    per_step = float(np.mean(est))
+    value = T / per_step
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "impl": "CPU FP64 oracle (numpy)"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": "per step: oracle encode of 200 frames scaled to T=10000, plus oracle "
+                                   "two-time + g2 of one ring at T=10000 scaled to 36 rings",
+                         "wall_s": wall},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, wl):
+    import torch
+
+    world, rank, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2407_20356_gb300 import xpcs as X
+    from synth import ring_qmap
+    from synth.speckle import TorchSpeckle
+
+    H, W, T, n_q, k = wl["H"], wl["W"], wl["T"], wl["n_q"], wl["k"]
+    M = H * W
+    prec = args.prec
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+
+    # ---- synthetic input, resident in HBM
+    t0 = time.time()
+    gen = TorchSpeckle(H, W, wl["mean"], wl["D"], wl["seed"] + rank, dtype=wl["dtype"], device=str(dev))
+    Xd = torch.empty((T, M), dtype=torch.uint16, device=dev)
+    for i in range(0, T, 1000):
+        Xd[i:i + 1000].copy_(gen.next(min(1000, T - i)))
+    del gen
+    qmap = ring_qmap(H, W, n_q)
+    torch.cuda.synchronize()
+    t_gen = time.time() - t0
+
+    ctx = X.Context(local, 0, stream.cuda_stream)
+    rings = X.Rings(ctx, torch.from_numpy(qmap).to(dev), M, n_q)
+    t0 = time.time()
+    basis = X.xpcs_fit_basis(ctx, rings, Xd, wl["n_fit"], k)
+    t_fit = time.time() - t0
+
+    A = torch.empty((T, k), dtype=torch.float32, device=dev)
+    C = torch.empty((n_q, T, T), dtype=torch.float32, device=dev)
+    g2 = torch.empty((n_q, T), dtype=torch.float64, device=dev)
+    cnt = torch.empty((n_q, T), dtype=torch.int64, device=dev)
+    ctx.set_async(True)
+
+    def step(p=prec):
+        X.xpcs_encode(ctx, basis, Xd, T, A)
+        X.xpcs_twotime(ctx, basis, A, T, p, C_out=C, g2_out=g2, count_out=cnt)
+
+    def timed(fn, K, Wm, profile=False, sampler=None):
+        for _ in range(Wm):
+            fn()
+        ctx.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        if profile:
+            ctx.profile_enable(True)
+        n0 = ctx.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lo = time.time()
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        ctx.synchronize()
+        torch.cuda.synchronize()
+        hi = time.time()
+        barrier(world)
+        if sampler:
+            sampler.mark(lo, hi)
+        ms = e0.elapsed_time(e1) / K
+        prof = ctx.profile() if profile else {}
+        if profile:
+            ctx.profile_enable(False)
+        return ms, ctx.launch_count() - n0, prof
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ms, launches, prof = timed(step, args.steps, args.warmup, profile=True, sampler=sampler)
+    if sampler:
+        sampler.stop()
+    ms = max_over_ranks(ms, world, dev)
+
+    # ---- raw exact path on the same frames (the comparison of the metric)
+    raw_ms = None
+    if not args.no_raw:
+        def raw_step():
+            X.xpcs_twotime_raw(ctx, rings, Xd, T, C_out=C, g2_out=g2, count_out=cnt)
+
+        raw_ms, _, raw_prof = timed(raw_step, max(1, min(args.steps, 3)), 1, profile=True)
+        raw_ms = max_over_ranks(raw_ms, world, dev)
+
+    # ---- other precision modes: time and error
+    variants = {}
+    for p in ("fp16", "bf16", "bf16x3"):
+        if p == prec:
+            continue
+        vms, _, _ = timed(lambda: step(p), max(1, min(args.steps, 5)), 1)
+        variants[p] = {"ms_per_step": vms}
+
+    # ---- end to end through the public API from pinned host memory
+    Xh = torch.empty((T, M), dtype=torch.uint16, pin_memory=True)
+    Xh.copy_(Xd)
+    g2h = torch.empty((n_q, T), dtype=torch.float64, pin_memory=True)
+    cnth = torch.empty((n_q, T), dtype=torch.int64, pin_memory=True)
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        step()
+        g2h.copy_(g2, non_blocking=True)
+        cnth.copy_(cnt, non_blocking=True)
+
+    e2e_ms, _, _ = timed(e2e_step, max(1, min(args.steps, 5)), 1)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    del Xh
+
+    # ---- parity at full size on sampled outputs, and the CPU oracle baseline (rank 0)
+    result = {}
+    if rank == 0:
+        step()
+        ctx.synchronize()
+        frames_host = Xd.cpu().numpy()
+        cpu_fps, cpu_s, info = oracle_cpu(frames_host, qmap, wl, n_rings_sample=1)
+        import oracle as O
+
+        rng = np.random.default_rng(1)
+        nsamp = 4096
+        qs = rng.integers(0, n_q, size=nsamp)
+        t1 = rng.integers(0, T, size=nsamp)
+        t2 = rng.integers(0, T, size=nsamp)
+        t1, t2 = np.minimum(t1, t2), np.maximum(t1, t2)
+        errs = {}
+        # g2 of ring 0 at the full T from the oracle
+        Cq = O.twotime_from_gram(O.compressed_ring_gram(info["A"], info["G"][0]), info["A"] @ info["s"][0],
+                                 info["A"] @ info["s"][0], info["Mq"][0])
+        gref, _ = O.g2_from_twotime(Cq)
+        del Cq
+        order = np.concatenate([np.flatnonzero(qs == q) for q in range(n_q)])
+        ref = np.concatenate([O.compressed_pair_values(info["A"], info["G"][q], info["s"][q], info["Mq"][q],
+                                                       t1[qs == q], t2[qs == q]) for q in range(n_q)])
+        idx = torch.from_numpy(((qs * T + t1) * T + t2).astype(np.int64)).to(dev)
+        for p in ("fp16", "bf16", "bf16x3"):
+            step(p)
+            ctx.synchronize()
+            gotq = C.view(-1)[idx].cpu().numpy().astype(np.float64)[order]
+            ok = ~np.isnan(ref) & ~np.isnan(gotq)
+            d = np.abs(gotq[ok] - ref[ok])
+            c_max = float(d.max() / np.abs(ref[ok]).max())
+            c_rms = float(np.sqrt((d ** 2).sum() / (ref[ok] ** 2).sum()))
+            gg = g2[0].cpu().numpy()
+            okg = ~np.isnan(gref) & ~np.isnan(gg)
+            g_max = float(np.abs(gg[okg] - gref[okg]).max() / np.abs(gref[okg]).max())
+            errs[p] = {"C_rel_max": c_max, "C_rel_rms": c_rms, "g2_rel_max_ring0": g_max,
+                       "pairs_sampled": int(ok.sum()),
+                       "nan_mismatch": int((np.isnan(ref) != np.isnan(gotq)).sum())}
+        result = dict(cpu_fps=cpu_fps, cpu_s=cpu_s, info=info, errs=errs)
+
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel (timed live over the timed region)
+    pk = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms_total, dom_n) = dom
+    dom_ms = dom_ms_total / max(1, dom_n)
+    nT = (T + 127) // 128
+    T_pad = nT * 128
+    Kc = ((3 if prec == "bf16x3" else 1) * k + 63) // 64 * 64
+    if dom_name == "twotime_gram":
+        c_elems = 0
+        for I in range(nT):
+            rows = min(128, T - 128 * I)
+            for J in range(I, nT):
+                c_elems += rows * min(128, T - 128 * J)
+        maxC = (nT + 7) // 8
+        alg = n_q * c_elems * 4 + 2 * n_q * T_pad * Kc * 2 + n_q * nT * maxC * 256 * 4
+        alg_note = "C upper-triangle tiles written (float32) + both operand matrices read once + diagonal partials"
+    elif dom_name == "encode":
+        kp = (k + 15) // 16 * 16
+        alg = T * M * 2 + 2 * kp * M * 2 + T_pad * k * 4
+        alg_note = "X read once (uint16) + hi/lo basis read once + partial coefficients"
+    else:
+        alg = None
+        alg_note = "no byte model"
+    achieved = alg / (dom_ms * 1e-3) / 1e9 if alg else None
+    traffic = None
+    prof_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_file):
+        tr = json.load(open(prof_file)).get(dom_name, {}).get(prec)
+        if tr:
+            traffic = tr
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": traffic,
+                "algorithmic_bytes": alg, "kernel_ms": dom_ms, "peak_source": pk["source"], "bytes_model": alg_note}
+
+    value = world * T / (ms * 1e-3)
+    h2d = T * M * 2
+    d2h = n_q * T * 16
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "precision": prec, "l2": "inputs larger than L2 (X = 5.24 GB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "raw_path": {"frames_per_s": (world * T / (raw_ms * 1e-3)) if raw_ms else None, "ms_per_step": raw_ms,
+                     "kernels_ms": {k_: v[0] / max(1, v[1]) for k_, v in raw_prof.items()} if raw_ms else None},
+        "speedup_vs_raw": (raw_ms / ms) if raw_ms else None,
+        "error_vs_fp64_oracle": result["errs"],
+        "precision_variants_ms": {p: v["ms_per_step"] for p, v in variants.items()},
+        "kernels_ms": {k_: v[0] / max(1, v[1]) for k_, v in prof.items()},
+        "setup_s": {"generate": t_gen, "fit_basis_gpu": t_fit},
+        "roofline": roofline,
+        "cpu_baseline": {"value": result["cpu_fps"], "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "oracle FP64 encode of all 10000 frames + two-time and g2 of ring 0 at T=10000, "
+                                   "scaled x36 rings (BLAS multithreaded, reductions single-threaded)",
+                         "seconds": result["cpu_s"]},
+        "e2e": {"value": world * T / (e2e_ms * 1e-3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "clocks": sampler.summary() if sampler else None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp16", "bf16", "bf16x3"])
+    ap.add_argument("--no-raw", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = dict(WORKLOAD)
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

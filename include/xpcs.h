@@ -71,6 +71,17 @@ xpcs_status xpcs_set_async(xpcs_ctx* ctx, int async);
 xpcs_status xpcs_synchronize(xpcs_ctx* ctx);
 /* Bytes the library currently holds on the device for this context and its handles. */
 size_t xpcs_device_bytes(const xpcs_ctx* ctx);
+/* Number of CUDA kernels the library has launched on this context so far. */
+uint64_t xpcs_launch_count(const xpcs_ctx* ctx);
+
+/* Per-kernel timing: when enabled, CUDA events on the context's stream bracket every
+ * launch site; entries accumulate per site name.  Enabling (or disabling) clears them.
+ * xpcs_profile_get waits for the stream, then reports entry i: name (NUL-terminated,
+ * truncated to name_cap), total milliseconds and number of timed launches. */
+xpcs_status xpcs_profile_enable(xpcs_ctx* ctx, int on);
+int xpcs_profile_count(const xpcs_ctx* ctx);
+xpcs_status xpcs_profile_get(xpcs_ctx* ctx, int i, char* name_host, size_t name_cap, double* ms_host,
+                             int64_t* launches_host);
 
 /* ------------------------------------------------------------------ q-rings (Sec. 2.2)
  * A ring plan fixes which pixels form each q-ring: qmap[p] in [0, n_q) is the ring of

@@ -10,78 +10,19 @@
 #include <string>
 #include <vector>
 
+#include "handles.h"
 #include "internal.h"
 
 using namespace xpcs;
 
-// ====================================================================== handles
-
-struct xpcs_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  size_t budget = 0;
-  size_t held = 0;
-  bool async = false;
-  std::string err;
-  int num_sms = 0;
-  uint32_t* d_status = nullptr;
-  void* scratch = nullptr;
-  size_t scratch_cap = 0;
-  cusolverDnHandle_t solver = nullptr;
-};
-
-struct xpcs_rings {
-  xpcs_ctx* ctx = nullptr;
-  int64_t M = 0;
-  int n_q = 0;
-  int64_t Mp = 0;                 // ring-sorted row length, each ring padded to 64
-  std::vector<int64_t> Mq;        // pixels per ring
-  std::vector<int> off;           // start of each ring's segment (multiple of 64)
-  std::vector<int> chunks;        // 64-wide chunks per ring segment (>= 1)
-  int* d_qmap = nullptr;
-  int* d_perm = nullptr;          // [Mp] pixel at each sorted position, -1 for padding
-  int* d_pos_ring = nullptr;      // [Mp] ring of each sorted position, -1 for padding
-  int* d_off = nullptr;
-  int* d_chunks = nullptr;
-  long long* d_Mq = nullptr;
-  size_t bytes = 0;
-};
-
-struct xpcs_basis {
-  xpcs_ctx* ctx = nullptr;
-  const xpcs_rings* rings = nullptr;
-  int k = 0;
-  int64_t M_pad = 0;
-  double* d_B = nullptr;          // M x k
-  double* d_G = nullptr;          // n_q x k x k
-  double* d_s = nullptr;          // n_q x k
-  float* d_G32 = nullptr;         // n_q x k x k
-  __nv_bfloat16* d_Bcat = nullptr;  // 2k x M_pad
-  size_t bytes = 0;
-};
-
 // ====================================================================== helpers
 
-namespace {
+namespace xpcs {
 
 xpcs_status fail(xpcs_ctx* ctx, xpcs_status s, const std::string& msg) {
   if (ctx) ctx->err = msg;
   return s;
 }
-
-#define XPCS_CUDA(ctx, call)                                                                               \
-  do {                                                                                                     \
-    cudaError_t e_ = (call);                                                                               \
-    if (e_ != cudaSuccess)                                                                                 \
-      return fail((ctx), XPCS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                 \
-  } while (0)
-
-#define XPCS_TRY(expr)                      \
-  do {                                      \
-    xpcs_status s_ = (expr);                \
-    if (s_ != XPCS_OK) return s_;           \
-  } while (0)
 
 xpcs_status dev_alloc(xpcs_ctx* ctx, void** p, size_t bytes) {
   *p = nullptr;
@@ -103,19 +44,6 @@ void dev_free(xpcs_ctx* ctx, void* p, size_t bytes) {
   cudaFree(p);
   ctx->held -= std::min(ctx->held, bytes);
 }
-
-// Scratch: one growing device buffer per context, carved per call.
-struct Carve {
-  size_t off = 0;
-  char* base = nullptr;
-  template <typename T>
-  T* take(size_t count) {
-    off = (off + 255) & ~size_t(255);
-    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
-    off += count * sizeof(T);
-    return p;
-  }
-};
 
 xpcs_status ensure_scratch(xpcs_ctx* ctx, size_t need) {
   if (need <= ctx->scratch_cap) return XPCS_OK;
@@ -168,6 +96,39 @@ xpcs_status make_map(xpcs_ctx* ctx, CUtensorMap* map, const void* base, CUtensor
   if (r != CUDA_SUCCESS) return fail(ctx, XPCS_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return XPCS_OK;
 }
+
+ProfScope::ProfScope(xpcs_ctx* c, const char* n) : ctx(c), name(n) {
+  if (!ctx->prof) return;
+  for (cudaEvent_t* e : {&a, &b}) {
+    if (!ctx->event_pool.empty()) {
+      *e = ctx->event_pool.back();
+      ctx->event_pool.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      *e = nullptr;
+    }
+  }
+  if (a) cudaEventRecord(a, ctx->stream);
+}
+
+void ProfScope::done() {
+  if (!ctx->prof || !a || !b) return;
+  cudaEventRecord(b, ctx->stream);
+  for (auto& en : ctx->prof_entries)
+    if (en.name == name) {
+      en.pending.push_back({a, b});
+      en.launches += 1;
+      return;
+    }
+  xpcs_prof_entry en;
+  en.name = name;
+  en.pending.push_back({a, b});
+  en.launches = 1;
+  ctx->prof_entries.push_back(std::move(en));
+}
+
+}  // namespace xpcs
+
+namespace {
 
 // Work items of the two-time kernel: (q, delta, I0, I1), tiles (I, I+delta) of one tile
 // diagonal, CH tiles per item; ordered ring by ring, chunk by chunk, delta ascending.
@@ -228,6 +189,8 @@ extern "C" xpcs_status xpcs_destroy(xpcs_ctx* ctx) {
   dev_free(ctx, ctx->scratch, ctx->scratch_cap);
   dev_free(ctx, ctx->d_status, 256);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  xpcs_profile_enable(ctx, 0);
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return XPCS_OK;
@@ -242,6 +205,45 @@ extern "C" xpcs_status xpcs_set_async(xpcs_ctx* ctx, int async) {
 }
 
 extern "C" size_t xpcs_device_bytes(const xpcs_ctx* ctx) { return ctx ? ctx->held : 0; }
+
+extern "C" uint64_t xpcs_launch_count(const xpcs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" xpcs_status xpcs_profile_enable(xpcs_ctx* ctx, int on) {
+  if (!ctx) return XPCS_EINVAL;
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto& en : ctx->prof_entries)
+    for (auto& pr : en.pending) {
+      ctx->event_pool.push_back(pr.first);
+      ctx->event_pool.push_back(pr.second);
+    }
+  ctx->prof_entries.clear();
+  ctx->prof = on != 0;
+  return XPCS_OK;
+}
+
+extern "C" int xpcs_profile_count(const xpcs_ctx* ctx) { return ctx ? (int)ctx->prof_entries.size() : 0; }
+
+extern "C" xpcs_status xpcs_profile_get(xpcs_ctx* ctx, int i, char* name_host, size_t name_cap, double* ms_host,
+                                        int64_t* launches_host) {
+  if (!ctx || i < 0 || i >= (int)ctx->prof_entries.size()) return fail(ctx, XPCS_EINVAL, "bad profile index");
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  auto& en = ctx->prof_entries[i];
+  for (auto& pr : en.pending) {
+    float ms = 0.f;
+    XPCS_CUDA(ctx, cudaEventElapsedTime(&ms, pr.first, pr.second));
+    en.ms += ms;
+    ctx->event_pool.push_back(pr.first);
+    ctx->event_pool.push_back(pr.second);
+  }
+  en.pending.clear();
+  if (name_host && name_cap) {
+    strncpy(name_host, en.name.c_str(), name_cap - 1);
+    name_host[name_cap - 1] = 0;
+  }
+  if (ms_host) *ms_host = en.ms;
+  if (launches_host) *launches_host = en.launches;
+  return XPCS_OK;
+}
 
 extern "C" xpcs_status xpcs_synchronize(xpcs_ctx* ctx) {
   if (!ctx) return XPCS_EINVAL;
@@ -262,13 +264,11 @@ extern "C" xpcs_status xpcs_synchronize(xpcs_ctx* ctx) {
 
 // ====================================================================== rings
 
-extern "C" xpcs_status xpcs_rings_create(xpcs_ctx* ctx, const int32_t* qmap, int64_t M, int n_q, xpcs_rings** out) {
-  if (!ctx || !qmap || !out || M <= 0 || n_q <= 0 || n_q > 1024) return fail(ctx, XPCS_EINVAL, "bad ring plan args");
+namespace xpcs {
+
+// Ring plan from a host label array (labels in [-1, n_q)).
+xpcs_status rings_from_host(xpcs_ctx* ctx, const int32_t* h, int64_t M, int n_q, xpcs_rings** out) {
   *out = nullptr;
-  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
-  std::vector<int32_t> h(M);
-  XPCS_CUDA(ctx, cudaMemcpyAsync(h.data(), qmap, M * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   auto* r = new xpcs_rings();
   r->ctx = ctx;
   r->M = M;
@@ -304,7 +304,6 @@ extern "C" xpcs_status xpcs_rings_create(xpcs_ctx* ctx, const int32_t* qmap, int
     pos[at] = q;
   }
   std::vector<long long> mq(r->Mq.begin(), r->Mq.end());
-  const size_t bytes = M * 4 + 2 * r->Mp * 4 + 2 * n_q * 4 + n_q * 8;
   xpcs_status s = XPCS_OK;
   void* p[6] = {};
   const size_t sz[6] = {(size_t)M * 4, (size_t)r->Mp * 4, (size_t)r->Mp * 4, (size_t)n_q * 4, (size_t)n_q * 4,
@@ -321,8 +320,8 @@ extern "C" xpcs_status xpcs_rings_create(xpcs_ctx* ctx, const int32_t* qmap, int
   r->d_off = (int*)p[3];
   r->d_chunks = (int*)p[4];
   r->d_Mq = (long long*)p[5];
-  r->bytes = bytes;
-  cudaError_t e = cudaMemcpy(r->d_qmap, h.data(), sz[0], cudaMemcpyHostToDevice);
+  r->bytes = sz[0] + sz[1] + sz[2] + sz[3] + sz[4] + sz[5];
+  cudaError_t e = cudaMemcpy(r->d_qmap, h, sz[0], cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(r->d_perm, perm.data(), sz[1], cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(r->d_pos_ring, pos.data(), sz[2], cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(r->d_off, r->off.data(), sz[3], cudaMemcpyHostToDevice);
@@ -334,6 +333,18 @@ extern "C" xpcs_status xpcs_rings_create(xpcs_ctx* ctx, const int32_t* qmap, int
   }
   *out = r;
   return XPCS_OK;
+}
+
+}  // namespace xpcs
+
+extern "C" xpcs_status xpcs_rings_create(xpcs_ctx* ctx, const int32_t* qmap, int64_t M, int n_q, xpcs_rings** out) {
+  if (!ctx || !qmap || !out || M <= 0 || n_q <= 0 || n_q > 1024) return fail(ctx, XPCS_EINVAL, "bad ring plan args");
+  *out = nullptr;
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  std::vector<int32_t> h(M);
+  XPCS_CUDA(ctx, cudaMemcpyAsync(h.data(), qmap, M * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return rings_from_host(ctx, h.data(), M, n_q, out);
 }
 
 extern "C" xpcs_status xpcs_rings_destroy(xpcs_rings* r) {
@@ -390,7 +401,7 @@ xpcs_status raw_ingest(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_d
   ip.S = S;
   ip.sq = b.sq;
   ip.status = ctx->d_status;
-  XPCS_CUDA(ctx, launch_raw_ingest(ip, ctx->stream));
+  XPCS_LAUNCH(ctx, "ingest", 1, launch_raw_ingest(ip, ctx->stream));
   return XPCS_OK;
 }
 
@@ -422,7 +433,7 @@ extern "C" xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* R, const 
   ip.S = reinterpret_cast<long long*>(S_out);
   ip.sq = b.sq;
   ip.status = ctx->d_status;
-  XPCS_CUDA(ctx, launch_raw_ingest(ip, ctx->stream));
+  XPCS_LAUNCH(ctx, "ingest", 1, launch_raw_ingest(ip, ctx->stream));
   return finish(ctx);
 }
 
@@ -437,11 +448,11 @@ xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap
   gp.items = d_items;
   gp.n_items = (int)items.size();
   const int grid = std::min<int>(gp.n_items, ctx->num_sms);
-  XPCS_CUDA(ctx, launch_gram(tmL, tmR, gp, grid, ctx->stream));
+  XPCS_LAUNCH(ctx, "twotime_gram", 1, launch_gram(tmL, tmR, gp, grid, ctx->stream));
   if (count) {
-    XPCS_CUDA(ctx, launch_counts(gp.r, n_q, T, T_pad, vbits, T_pad / 32, count, ctx->stream));
+    XPCS_LAUNCH(ctx, "pair_counts", 2, launch_counts(gp.r, n_q, T, T_pad, vbits, T_pad / 32, count, ctx->stream));
     if (g2_out)
-      XPCS_CUDA(ctx, launch_g2_finalize(gp.partials, count, n_q, T, nT, maxC, gp.CH, g2_out, ctx->stream));
+      XPCS_LAUNCH(ctx, "g2_finalize", 1, launch_g2_finalize(gp.partials, count, n_q, T, nT, maxC, gp.CH, g2_out, ctx->stream));
   }
   return XPCS_OK;
 }
@@ -481,7 +492,7 @@ extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, cons
   layout(c1, b);
   if (count_out) b.count = reinterpret_cast<long long*>(count_out);
   XPCS_TRY(raw_ingest(ctx, R, X, dtype, T, T_pad, nT, true, b.S, b));
-  XPCS_CUDA(ctx, launch_raw_scales(b.S, R->d_Mq, n_q, T, T_pad, nT, b.sq, b.r, b.blk_bad, ctx->d_status,
+  XPCS_LAUNCH(ctx, "raw_scales", 1, launch_raw_scales(b.S, R->d_Mq, n_q, T, T_pad, nT, b.sq, b.r, b.blk_bad, ctx->d_status,
                                    ctx->stream));
   CUtensorMap tm;
   XPCS_TRY(make_map(ctx, &tm, b.Xp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, R->Mp, T_pad, KCH, TILE,
@@ -517,10 +528,11 @@ xpcs_status basis_alloc(xpcs_ctx* ctx, const xpcs_rings* R, int k, xpcs_basis** 
   B->ctx = ctx;
   B->rings = R;
   B->k = k;
+  B->kp = (k + 15) / 16 * 16;
   B->M_pad = (R->M + 63) / 64 * 64;
   const int n_q = R->n_q;
   const size_t szs[5] = {(size_t)R->M * k * 8, (size_t)n_q * k * k * 8, (size_t)n_q * k * 8,
-                         (size_t)n_q * k * k * 4, (size_t)2 * k * B->M_pad * 2};
+                         (size_t)n_q * k * k * 4, (size_t)2 * B->kp * B->M_pad * 2};
   void* p[5] = {};
   xpcs_status s = XPCS_OK;
   for (int i = 0; i < 5 && s == XPCS_OK; ++i) s = dev_alloc(ctx, &p[i], szs[i]);
@@ -553,10 +565,10 @@ xpcs_status basis_finish(xpcs_ctx* ctx, xpcs_basis* B) {
   Carve c{0, static_cast<char*>(ctx->scratch)};
   double* Gpart = c.take<double>((size_t)n_q * n_split * k * k);
   double* spart = c.take<double>((size_t)n_q * n_split * k);
-  XPCS_CUDA(ctx, launch_ring_factors2(B->d_B, k, R->d_perm, R->d_off, R->d_Mq, n_q, n_split, Gpart, spart,
+  XPCS_LAUNCH(ctx, "ring_factors", 1, launch_ring_factors2(B->d_B, k, R->d_perm, R->d_off, R->d_Mq, n_q, n_split, Gpart, spart,
                                       ctx->stream));
-  XPCS_CUDA(ctx, launch_ring_factors_reduce(Gpart, spart, n_split, n_q, k, B->d_G, B->d_s, B->d_G32, ctx->stream));
-  XPCS_CUDA(ctx, launch_basis_pack(B->d_B, R->M, B->M_pad, k, B->d_Bcat, ctx->stream));
+  XPCS_LAUNCH(ctx, "ring_factors_reduce", 1, launch_ring_factors_reduce(Gpart, spart, n_split, n_q, k, B->d_G, B->d_s, B->d_G32, ctx->stream));
+  XPCS_LAUNCH(ctx, "basis_pack", 1, launch_basis_pack(B->d_B, R->M, B->M_pad, k, B->kp, B->d_Bcat, ctx->stream));
   return XPCS_OK;
 }
 
@@ -611,8 +623,98 @@ extern "C" xpcs_status xpcs_basis_destroy(xpcs_basis* B) {
   dev_free(ctx, B->d_G, (size_t)n_q * k * k * 8);
   dev_free(ctx, B->d_s, (size_t)n_q * k * 8);
   dev_free(ctx, B->d_G32, (size_t)n_q * k * k * 4);
-  dev_free(ctx, B->d_Bcat, (size_t)2 * k * B->M_pad * 2);
+  dev_free(ctx, B->d_Bcat, (size_t)2 * B->kp * B->M_pad * 2);
   delete B;
+  return XPCS_OK;
+}
+
+
+// ====================================================================== basis fit (Eq. 3-6)
+
+extern "C" xpcs_status xpcs_fit_basis(xpcs_ctx* ctx, const xpcs_rings* R, const void* F, xpcs_dtype dtype,
+                                      int64_t n_fit, int k, xpcs_basis** out, double* sigma_host) {
+  if (!ctx || !R || !F || !out || R->ctx != ctx || n_fit < 1 || k < 1 || k > 256 || k > n_fit ||
+      (dtype != XPCS_U8 && dtype != XPCS_U16))
+    return fail(ctx, XPCS_EINVAL, "bad fit_basis args");
+  if (n_fit > 32768) return fail(ctx, XPCS_ENOTSUP, "n_fit too large for the dense eigensolver");
+  *out = nullptr;
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int n = (int)n_fit;
+  const int64_t M = R->M;
+  // 1. exact integer Gram F F^T of the fit frames over all pixels (one ring = every pixel)
+  std::vector<int32_t> all(M, 0);
+  xpcs_rings* P = nullptr;
+  XPCS_TRY(rings_from_host(ctx, all.data(), M, 1, &P));
+  struct Tmp {
+    xpcs_ctx* ctx;
+    std::vector<std::pair<void*, size_t>> v;
+    ~Tmp() {
+      for (auto& a : v) dev_free(ctx, a.first, a.second);
+    }
+    xpcs_status get(void** p, size_t b) {
+      xpcs_status s = dev_alloc(ctx, p, b);
+      if (s == XPCS_OK) v.push_back({*p, b});
+      return s;
+    }
+  } tmp{ctx, {}};
+  long long* N = nullptr;
+  double *Gf = nullptr, *W = nullptr, *nrm = nullptr, *Z = nullptr, *work = nullptr;
+  int* info = nullptr;
+  xpcs_status s = tmp.get((void**)&N, (size_t)n * n * 8);
+  if (s == XPCS_OK) s = tmp.get((void**)&Gf, (size_t)n * n * 8);
+  if (s == XPCS_OK) s = tmp.get((void**)&W, (size_t)n * 8);
+  if (s == XPCS_OK) s = tmp.get((void**)&nrm, (size_t)n * 8);
+  if (s == XPCS_OK) s = tmp.get((void**)&Z, (size_t)n * k * 8);
+  if (s == XPCS_OK) s = tmp.get((void**)&info, 4);
+  if (s == XPCS_OK) s = xpcs_twotime_raw(ctx, P, F, dtype, n_fit, nullptr, reinterpret_cast<int64_t*>(N), nullptr,
+                                         nullptr);
+  xpcs_rings_destroy(P);
+  XPCS_TRY(s);
+  // 2. Gram of the Frobenius-normalised frames (Sec. 2.1)
+  XPCS_LAUNCH(ctx, "fit_normalise", 1, launch_gram_normalise(N, n, Gf, nrm, ctx->stream));
+  // 3. FP64 eigendecomposition (library call, setup only)
+  if (!ctx->solver && cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS)
+    return fail(ctx, XPCS_ECUDA, "cusolverDnCreate failed");
+  if (cusolverDnSetStream(ctx->solver, ctx->stream) != CUSOLVER_STATUS_SUCCESS)
+    return fail(ctx, XPCS_ECUDA, "cusolverDnSetStream failed");
+  int lwork = 0;
+  if (cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, Gf, n, W,
+                                  &lwork) != CUSOLVER_STATUS_SUCCESS)
+    return fail(ctx, XPCS_ECUDA, "cusolverDnDsyevd_bufferSize failed");
+  XPCS_TRY(tmp.get((void**)&work, (size_t)std::max(1, lwork) * 8));
+  if (cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, Gf, n, W, work, lwork,
+                       info) != CUSOLVER_STATUS_SUCCESS)
+    return fail(ctx, XPCS_ECUDA, "cusolverDnDsyevd failed");
+  std::vector<double> lam(n);
+  int hinfo = 0;
+  XPCS_CUDA(ctx, cudaMemcpyAsync(lam.data(), W, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  XPCS_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hinfo != 0) return fail(ctx, XPCS_ECUDA, "eigensolver did not converge: info " + std::to_string(hinfo));
+  // 4. rank and singular values (eigenvalues ascending from the solver)
+  const double lmax = std::max(lam[n - 1], 0.0);
+  const double tol = (double)n * 2.220446049250313e-16 * lmax;
+  int rank = 0;
+  for (int i = 0; i < n; ++i) rank += lam[i] > tol;
+  if (sigma_host)
+    for (int i = 0; i < n; ++i) sigma_host[i] = std::sqrt(std::max(lam[n - 1 - i], 0.0));
+  if (k > rank) return fail(ctx, XPCS_EINVAL, "k=" + std::to_string(k) + " exceeds the rank " + std::to_string(rank));
+  // 5. V_K = F^T U_k Sigma_k^-1 with the row norms folded in, sign convention, ring factors
+  XPCS_LAUNCH(ctx, "fit_z", 1, launch_basis_z(Gf, W, nrm, n, k, Z, ctx->stream));
+  xpcs_basis* B = nullptr;
+  XPCS_TRY(basis_alloc(ctx, R, k, &B));
+  xpcs_status st = XPCS_OK;
+  if (launch_basis_build(F, dtype, n, M, Z, k, B->d_B, ctx->stream) != cudaSuccess ||
+      launch_basis_sign(B->d_B, M, k, ctx->stream) != cudaSuccess)
+    st = fail(ctx, XPCS_ECUDA, "basis build launch failed");
+  ctx->launches += 2;
+  if (st == XPCS_OK) st = basis_finish(ctx, B);
+  if (st == XPCS_OK) st = xpcs_synchronize(ctx);
+  if (st != XPCS_OK) {
+    xpcs_basis_destroy(B);
+    return st;
+  }
+  *out = B;
   return XPCS_OK;
 }
 
@@ -682,7 +784,7 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   pp.r = b.r;
   pp.blk_bad = b.blk_bad;
   pp.St = nullptr;
-  XPCS_CUDA(ctx, launch_prep_compressed(pp, ctx->stream));
+  XPCS_LAUNCH(ctx, "compressed_prep", 2, launch_prep_compressed(pp, ctx->stream));
   const CUtensorMapDataType dt =
       prec == XPCS_PREC_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap tmL, tmR;
@@ -727,8 +829,8 @@ extern "C" xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T
   Carve c{0, static_cast<char*>(ctx->scratch)};
   double* part = c.take<double>((size_t)splits * n_q * T);
   long long* cpart = c.take<long long>((size_t)splits * n_q * T);
-  XPCS_CUDA(ctx, launch_g2_from_C(C, n_q, T, part, splits, cpart, ctx->stream));
-  XPCS_CUDA(ctx, launch_g2_from_C_reduce(part, cpart, n_q, T, splits, g2_out,
+  XPCS_LAUNCH(ctx, "g2_from_C", 1, launch_g2_from_C(C, n_q, T, part, splits, cpart, ctx->stream));
+  XPCS_LAUNCH(ctx, "g2_from_C_reduce", 1, launch_g2_from_C_reduce(part, cpart, n_q, T, splits, g2_out,
                                          reinterpret_cast<long long*>(count_out), ctx->stream));
   return finish(ctx);
 }

@@ -177,9 +177,11 @@ __global__ void ring_factors_reduce_kernel(const double* Gpart, const double* sp
   }
 }
 
-// Bcat (2k x M_pad, bf16, pixel-contiguous rows): rows 0..k-1 = hi(B^T), rows k..2k-1 =
-// lo(B^T) = bf16(B - hi); padded pixels are zero.  Tiled transpose through shared memory.
-__global__ void basis_pack_kernel(const double* B, long long M, long long M_pad, int k, __nv_bfloat16* Bcat) {
+// Bcat (2kp x M_pad, bf16, pixel-contiguous rows): rows 0..k-1 = hi(B^T), rows kp..kp+k-1 =
+// lo(B^T) = bf16(B - hi); padded pixels and rows stay zero.  Tiled transpose through
+// shared memory.
+__global__ void basis_pack_kernel(const double* B, long long M, long long M_pad, int k, int kp,
+                                  __nv_bfloat16* Bcat) {
   __shared__ double tile[32][33];
   const long long p0 = (long long)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
@@ -198,7 +200,7 @@ __global__ void basis_pack_kernel(const double* B, long long M, long long M_pad,
       const __nv_bfloat16 hi = __float2bfloat16_rn(v);
       const __nv_bfloat16 lo = __float2bfloat16_rn((float)((double)tile[tx][yy] - (double)__bfloat162float(hi)));
       Bcat[(size_t)c * M_pad + p] = hi;
-      Bcat[(size_t)(k + c) * M_pad + p] = lo;
+      Bcat[(size_t)(kp + c) * M_pad + p] = lo;
     }
   }
 }
@@ -246,10 +248,12 @@ cudaError_t launch_ring_factors_reduce(const double* Gpart, const double* spart,
   return cudaGetLastError();
 }
 
-cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, __nv_bfloat16* Bcat,
+cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, int kp, __nv_bfloat16* Bcat,
                               cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(Bcat, 0, (size_t)2 * kp * M_pad * sizeof(__nv_bfloat16), st);
+  if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((M_pad + 31) / 32), (k + 31) / 32);
-  basis_pack_kernel<<<grid, 256, 0, st>>>(B, M, M_pad, k, Bcat);
+  basis_pack_kernel<<<grid, 256, 0, st>>>(B, M, M_pad, k, kp, Bcat);
   return cudaGetLastError();
 }
 

@@ -1,9 +1,338 @@
-// placeholder, replaced by the tcgen05 encode
+// Encode: coefficients A = X V_K (Eq. 7) on the tcgen05 tensor cores, sm_103a.
+//
+// X (T x M counts, u8 or u16) streams from HBM once; V_K is held as Bcat, a 2kp x M bf16
+// matrix (kp = k rounded up to 16) whose rows 0..k-1 are hi(V_K^T) and rows kp..kp+k-1 are
+// lo(V_K^T) = bf16(V - hi), so one MMA with N = 2kp gives X hi and X lo in two halves of
+// the accumulator and the encode keeps ~16 bits of the basis.  Counts are exact in bf16
+// up to 256.
+//
+// Work item = (frame block m of 128 frames, pixel split s).  Per 64-pixel chunk:
+//   warp 0      TMA: raw X tile (128 x 64, no swizzle) and the Bcat tile (2k x 64, SW128)
+//   warps 2..5  convert the raw tile to bf16 in the 128-byte-swizzled K-major layout
+//   warp 1      MMA into a 128 x 2k f32 TMEM accumulator (N <= 256 per instruction)
+// After the split's last chunk warps 2..5 drain TMEM, add the two halves and write the
+// split's partial coefficients; a second kernel sums the splits in a fixed order.
+#include <algorithm>
+
+#include "common.cuh"
+#include "handles.h"
 #include "internal.h"
-extern "C" xpcs_status xpcs_encode(xpcs_ctx*, const xpcs_basis*, const void*, xpcs_dtype, int64_t, float*) {
-  return XPCS_ENOTSUP;
+
+namespace xpcs {
+
+namespace {
+
+constexpr int ENC_THREADS = 64 + 128;
+constexpr int CONV_BYTES = TILE * KCH * 2;  // converted bf16 tile: 16 KB
+
+struct EncLayout {
+  int k, kp, N, nload, ns, raw_bytes, b_bytes, stage_bytes, tmem_cols;
+  __host__ __device__ EncLayout(int k_, int dtype) {
+    k = k_;
+    kp = (k_ + 15) / 16 * 16;  // lo half starts at column kp; N = 2 kp is a multiple of 32
+    N = 2 * kp;
+    nload = (N + 255) / 256;
+    raw_bytes = TILE * KCH * (dtype == 0 ? 1 : 2);
+    raw_bytes = (raw_bytes + 1023) / 1024 * 1024;
+    b_bytes = N * 128;
+    stage_bytes = raw_bytes + b_bytes + CONV_BYTES;
+    ns = (200 * 1024) / stage_bytes;
+    if (ns > 4) ns = 4;
+    tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
+  }
+  __host__ __device__ int smem() const { return 1024 + ns * stage_bytes + 256; }
+};
+
+__global__ void __launch_bounds__(ENC_THREADS, 1)
+encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, const EncodeParams p,
+              int n_items) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const EncLayout lay(p.k, p.dtype);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.ns * lay.stage_bytes);
+  uint64_t* full = bars;               // [4] TMA landed (raw X + B)
+  uint64_t* empty = bars + 4;          // [4] MMA done with the stage
+  uint64_t* cfull = bars + 8;          // [4] conversion done
+  uint64_t* tfull = bars + 12;         // accumulator ready
+  uint64_t* tempty = bars + 13;        // accumulator drained
+  uint64_t* mma_done = bars + 14;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 15);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto raw_of = [&](int s) { return smem + s * lay.stage_bytes; };
+  auto b_of = [&](int s) { return smem + s * lay.stage_bytes + lay.raw_bytes; };
+  auto conv_of = [&](int s) { return smem + s * lay.stage_bytes + lay.raw_bytes + lay.b_bytes; };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_chunks = (int)(p.px_per_split / KCH);
+  const int n_m = p.T_pad / TILE;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < lay.ns; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&cfull[s], 128);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 4);
+    mbar_init(mma_done, 1);
+    mbar_fence_init();
+    *abort_flag = 0;
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, lay.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tma_prefetch_desc(&tmX);
+      tma_prefetch_desc(&tmB);
+      uint32_t it = 0;
+      bool ok = true;
+      const uint32_t tx = (uint32_t)(TILE * KCH * (p.dtype == 0 ? 1 : 2) + lay.b_bytes);
+      for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+        const int m = item % n_m, sp = item / n_m;
+        const long long px0 = (long long)sp * p.px_per_split;
+        for (int c = 0; c < n_chunks; ++c, ++it) {
+          const uint32_t s = it % lay.ns, ph = (it / lay.ns) & 1;
+          if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, p.status)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          const int x = (int)(px0 + (long long)c * KCH);
+          mbar_arrive_expect_tx(&full[s], tx);
+          tma_load_2d(raw_of(s), &tmX, &full[s], x, m * TILE);
+          for (int l = 0; l < lay.nload; ++l)
+            tma_load_2d(b_of(s) + l * (lay.N / lay.nload) * 128, &tmB, &full[s], x, l * (lay.N / lay.nload));
+        }
+      }
+      for (uint32_t j = (it > (uint32_t)lay.ns ? it - lay.ns : 0); j < it; ++j)
+        mbar_wait(&full[j % lay.ns], (j / lay.ns) & 1, p.status);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const int nmma = (lay.N + 255) / 256;
+      const int nper = lay.N / nmma;
+      const uint32_t idesc = idesc_f16(1, TILE, nper);
+      uint32_t it = 0, item_i = 0;
+      bool ok = true, issued = false;
+      for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++item_i) {
+        if (*abort_flag || !mbar_wait(tempty, (item_i & 1) ^ 1, p.status)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        for (int c = 0; c < n_chunks; ++c, ++it) {
+          const uint32_t s = it % lay.ns, ph = (it / lay.ns) & 1;
+          if (*abort_flag || !mbar_wait(&cfull[s], ph, p.status)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = smem_desc_sw128(conv_of(s));
+          for (int h = 0; h < nmma; ++h) {
+            const uint64_t bd = smem_desc_sw128(b_of(s) + h * nper * 128);
+#pragma unroll
+            for (int kk = 0; kk < KCH / 16; ++kk)
+              tc_mma_f16(tmem_base + h * nper, ad + 2 * kk, bd + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+          }
+          issued = true;
+          tc_commit(&empty[s]);
+        }
+        if (!ok) break;
+        tc_commit(tfull);
+      }
+      if (issued) {
+        tc_commit(mma_done);
+        mbar_wait(mma_done, 0, p.status);
+      }
+    }
+    __syncwarp();
+  } else {
+    // converters + epilogue: 128 threads
+    const int ct = threadIdx.x - 64;
+    const int quarter = warp & 3;
+    uint32_t it = 0, item_i = 0;
+    bool too_big = false;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++item_i) {
+      const int m = item % n_m, sp = item / n_m;
+      bool ok = true;
+      for (int c = 0; c < n_chunks; ++c, ++it) {
+        const uint32_t s = it % lay.ns, ph = (it / lay.ns) & 1;
+        // warp-uniform decision so the warp stays converged for tcgen05.ld
+        if (!__all_sync(0xffffffffu, !*abort_flag && mbar_wait(&full[s], ph, p.status))) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        const uint8_t* raw = raw_of(s);
+        uint8_t* conv = conv_of(s);
+#pragma unroll
+        for (int u8i = 0; u8i < 8; ++u8i) {
+          const int unit = u8i * 128 + ct;
+          const int row = unit >> 3, ch = unit & 7;
+          float f[8];
+          if (p.dtype == 1) {
+            const uint4 v = *reinterpret_cast<const uint4*>(raw + row * 128 + ch * 16);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              f[2 * e] = (float)(w[e] & 0xFFFFu);
+              f[2 * e + 1] = (float)(w[e] >> 16);
+            }
+          } else {
+            const uint2 v = *reinterpret_cast<const uint2*>(raw + row * 64 + ch * 8);
+            const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) f[4 * e + b] = (float)((w[e] >> (8 * b)) & 0xFFu);
+          }
+          uint32_t o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            too_big |= (f[2 * e] > 256.f) | (f[2 * e + 1] > 256.f);
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+            o[e] = *reinterpret_cast<uint32_t*>(&b2);
+          }
+          *reinterpret_cast<uint4*>(conv + row * 128 + ((ch ^ (row & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+        fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
+        mbar_arrive(&cfull[s]);
+      }
+      if (!ok) break;
+      // drain the accumulator: partial coefficients of this split
+      if (!__all_sync(0xffffffffu, mbar_wait(tfull, item_i & 1, p.status))) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const int row = quarter * 32 + lane;
+      float* dst = p.partials + ((size_t)sp * p.T_pad + (size_t)m * TILE + row) * p.k;
+      for (int j0 = 0; j0 < p.k; j0 += 32) {
+        uint32_t hi[32], lo[32];
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        tmem_ld32(lane_base + j0, hi);
+        tmem_ld32(lane_base + lay.kp + j0, lo);
+        tc_wait_ld();
+        const int nj = min(32, p.k - j0);
+        for (int j = 0; j < nj; ++j) dst[j0 + j] = __uint_as_float(hi[j]) + __uint_as_float(lo[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+    }
+    if (too_big) set_status(p.status, XPCS_DEV_RANGE);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, lay.tmem_cols);
+  }
 }
-extern "C" xpcs_status xpcs_fit_basis(xpcs_ctx*, const xpcs_rings*, const void*, xpcs_dtype, int64_t, int,
-                                      xpcs_basis**, double*) {
-  return XPCS_ENOTSUP;
+
+__global__ void encode_reduce_kernel(const float* partials, int n_split, long long T, int T_pad, int k, float* A) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= T * k) return;
+  const long long t = gid / k;
+  const int j = (int)(gid % k);
+  float a = 0.f;
+  for (int s = 0; s < n_split; ++s) a += partials[((size_t)s * T_pad + t) * k + j];
+  A[gid] = a;
+}
+
+}  // namespace
+
+int encode_smem_bytes(int k) { return EncLayout(k, 1).smem(); }
+
+cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const EncodeParams& p, int grid,
+                          cudaStream_t st) {
+  const EncLayout lay(p.k, p.dtype);
+  cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.smem());
+  if (e != cudaSuccess) return e;
+  const int n_items = (p.T_pad / TILE) * p.n_split;
+  encode_kernel<<<grid, ENC_THREADS, lay.smem(), st>>>(tmX, tmB, p, n_items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float* A,
+                                 cudaStream_t st) {
+  const long long n = T * k;
+  encode_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, n_split, T, T_pad, k, A);
+  return cudaGetLastError();
+}
+
+}  // namespace xpcs
+
+// ====================================================================== ABI
+
+using namespace xpcs;
+
+// Pixel splits: choose the count whose item total best fills whole waves of SMs.
+static int pick_splits(int n_m, long long M_pad, int num_sms) {
+  const long long max_split = std::max<long long>(1, M_pad / (KCH * 8));
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= 64 && s <= max_split; ++s) {
+    const long long items = (long long)n_m * s;
+    const long long waves = (items + num_sms - 1) / num_sms;
+    // per-item work shrinks as s grows; efficiency of the last wave and a mild
+    // preference for fewer, longer items
+    const double eff = (double)items / (double)(waves * num_sms) - 0.002 * s;
+    if (items >= num_sms / 2 && eff > best_eff) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  if (best_eff == 0.0) best = (int)std::min<long long>(max_split, std::max(1, (num_sms + n_m - 1) / n_m));
+  return best;
+}
+
+extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const void* X, xpcs_dtype dtype, int64_t T,
+                                   float* A_out) {
+  if (!ctx || !B || !X || !A_out || T <= 0 || B->ctx != ctx || (dtype != XPCS_U8 && dtype != XPCS_U16))
+    return fail(ctx, XPCS_EINVAL, "bad encode args");
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t M = B->rings->M;
+  const int eb = dtype == XPCS_U8 ? 1 : 2;
+  if ((M * eb) % 16) return fail(ctx, XPCS_ENOTSUP, "encode needs M*elem_bytes to be a multiple of 16");
+  const int k = B->k;
+  const int nT = (int)((T + TILE - 1) / TILE);
+  const int T_pad = nT * TILE;
+  const int n_split = pick_splits(nT, B->M_pad, ctx->num_sms);
+  const long long per = ((B->M_pad + n_split - 1) / n_split + KCH - 1) / KCH * KCH;
+  Carve c0;
+  c0.take<float>((size_t)n_split * T_pad * k);
+  XPCS_TRY(ensure_scratch(ctx, c0.off));
+  Carve c{0, static_cast<char*>(ctx->scratch)};
+  float* partials = c.take<float>((size_t)n_split * T_pad * k);
+  CUtensorMap tmX, tmB;
+  XPCS_TRY(make_map(ctx, &tmX, X, dtype == XPCS_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                    eb, M, T, KCH, TILE, CU_TENSOR_MAP_SWIZZLE_NONE));
+  const int N = 2 * B->kp;
+  XPCS_TRY(make_map(ctx, &tmB, B->d_Bcat, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B->M_pad, N, KCH,
+                    N / ((N + 255) / 256), CU_TENSOR_MAP_SWIZZLE_128B));
+  EncodeParams p{};
+  p.T = T;
+  p.M = M;
+  p.k = k;
+  p.dtype = dtype;
+  p.n_split = n_split;
+  p.px_per_split = per;
+  p.partials = partials;
+  p.T_pad = T_pad;
+  p.status = ctx->d_status;
+  const int n_items = nT * n_split;
+  XPCS_LAUNCH(ctx, "encode", 1, launch_encode(tmX, tmB, p, std::min(n_items, ctx->num_sms), ctx->stream));
+  XPCS_LAUNCH(ctx, "encode_reduce", 1, launch_encode_reduce(partials, n_split, T, T_pad, k, A_out, ctx->stream));
+  return finish(ctx);
 }

@@ -1,0 +1,125 @@
+// Library handle types and host helpers shared by the API translation units.
+#pragma once
+#include <cusolverDn.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+// Per-kernel CUDA-event timing (enabled with xpcs_profile_enable).
+struct xpcs_prof_entry {
+  std::string name;
+  double ms = 0.0;
+  int64_t launches = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+struct xpcs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  size_t held = 0;
+  bool async = false;
+  std::string err;
+  int num_sms = 0;
+  uint32_t* d_status = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_cap = 0;
+  cusolverDnHandle_t solver = nullptr;
+  uint64_t launches = 0;  // kernels this library has launched on the context
+  bool prof = false;
+  std::vector<xpcs_prof_entry> prof_entries;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+struct xpcs_rings {
+  xpcs_ctx* ctx = nullptr;
+  int64_t M = 0;
+  int n_q = 0;
+  int64_t Mp = 0;                 // ring-sorted row length, each ring padded to 64
+  std::vector<int64_t> Mq;        // pixels per ring
+  std::vector<int> off;           // start of each ring's segment (multiple of 64)
+  std::vector<int> chunks;        // 64-wide chunks per ring segment (>= 1)
+  int* d_qmap = nullptr;
+  int* d_perm = nullptr;          // [Mp] pixel at each sorted position, -1 for padding
+  int* d_pos_ring = nullptr;      // [Mp] ring of each sorted position, -1 for padding
+  int* d_off = nullptr;
+  int* d_chunks = nullptr;
+  long long* d_Mq = nullptr;
+  size_t bytes = 0;
+};
+
+struct xpcs_basis {
+  xpcs_ctx* ctx = nullptr;
+  const xpcs_rings* rings = nullptr;
+  int k = 0;
+  int kp = 0;                     // k rounded up to 16: lo half of Bcat starts at row kp
+  int64_t M_pad = 0;
+  double* d_B = nullptr;          // M x k
+  double* d_G = nullptr;          // n_q x k x k
+  double* d_s = nullptr;          // n_q x k
+  float* d_G32 = nullptr;         // n_q x k x k
+  __nv_bfloat16* d_Bcat = nullptr;  // 2kp x M_pad
+  size_t bytes = 0;
+};
+
+namespace xpcs {
+
+xpcs_status fail(xpcs_ctx* ctx, xpcs_status s, const std::string& msg);
+xpcs_status dev_alloc(xpcs_ctx* ctx, void** p, size_t bytes);
+void dev_free(xpcs_ctx* ctx, void* p, size_t bytes);
+xpcs_status ensure_scratch(xpcs_ctx* ctx, size_t need);
+xpcs_status rings_from_host(xpcs_ctx* ctx, const int32_t* qmap_host, int64_t M, int n_q, xpcs_rings** out);
+xpcs_status finish(xpcs_ctx* ctx);
+xpcs_status make_map(xpcs_ctx* ctx, CUtensorMap* map, const void* base, CUtensorMapDataType dt, int elem_bytes,
+                     uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw);
+
+// Scratch: one growing device buffer per context, carved per call.
+struct Carve {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Records CUDA events around one launch site when profiling is on.
+struct ProfScope {
+  xpcs_ctx* ctx;
+  const char* name;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(xpcs_ctx* c, const char* n);
+  void done();
+};
+
+}  // namespace xpcs
+
+// Launch through a library launcher, counting `nk` kernels and timing the site.
+#define XPCS_LAUNCH(ctx, name, nk, call)                                                              \
+  do {                                                                                                \
+    ::xpcs::ProfScope ps_((ctx), (name));                                                             \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return ::xpcs::fail((ctx), XPCS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    (ctx)->launches += (nk);                                                                          \
+    ps_.done();                                                                                       \
+  } while (0)
+
+#define XPCS_CUDA(ctx, call)                                                                          \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return ::xpcs::fail((ctx), XPCS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+#define XPCS_TRY(expr)            \
+  do {                            \
+    xpcs_status s_ = (expr);      \
+    if (s_ != XPCS_OK) return s_; \
+  } while (0)

@@ -133,7 +133,7 @@ cudaError_t launch_ring_factors2(const double* B, int k, const int* perm, const 
                                  int n_q, int n_split, double* Gpart, double* spart, cudaStream_t st);
 cudaError_t launch_ring_factors_reduce(const double* Gpart, const double* spart, int n_chunks, int n_q, int k,
                                        double* G, double* s, float* G32, cudaStream_t st);
-cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, __nv_bfloat16* Bcat,
+cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, int kp, __nv_bfloat16* Bcat,
                               cudaStream_t st);
 
 }  // namespace xpcs

@@ -38,6 +38,11 @@ _SIGS = {
     "xpcs_set_async": (C.c_int, [vp, C.c_int]),
     "xpcs_synchronize": (C.c_int, [vp]),
     "xpcs_device_bytes": (C.c_size_t, [vp]),
+    "xpcs_launch_count": (C.c_uint64, [vp]),
+    "xpcs_profile_enable": (C.c_int, [vp, C.c_int]),
+    "xpcs_profile_count": (C.c_int, [vp]),
+    "xpcs_profile_get": (C.c_int, [vp, C.c_int, C.c_char_p, C.c_size_t, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int64)]),
     "xpcs_rings_create": (C.c_int, [vp, vp, i64, C.c_int, C.POINTER(vp)]),
     "xpcs_rings_destroy": (C.c_int, [vp]),
     "xpcs_rings_sizes": (C.c_int, [vp, vp]),
@@ -126,6 +131,23 @@ class Context:
 
     def device_bytes(self) -> int:
         return int(_lib.xpcs_device_bytes(self.h))
+
+    def launch_count(self) -> int:
+        return int(_lib.xpcs_launch_count(self.h))
+
+    def profile_enable(self, on: bool = True):
+        self.check(_lib.xpcs_profile_enable(self.h, 1 if on else 0))
+
+    def profile(self) -> dict:
+        """{site name: (total ms, launches)} of the timed launch sites."""
+        out = {}
+        for i in range(_lib.xpcs_profile_count(self.h)):
+            buf = C.create_string_buffer(64)
+            ms = C.c_double()
+            n = C.c_int64()
+            self.check(_lib.xpcs_profile_get(self.h, i, buf, 64, C.byref(ms), C.byref(n)))
+            out[buf.value.decode()] = (ms.value, n.value)
+        return out
 
 
 class Rings:
