@@ -5,7 +5,7 @@ Workload (512x512 detector, T = 10,000 frames, uint16 Poisson counts of mean 0.1
 AR(1) speckle with D = 5e-4, 36 equal-width q-rings, basis of rank k = 64 fit in FP64 on
 the first 1000 frames).  One step = the compressed path over the whole series:
 encode A = X V_K (Eq. 7) + two-time C_q for every ring from the coefficients
-(Eq. 10 with ring factors, C stored as the float32 upper triangle) + g2.  The exact raw
+(Eq. 10 with ring factors, C stored as the float32 lower triangle) + g2.  The exact raw
 path (Eq. 1-2 on integer counts) is timed in the same run for the speed-up.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle instead.
@@ -28,9 +28,11 @@ if ROOT not in sys.path:
 
 WORKLOAD = dict(H=512, W=512, T=10000, dtype="uint16", mean=0.1, D=5e-4, n_q=36, k=64, n_fit=1000,
                 seed=20356002)
+# smaller case of the same kernels for profiler captures: inputs and outputs still exceed L2
+SMALL = dict(H=256, W=256, T=4096, dtype="uint16", mean=0.1, D=2e-3, n_q=16, k=64, n_fit=500, seed=20356012)
 WORKLOAD_NAME = ("512x512 detector, T=10000 frames, uint16 Poisson AR(1) speckle mean 0.1 D=5e-4, "
                  "36 q-rings, k=64 basis fit on the first 1000 frames; step = encode + two-time (C stored, "
-                 "float32 upper triangle) + g2")
+                 "float32 lower triangle) + g2")
 METRIC = "frames/s correlated (compressed vs exact raw path) at stated err; p99 frame latency"
 
 
@@ -315,6 +317,13 @@ def run_ours(args, wl):
         variants[p] = {"ms_per_step": vms}
 
     # ---- end to end through the public API from pinned host memory
+    if args.no_host:
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "ms_per_step": ms, "frames_per_s": world * T / (ms * 1e-3),
+                              "raw_ms": raw_ms, "variants_ms": {p: v["ms_per_step"] for p, v in variants.items()},
+                              "kernels_ms": {k_: v[0] / max(1, v[1]) for k_, v in prof.items()},
+                              "gpu_launches": launches}), flush=True)
+        return
     Xh = torch.empty((T, M), dtype=torch.uint16, pin_memory=True)
     Xh.copy_(Xd)
     g2h = torch.empty((n_q, T), dtype=torch.float64, pin_memory=True)
@@ -354,7 +363,7 @@ def run_ours(args, wl):
         order = np.concatenate([np.flatnonzero(qs == q) for q in range(n_q)])
         ref = np.concatenate([O.compressed_pair_values(info["A"], info["G"][q], info["s"][q], info["Mq"][q],
                                                        t1[qs == q], t2[qs == q]) for q in range(n_q)])
-        idx = torch.from_numpy(((qs * T + t1) * T + t2).astype(np.int64)).to(dev)
+        idx = torch.from_numpy(((qs * T + t2) * T + t1).astype(np.int64)).to(dev)  # lower triangle
         for p in ("fp16", "bf16", "bf16x3"):
             step(p)
             ctx.synchronize()
@@ -390,7 +399,7 @@ def run_ours(args, wl):
                 c_elems += rows * min(128, T - 128 * J)
         maxC = (nT + 7) // 8
         alg = n_q * c_elems * 4 + 2 * n_q * T_pad * Kc * 2 + n_q * nT * maxC * 256 * 4
-        alg_note = "C upper-triangle tiles written (float32) + both operand matrices read once + diagonal partials"
+        alg_note = "C triangle tiles written (float32) + both operand matrices read once + diagonal partials"
     elif dom_name == "encode":
         kp = (k + 15) // 16 * 16
         alg = T * M * 2 + 2 * kp * M * 2 + T_pad * k * 4
@@ -446,10 +455,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp16", "bf16", "bf16x3"])
     ap.add_argument("--no-raw", action="store_true")
+    ap.add_argument("--no-host", action="store_true",
+                    help="skip the host-side legs (e2e, sampled parity, CPU baseline); for profiler runs")
+    ap.add_argument("--workload", default="c2", choices=["c2", "small"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    wl = dict(WORKLOAD)
+    wl = dict(WORKLOAD if args.workload == "c2" else SMALL)
     if args.impl == "reference":
         run_reference(args, wl)
     else:

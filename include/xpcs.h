@@ -8,16 +8,18 @@
  *    name ends in `_host`, in which case they are host pointers.
  *  - The caller owns every data buffer.  The library owns the opaque handles it creates
  *    (context, ring plan, basis, stream) and frees them in the matching destroy/close.
+ *    Destroy every handle before the context it was created on.
  *  - Matrices are dense row-major.  X is T x M (frame t, pixel p), one frame per row.
  *  - Work is enqueued on the context's CUDA stream.  Unless the context is in
  *    asynchronous mode (xpcs_set_async), each call waits for its work and returns any
  *    error it raised; in asynchronous mode errors surface at xpcs_synchronize().
  *  - Functions return an xpcs_status; nothing throws or aborts across the ABI.  The text
  *    of the last error of a context is available from xpcs_last_error().
- *  - Two-time outputs C are n_q x T x T float32 with only the upper triangle
- *    (t2 >= t1) written; the lower triangle is left untouched.  Undefined pairs (a ring
- *    sum <= 0) are NaN.  g2 and count arrays are n_q x T, indexed by lag tau = 0..T-1;
- *    g2 is NaN where count is 0.
+ *  - The two-time matrix is symmetric; outputs hold its lower triangle: C[q][t1][t2]
+ *    (and N[q][t1][t2]) for t1 >= t2, n_q x T x T row-major, float32 (int64 for N).
+ *    Entries above the diagonal are left untouched.  Undefined pairs (a ring sum <= 0)
+ *    are NaN.  g2 and count arrays are n_q x T, indexed by lag tau = 0..T-1; g2 is NaN
+ *    where count is 0.
  */
 #ifndef XPCS_GB300_H
 #define XPCS_GB300_H
@@ -104,8 +106,8 @@ xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X
  * The integer Gram is computed exactly on the tensor cores (bf16 operands, f32
  * accumulation kept below 2^24); counts above 256, or a ring whose largest per-frame
  * sum of squared counts reaches 2^24, return XPCS_ERANGE.
- * Outputs (all nullable): C_out n_q x T x T f32 (upper triangle), N_out n_q x T x T
- * int64 (upper triangle), g2_out n_q x T f64, count_out n_q x T int64. */
+ * Outputs (all nullable): C_out n_q x T x T f32 (lower triangle), N_out n_q x T x T
+ * int64 (lower triangle), g2_out n_q x T f64, count_out n_q x T int64. */
 xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X, xpcs_dtype dtype, int64_t T,
                              float* C_out, int64_t* N_out, double* g2_out, int64_t* count_out);
 
@@ -130,8 +132,8 @@ xpcs_status xpcs_basis_destroy(xpcs_basis* basis);
 
 /* ------------------------------------------------------------------ encode (Eq. 7)
  * Coefficients Y_K = X V_K: A_out is T x k float32.  X: T x M counts (M a multiple of 8
- * for u16, 16 for u8).  Tensor cores: counts as bf16 (exact up to 256, else
- * XPCS_ERANGE), V_K as a hi/lo bf16 pair, f32 accumulation. */
+ * for u16, 16 for u8).  Tensor cores: counts as f16 (exact up to 1023, else
+ * XPCS_ERANGE), V_K as a power-of-two-scaled hi/lo f16 pair, f32 accumulation. */
 xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* basis, const void* X, xpcs_dtype dtype, int64_t T,
                         float* A_out);
 
@@ -144,7 +146,7 @@ xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A,
                          float* C_out, double* g2_out, int64_t* count_out);
 
 /* ------------------------------------------------------------------ g2 over a stored C
- * g2_q(tau) = mean over t of C[q][t][t+tau], NaN entries skipped, from the upper
+ * g2_q(tau) = mean over t of C[q][t+tau][t], NaN entries skipped, from the lower
  * triangle of C (n_q x T x T float32).  g2_out n_q x T f64, count_out nullable. */
 xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out, int64_t* count_out);
 

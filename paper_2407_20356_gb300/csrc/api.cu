@@ -507,6 +507,7 @@ extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, cons
   gp.k_chunks = R->d_chunks;
   gp.ring_rows = 0;
   gp.fmt = 1;
+  gp.split = 0;
   gp.raw = 1;
   gp.r = b.r;
   gp.blk_bad = b.blk_bad;
@@ -545,7 +546,7 @@ xpcs_status basis_alloc(xpcs_ctx* ctx, const xpcs_rings* R, int k, xpcs_basis** 
   B->d_G = (double*)p[1];
   B->d_s = (double*)p[2];
   B->d_G32 = (float*)p[3];
-  B->d_Bcat = (__nv_bfloat16*)p[4];
+  B->d_Bcat = (__half*)p[4];
   B->bytes = szs[0] + szs[1] + szs[2] + szs[3] + szs[4];
   *out = B;
   return XPCS_OK;
@@ -561,6 +562,7 @@ xpcs_status basis_finish(xpcs_ctx* ctx, xpcs_basis* B) {
   Carve c0;
   c0.take<double>((size_t)n_q * n_split * k * k);
   c0.take<double>((size_t)n_q * n_split * k);
+  c0.take<double>(256);
   XPCS_TRY(ensure_scratch(ctx, c0.off));
   Carve c{0, static_cast<char*>(ctx->scratch)};
   double* Gpart = c.take<double>((size_t)n_q * n_split * k * k);
@@ -568,7 +570,16 @@ xpcs_status basis_finish(xpcs_ctx* ctx, xpcs_basis* B) {
   XPCS_LAUNCH(ctx, "ring_factors", 1, launch_ring_factors2(B->d_B, k, R->d_perm, R->d_off, R->d_Mq, n_q, n_split, Gpart, spart,
                                       ctx->stream));
   XPCS_LAUNCH(ctx, "ring_factors_reduce", 1, launch_ring_factors_reduce(Gpart, spart, n_split, n_q, k, B->d_G, B->d_s, B->d_G32, ctx->stream));
-  XPCS_LAUNCH(ctx, "basis_pack", 1, launch_basis_pack(B->d_B, R->M, B->M_pad, k, B->kp, B->d_Bcat, ctx->stream));
+  // power-of-two scale of the f16 encode operand: max|V| 2^s in [2^14, 2^15)
+  double* mx = c.take<double>(256);
+  XPCS_LAUNCH(ctx, "basis_absmax", 1, launch_basis_absmax(B->d_B, (long long)R->M * k, mx, ctx->stream));
+  std::vector<double> hmx(256);
+  XPCS_CUDA(ctx, cudaMemcpyAsync(hmx.data(), mx, 256 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const double amax = *std::max_element(hmx.begin(), hmx.end());
+  B->enc_log2 = amax > 0 ? 14 - (int)std::floor(std::log2(amax)) : 0;
+  XPCS_LAUNCH(ctx, "basis_pack", 1,
+              launch_basis_pack(B->d_B, R->M, B->M_pad, k, B->kp, B->enc_log2, B->d_Bcat, ctx->stream));
   return XPCS_OK;
 }
 
@@ -731,8 +742,9 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   const int T_pad = nT * TILE;
   const int CH = CHUNK_TILES;
   const int maxC = (nT + CH - 1) / CH;
-  const int nseg = prec == XPCS_PREC_BF16X3 ? 3 : 1;
-  const int Kc = (nseg * k + KCH - 1) / KCH * KCH;
+  const bool split = prec == XPCS_PREC_BF16X3;
+  const int nkp = (k + KCH - 1) / KCH;           // 64-wide chunks per operand piece
+  const int Kc = (split ? 2 : 1) * nkp * KCH;
   const bool want_g2 = g2_out != nullptr;
   const bool want_cnt = want_g2 || count_out;
   const std::vector<int4> items = make_items(n_q, nT, CH);
@@ -764,7 +776,7 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   Carve c1{0, static_cast<char*>(ctx->scratch)};
   layout(c1);
   if (count_out) b.count = reinterpret_cast<long long*>(count_out);
-  std::vector<int> koff(n_q, 0), kch(n_q, Kc / KCH);
+  std::vector<int> koff(n_q, 0), kch(n_q, nkp);
   XPCS_CUDA(ctx, cudaMemcpyAsync(b.koff, koff.data(), n_q * 4, cudaMemcpyHostToDevice, ctx->stream));
   XPCS_CUDA(ctx, cudaMemcpyAsync(b.kch, kch.data(), n_q * 4, cudaMemcpyHostToDevice, ctx->stream));
   PrepParams pp{};
@@ -800,6 +812,7 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   gp.k_chunks = b.kch;
   gp.ring_rows = T_pad;
   gp.fmt = prec == XPCS_PREC_FP16 ? 0 : 1;
+  gp.split = split ? 1 : 0;
   gp.raw = 0;
   gp.r = b.r;
   gp.blk_bad = b.blk_bad;

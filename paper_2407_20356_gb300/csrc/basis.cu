@@ -9,7 +9,7 @@ namespace xpcs {
 namespace {
 
 // Gf[i][j] = N[i][j] / sqrt(N[i][i] N[j][j]): the Gram of the Frobenius-normalised frames
-// (Sec. 2.1) from the exact integer Gram (upper triangle valid).  Zero frames give zero
+// (Sec. 2.1) from the exact integer Gram (lower triangle valid).  Zero frames give zero
 // rows and columns, which only add zero eigenvalues.
 __global__ void gram_normalise_kernel(const long long* N, int n, double* Gf, double* nrm) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -17,7 +17,7 @@ __global__ void gram_normalise_kernel(const long long* N, int n, double* Gf, dou
   const int i = (int)(gid / n), j = (int)(gid % n);
   const int a = min(i, j), b = max(i, j);
   const double di = (double)N[(size_t)i * n + i], dj = (double)N[(size_t)j * n + j];
-  const double v = (double)N[(size_t)a * n + b];
+  const double v = (double)N[(size_t)b * n + a];
   Gf[gid] = (di > 0 && dj > 0) ? v / sqrt(di * dj) : 0.0;
   if (j == 0) nrm[i] = sqrt(di);
 }
@@ -177,11 +177,11 @@ __global__ void ring_factors_reduce_kernel(const double* Gpart, const double* sp
   }
 }
 
-// Bcat (2kp x M_pad, bf16, pixel-contiguous rows): rows 0..k-1 = hi(B^T), rows kp..kp+k-1 =
-// lo(B^T) = bf16(B - hi); padded pixels and rows stay zero.  Tiled transpose through
-// shared memory.
-__global__ void basis_pack_kernel(const double* B, long long M, long long M_pad, int k, int kp,
-                                  __nv_bfloat16* Bcat) {
+// Bcat (2kp x M_pad, f16, pixel-contiguous rows): rows 0..k-1 = hi = f16(V^T 2^s), rows
+// kp..kp+k-1 = lo = f16(V^T 2^s - hi); padded pixels and rows stay zero.  Tiled transpose
+// through shared memory.
+__global__ void basis_pack_kernel(const double* B, long long M, long long M_pad, int k, int kp, int log2_scale,
+                                  __half* Bcat) {
   __shared__ double tile[32][33];
   const long long p0 = (long long)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
@@ -189,20 +189,34 @@ __global__ void basis_pack_kernel(const double* B, long long M, long long M_pad,
   for (int yy = ty; yy < 32; yy += 8) {
     const long long p = p0 + yy;
     const int c = c0 + tx;
-    tile[yy][tx] = (p < M && c < k) ? B[(size_t)p * k + c] : 0.0;
+    tile[yy][tx] = (p < M && c < k) ? ldexp(B[(size_t)p * k + c], log2_scale) : 0.0;
   }
   __syncthreads();
   for (int yy = ty; yy < 32; yy += 8) {
     const int c = c0 + yy;
     const long long p = p0 + tx;
     if (c < k && p < M_pad) {
-      const float v = (float)tile[tx][yy];
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      const __nv_bfloat16 lo = __float2bfloat16_rn((float)((double)tile[tx][yy] - (double)__bfloat162float(hi)));
+      const double v = tile[tx][yy];
+      const __half hi = __double2half(v);
+      const __half lo = __double2half(v - (double)__half2float(hi));
       Bcat[(size_t)c * M_pad + p] = hi;
       Bcat[(size_t)(kp + c) * M_pad + p] = lo;
     }
   }
+}
+
+__global__ void absmax_kernel(const double* B, long long n, double* out) {
+  __shared__ double sm[256];
+  double m = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(B[i]));
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
 }
 
 }  // namespace
@@ -248,12 +262,17 @@ cudaError_t launch_ring_factors_reduce(const double* Gpart, const double* spart,
   return cudaGetLastError();
 }
 
-cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, int kp, __nv_bfloat16* Bcat,
-                              cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(Bcat, 0, (size_t)2 * kp * M_pad * sizeof(__nv_bfloat16), st);
+cudaError_t launch_basis_absmax(const double* B, long long n, double* out, cudaStream_t st) {
+  absmax_kernel<<<256, 256, 0, st>>>(B, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, int kp, int log2_scale,
+                              __half* Bcat, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(Bcat, 0, (size_t)2 * kp * M_pad * sizeof(__half), st);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((M_pad + 31) / 32), (k + 31) / 32);
-  basis_pack_kernel<<<grid, 256, 0, st>>>(B, M, M_pad, k, kp, Bcat);
+  basis_pack_kernel<<<grid, 256, 0, st>>>(B, M, M_pad, k, kp, log2_scale, Bcat);
   return cudaGetLastError();
 }
 

@@ -76,6 +76,16 @@ XPCS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
   }
 }
 
+// Warp-wide bounded wait: lane 0 polls, the warp then agrees on the outcome.  The
+// __syncwarp orders the other lanes after lane 0's acquire of the phase.
+XPCS_DEV bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint32_t* status) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, status);
+  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  __syncwarp();
+  return ok;
+}
+
 // ------------------------------------------------------------------ TMA (no multicast)
 
 XPCS_DEV void tma_prefetch_desc(const void* map) {

@@ -1,18 +1,24 @@
 // Encode: coefficients A = X V_K (Eq. 7) on the tcgen05 tensor cores, sm_103a.
 //
-// X (T x M counts, u8 or u16) streams from HBM once; V_K is held as Bcat, a 2kp x M bf16
-// matrix (kp = k rounded up to 16) whose rows 0..k-1 are hi(V_K^T) and rows kp..kp+k-1 are
-// lo(V_K^T) = bf16(V - hi), so one MMA with N = 2kp gives X hi and X lo in two halves of
-// the accumulator and the encode keeps ~16 bits of the basis.  Counts are exact in bf16
-// up to 256.
+// X (T x M counts, u8 or u16) streams from HBM once.  V_K is held as Bcat, a 2kp x M f16
+// matrix (kp = k rounded up to 16) scaled by 2^s (s chosen so max|V| 2^s < 2^15): rows
+// 0..k-1 hold hi = f16(V 2^s), rows kp..kp+k-1 hold lo = f16(V 2^s - hi).  One MMA with
+// N = 2kp gives X hi and X lo in two halves of the accumulator (about 22 bits of the
+// basis); the reduction adds them and multiplies by 2^-s, which is exact.
+// Counts become f16 without any conversion instruction: for v < 1024 the f16 with bits
+// 0x6400 | v is exactly 1024 + v, so one OR and one packed subtract give v.  Counts of
+// 1024 or more are flagged (XPCS_ERANGE).
 //
 // Work item = (frame block m of 128 frames, pixel split s).  Per 64-pixel chunk:
-//   warp 0      TMA: raw X tile (128 x 64, no swizzle) and the Bcat tile (2k x 64, SW128)
-//   warps 2..5  convert the raw tile to bf16 in the 128-byte-swizzled K-major layout
-//   warp 1      MMA into a 128 x 2k f32 TMEM accumulator (N <= 256 per instruction)
+//   warp 0      TMA: X tile (128 x 64) and the Bcat tile (2kp x 64, 128-byte swizzle)
+//   warps 2..5  convert X to f16: u16 tiles in place (loaded with the same swizzle the
+//               MMA reads, so the conversion is position-agnostic); u8 tiles into a
+//               separate swizzled buffer
+//   warp 1      MMA into a 128 x 2kp f32 TMEM accumulator (N <= 256 per instruction)
 // After the split's last chunk warps 2..5 drain TMEM, add the two halves and write the
 // split's partial coefficients; a second kernel sums the splits in a fixed order.
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "handles.h"
@@ -32,12 +38,11 @@ struct EncLayout {
     kp = (k_ + 15) / 16 * 16;  // lo half starts at column kp; N = 2 kp is a multiple of 32
     N = 2 * kp;
     nload = (N + 255) / 256;
-    raw_bytes = TILE * KCH * (dtype == 0 ? 1 : 2);
-    raw_bytes = (raw_bytes + 1023) / 1024 * 1024;
+    raw_bytes = dtype == 0 ? TILE * KCH : 0;  // u16 converts in place
     b_bytes = N * 128;
     stage_bytes = raw_bytes + b_bytes + CONV_BYTES;
     ns = (200 * 1024) / stage_bytes;
-    if (ns > 4) ns = 4;
+    if (ns > 8) ns = 8;
     tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
   }
   __host__ __device__ int smem() const { return 1024 + ns * stage_bytes + 256; }
@@ -50,13 +55,13 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const EncLayout lay(p.k, p.dtype);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.ns * lay.stage_bytes);
-  uint64_t* full = bars;               // [4] TMA landed (raw X + B)
-  uint64_t* empty = bars + 4;          // [4] MMA done with the stage
-  uint64_t* cfull = bars + 8;          // [4] conversion done
-  uint64_t* tfull = bars + 12;         // accumulator ready
-  uint64_t* tempty = bars + 13;        // accumulator drained
-  uint64_t* mma_done = bars + 14;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 15);
+  uint64_t* full = bars;               // [8] TMA landed (X + B)
+  uint64_t* empty = bars + 8;          // [8] MMA done with the stage
+  uint64_t* cfull = bars + 16;         // [8] conversion done
+  uint64_t* tfull = bars + 24;         // accumulator ready
+  uint64_t* tempty = bars + 25;        // accumulator drained
+  uint64_t* mma_done = bars + 26;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 27);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto raw_of = [&](int s) { return smem + s * lay.stage_bytes; };
   auto b_of = [&](int s) { return smem + s * lay.stage_bytes + lay.raw_bytes; };
@@ -106,7 +111,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           }
           const int x = (int)(px0 + (long long)c * KCH);
           mbar_arrive_expect_tx(&full[s], tx);
-          tma_load_2d(raw_of(s), &tmX, &full[s], x, m * TILE);
+          tma_load_2d(p.dtype == 0 ? raw_of(s) : conv_of(s), &tmX, &full[s], x, m * TILE);
           for (int l = 0; l < lay.nload; ++l)
             tma_load_2d(b_of(s) + l * (lay.N / lay.nload) * 128, &tmB, &full[s], x, l * (lay.N / lay.nload));
         }
@@ -119,7 +124,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     if (lane == 0) {
       const int nmma = (lay.N + 255) / 256;
       const int nper = lay.N / nmma;
-      const uint32_t idesc = idesc_f16(1, TILE, nper);
+      const uint32_t idesc = idesc_f16(0, TILE, nper);
       uint32_t it = 0, item_i = 0;
       bool ok = true, issued = false;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++item_i) {
@@ -160,7 +165,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     const int ct = threadIdx.x - 64;
     const int quarter = warp & 3;
     uint32_t it = 0, item_i = 0;
-    bool too_big = false;
+    uint32_t over = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++item_i) {
       const int m = item % n_m, sp = item / n_m;
       bool ok = true;
@@ -172,37 +177,41 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           ok = false;
           break;
         }
-        const uint8_t* raw = raw_of(s);
         uint8_t* conv = conv_of(s);
+        if (p.dtype == 1) {
+          // in place: 1024 16-byte chunks, 8 per thread
 #pragma unroll
-        for (int u8i = 0; u8i < 8; ++u8i) {
-          const int unit = u8i * 128 + ct;
-          const int row = unit >> 3, ch = unit & 7;
-          float f[8];
-          if (p.dtype == 1) {
-            const uint4 v = *reinterpret_cast<const uint4*>(raw + row * 128 + ch * 16);
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+          for (int u = 0; u < 8; ++u) {
+            uint4* ptr = reinterpret_cast<uint4*>(conv) + u * 128 + ct;
+            uint4 v = *ptr;
+            uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              f[2 * e] = (float)(w[e] & 0xFFFFu);
-              f[2 * e + 1] = (float)(w[e] >> 16);
+              over |= w[e] & 0xFC00FC00u;
+              __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&(w[e] |= 0x64006400u)),
+                                  __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+              w[e] = *reinterpret_cast<uint32_t*>(&h);
             }
-          } else {
+            *ptr = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        } else {
+          const uint8_t* raw = raw_of(s);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int unit = u * 128 + ct;
+            const int row = unit >> 3, ch = unit & 7;
             const uint2 v = *reinterpret_cast<const uint2*>(raw + row * 64 + ch * 8);
-            const uint32_t w[2] = {v.x, v.y};
+            uint32_t w[4] = {__byte_perm(v.x, 0, 0x4140), __byte_perm(v.x, 0, 0x4342), __byte_perm(v.y, 0, 0x4140),
+                             __byte_perm(v.y, 0, 0x4342)};
 #pragma unroll
-            for (int e = 0; e < 2; ++e)
-#pragma unroll
-              for (int b = 0; b < 4; ++b) f[4 * e + b] = (float)((w[e] >> (8 * b)) & 0xFFu);
+            for (int e = 0; e < 4; ++e) {
+              w[e] |= 0x64006400u;
+              __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&w[e]),
+                                  __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+              w[e] = *reinterpret_cast<uint32_t*>(&h);
+            }
+            *reinterpret_cast<uint4*>(conv + row * 128 + ((ch ^ (row & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
           }
-          uint32_t o[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            too_big |= (f[2 * e] > 256.f) | (f[2 * e + 1] > 256.f);
-            __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
-            o[e] = *reinterpret_cast<uint32_t*>(&b2);
-          }
-          *reinterpret_cast<uint4*>(conv + row * 128 + ((ch ^ (row & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
         }
         fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
         mbar_arrive(&cfull[s]);
@@ -229,7 +238,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty);
     }
-    if (too_big) set_status(p.status, XPCS_DEV_RANGE);
+    if (over) set_status(p.status, XPCS_DEV_RANGE);
   }
 
   tc_fence_before();
@@ -240,14 +249,15 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   }
 }
 
-__global__ void encode_reduce_kernel(const float* partials, int n_split, long long T, int T_pad, int k, float* A) {
+__global__ void encode_reduce_kernel(const float* partials, int n_split, long long T, int T_pad, int k, float scale,
+                                     float* A) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= T * k) return;
   const long long t = gid / k;
   const int j = (int)(gid % k);
   float a = 0.f;
   for (int s = 0; s < n_split; ++s) a += partials[((size_t)s * T_pad + t) * k + j];
-  A[gid] = a;
+  A[gid] = a * scale;
 }
 
 }  // namespace
@@ -264,10 +274,10 @@ cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float* A,
-                                 cudaStream_t st) {
+cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float scale,
+                                 float* A, cudaStream_t st) {
   const long long n = T * k;
-  encode_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, n_split, T, T_pad, k, A);
+  encode_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, n_split, T, T_pad, k, scale, A);
   return cudaGetLastError();
 }
 
@@ -317,9 +327,9 @@ extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const voi
   float* partials = c.take<float>((size_t)n_split * T_pad * k);
   CUtensorMap tmX, tmB;
   XPCS_TRY(make_map(ctx, &tmX, X, dtype == XPCS_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
-                    eb, M, T, KCH, TILE, CU_TENSOR_MAP_SWIZZLE_NONE));
+                    eb, M, T, KCH, TILE, dtype == XPCS_U8 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B));
   const int N = 2 * B->kp;
-  XPCS_TRY(make_map(ctx, &tmB, B->d_Bcat, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B->M_pad, N, KCH,
+  XPCS_TRY(make_map(ctx, &tmB, B->d_Bcat, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, B->M_pad, N, KCH,
                     N / ((N + 255) / 256), CU_TENSOR_MAP_SWIZZLE_128B));
   EncodeParams p{};
   p.T = T;
@@ -333,6 +343,7 @@ extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const voi
   p.status = ctx->d_status;
   const int n_items = nT * n_split;
   XPCS_LAUNCH(ctx, "encode", 1, launch_encode(tmX, tmB, p, std::min(n_items, ctx->num_sms), ctx->stream));
-  XPCS_LAUNCH(ctx, "encode_reduce", 1, launch_encode_reduce(partials, n_split, T, T_pad, k, A_out, ctx->stream));
+  XPCS_LAUNCH(ctx, "encode_reduce", 1,
+              launch_encode_reduce(partials, n_split, T, T_pad, k, std::ldexp(1.0f, -B->enc_log2), A_out, ctx->stream));
   return finish(ctx);
 }

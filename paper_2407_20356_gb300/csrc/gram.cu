@@ -17,10 +17,17 @@
 // Structure (one CTA per SM, persistent over work items):
 //   warp 0      TMA producer: 64-wide K chunks of the L and R row blocks, NSTAGE ring
 //   warp 1      TMEM allocator and MMA issuer: 128x128 f32 accumulator, 2 TMEM buffers
-//   warps 2..9  epilogue: TMEM -> registers -> skewed shared tile -> (C store, diagonal sums)
+//   warps 2..5  drain: TMEM -> registers -> C store
+//   warps 6..13 TMEM -> skewed shared tile -> diagonal sums
+// Any warp may read the TMEM lanes of its quarter (warp id mod 4), so both groups read
+// the accumulator independently; they meet only at the TMEM full/empty barriers, and the
+// C stores of one tile overlap the diagonal pass of another.
 //
 // Work item = (q, delta, I0, I1): the tiles (I, I+delta) for I in [I0, I1) of one tile
 // diagonal.  Its diagonal sums go to one partial slot; no atomics, deterministic.
+//
+// C store: C is symmetric, so tile (I, J >= I) is written transposed into the lower
+// triangle, straight from registers and fully coalesced.
 //
 // Skewed tile: element (i, j) of the tile is written to shared row i, column
 // 128 - i + j.  Column c then holds the tile diagonal j - i = c - 128 (c >= 128: upper
@@ -33,18 +40,57 @@ namespace xpcs {
 
 namespace {
 
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 3;
 constexpr int CHUNK_BYTES = TILE * KCH * 2;        // one operand chunk: 128 rows x 128 B
 constexpr int STAGE_BYTES = 2 * CHUNK_BYTES;       // L + R
 constexpr int SKEW_LD = 258;                       // floats per skewed row (257 = 1 mod 32)
 constexpr int SKEW_BYTES = TILE * SKEW_LD * 4;
-constexpr int N_EPI_WARPS = 8;
-constexpr int N_EPI_THREADS = 32 * N_EPI_WARPS;
-constexpr int GRAM_THREADS = 64 + N_EPI_THREADS;
+constexpr int N_DIAG_WARPS = 8;
+constexpr int GRAM_THREADS = 64 + 4 * 32 + N_DIAG_WARPS * 32;  // producer, MMA, 4 drain, 8 diagonal warps
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + SKEW_BYTES + BAR_BYTES;
 constexpr uint32_t TMEM_COLS = 256;                // two 128-column accumulators
-constexpr int EPI_BAR = 1;                         // named barrier id for the epilogue warps
+constexpr int DIAG_BAR = 1;                        // named barrier of the four diagonal warps
+
+// Stores one 32-column chunk of a tile row: element (i, j) of tile (I, J) is C(t1, t2)
+// with t1 = 128 I + i, t2 = 128 J + j, written transposed at [t2][t1] (lower triangle) so
+// that for a fixed j the warp's 32 lanes write 32 consecutive values.  Raw mode also
+// writes the exact integer Gram N and scales the accumulator by r(t1) r(t2).
+__device__ __forceinline__ void store_chunk(const GramParams& p, uint32_t (&v)[32], int q, int I, int J, int col0,
+                                            long long t1, float ri, const float* rq, bool bad, bool interior) {
+  const long long T = p.T;
+  const float* rj = rq + (size_t)J * TILE + col0;
+  const size_t obase = ((size_t)q * T + (size_t)J * TILE + col0) * T + (size_t)t1;
+  if (p.raw) {
+    if (p.Nout) {
+      if (interior) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) p.Nout[obase + (size_t)j * T] = (long long)__uint_as_float(v[j]);
+      } else if (t1 < T) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if ((long long)J * TILE + col0 + j < T) p.Nout[obase + (size_t)j * T] = (long long)__uint_as_float(v[j]);
+      }
+    }
+    if (!p.C) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + j));
+  }
+  if (interior) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) __stcs(p.C + obase + (size_t)j * T, __uint_as_float(v[j]));
+  } else if (t1 < T) {
+    const bool row_ok = ri > 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if ((long long)J * TILE + col0 + j < T) {
+        float val = __uint_as_float(v[j]);
+        if (bad && !(row_ok && __ldg(rj + j) > 0.f)) val = __int_as_float(0x7fc00000);
+        __stcs(p.C + obase + (size_t)j * T, val);
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(GRAM_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR,
@@ -72,7 +118,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], N_EPI_WARPS);
+      mbar_init(&tempty[b], p.partials ? 4 + N_DIAG_WARPS : 4);  // drain (+ diagonal) warps
     }
     mbar_init(mma_done, 1);
     mbar_fence_init();
@@ -99,21 +145,24 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
         const int4 w = p.items[item];
         const int q = w.x, delta = w.y;
         const int nk = p.k_chunks[q];
+        const int nc = p.split ? 2 * nk : nk;  // chunks per tile
         const int koff = p.k_off[q];
         const int rowbase = q * p.ring_rows;
         for (int I = w.z; I < w.w && ok; ++I) {
           const int J = I + delta;
-          for (int c = 0; c < nk; ++c, ++it) {
+          for (int c = 0; c < nc; ++c, ++it) {
             const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
             if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, p.status)) {
               *abort_flag = 1;
               ok = false;
               break;
             }
+            // split: chunk 2 kc holds the hi pieces of K-block kc, chunk 2 kc + 1 the lo pieces
+            const int x = koff + (p.split ? ((c & 1) * nk + (c >> 1)) * KCH : c * KCH);
             uint8_t* st = stages + s * STAGE_BYTES;
             mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-            tma_load_2d(st, &tmL, &full[s], koff + c * KCH, rowbase + I * TILE);
-            tma_load_2d(st + CHUNK_BYTES, &tmR, &full[s], koff + c * KCH, rowbase + J * TILE);
+            tma_load_2d(st, &tmL, &full[s], x, rowbase + I * TILE);
+            tma_load_2d(st + CHUNK_BYTES, &tmR, &full[s], x, rowbase + J * TILE);
           }
         }
       }
@@ -131,6 +180,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const int4 w = p.items[item];
         const int nk = p.k_chunks[w.x];
+        const int nc = p.split ? 2 * nk : nk;
         for (int I = w.z; I < w.w && ok; ++I, ++tile) {
           const uint32_t b = tile & 1, tph = (tile >> 1) & 1;
           if (*abort_flag || !mbar_wait(&tempty[b], tph ^ 1, p.status)) {
@@ -140,7 +190,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           }
           tc_fence_after();
           const uint32_t d = tmem_base + b * TILE;
-          for (int c = 0; c < nk; ++c, ++it) {
+          for (int c = 0; c < nc; ++c, ++it) {
             const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
             if (*abort_flag || !mbar_wait(&full[s], ph, p.status)) {
               *abort_flag = 1;
@@ -151,11 +201,31 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
             const uint8_t* st = stages + s * STAGE_BYTES;
             const uint64_t ad = smem_desc_sw128(st);
             const uint64_t bd = smem_desc_sw128(st + CHUNK_BYTES);
+            if (!p.split) {
 #pragma unroll
-            for (int kk = 0; kk < KCH / 16; ++kk)  // 16 elements = 32 B per MMA
-              tc_mma_f16(d, ad + 2 * kk, bd + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              for (int kk = 0; kk < KCH / 16; ++kk)  // 16 elements = 32 B per MMA
+                tc_mma_f16(d, ad + 2 * kk, bd + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              tc_commit(&empty[s]);
+            } else if ((c & 1) == 0) {
+              // hi pieces: L_hi R_hi now; the stage stays until the lo pieces arrive
+#pragma unroll
+              for (int kk = 0; kk < KCH / 16; ++kk)
+                tc_mma_f16(d, ad + 2 * kk, bd + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            } else {
+              // lo pieces: L_lo R_hi and L_hi R_lo with the previous stage's hi pieces
+              const uint32_t sp = (it - 1) % NSTAGE;
+              const uint8_t* sth = stages + sp * STAGE_BYTES;
+              const uint64_t adh = smem_desc_sw128(sth);
+              const uint64_t bdh = smem_desc_sw128(sth + CHUNK_BYTES);
+#pragma unroll
+              for (int kk = 0; kk < KCH / 16; ++kk) {
+                tc_mma_f16(d, ad + 2 * kk, bdh + 2 * kk, idesc, 1u);
+                tc_mma_f16(d, adh + 2 * kk, bd + 2 * kk, idesc, 1u);
+              }
+              tc_commit(&empty[sp]);
+              tc_commit(&empty[s]);
+            }
             issued = true;
-            tc_commit(&empty[s]);
           }
           if (!ok) break;
           tc_commit(&tfull[b]);
@@ -167,104 +237,160 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       }
     }
     __syncwarp();
-  } else {
-    // ------------------------------------------------------------ epilogue
-    const int ew = warp - 2;              // 0..7
-    const int quarter = warp & 3;         // TMEM lane quarter this warp may access
-    const int h = ew >> 2;                // column half of the tile
-    const int e = ew * 32 + lane;         // skew column owned in the diagonal pass
-    const int i_row = quarter * 32 + lane;  // tile row owned when draining TMEM
-    const int dlo = (ew >= 4) ? 0 : 97 - 32 * ew;
-    const int dhi = (ew >= 4) ? 256 - 32 * ew : TILE;
+  } else if (warp < 6) {
+    // ------------------------------------------------------------ drain warps (2..5)
+    // One warp per TMEM lane quarter: thread = tile row i.  TMEM -> registers -> C store,
+    // transposed into the lower triangle: for a fixed column j the warp's 32 lanes write
+    // 32 consecutive floats of output row t2.
+    const int quarter = warp & 3;
+    const int i_row = quarter * 32 + lane;
     const long long T = p.T;
+    const bool work = p.C || p.Nout;
     uint32_t tile = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
       const int4 w = p.items[item];
       const int q = w.x, delta = w.y;
       const float* rq = p.r + (size_t)q * p.T_pad;
-      float acc = 0.f;
       for (int I = w.z; I < w.w; ++I, ++tile) {
         const int J = I + delta;
         const uint32_t b = tile & 1, tph = (tile >> 1) & 1;
-        if (!mbar_wait(&tfull[b], tph, p.status)) *abort_flag = 1;
-        named_bar_sync(EPI_BAR, N_EPI_THREADS);
-        if (*abort_flag) {
+        // per-tile metadata first, so its load latency overlaps the wait for the MMA
+        const long long t1 = (long long)I * TILE + i_row;
+        const float ri = rq[t1];
+        const bool bad = p.blk_bad[(size_t)q * p.nT + I] | p.blk_bad[(size_t)q * p.nT + J];
+        const bool interior = !bad && (long long)(I + 1) * TILE <= T && (long long)(J + 1) * TILE <= T;
+        if (!mbar_wait_warp(&tfull[b], tph, p.status)) {  // warp-uniform outcome
+          *abort_flag = 1;
           ok = false;
           break;
         }
         tc_fence_after();
-        const long long t1 = (long long)I * TILE + i_row;
-        const float ri = p.raw ? rq[t1] : 1.f;
-        float* dst_row = skew + i_row * SKEW_LD + TILE - i_row;
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int col0 = 64 * h + 32 * cc;
-          uint32_t v[32];
-          tmem_ld32(tmem_base + b * TILE + ((uint32_t)(quarter * 32) << 16) + col0, v);
-          tc_wait_ld();
-          if (p.raw) {
-            const float* rj = rq + (size_t)J * TILE + col0;
-            if (p.Nout && t1 < T) {
-              long long* nrow = p.Nout + ((size_t)q * T + t1) * T + (size_t)J * TILE + col0;
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if ((long long)J * TILE + col0 + j < T) nrow[j] = (long long)__uint_as_float(v[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) dst_row[col0 + j] = (__uint_as_float(v[j]) * ri) * __ldg(rj + j);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) dst_row[col0 + j] = __uint_as_float(v[j]);
+        if (work) {
+          const uint32_t tbase = tmem_base + b * TILE + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+          for (int cc = 0; cc < 4; cc += 2) {
+            uint32_t v0[32], v1[32];
+            tmem_ld32(tbase + 32 * cc, v0);
+            tmem_ld32(tbase + 32 * cc + 32, v1);
+            tc_wait_ld();
+            store_chunk(p, v0, q, I, J, 32 * cc, t1, ri, rq, bad, interior);
+            store_chunk(p, v1, q, I, J, 32 * cc + 32, t1, ri, rq, bad, interior);
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
-        named_bar_sync(EPI_BAR, N_EPI_THREADS);
-
-        // diagonal sums of this tile: column e over the warp's row range
-        {
-          float s0 = 0.f, s1 = 0.f;
-          const float* col = skew + e;
-          int i = dlo;
-          for (; i + 1 < dhi; i += 2) {
-            s0 += col[i * SKEW_LD];
-            s1 += col[(i + 1) * SKEW_LD];
-          }
-          if (i < dhi) s0 += col[i * SKEW_LD];
-          acc += s0 + s1;
+      }
+    }
+  } else if (p.partials) {
+    // ------------------------------------------------------------ diagonal warps (6..13)
+    // Warps dw and dw + 4 share a TMEM lane quarter (warp id mod 4): each copies half of the
+    // quarter's 32 tile rows' columns into the skewed shared tile.  After the eight warps
+    // meet, warp dw reduces skew columns 32 g + lane (lower diagonals, rows
+    // [97 - 32 g, 128)) and 128 + 32 g + lane (upper diagonals, rows [0, 128 - 32 g)),
+    // g = dw mod 4, over every other row starting at dw / 4: together 159 rows per g.
+    // Cells outside a row's band are never written and stay zero, so the warp-uniform
+    // row ranges give exact diagonal sums.
+    const int dw = warp - 6;              // 0..7
+    const int quarter = warp & 3;
+    const int half = dw >> 2;             // column half copied, row parity reduced
+    const int i_row = quarter * 32 + lane;
+    const int g = dw & 3;
+    const float* col_lo = skew + 32 * g + lane;
+    const float* col_hi = skew + TILE + 32 * g + lane;
+    float* dst_row = skew + i_row * SKEW_LD + TILE - i_row + 64 * half;
+    const int lo0 = 97 - 32 * g + half;
+    const int hi1 = TILE - 32 * g;
+    uint32_t tile = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      const int4 w = p.items[item];
+      const int q = w.x, delta = w.y;
+      const float* rq = p.r + (size_t)q * p.T_pad;
+      float acc_lo = 0.f, acc_hi = 0.f;
+      for (int I = w.z; I < w.w; ++I, ++tile) {
+        const int J = I + delta;
+        const uint32_t b = tile & 1, tph = (tile >> 1) & 1;
+        const float ri = p.raw ? rq[(size_t)I * TILE + i_row] : 1.f;
+        const bool okw = mbar_wait_warp(&tfull[b], tph, p.status);
+        if (!okw) *abort_flag = 1;
+        named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);  // skew buffer free (previous tile reduced)
+        if (*abort_flag) {
+          ok = false;
+          break;
         }
-
-        // C store: rows of the tile, coalesced along t2, NaN for undefined pairs
-        if (p.C) {
-          const bool bad = p.blk_bad[(size_t)q * p.nT + I] | p.blk_bad[(size_t)q * p.nT + J];
-          for (int rr = 0; rr < TILE / N_EPI_WARPS; ++rr) {
-            const int i = ew * (TILE / N_EPI_WARPS) + rr;
-            const long long tt1 = (long long)I * TILE + i;
-            if (tt1 >= T) break;
-            const float* src = skew + i * SKEW_LD + TILE - i;
-            float* crow = p.C + ((size_t)q * T + tt1) * T + (size_t)J * TILE;
-            const bool row_ok = !bad || rq[tt1] > 0.f;
+        tc_fence_after();
+        {
+          const uint32_t tbase = tmem_base + b * TILE + ((uint32_t)(quarter * 32) << 16) + 64 * half;
+          uint32_t v0[32], v1[32];
+          tmem_ld32(tbase, v0);
+          tmem_ld32(tbase + 32, v1);
+          tc_wait_ld();
+          if (p.raw) {
+            const float* rj = rq + (size_t)J * TILE + 64 * half;
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              const int j = lane + 32 * m;
-              const long long tt2 = (long long)J * TILE + j;
-              if (tt2 < T) {
-                float val = src[j];
-                if (bad && !(row_ok && rq[tt2] > 0.f)) val = __int_as_float(0x7fc00000);
-                __stcs(crow + j, val);
-              }
+            for (int j = 0; j < 32; ++j) {
+              v0[j] = __float_as_uint((__uint_as_float(v0[j]) * ri) * __ldg(rj + j));
+              v1[j] = __float_as_uint((__uint_as_float(v1[j]) * ri) * __ldg(rj + 32 + j));
             }
           }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            dst_row[j] = __uint_as_float(v0[j]);
+            dst_row[32 + j] = __uint_as_float(v1[j]);
+          }
         }
-        named_bar_sync(EPI_BAR, N_EPI_THREADS);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+        named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);  // skew buffer complete
+        float sl[8], sh[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sl[u] = sh[u] = 0.f;
+        int i = lo0;
+        for (; i + 14 < TILE; i += 16) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sl[u] += col_lo[(i + 2 * u) * SKEW_LD];
+        }
+        for (; i < TILE; i += 2) sl[0] += col_lo[i * SKEW_LD];
+        for (i = half; i + 14 < hi1; i += 16) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sh[u] += col_hi[(i + 2 * u) * SKEW_LD];
+        }
+        for (; i < hi1; i += 2) sh[0] += col_hi[i * SKEW_LD];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) {
+          sl[0] += sl[u];
+          sh[0] += sh[u];
+        }
+        acc_lo += sl[0];
+        acc_hi += sh[0];
       }
       if (!ok) break;
-      if (p.partials) {
-        const int chunk = w.z / p.CH;
-        p.partials[(((size_t)q * p.nT + delta) * p.maxC + chunk) * DIAG_SLOTS + e] = acc;
+      // combine the two row parities of each column group through the (free) skew buffer
+      // cells of row 0 outside its band, then restore them to zero
+      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
+      float* red = skew;  // row 0, columns 0..127 lie outside row 0's band [128, 256)
+      if (half) {
+        red[32 * g + lane] = acc_lo;
       }
+      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
+      if (!half) acc_lo += red[32 * g + lane];
+      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
+      if (half) {
+        red[32 * g + lane] = acc_hi;
+      }
+      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
+      if (!half) {
+        acc_hi += red[32 * g + lane];
+        const int chunk = w.z / p.CH;
+        float* slot = p.partials + (((size_t)q * p.nT + delta) * p.maxC + chunk) * DIAG_SLOTS;
+        slot[32 * g + lane] = acc_lo;
+        slot[TILE + 32 * g + lane] = acc_hi;
+      }
+      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
+      if (half) red[32 * g + lane] = 0.f;
     }
   }
 

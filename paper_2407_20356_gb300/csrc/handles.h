@@ -61,7 +61,8 @@ struct xpcs_basis {
   double* d_G = nullptr;          // n_q x k x k
   double* d_s = nullptr;          // n_q x k
   float* d_G32 = nullptr;         // n_q x k x k
-  __nv_bfloat16* d_Bcat = nullptr;  // 2kp x M_pad
+  __half* d_Bcat = nullptr;       // 2kp x M_pad: f16 hi/lo of V^T 2^enc_log2
+  int enc_log2 = 0;
   size_t bytes = 0;
 };
 

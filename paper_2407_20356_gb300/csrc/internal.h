@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <string>
@@ -38,6 +39,8 @@ struct GramParams {
   const int* k_chunks;     // per ring: number of 64-wide K chunks, >= 1
   int ring_rows;           // operand row offset between rings (0 when rings share rows)
   int fmt;                 // 0 = f16, 1 = bf16
+  int split;               // 1: operand rows are [hi | lo] pieces of k_chunks chunks each;
+                           //    C = L_hi R_hi + L_lo R_hi + L_hi R_lo
   int raw;                 // 1: C = acc * r(t1) * r(t2); 0: operands already scaled
   const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined
   const uint8_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
@@ -118,8 +121,8 @@ struct EncodeParams {
 cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const EncodeParams& p, int grid,
                           cudaStream_t st);
 int encode_smem_bytes(int k);
-cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float* A,
-                                 cudaStream_t st);
+cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float scale,
+                                 float* A, cudaStream_t st);
 
 // ------------------------------------------------------------------ basis
 
@@ -133,7 +136,8 @@ cudaError_t launch_ring_factors2(const double* B, int k, const int* perm, const 
                                  int n_q, int n_split, double* Gpart, double* spart, cudaStream_t st);
 cudaError_t launch_ring_factors_reduce(const double* Gpart, const double* spart, int n_chunks, int n_q, int k,
                                        double* G, double* s, float* G32, cudaStream_t st);
-cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, int kp, __nv_bfloat16* Bcat,
-                              cudaStream_t st);
+cudaError_t launch_basis_absmax(const double* B, long long n, double* out, cudaStream_t st);
+cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, int kp, int log2_scale,
+                              __half* Bcat, cudaStream_t st);
 
 }  // namespace xpcs

@@ -13,12 +13,16 @@ constexpr int MAX_RINGS_SMEM = 1024;
 
 // ---------------------------------------------------------------- raw ingest (ring sums)
 // One CTA per (padded) frame.  Gathers the frame's pixels into ring-sorted order as bf16
-// (exact for counts <= 256), accumulates S_q(t) = sum of counts and sum of squares per
-// ring (Eq. 1 denominators and the exactness bound of the f32 Gram).
-__global__ void raw_ingest_kernel(const RawIngestParams p) {
+// (exact for counts <= 256) and accumulates S_q(t) = sum of counts and the sum of squares
+// per ring (Eq. 1 denominators and the exactness bound of the f32 Gram).
+// Each warp step covers 64 consecutive sorted positions (2 per lane).  Ring segments
+// start at multiples of 64, so those 64 positions belong to one ring (or its padding):
+// the warp reduces its counts with shuffles and issues one shared atomic per step.
+__global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p) {
   __shared__ unsigned long long ssum[MAX_RINGS_SMEM];
   __shared__ unsigned long long ssq[MAX_RINGS_SMEM];
   const long long t = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int q = threadIdx.x; q < p.n_q; q += blockDim.x) {
     ssum[q] = 0;
     ssq[q] = 0;
@@ -26,19 +30,34 @@ __global__ void raw_ingest_kernel(const RawIngestParams p) {
   __syncthreads();
   const bool live = t < p.T;
   bool too_big = false;
-  for (long long o = threadIdx.x; o < p.Mp; o += blockDim.x) {
-    unsigned x = 0;
-    const int src = p.perm[o];
-    if (live && src >= 0) {
-      x = p.dtype == 0 ? (unsigned)static_cast<const uint8_t*>(p.X)[t * p.M + src]
-                       : (unsigned)static_cast<const uint16_t*>(p.X)[t * p.M + src];
+  const uint8_t* x8 = static_cast<const uint8_t*>(p.X) + t * p.M;
+  const uint16_t* x16 = static_cast<const uint16_t*>(p.X) + t * p.M;
+  for (long long base = (long long)warp * 64; base < p.Mp; base += 64 * 8) {
+    const long long o = base + 2 * lane;
+    const int2 src = *reinterpret_cast<const int2*>(p.perm + o);
+    unsigned x0 = 0, x1 = 0;
+    if (live) {
+      if (src.x >= 0) x0 = p.dtype == 0 ? (unsigned)x8[src.x] : (unsigned)x16[src.x];
+      if (src.y >= 0) x1 = p.dtype == 0 ? (unsigned)x8[src.y] : (unsigned)x16[src.y];
     }
-    if (x > 256u) too_big = true;
-    if (p.Xp) p.Xp[t * p.Mp + o] = __float2bfloat16_rn((float)x);
-    if (x) {
-      const int q = p.pos_ring[o];
-      atomicAdd(&ssum[q], (unsigned long long)x);
-      atomicAdd(&ssq[q], (unsigned long long)x * x);
+    const bool big = (x0 > 256u) | (x1 > 256u);
+    too_big |= big;
+    if (p.Xp) {
+      __nv_bfloat162 v = __floats2bfloat162_rn((float)x0, (float)x1);
+      *reinterpret_cast<__nv_bfloat162*>(p.Xp + t * p.Mp + o) = v;
+    }
+    const int q = __reduce_max_sync(0xffffffffu, max(p.pos_ring[o], p.pos_ring[o + 1]));
+    if (q < 0) continue;
+    if (!__any_sync(0xffffffffu, big)) {
+      const unsigned s = __reduce_add_sync(0xffffffffu, x0 + x1);
+      const unsigned s2 = __reduce_add_sync(0xffffffffu, x0 * x0 + x1 * x1);
+      if (lane == 0 && s) {
+        atomicAdd(&ssum[q], (unsigned long long)s);
+        atomicAdd(&ssq[q], (unsigned long long)s2);
+      }
+    } else if (x0 | x1) {
+      atomicAdd(&ssum[q], (unsigned long long)x0 + x1);
+      atomicAdd(&ssq[q], (unsigned long long)x0 * x0 + (unsigned long long)x1 * x1);
     }
   }
   if (too_big && p.Xp) set_status(p.status, XPCS_DEV_RANGE);
@@ -106,15 +125,17 @@ constexpr int PREP_FRAMES = 64;
 constexpr int PREP_COLS = 32;
 
 // Operand rows for one ring and 64 frames: L = r * (a G_q), R = r * a, in the requested
-// 16-bit format.  BF16X3 stores [hi | hi | lo] for L and [hi | lo | hi] for R so one
-// K-concatenated product gives hi*hi + hi*lo + lo*hi.
+// 16-bit format.  BF16X3 stores [hi | lo] pieces (each padded to a multiple of 64) for
+// both, and the two-time kernel forms hi*hi + lo*hi + hi*lo.  W = a G_q is formed in shared
+// memory (f32 FMA), then whole rows are written with coalesced 16-byte stores.
 template <typename T16, bool SPLIT>
 __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) {
   extern __shared__ float sm[];
   const int k = p.k;
   const int lda = k + 1;
-  float* As = sm;                          // [64][k+1]
-  float* Gs = sm + PREP_FRAMES * lda;      // [k][32]
+  float* As = sm;                          // [64][k+1]  r * a
+  float* Ws = As + PREP_FRAMES * lda;      // [64][k+1]  r * a G_q
+  float* Gs = Ws + PREP_FRAMES * lda;      // [k][32]
   const int q = blockIdx.y;
   const long long t0 = (long long)blockIdx.x * PREP_FRAMES;
   const float* rq = p.r + (size_t)q * p.T_pad;
@@ -123,12 +144,9 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
     const long long t = t0 + f;
     As[f * lda + c] = (t < p.T) ? p.A[t * k + c] * rq[t] : 0.f;
   }
-  T16* L = static_cast<T16*>(p.L) + ((size_t)q * p.T_pad + t0) * p.Kc;
-  T16* R = static_cast<T16*>(p.R) + ((size_t)q * p.T_pad + t0) * p.Kc;
   const int f = threadIdx.x % PREP_FRAMES;
   const int g = threadIdx.x / PREP_FRAMES;  // 0..3 -> 8 columns each
   const float* Gq = p.G32 + (size_t)q * k * k;
-  const int nseg = SPLIT ? 3 : 1;
   for (int j0 = 0; j0 < k; j0 += PREP_COLS) {
     const int nc = min(PREP_COLS, k - j0);
     __syncthreads();
@@ -148,38 +166,39 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
       for (int u = 0; u < 8; ++u) w[u] = fmaf(a, gr[u], w[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int j = j0 + 8 * g + u;
-      if (8 * g + u >= nc) break;
-      const float av = arow[j];
-      T16* lrow = L + (size_t)f * p.Kc;
-      T16* rrow = R + (size_t)f * p.Kc;
-      if (!SPLIT) {
-        lrow[j] = to16<T16>(w[u]);
-        rrow[j] = to16<T16>(av);
-      } else {
-        const T16 wh = to16<T16>(w[u]);
-        const T16 wl = to16<T16>(w[u] - (float)wh);
-        const T16 ah = to16<T16>(av);
-        const T16 al = to16<T16>(av - (float)ah);
-        lrow[j] = wh;
-        lrow[k + j] = wh;
-        lrow[2 * k + j] = wl;
-        rrow[j] = ah;
-        rrow[k + j] = al;
-        rrow[2 * k + j] = ah;
-      }
-    }
+    for (int u = 0; u < 8; ++u)
+      if (8 * g + u < nc) Ws[f * lda + j0 + 8 * g + u] = w[u];
   }
-  // zero the K padding
-  const int used = nseg * k;
-  const int pad = p.Kc - used;
-  if (pad > 0) {
-    for (int i = threadIdx.x; i < PREP_FRAMES * pad; i += blockDim.x) {
-      const int ff = i / pad, c = used + i % pad;
-      L[(size_t)ff * p.Kc + c] = to16<T16>(0.f);
-      R[(size_t)ff * p.Kc + c] = to16<T16>(0.f);
+  __syncthreads();
+  const int nvec = p.Kc / 8;
+  const int piece = SPLIT ? p.Kc / 2 : p.Kc;  // split rows are [hi | lo], each `piece` wide
+  uint4* L = reinterpret_cast<uint4*>(static_cast<T16*>(p.L) + ((size_t)q * p.T_pad + t0) * p.Kc);
+  uint4* R = reinterpret_cast<uint4*>(static_cast<T16*>(p.R) + ((size_t)q * p.T_pad + t0) * p.Kc);
+  for (int v = threadIdx.x; v < PREP_FRAMES * nvec; v += blockDim.x) {
+    const int ff = v / nvec, c0 = (v % nvec) * 8;
+    alignas(16) T16 lv[8];
+    alignas(16) T16 rv[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int col = c0 + e;
+      const int seg = col / piece, j = col - seg * piece;
+      float wl = 0.f, ar = 0.f;
+      if (j < k) {
+        const float wv = Ws[ff * lda + j], av = As[ff * lda + j];
+        if (!SPLIT) {
+          wl = wv;
+          ar = av;
+        } else {
+          const float wh = (float)to16<T16>(wv), ah = (float)to16<T16>(av);
+          wl = seg == 0 ? wh : wv - wh;
+          ar = seg == 0 ? ah : av - ah;
+        }
+      }
+      lv[e] = to16<T16>(wl);
+      rv[e] = to16<T16>(ar);
     }
+    L[(size_t)ff * nvec + (v % nvec)] = *reinterpret_cast<const uint4*>(lv);
+    R[(size_t)ff * nvec + (v % nvec)] = *reinterpret_cast<const uint4*>(rv);
   }
 }
 
@@ -238,9 +257,10 @@ __global__ void g2_finalize_kernel(const float* partials, const long long* count
 }
 
 // ---------------------------------------------------------------- g2 over a stored C
+// C holds the lower triangle: C[s][s - tau] = C(s - tau, s) for tau >= 0.
 // Grid (lag blocks of 128, rings, row splits); 8 warps.  Lane l of every warp owns lags
-// L0 + l + 32 m (m = 0..3); the warp walks rows t, reading C[t][t + lag] as 128-byte
-// coalesced segments.  Undefined (NaN) entries are skipped and counted out.
+// L0 + l + 32 m (m = 0..3); the warp walks rows s, reading C[s][s - L0 - 127 .. s - L0]
+// as 128-byte coalesced segments.  Undefined (NaN) entries are skipped and counted out.
 constexpr int G2C_WARPS = 8;
 __global__ void __launch_bounds__(256) g2_from_C_kernel(const float* __restrict__ C, int n_q, long long T,
                                                         double* partial, long long* cnt_partial, int row_splits) {
@@ -251,19 +271,19 @@ __global__ void __launch_bounds__(256) g2_from_C_kernel(const float* __restrict_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long nrows = T - L0;
   const long long per = (nrows + row_splits - 1) / row_splits;
-  const long long r0 = (long long)split * per;
-  const long long r1 = min(nrows, r0 + per);
+  const long long r0 = L0 + (long long)split * per;
+  const long long r1 = min(T, r0 + per);
   float s[4] = {0.f, 0.f, 0.f, 0.f};
   int c[4] = {0, 0, 0, 0};
   const float* Cq = C + (size_t)q * T * T;
-  for (long long t = r0 + warp; t < r1; t += G2C_WARPS) {
-    const float* row = Cq + (size_t)t * T + t + L0;
-    const long long lim = T - t - L0;
+  for (long long row = r0 + warp; row < r1; row += G2C_WARPS) {
+    const float* p = Cq + (size_t)row * T + (row - L0);  // element of lag L0
+    const long long lim = row - L0;                      // lags L0 + l with l <= lim
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int l = lane + 32 * m;
-      if (l < lim) {
-        const float v = __ldcs(row + l);
+      if (l <= lim) {
+        const float v = __ldcs(p - l);
         if (v == v) {
           s[m] += v;
           c[m] += 1;
@@ -327,7 +347,7 @@ cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st) {
   comp_scales_kernel<<<dim3(p.nT, p.n_q), TILE, 0, st>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int smem = (PREP_FRAMES * (p.k + 1) + p.k * PREP_COLS) * (int)sizeof(float);
+  const int smem = (2 * PREP_FRAMES * (p.k + 1) + p.k * PREP_COLS) * (int)sizeof(float);
   const dim3 grid(p.T_pad / PREP_FRAMES, p.n_q);
 #define XPCS_PREP_LAUNCH(T16, SPLIT)                                                                  \
   do {                                                                                                \

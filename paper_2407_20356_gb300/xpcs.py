@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -103,17 +104,25 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget: int = 0, stream=None):
         h = vp()
+        self.h = None
+        self._children = weakref.WeakSet()
         st = _lib.xpcs_create(device, hbm_budget, stream, C.byref(h))
         if st != XPCS_OK:
             raise XpcsError(st, "xpcs_create failed")
         self.h = h
+
+    def _adopt(self, child):
+        self._children.add(child)
 
     def check(self, st):
         if st != XPCS_OK:
             raise XpcsError(st, _lib.xpcs_last_error(self.h).decode())
 
     def close(self):
+        """Destroy the context after every handle created on it (handles first)."""
         if self.h:
+            for ch in list(self._children):
+                ch.close()
             _lib.xpcs_destroy(self.h)
             self.h = None
 
@@ -155,6 +164,7 @@ class Rings:
         h = vp()
         ctx.check(_lib.xpcs_rings_create(ctx.h, _ptr(qmap), M, n_q, C.byref(h)))
         self.ctx, self.h, self.M, self.n_q = ctx, h, M, n_q
+        ctx._adopt(self)
 
     def sizes(self) -> np.ndarray:
         out = np.zeros(self.n_q, dtype=np.int64)
@@ -162,9 +172,9 @@ class Rings:
         return out
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             _lib.xpcs_rings_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -176,6 +186,7 @@ class Rings:
 class Basis:
     def __init__(self, ctx: Context, rings: Rings, h, k: int):
         self.ctx, self.rings, self.h, self.k = ctx, rings, h, k
+        ctx._adopt(self)
 
     def export(self):
         M, n_q, k = self.rings.M, self.rings.n_q, self.k
@@ -186,9 +197,9 @@ class Basis:
         return B, G, s
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             _lib.xpcs_basis_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

@@ -20,11 +20,11 @@ def rel_errors(got, ref):
     return float(d.max() / np.abs(ref[ok]).max()), float(np.sqrt((d ** 2).sum() / (ref[ok] ** 2).sum()))
 
 
-def upper(a):
-    """Upper triangle (t2 >= t1) of the last two axes as a flat array per leading index."""
+def lower(a):
+    """Lower triangle (t1 >= t2) of the last two axes as a flat array per leading index."""
     T = a.shape[-1]
-    iu = np.triu_indices(T)
-    return a[..., iu[0], iu[1]]
+    il = np.tril_indices(T)
+    return a[..., il[0], il[1]]
 
 
 def run_raw(X, ctx, frames, qmap, n_q, want_C=True, want_N=True):

@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 from synth import ring_qmap, speckle_counts
-from tests.gpu_util import rel_errors, torch_cuda, upper
+from tests.gpu_util import lower, rel_errors, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,7 @@ def run_compressed(X, ctx, B, A, qmap, n_q, prec, want_C=True):
 
 
 def _check(out, Cref, n_q, prec):
-    rm, rr = rel_errors(upper(out["C"]), upper(Cref))
+    rm, rr = rel_errors(lower(out["C"]), lower(Cref))
     assert rm < TOL[prec], (prec, rm, rr)
     for q in range(n_q):
         g_ref, c_ref = O.g2_from_twotime(Cref[q])
@@ -119,5 +119,5 @@ def test_compressed_undefined_frames(X, ctx):
     Cref, St = O.compressed_twotime(A, G, s, Mq)
     assert (St <= 0).any()
     out = run_compressed(X, ctx, B, A, qmap, n_q, "bf16x3")
-    np.testing.assert_array_equal(np.isnan(upper(out["C"])), np.isnan(upper(Cref)))
+    np.testing.assert_array_equal(np.isnan(lower(out["C"])), np.isnan(lower(Cref)))
     _check(out, Cref, n_q, "bf16x3")

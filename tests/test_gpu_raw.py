@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from synth import ring_qmap, speckle_counts
-from tests.gpu_util import run_raw, torch_cuda, upper
+from tests.gpu_util import lower, run_raw, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -29,8 +29,8 @@ def ctx(X):
 def _check_raw(X, ctx, frames, qmap, n_q):
     out = run_raw(X, ctx, frames, qmap, n_q)
     Cref, Nref, Sref, Mq = O.raw_twotime(frames, qmap, n_q)
-    assert np.array_equal(upper(out["N"]), upper(Nref)), "integer Gram not bit-exact"
-    Cu, Cr = upper(out["C"]), upper(Cref)
+    assert np.array_equal(lower(out["N"]), lower(Nref)), "integer Gram not bit-exact"
+    Cu, Cr = lower(out["C"]), lower(Cref)
     np.testing.assert_array_equal(np.isnan(Cu), np.isnan(Cr))
     ok = ~np.isnan(Cr)
     np.testing.assert_allclose(Cu[ok], Cr[ok], rtol=1e-6, atol=0)
@@ -113,7 +113,7 @@ def test_g2_over_stored_twotime(X, ctx):
     X.xpcs_g2(ctx, C, 3, 333, g2, cnt)
     for q in range(3):
         Cq = out["C"][q].astype(np.float64)
-        Cq = np.triu(Cq) + np.triu(Cq, 1).T  # the oracle reads a full matrix
+        Cq = np.tril(Cq) + np.tril(Cq, -1).T  # the oracle reads a full matrix
         g_ref, c_ref = O.g2_from_twotime(Cq)
         np.testing.assert_array_equal(cnt[q].cpu().numpy(), c_ref)
         g = g2[q].cpu().numpy()
