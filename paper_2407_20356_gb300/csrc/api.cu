@@ -143,6 +143,34 @@ std::vector<int4> make_items(int n_q, int nT, int CH) {
   return items;
 }
 
+// Device copy of the work items for (n_q, nT, CH), rebuilt only when they change.
+xpcs_status cached_items(xpcs_ctx* ctx, int n_q, int nT, int CH, int4** d_items, int* n_items) {
+  if (ctx->items_key[0] != n_q || ctx->items_key[1] != nT || ctx->items_key[2] != CH) {
+    const std::vector<int4> items = make_items(n_q, nT, CH);
+    const size_t bytes = items.size() * sizeof(int4);
+    if (bytes > ctx->items_bytes) {
+      XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      dev_free(ctx, ctx->d_items, ctx->items_bytes);
+      ctx->d_items = nullptr;
+      ctx->items_bytes = 0;
+      void* p = nullptr;
+      XPCS_TRY(dev_alloc(ctx, &p, bytes));
+      ctx->d_items = static_cast<int4*>(p);
+      ctx->items_bytes = bytes;
+    } else {
+      XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // earlier kernels may still read them
+    }
+    XPCS_CUDA(ctx, cudaMemcpy(ctx->d_items, items.data(), bytes, cudaMemcpyHostToDevice));
+    ctx->items_n = items.size();
+    ctx->items_key[0] = n_q;
+    ctx->items_key[1] = nT;
+    ctx->items_key[2] = CH;
+  }
+  *d_items = ctx->d_items;
+  *n_items = (int)ctx->items_n;
+  return XPCS_OK;
+}
+
 }  // namespace
 
 // ====================================================================== context
@@ -187,6 +215,7 @@ extern "C" xpcs_status xpcs_destroy(xpcs_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   dev_free(ctx, ctx->scratch, ctx->scratch_cap);
+  dev_free(ctx, ctx->d_items, ctx->items_bytes);
   dev_free(ctx, ctx->d_status, 256);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   xpcs_profile_enable(ctx, 0);
@@ -376,7 +405,7 @@ struct RawBuffers {
   long long* S;
   unsigned long long* sq;
   float* r;
-  uint8_t* blk_bad;
+  uint32_t* blk_bad;
   float* partials;
   uint32_t* vbits;
   long long* count;
@@ -441,12 +470,13 @@ namespace {
 
 // Shared tail of both two-time paths: the Gram launch, pair counts and g2.
 xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap& tmR, GramParams gp, int n_q,
-                        int64_t T, int T_pad, int nT, int maxC, const std::vector<int4>& items, int4* d_items,
-                        uint32_t* vbits, long long* count, double* g2_out) {
-  XPCS_CUDA(ctx, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
-                                 ctx->stream));
+                        int64_t T, int T_pad, int nT, int maxC, uint32_t* vbits, long long* count,
+                        double* g2_out) {
+  int4* d_items = nullptr;
+  int n_items = 0;
+  XPCS_TRY(cached_items(ctx, n_q, nT, gp.CH, &d_items, &n_items));
   gp.items = d_items;
-  gp.n_items = (int)items.size();
+  gp.n_items = n_items;
   const int grid = std::min<int>(gp.n_items, ctx->num_sms);
   XPCS_LAUNCH(ctx, "twotime_gram", 1, launch_gram(tmL, tmR, gp, grid, ctx->stream));
   if (count) {
@@ -472,17 +502,15 @@ extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, cons
   const int maxC = (nT + CH - 1) / CH;
   const bool want_g2 = g2_out != nullptr;
   const bool want_cnt = want_g2 || count_out;
-  const std::vector<int4> items = make_items(n_q, nT, CH);
   auto layout = [&](Carve& c, RawBuffers& b) {
     b.Xp = c.take<__nv_bfloat16>((size_t)T_pad * R->Mp);
     b.S = c.take<long long>((size_t)n_q * T);
     b.sq = c.take<unsigned long long>(n_q);
     b.r = c.take<float>((size_t)n_q * T_pad);
-    b.blk_bad = c.take<uint8_t>((size_t)n_q * nT);
+    b.blk_bad = c.take<uint32_t>((size_t)n_q * nT);
     b.partials = want_g2 ? c.take<float>((size_t)n_q * nT * maxC * DIAG_SLOTS) : nullptr;
     b.vbits = c.take<uint32_t>((size_t)n_q * (T_pad / 32));
     b.count = (want_cnt && !count_out) ? c.take<long long>((size_t)n_q * T) : nullptr;
-    b.items = c.take<int4>(items.size());
   };
   RawBuffers b{};
   Carve c0;
@@ -515,8 +543,7 @@ extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, cons
   gp.Nout = reinterpret_cast<long long*>(N_out);
   gp.partials = b.partials;
   gp.status = ctx->d_status;
-  XPCS_TRY(run_twotime(ctx, tm, tm, gp, n_q, T, T_pad, nT, maxC, items, b.items, b.vbits,
-                       want_cnt ? b.count : nullptr, g2_out));
+  XPCS_TRY(run_twotime(ctx, tm, tm, gp, n_q, T, T_pad, nT, maxC, b.vbits, want_cnt ? b.count : nullptr, g2_out));
   return finish(ctx);
 }
 
@@ -532,22 +559,36 @@ xpcs_status basis_alloc(xpcs_ctx* ctx, const xpcs_rings* R, int k, xpcs_basis** 
   B->kp = (k + 15) / 16 * 16;
   B->M_pad = (R->M + 63) / 64 * 64;
   const int n_q = R->n_q;
-  const size_t szs[5] = {(size_t)R->M * k * 8, (size_t)n_q * k * k * 8, (size_t)n_q * k * 8,
-                         (size_t)n_q * k * k * 4, (size_t)2 * B->kp * B->M_pad * 2};
-  void* p[5] = {};
+  const size_t szs[8] = {(size_t)R->M * k * 8, (size_t)n_q * k * k * 8, (size_t)n_q * k * 8,
+                         (size_t)n_q * k * k * 4, (size_t)2 * B->kp * B->M_pad * 2, (size_t)n_q * 4,
+                         (size_t)n_q * 4, (size_t)n_q * k * 8};
+  void* p[8] = {};
   xpcs_status s = XPCS_OK;
-  for (int i = 0; i < 5 && s == XPCS_OK; ++i) s = dev_alloc(ctx, &p[i], szs[i]);
+  for (int i = 0; i < 8 && s == XPCS_OK; ++i) s = dev_alloc(ctx, &p[i], szs[i]);
   if (s != XPCS_OK) {
-    for (int i = 0; i < 5; ++i) dev_free(ctx, p[i], szs[i]);
+    for (int i = 0; i < 8; ++i) dev_free(ctx, p[i], szs[i]);
     delete B;
     return s;
+  }
+  B->d_koff = (int*)p[5];
+  B->d_kch = (int*)p[6];
+  B->d_s32 = (float2*)p[7];
+  {
+    const std::vector<int> koff(n_q, 0), kch(n_q, (k + KCH - 1) / KCH);
+    cudaError_t e = cudaMemcpy(B->d_koff, koff.data(), szs[5], cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_kch, kch.data(), szs[6], cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      for (int i = 0; i < 8; ++i) dev_free(ctx, p[i], szs[i]);
+      delete B;
+      return fail(ctx, XPCS_ECUDA, std::string("basis metadata upload: ") + cudaGetErrorString(e));
+    }
   }
   B->d_B = (double*)p[0];
   B->d_G = (double*)p[1];
   B->d_s = (double*)p[2];
   B->d_G32 = (float*)p[3];
   B->d_Bcat = (__half*)p[4];
-  B->bytes = szs[0] + szs[1] + szs[2] + szs[3] + szs[4];
+  B->bytes = szs[0] + szs[1] + szs[2] + szs[3] + szs[4] + szs[5] + szs[6] + szs[7];
   *out = B;
   return XPCS_OK;
 }
@@ -569,7 +610,8 @@ xpcs_status basis_finish(xpcs_ctx* ctx, xpcs_basis* B) {
   double* spart = c.take<double>((size_t)n_q * n_split * k);
   XPCS_LAUNCH(ctx, "ring_factors", 1, launch_ring_factors2(B->d_B, k, R->d_perm, R->d_off, R->d_Mq, n_q, n_split, Gpart, spart,
                                       ctx->stream));
-  XPCS_LAUNCH(ctx, "ring_factors_reduce", 1, launch_ring_factors_reduce(Gpart, spart, n_split, n_q, k, B->d_G, B->d_s, B->d_G32, ctx->stream));
+  XPCS_LAUNCH(ctx, "ring_factors_reduce", 1, launch_ring_factors_reduce(Gpart, spart, n_split, n_q, k, B->d_G, B->d_s, B->d_G32, B->d_s32,
+                                                         ctx->stream));
   // power-of-two scale of the f16 encode operand: max|V| 2^s in [2^14, 2^15)
   double* mx = c.take<double>(256);
   XPCS_LAUNCH(ctx, "basis_absmax", 1, launch_basis_absmax(B->d_B, (long long)R->M * k, mx, ctx->stream));
@@ -635,6 +677,9 @@ extern "C" xpcs_status xpcs_basis_destroy(xpcs_basis* B) {
   dev_free(ctx, B->d_s, (size_t)n_q * k * 8);
   dev_free(ctx, B->d_G32, (size_t)n_q * k * k * 4);
   dev_free(ctx, B->d_Bcat, (size_t)2 * B->kp * B->M_pad * 2);
+  dev_free(ctx, B->d_koff, (size_t)n_q * 4);
+  dev_free(ctx, B->d_kch, (size_t)n_q * 4);
+  dev_free(ctx, B->d_s32, (size_t)n_q * k * 8);
   delete B;
   return XPCS_OK;
 }
@@ -747,28 +792,22 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   const int Kc = (split ? 2 : 1) * nkp * KCH;
   const bool want_g2 = g2_out != nullptr;
   const bool want_cnt = want_g2 || count_out;
-  const std::vector<int4> items = make_items(n_q, nT, CH);
   struct Bufs {
     uint16_t *L, *R;
     float* r;
-    uint8_t* blk_bad;
+    uint32_t* blk_bad;
     float* partials;
     uint32_t* vbits;
     long long* count;
-    int4* items;
-    int *koff, *kch;
   } b{};
   auto layout = [&](Carve& c) {
     b.L = c.take<uint16_t>((size_t)n_q * T_pad * Kc);
     b.R = c.take<uint16_t>((size_t)n_q * T_pad * Kc);
     b.r = c.take<float>((size_t)n_q * T_pad);
-    b.blk_bad = c.take<uint8_t>((size_t)n_q * nT);
+    b.blk_bad = c.take<uint32_t>((size_t)n_q * nT);
     b.partials = want_g2 ? c.take<float>((size_t)n_q * nT * maxC * DIAG_SLOTS) : nullptr;
     b.vbits = c.take<uint32_t>((size_t)n_q * (T_pad / 32));
     b.count = (want_cnt && !count_out) ? c.take<long long>((size_t)n_q * T) : nullptr;
-    b.items = c.take<int4>(items.size());
-    b.koff = c.take<int>(n_q);
-    b.kch = c.take<int>(n_q);
   };
   Carve c0;
   layout(c0);
@@ -776,9 +815,6 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   Carve c1{0, static_cast<char*>(ctx->scratch)};
   layout(c1);
   if (count_out) b.count = reinterpret_cast<long long*>(count_out);
-  std::vector<int> koff(n_q, 0), kch(n_q, nkp);
-  XPCS_CUDA(ctx, cudaMemcpyAsync(b.koff, koff.data(), n_q * 4, cudaMemcpyHostToDevice, ctx->stream));
-  XPCS_CUDA(ctx, cudaMemcpyAsync(b.kch, kch.data(), n_q * 4, cudaMemcpyHostToDevice, ctx->stream));
   PrepParams pp{};
   pp.A = A;
   pp.T = T;
@@ -788,6 +824,7 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   pp.nT = nT;
   pp.G32 = B->d_G32;
   pp.s64 = B->d_s;
+  pp.s32 = B->d_s32;
   pp.Mq = B->rings->d_Mq;
   pp.prec = prec;
   pp.Kc = Kc;
@@ -796,7 +833,7 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   pp.r = b.r;
   pp.blk_bad = b.blk_bad;
   pp.St = nullptr;
-  XPCS_LAUNCH(ctx, "compressed_prep", 2, launch_prep_compressed(pp, ctx->stream));
+  XPCS_LAUNCH(ctx, "compressed_prep", 1, launch_prep_compressed(pp, ctx->stream));
   const CUtensorMapDataType dt =
       prec == XPCS_PREC_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap tmL, tmR;
@@ -808,8 +845,8 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   gp.T_pad = T_pad;
   gp.maxC = maxC;
   gp.CH = CH;
-  gp.k_off = b.koff;
-  gp.k_chunks = b.kch;
+  gp.k_off = B->d_koff;
+  gp.k_chunks = B->d_kch;
   gp.ring_rows = T_pad;
   gp.fmt = prec == XPCS_PREC_FP16 ? 0 : 1;
   gp.split = split ? 1 : 0;
@@ -820,8 +857,7 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   gp.Nout = nullptr;
   gp.partials = b.partials;
   gp.status = ctx->d_status;
-  XPCS_TRY(run_twotime(ctx, tmL, tmR, gp, n_q, T, T_pad, nT, maxC, items, b.items, b.vbits,
-                       want_cnt ? b.count : nullptr, g2_out));
+  XPCS_TRY(run_twotime(ctx, tmL, tmR, gp, n_q, T, T_pad, nT, maxC, b.vbits, want_cnt ? b.count : nullptr, g2_out));
   return finish(ctx);
 }
 

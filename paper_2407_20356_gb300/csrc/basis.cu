@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) ring_factors_kernel(const double* B, int 
 }
 
 __global__ void ring_factors_reduce_kernel(const double* Gpart, const double* spart, int n_split, int n_q, int k,
-                                           double* G, double* s, float* G32) {
+                                           double* G, double* s, float* G32, float2* s32) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long kk = (long long)k * k;
   if (gid < (long long)n_q * kk) {
@@ -174,6 +174,8 @@ __global__ void ring_factors_reduce_kernel(const double* Gpart, const double* sp
     double a = 0.0;
     for (int sp = 0; sp < n_split; ++sp) a += spart[((size_t)q * n_split + sp) * k + c];
     s[gid] = a;
+    const float hi = (float)a;
+    s32[gid] = make_float2(hi, (float)(a - (double)hi));
   }
 }
 
@@ -255,10 +257,10 @@ cudaError_t launch_ring_factors2(const double* B, int k, const int* perm, const 
 }
 
 cudaError_t launch_ring_factors_reduce(const double* Gpart, const double* spart, int n_chunks, int n_q, int k,
-                                       double* G, double* s, float* G32, cudaStream_t st) {
+                                       double* G, double* s, float* G32, float2* s32, cudaStream_t st) {
   const long long tot = (long long)n_q * k * k;
   ring_factors_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Gpart, spart, n_chunks, n_q, k, G, s,
-                                                                           G32);
+                                                                           G32, s32);
   return cudaGetLastError();
 }
 

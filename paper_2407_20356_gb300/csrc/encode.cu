@@ -267,8 +267,12 @@ int encode_smem_bytes(int k) { return EncLayout(k, 1).smem(); }
 cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const EncodeParams& p, int grid,
                           cudaStream_t st) {
   const EncLayout lay(p.k, p.dtype);
-  cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.smem());
-  if (e != cudaSuccess) return e;
+  static int attr_bytes = 0;  // the attribute only ever grows
+  if (lay.smem() > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.smem());
+    if (e != cudaSuccess) return e;
+    attr_bytes = lay.smem();
+  }
   const int n_items = (p.T_pad / TILE) * p.n_split;
   encode_kernel<<<grid, ENC_THREADS, lay.smem(), st>>>(tmX, tmB, p, n_items);
   return cudaGetLastError();

@@ -29,6 +29,10 @@ struct xpcs_ctx {
   size_t scratch_cap = 0;
   cusolverDnHandle_t solver = nullptr;
   uint64_t launches = 0;  // kernels this library has launched on the context
+  // work items of the two-time kernel, cached for the last (n_q, nT, CH)
+  int4* d_items = nullptr;
+  size_t items_n = 0, items_bytes = 0;
+  int items_key[3] = {-1, -1, -1};
   bool prof = false;
   std::vector<xpcs_prof_entry> prof_entries;
   std::vector<cudaEvent_t> event_pool;
@@ -60,8 +64,11 @@ struct xpcs_basis {
   double* d_B = nullptr;          // M x k
   double* d_G = nullptr;          // n_q x k x k
   double* d_s = nullptr;          // n_q x k
+  float2* d_s32 = nullptr;        // n_q x k: s_q as (hi, lo) f32 pieces
   float* d_G32 = nullptr;         // n_q x k x k
   __half* d_Bcat = nullptr;       // 2kp x M_pad: f16 hi/lo of V^T 2^enc_log2
+  int* d_koff = nullptr;          // n_q zeros: K offsets of the compressed operands
+  int* d_kch = nullptr;           // n_q x ceil(k/64): K chunks per operand piece
   int enc_log2 = 0;
   size_t bytes = 0;
 };

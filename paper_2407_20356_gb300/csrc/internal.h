@@ -43,7 +43,7 @@ struct GramParams {
                            //    C = L_hi R_hi + L_lo R_hi + L_hi R_lo
   int raw;                 // 1: C = acc * r(t1) * r(t2); 0: operands already scaled
   const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined
-  const uint8_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
+  const uint32_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
   float* C;                // nullable [n_q][T][T]
   long long* Nout;         // nullable, raw only [n_q][T][T]
   float* partials;         // nullable [n_q][nT][maxC][256]
@@ -75,7 +75,7 @@ cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st);
 // r[q][t] = sqrt(Mq)/S (raw int64 sums) and block flags
 // (also flags XPCS_DEV_RANGE when a ring's max sum of squares reaches 2^24)
 cudaError_t launch_raw_scales(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
-                              const unsigned long long* sq, float* r, uint8_t* blk_bad, uint32_t* status,
+                              const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status,
                               cudaStream_t st);
 
 struct PrepParams {
@@ -86,13 +86,14 @@ struct PrepParams {
   int T_pad, nT;
   const float* G32;        // [n_q][k][k]
   const double* s64;       // [n_q][k]
+  const float2* s32;       // [n_q][k] (hi, lo) f32 pieces of s64
   const long long* Mq;     // [n_q]
   int prec;                // xpcs_precision
   int Kc;                  // operand row length (elements, multiple of 64)
   void* L;                 // [n_q][T_pad][Kc] 16-bit
   void* R;                 // [n_q][T_pad][Kc] 16-bit
   float* r;                // [n_q][T_pad]
-  uint8_t* blk_bad;        // [n_q][nT]
+  uint32_t* blk_bad;        // [n_q][nT]
   double* St;              // nullable [n_q][T] compressed ring sums
 };
 cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st);
@@ -135,7 +136,7 @@ cudaError_t launch_basis_sign(double* B, long long M, int k, cudaStream_t st);
 cudaError_t launch_ring_factors2(const double* B, int k, const int* perm, const int* off, const long long* Mq,
                                  int n_q, int n_split, double* Gpart, double* spart, cudaStream_t st);
 cudaError_t launch_ring_factors_reduce(const double* Gpart, const double* spart, int n_chunks, int n_q, int k,
-                                       double* G, double* s, float* G32, cudaStream_t st);
+                                       double* G, double* s, float* G32, float2* s32, cudaStream_t st);
 cudaError_t launch_basis_absmax(const double* B, long long n, double* out, cudaStream_t st);
 cudaError_t launch_basis_pack(const double* B, long long M, long long M_pad, int k, int kp, int log2_scale,
                               __half* Bcat, cudaStream_t st);

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p
 // r[q][t] = sqrt(M_q) / S_q(t) for defined frames, 0 otherwise; blk_bad marks tiles with
 // an undefined frame inside the series.
 __global__ void raw_scales_kernel(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
-                                  const unsigned long long* sq, float* r, uint8_t* blk_bad, uint32_t* status) {
+                                  const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status) {
   const int q = blockIdx.y, I = blockIdx.x;
   if (I == 0 && threadIdx.x == 0 && sq && sq[q] >= (1ull << 24)) set_status(status, XPCS_DEV_RANGE);
   const long long t = (long long)I * TILE + threadIdx.x;
@@ -88,32 +88,10 @@ __global__ void raw_scales_kernel(const long long* S, const long long* Mq, int n
   }
   r[(size_t)q * T_pad + t] = v;
   const int any = __syncthreads_or(bad);
-  if (threadIdx.x == 0) blk_bad[(size_t)q * nT + I] = (uint8_t)any;
+  if (threadIdx.x == 0) blk_bad[(size_t)q * nT + I] = (uint32_t)any;
 }
 
 // ---------------------------------------------------------------- compressed preparation
-// Ring sums of the decompressed frames S~_q(t) = a_t . s_q (FP64), r = sqrt(M_q)/S~.
-__global__ void comp_scales_kernel(const PrepParams p) {
-  const int q = blockIdx.y, I = blockIdx.x;
-  const long long t = (long long)I * TILE + threadIdx.x;
-  float v = 0.f;
-  bool bad = false;
-  if (t < p.T) {
-    const float* a = p.A + t * p.k;
-    const double* s = p.s64 + (size_t)q * p.k;
-    double acc = 0.0;
-    for (int c = 0; c < p.k; ++c) acc += (double)a[c] * s[c];
-    if (p.St) p.St[(size_t)q * p.T + t] = acc;
-    if (acc > 0.0)
-      v = (float)(sqrt((double)p.Mq[q]) / acc);
-    else
-      bad = true;
-  }
-  p.r[(size_t)q * p.T_pad + t] = v;
-  const int any = __syncthreads_or(bad);
-  if (threadIdx.x == 0) p.blk_bad[(size_t)q * p.nT + I] = (uint8_t)any;
-}
-
 template <typename T16>
 XPCS_DEV T16 to16(float x);
 template <>
@@ -135,70 +113,134 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   const int lda = k + 1;
   float* As = sm;                          // [64][k+1]  r * a
   float* Ws = As + PREP_FRAMES * lda;      // [64][k+1]  r * a G_q
-  float* Gs = Ws + PREP_FRAMES * lda;      // [k][32]
+  float* Gs = Ws + PREP_FRAMES * lda;      // [k][64]
   const int q = blockIdx.y;
   const long long t0 = (long long)blockIdx.x * PREP_FRAMES;
   const float* rq = p.r + (size_t)q * p.T_pad;
-  for (int i = threadIdx.x; i < PREP_FRAMES * k; i += blockDim.x) {
-    const int f = i / k, c = i % k;
+  const int tid = threadIdx.x;
+  float* rs = Gs + k * 64;                 // [64] r of this block's frames
+  // A rows: 4 rows per pass, 64 columns per row chunk (coalesced, no integer division)
+  for (int f = tid >> 6; f < PREP_FRAMES; f += 4) {
     const long long t = t0 + f;
-    As[f * lda + c] = (t < p.T) ? p.A[t * k + c] * rq[t] : 0.f;
+    for (int c = tid & 63; c < k; c += 64) As[f * lda + c] = (t < p.T) ? p.A[t * k + c] : 0.f;
   }
-  const int f = threadIdx.x % PREP_FRAMES;
-  const int g = threadIdx.x / PREP_FRAMES;  // 0..3 -> 8 columns each
+  __syncthreads();
+  // ring sums of the decompressed frames S~_q(t) = a_t . s_q: 4 threads per frame, each a
+  // compensated f32 dot product (TwoProduct by fma, TwoSum; Ogita, Rump and Oishi, 2005)
+  // over a quarter of the coefficients, combined by shuffles with the same transformations.
+  // The result carries about twice the f32 precision, so lossy sums near zero keep
+  // their sign without the FP64 units.
+  {
+    const int f = tid >> 2, part = tid & 3;
+    const float2* sq = p.s32 + (size_t)q * k;
+    const float* arow = As + f * lda;
+    float hi = 0.f, lo = 0.f;
+    for (int c = part; c < k; c += 4) {
+      const float2 sv = sq[c];
+      const float x = arow[c];
+      const float prod = x * sv.x;
+      const float perr = fmaf(x, sv.x, -prod) + x * sv.y;
+      const float sum = hi + prod;
+      const float z = sum - hi;
+      lo += ((hi - (sum - z)) + (prod - z)) + perr;
+      hi = sum;
+    }
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+      const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+      const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+      const float sum = hi + ohi;
+      const float z = sum - hi;
+      lo += ((hi - (sum - z)) + (ohi - z)) + olo;
+      hi = sum;
+    }
+    if (part == 0) {
+      const long long t = t0 + f;
+      float v = 0.f;
+      if (t < p.T) {
+        const double acc = (double)hi + (double)lo;
+        if (p.St) p.St[(size_t)q * p.T + t] = acc;
+        if (acc > 0.0)
+          v = (float)(sqrt((double)p.Mq[q]) / acc);
+        else
+          atomicOr(&p.blk_bad[(size_t)q * p.nT + (t >> 7)], 1u);
+      }
+      p.r[(size_t)q * p.T_pad + t] = v;
+      rs[f] = v;
+    }
+  }
+  __syncthreads();
+  for (int f = tid >> 6; f < PREP_FRAMES; f += 4)
+    for (int c = tid & 63; c < k; c += 64) As[f * lda + c] *= rs[f];
+  // W = (r a) G_q in 64-column chunks: thread (fl, cg) computes frames fl and fl + 32,
+  // columns 8 cg .. 8 cg + 7 of the chunk (16 outputs, 4 shared loads per 16 FMAs)
+  const int fl = tid & 31, cg = tid >> 5;
   const float* Gq = p.G32 + (size_t)q * k * k;
-  for (int j0 = 0; j0 < k; j0 += PREP_COLS) {
-    const int nc = min(PREP_COLS, k - j0);
+  for (int j0 = 0; j0 < k; j0 += 64) {
+    const int nc = min(64, k - j0);
     __syncthreads();
-    for (int i = threadIdx.x; i < k * PREP_COLS; i += blockDim.x) {
-      const int c = i / PREP_COLS, j = i % PREP_COLS;
-      Gs[i] = (j < nc) ? Gq[(size_t)c * k + j0 + j] : 0.f;
+    for (int c = tid >> 6; c < k; c += 4) {
+      const int j = tid & 63;
+      Gs[c * 64 + j] = (j < nc) ? Gq[(size_t)c * k + j0 + j] : 0.f;
     }
     __syncthreads();
-    float w[8];
+    float w0[8], w1[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) w[u] = 0.f;
-    const float* arow = As + f * lda;
+    for (int u = 0; u < 8; ++u) w0[u] = w1[u] = 0.f;
+    const float* a0 = As + fl * lda;
+    const float* a1 = As + (fl + 32) * lda;
+#pragma unroll 4
     for (int c = 0; c < k; ++c) {
-      const float a = arow[c];
-      const float* gr = Gs + c * PREP_COLS + 8 * g;
+      const float x0 = a0[c], x1 = a1[c];
+      const float4 g0 = *reinterpret_cast<const float4*>(Gs + c * 64 + 8 * cg);
+      const float4 g1 = *reinterpret_cast<const float4*>(Gs + c * 64 + 8 * cg + 4);
+      const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-      for (int u = 0; u < 8; ++u) w[u] = fmaf(a, gr[u], w[u]);
+      for (int u = 0; u < 8; ++u) {
+        w0[u] = fmaf(x0, gv[u], w0[u]);
+        w1[u] = fmaf(x1, gv[u], w1[u]);
+      }
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      if (8 * g + u < nc) Ws[f * lda + j0 + 8 * g + u] = w[u];
+      if (8 * cg + u < nc) {
+        Ws[fl * lda + j0 + 8 * cg + u] = w0[u];
+        Ws[(fl + 32) * lda + j0 + 8 * cg + u] = w1[u];
+      }
   }
   __syncthreads();
+  // rows out: 8 threads per row, 16-byte vectors, coalesced 128-byte segments
   const int nvec = p.Kc / 8;
   const int piece = SPLIT ? p.Kc / 2 : p.Kc;  // split rows are [hi | lo], each `piece` wide
   uint4* L = reinterpret_cast<uint4*>(static_cast<T16*>(p.L) + ((size_t)q * p.T_pad + t0) * p.Kc);
   uint4* R = reinterpret_cast<uint4*>(static_cast<T16*>(p.R) + ((size_t)q * p.T_pad + t0) * p.Kc);
-  for (int v = threadIdx.x; v < PREP_FRAMES * nvec; v += blockDim.x) {
-    const int ff = v / nvec, c0 = (v % nvec) * 8;
-    alignas(16) T16 lv[8];
-    alignas(16) T16 rv[8];
+  for (int ff = tid >> 3; ff < PREP_FRAMES; ff += 32) {
+    for (int vv = tid & 7; vv < nvec; vv += 8) {
+      alignas(16) T16 lv[8];
+      alignas(16) T16 rv[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int col = c0 + e;
-      const int seg = col / piece, j = col - seg * piece;
-      float wl = 0.f, ar = 0.f;
-      if (j < k) {
-        const float wv = Ws[ff * lda + j], av = As[ff * lda + j];
-        if (!SPLIT) {
-          wl = wv;
-          ar = av;
-        } else {
-          const float wh = (float)to16<T16>(wv), ah = (float)to16<T16>(av);
-          wl = seg == 0 ? wh : wv - wh;
-          ar = seg == 0 ? ah : av - ah;
+      for (int e = 0; e < 8; ++e) {
+        const int col = vv * 8 + e;
+        const int seg = (SPLIT && col >= piece) ? 1 : 0;
+        const int j = col - seg * piece;
+        float wl = 0.f, ar = 0.f;
+        if (j < k) {
+          const float wv = Ws[ff * lda + j], av = As[ff * lda + j];
+          if (!SPLIT) {
+            wl = wv;
+            ar = av;
+          } else {
+            const float wh = (float)to16<T16>(wv), ah = (float)to16<T16>(av);
+            wl = seg == 0 ? wh : wv - wh;
+            ar = seg == 0 ? ah : av - ah;
+          }
         }
+        lv[e] = to16<T16>(wl);
+        rv[e] = to16<T16>(ar);
       }
-      lv[e] = to16<T16>(wl);
-      rv[e] = to16<T16>(ar);
+      L[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(lv);
+      R[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(rv);
     }
-    L[(size_t)ff * nvec + (v % nvec)] = *reinterpret_cast<const uint4*>(lv);
-    R[(size_t)ff * nvec + (v % nvec)] = *reinterpret_cast<const uint4*>(rv);
   }
 }
 
@@ -337,23 +379,26 @@ cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st) {
 }
 
 cudaError_t launch_raw_scales(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
-                              const unsigned long long* sq, float* r, uint8_t* blk_bad, uint32_t* status,
+                              const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status,
                               cudaStream_t st) {
   raw_scales_kernel<<<dim3(nT, n_q), TILE, 0, st>>>(S, Mq, n_q, T, T_pad, nT, sq, r, blk_bad, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st) {
-  comp_scales_kernel<<<dim3(p.nT, p.n_q), TILE, 0, st>>>(p);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(p.blk_bad, 0, (size_t)p.n_q * p.nT * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  const int smem = (2 * PREP_FRAMES * (p.k + 1) + p.k * PREP_COLS) * (int)sizeof(float);
+  const int smem = (2 * PREP_FRAMES * (p.k + 1) + p.k * 64 + PREP_FRAMES) * (int)sizeof(float);
   const dim3 grid(p.T_pad / PREP_FRAMES, p.n_q);
 #define XPCS_PREP_LAUNCH(T16, SPLIT)                                                                  \
   do {                                                                                                \
-    e = cudaFuncSetAttribute(comp_operands_kernel<T16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             smem);                                                                   \
-    if (e != cudaSuccess) return e;                                                                   \
+    static int attr_bytes = 0; /* the attribute only ever grows */                                   \
+    if (smem > attr_bytes) {                                                                          \
+      e = cudaFuncSetAttribute(comp_operands_kernel<T16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                               smem);                                                                 \
+      if (e != cudaSuccess) return e;                                                                 \
+      attr_bytes = smem;                                                                              \
+    }                                                                                                 \
     comp_operands_kernel<T16, SPLIT><<<grid, 256, smem, st>>>(p);                                     \
   } while (0)
   if (p.prec == XPCS_PREC_FP16)
