@@ -54,6 +54,7 @@ typedef enum xpcs_precision {
 typedef struct xpcs_ctx xpcs_ctx;
 typedef struct xpcs_rings xpcs_rings;
 typedef struct xpcs_basis xpcs_basis;
+typedef struct xpcs_stream xpcs_stream;
 
 /* ------------------------------------------------------------------ context */
 
@@ -149,6 +150,43 @@ xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A,
  * g2_q(tau) = mean over t of C[q][t+tau][t], NaN entries skipped, from the lower
  * triangle of C (n_q x T x T float32).  g2_out n_q x T f64, count_out nullable. */
 xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out, int64_t* count_out);
+
+/* ------------------------------------------------------------------ online stream (Sec. 2.2, Fig. 1c)
+ * Online compression with a basis fit before acquisition: every pushed frame is encoded
+ * (a_t = x_t V_K, sparse: only nonzero pixels read their basis row, f32), appended to a
+ * device ring buffer of the last `history` coefficient rows, and its two-time row
+ * C_q(t, s) for s in (t - history, t] is folded into running sums over lags
+ * tau = 0 .. history-1 (C itself is not stored).  xpcs_stream_read_g2 returns
+ * g2_q(tau) = mean over t of C_q(t, t - tau) for every pushed frame t, and the pair count.
+ * Work runs on the stream's own CUDA stream, so several streams overlap on the device.
+ * Destroy streams before their basis and context. */
+
+/* Open a stream on `basis` for frames of `dtype`, keeping `history` lags, with batches
+ * of up to `max_batch` frames.  XPCS_EBUSY if its device memory does not fit the
+ * context's budget now (retry once other streams close). */
+xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t history, int max_batch,
+                             xpcs_dtype dtype, xpcs_stream** out);
+/* Push n frames (n x M counts in host memory).  The frames are copied before the call
+ * returns, so the caller may reuse its buffer.  *ticket (nullable) = frames pushed so far;
+ * pass it to xpcs_stream_poll. */
+xpcs_status xpcs_stream_push(xpcs_stream* s, const void* frames_host, int64_t n_frames, uint64_t* ticket);
+/* Push n frames already in device memory (the buffer must stay valid until the ticket
+ * completes). */
+xpcs_status xpcs_stream_push_device(xpcs_stream* s, const void* frames, int64_t n_frames, uint64_t* ticket);
+/* XPCS_OK once every frame up to `ticket` is folded into the sums; XPCS_EBUSY if not
+ * within timeout_ms (0 = just check). */
+xpcs_status xpcs_stream_poll(xpcs_stream* s, uint64_t ticket, int timeout_ms);
+/* g2_host (nullable): n_q x history f64; count_host (nullable): n_q x history int64.
+ * Waits for the stream's pending work. */
+xpcs_status xpcs_stream_read_g2(xpcs_stream* s, double* g2_host, int64_t* count_host);
+/* Frames pushed so far. */
+int64_t xpcs_stream_frames(const xpcs_stream* s);
+/* Push-to-done latency of completed pushes (host steady clock: from entering the push
+ * call to the end of the batch's device work), in microseconds.  reset != 0 forgets the
+ * completed ones afterwards. */
+xpcs_status xpcs_stream_latency(xpcs_stream* s, int reset, double* p50_us, double* p99_us, double* max_us,
+                                int64_t* n_batches);
+xpcs_status xpcs_stream_close(xpcs_stream* s);
 
 #ifdef __cplusplus
 }

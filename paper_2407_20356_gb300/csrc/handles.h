@@ -65,6 +65,8 @@ struct xpcs_basis {
   double* d_G = nullptr;          // n_q x k x k
   double* d_s = nullptr;          // n_q x k
   float2* d_s32 = nullptr;        // n_q x k: s_q as (hi, lo) f32 pieces
+  float* d_B32 = nullptr;         // M x k f32 copy of V_K for the sparse streaming encode
+                                  // (made on first use)
   float* d_G32 = nullptr;         // n_q x k x k
   __half* d_Bcat = nullptr;       // 2kp x M_pad: f16 hi/lo of V^T 2^enc_log2
   int* d_koff = nullptr;          // n_q zeros: K offsets of the compressed operands
@@ -73,7 +75,49 @@ struct xpcs_basis {
   size_t bytes = 0;
 };
 
+// Online stream (Sec. 2.2, Fig. 1c): a device ring buffer of coefficient rows and
+// per-ring factors, and running g2 sums over lags 0..W-1.
+struct xpcs_stream {
+  xpcs_ctx* ctx = nullptr;
+  const xpcs_basis* basis = nullptr;
+  cudaStream_t stream = nullptr;     // own CUDA stream: streams overlap on the device
+  int64_t W = 0;                     // history window (lags kept)
+  int64_t cap = 0;                   // ring slots = W + max_batch
+  int max_batch = 0;
+  int64_t frames = 0;                // frames enqueued so far
+  int nblk = 0;                      // pixel slices of the sparse encode
+  // device
+  void* d_frames = nullptr;          // max_batch x M counts (u16 or u8)
+  float* d_Ah = nullptr;             // cap x k coefficient history
+  float* d_Rh = nullptr;             // cap x n_q  r_q(s) = sqrt(M_q)/S~_q(s), 0 if undefined
+  double* d_g2sum = nullptr;         // n_q x W
+  long long* d_cnt = nullptr;        // n_q x W
+  float* d_part = nullptr;           // max_batch x nblk x k sparse-encode partials
+  float* d_a = nullptr;              // max_batch x k
+  float* d_w = nullptr;              // max_batch x n_q x k   r_q(t) a_t G_q
+  double* d_g2 = nullptr;            // n_q x W read-out buffer
+  uint32_t* d_status = nullptr;
+  size_t bytes = 0;
+  // host
+  void* h_stage[2] = {nullptr, nullptr};  // pinned staging, double-buffered
+  cudaEvent_t stage_done[2] = {nullptr, nullptr};
+  int stage_i = 0;
+  int dtype = -1;
+  std::vector<std::pair<uint64_t, cudaEvent_t>> tickets;  // (last frame + 1, event)
+  std::vector<cudaEvent_t> event_pool;
+  // per-batch latency stamps: push time and completion time (host steady clock, ns),
+  // the latter written by a host function queued behind the batch
+  struct Stamp {
+    int64_t push_ns = 0;
+    volatile int64_t done_ns = 0;
+    int64_t n_frames = 0;
+  };
+  std::vector<Stamp*> stamps;
+};
+
 namespace xpcs {
+
+size_t stream_footprint(const xpcs_basis* B, int64_t W, int max_batch, int elem_bytes);
 
 xpcs_status fail(xpcs_ctx* ctx, xpcs_status s, const std::string& msg);
 xpcs_status dev_alloc(xpcs_ctx* ctx, void** p, size_t bytes);

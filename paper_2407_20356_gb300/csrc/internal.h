@@ -125,6 +125,32 @@ int encode_smem_bytes(int k);
 cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float scale,
                                  float* A, cudaStream_t st);
 
+// ------------------------------------------------------------------ stream
+
+struct StreamStep {
+  const void* X;           // b x M counts (device)
+  int dtype;               // 0 u8, 1 u16
+  long long M;
+  int k, n_q, b;
+  long long t0;            // index of the first frame of the batch
+  long long W, cap;
+  int nblk;
+  const float* B32;        // M x k
+  const float* G32;        // n_q x k x k
+  const double* s64;       // n_q x k
+  const long long* Mq;     // n_q
+  float* part;             // b x nblk x k
+  float* a;                // b x k
+  float* w;                // b x n_q x k
+  float* Ah;               // cap x k
+  float* Rh;               // cap x n_q
+  double* g2sum;           // n_q x W
+  long long* cnt;          // n_q x W
+};
+cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st);
+cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, long long n, double* g2, cudaStream_t st);
+cudaError_t launch_basis_f32(const double* B, long long n, float* B32, cudaStream_t st);
+
 // ------------------------------------------------------------------ basis
 
 cudaError_t launch_gram_normalise(const long long* N, int n, double* Gf, double* nrm, cudaStream_t st);

@@ -100,7 +100,6 @@ template <>
 XPCS_DEV __nv_bfloat16 to16<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
 constexpr int PREP_FRAMES = 64;
-constexpr int PREP_COLS = 32;
 
 // Operand rows for one ring and 64 frames: L = r * (a G_q), R = r * a, in the requested
 // 16-bit format.  BF16X3 stores [hi | lo] pieces (each padded to a multiple of 64) for
@@ -116,7 +115,6 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   float* Gs = Ws + PREP_FRAMES * lda;      // [k][64]
   const int q = blockIdx.y;
   const long long t0 = (long long)blockIdx.x * PREP_FRAMES;
-  const float* rq = p.r + (size_t)q * p.T_pad;
   const int tid = threadIdx.x;
   float* rs = Gs + k * 64;                 // [64] r of this block's frames
   // A rows: 4 rows per pass, 64 columns per row chunk (coalesced, no integer division)

@@ -1,0 +1,323 @@
+// C ABI of the online stream (Sec. 2.2, Fig. 1c): open, push frames, poll, read g2.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "handles.h"
+#include "internal.h"
+
+using namespace xpcs;
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+void CUDART_CB stamp_done(void* p) { static_cast<xpcs_stream::Stamp*>(p)->done_ns = now_ns(); }
+
+int ka_of(int k) { return (k + 31) / 32 * 32; }
+int nqp_of(int n_q) { return (n_q + 11) / 12 * 12; }
+int nblk_of(int64_t M) { return (int)((M + 4095) / 4096); }
+
+struct Sizes {
+  size_t frames, Ah, Rh, g2sum, cnt, part, a, w, g2, stage;
+};
+
+Sizes stream_sizes(const xpcs_basis* B, int64_t W, int max_batch, int eb) {
+  const int64_t M = B->rings->M;
+  const int n_q = B->rings->n_q, k = B->k;
+  const int64_t cap = W + max_batch;
+  Sizes z;
+  z.frames = (size_t)max_batch * M * eb;
+  z.Ah = (size_t)cap * ka_of(k) * 4;
+  z.Rh = (size_t)cap * n_q * 4;
+  z.g2sum = (size_t)n_q * W * 8;
+  z.cnt = (size_t)n_q * W * 8;
+  z.part = (size_t)max_batch * nblk_of(M) * k * 4;
+  z.a = (size_t)max_batch * k * 4;
+  z.w = (size_t)max_batch * nqp_of(n_q) * ka_of(k) * 4;
+  z.g2 = (size_t)n_q * W * 8;
+  z.stage = (size_t)max_batch * M * eb;
+  return z;
+}
+
+void stream_free(xpcs_stream* S) {
+  xpcs_ctx* ctx = S->ctx;
+  if (S->stream) cudaStreamSynchronize(S->stream);
+  const Sizes z = stream_sizes(S->basis, S->W, S->max_batch, S->dtype == XPCS_U8 ? 1 : 2);
+  dev_free(ctx, S->d_frames, z.frames);
+  dev_free(ctx, S->d_Ah, z.Ah);
+  dev_free(ctx, S->d_Rh, z.Rh);
+  dev_free(ctx, S->d_g2sum, z.g2sum);
+  dev_free(ctx, S->d_cnt, z.cnt);
+  dev_free(ctx, S->d_part, z.part);
+  dev_free(ctx, S->d_a, z.a);
+  dev_free(ctx, S->d_w, z.w);
+  dev_free(ctx, S->d_g2, z.g2);
+  for (int i = 0; i < 2; ++i) {
+    if (S->h_stage[i]) cudaFreeHost(S->h_stage[i]);
+    if (S->stage_done[i]) cudaEventDestroy(S->stage_done[i]);
+  }
+  for (auto& t : S->tickets) cudaEventDestroy(t.second);
+  for (auto e : S->event_pool) cudaEventDestroy(e);
+  for (auto st : S->stamps) delete st;
+  if (S->stream) cudaStreamDestroy(S->stream);
+  delete S;
+}
+
+}  // namespace
+
+namespace xpcs {
+
+size_t stream_footprint(const xpcs_basis* B, int64_t W, int max_batch, int elem_bytes) {
+  const Sizes z = stream_sizes(B, W, max_batch, elem_bytes);
+  size_t b = z.frames + z.Ah + z.Rh + z.g2sum + z.cnt + z.part + z.a + z.w + z.g2;
+  if (!B->d_B32) b += (size_t)B->rings->M * B->k * 4;  // f32 basis copy made on first use
+  return b;
+}
+
+}  // namespace xpcs
+
+extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int64_t history, int max_batch,
+                                        xpcs_dtype dtype, xpcs_stream** out) {
+  if (!ctx || !B || !out || B->ctx != ctx || history < 1 || max_batch < 1 || max_batch > 1024 || B->k > 256 ||
+      (dtype != XPCS_U8 && dtype != XPCS_U16))
+    return fail(ctx, XPCS_EINVAL, "bad stream_open args");
+  *out = nullptr;
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int eb = dtype == XPCS_U8 ? 1 : 2;
+  const size_t need = stream_footprint(B, history, max_batch, eb);
+  if (ctx->budget && ctx->held + need > ctx->budget)
+    return fail(ctx, XPCS_EBUSY,
+                "stream needs " + std::to_string(need) + " device bytes; " +
+                    std::to_string(ctx->budget > ctx->held ? ctx->budget - ctx->held : 0) + " free in the budget");
+  xpcs_basis* Bm = const_cast<xpcs_basis*>(B);
+  if (!Bm->d_B32) {
+    void* p = nullptr;
+    XPCS_TRY(dev_alloc(ctx, &p, (size_t)B->rings->M * B->k * 4));
+    Bm->d_B32 = static_cast<float*>(p);
+    Bm->bytes += (size_t)B->rings->M * B->k * 4;
+    XPCS_LAUNCH(ctx, "basis_f32", 1, launch_basis_f32(B->d_B, (long long)B->rings->M * B->k, Bm->d_B32, ctx->stream));
+    XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  auto* S = new xpcs_stream();
+  S->ctx = ctx;
+  S->basis = B;
+  S->W = history;
+  S->cap = history + max_batch;
+  S->max_batch = max_batch;
+  S->dtype = dtype;
+  S->nblk = nblk_of(B->rings->M);
+  const Sizes z = stream_sizes(B, history, max_batch, eb);
+  xpcs_status st = XPCS_OK;
+  void* p = nullptr;
+#define XPCS_SALLOC(field, bytes, T)                  \
+  if (st == XPCS_OK) {                                \
+    st = dev_alloc(ctx, &p, (bytes));                 \
+    S->field = static_cast<T>(p);                     \
+  }
+  XPCS_SALLOC(d_frames, z.frames, void*)
+  XPCS_SALLOC(d_Ah, z.Ah, float*)
+  XPCS_SALLOC(d_Rh, z.Rh, float*)
+  XPCS_SALLOC(d_g2sum, z.g2sum, double*)
+  XPCS_SALLOC(d_cnt, z.cnt, long long*)
+  XPCS_SALLOC(d_part, z.part, float*)
+  XPCS_SALLOC(d_a, z.a, float*)
+  XPCS_SALLOC(d_w, z.w, float*)
+  XPCS_SALLOC(d_g2, z.g2, double*)
+#undef XPCS_SALLOC
+  cudaError_t e = cudaSuccess;
+  if (st == XPCS_OK) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && st == XPCS_OK && e == cudaSuccess; ++i) {
+    e = cudaHostAlloc(&S->h_stage[i], z.stage, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->stage_done[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(S->stage_done[i], S->stream);
+  }
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_Ah, 0, z.Ah, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_Rh, 0, z.Rh, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_g2sum, 0, z.g2sum, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_cnt, 0, z.cnt, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+  if (st == XPCS_OK && e != cudaSuccess) st = fail(ctx, XPCS_ECUDA, std::string("stream setup: ") + cudaGetErrorString(e));
+  if (st != XPCS_OK) {
+    stream_free(S);
+    return st;
+  }
+  S->bytes = need;
+  *out = S;
+  return XPCS_OK;
+}
+
+namespace {
+
+cudaEvent_t take_event(xpcs_stream* S) {
+  if (!S->event_pool.empty()) {
+    cudaEvent_t e = S->event_pool.back();
+    S->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  return e;
+}
+
+// Enqueue one batch whose counts are already on the device.
+xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream::Stamp* stamp) {
+  xpcs_ctx* ctx = S->ctx;
+  const xpcs_basis* B = S->basis;
+  StreamStep s{};
+  s.X = X;
+  s.dtype = S->dtype;
+  s.M = B->rings->M;
+  s.k = B->k;
+  s.n_q = B->rings->n_q;
+  s.b = (int)n;
+  s.t0 = S->frames;
+  s.W = S->W;
+  s.cap = S->cap;
+  s.nblk = S->nblk;
+  s.B32 = B->d_B32;
+  s.G32 = B->d_G32;
+  s.s64 = B->d_s;
+  s.Mq = B->rings->d_Mq;
+  s.part = S->d_part;
+  s.a = S->d_a;
+  s.w = S->d_w;
+  s.Ah = S->d_Ah;
+  s.Rh = S->d_Rh;
+  s.g2sum = S->d_g2sum;
+  s.cnt = S->d_cnt;
+  cudaError_t e = launch_stream_step(s, S->stream);
+  if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream step: ") + cudaGetErrorString(e));
+  ctx->launches += 4;
+  S->frames += n;
+  if (stamp) {
+    e = cudaLaunchHostFunc(S->stream, stamp_done, stamp);
+    if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream stamp: ") + cudaGetErrorString(e));
+    S->stamps.push_back(stamp);
+  }
+  cudaEvent_t ev = take_event(S);
+  e = cudaEventRecord(ev, S->stream);
+  if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream event: ") + cudaGetErrorString(e));
+  S->tickets.push_back({(uint64_t)S->frames, ev});
+  return XPCS_OK;
+}
+
+}  // namespace
+
+extern "C" xpcs_status xpcs_stream_push(xpcs_stream* S, const void* frames_host, int64_t n_frames, uint64_t* ticket) {
+  if (!S || !frames_host || n_frames < 0) return XPCS_EINVAL;
+  xpcs_ctx* ctx = S->ctx;
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t M = S->basis->rings->M;
+  const size_t fb = (size_t)M * (S->dtype == XPCS_U8 ? 1 : 2);
+  const char* src = static_cast<const char*>(frames_host);
+  for (int64_t off = 0; off < n_frames; off += S->max_batch) {
+    const int64_t n = std::min<int64_t>(S->max_batch, n_frames - off);
+    auto* stamp = new xpcs_stream::Stamp();
+    stamp->push_ns = now_ns();
+    stamp->n_frames = n;
+    const int i = S->stage_i;
+    S->stage_i ^= 1;
+    XPCS_CUDA(ctx, cudaEventSynchronize(S->stage_done[i]));  // the staging buffer is free again
+    memcpy(S->h_stage[i], src + off * fb, n * fb);
+    XPCS_CUDA(ctx, cudaMemcpyAsync(S->d_frames, S->h_stage[i], n * fb, cudaMemcpyHostToDevice, S->stream));
+    XPCS_CUDA(ctx, cudaEventRecord(S->stage_done[i], S->stream));
+    XPCS_TRY(enqueue_batch(S, S->d_frames, n, stamp));
+  }
+  if (ticket) *ticket = (uint64_t)S->frames;
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_stream_push_device(xpcs_stream* S, const void* frames, int64_t n_frames,
+                                               uint64_t* ticket) {
+  if (!S || !frames || n_frames < 0) return XPCS_EINVAL;
+  xpcs_ctx* ctx = S->ctx;
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t fb = (size_t)S->basis->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
+  for (int64_t off = 0; off < n_frames; off += S->max_batch) {
+    const int64_t n = std::min<int64_t>(S->max_batch, n_frames - off);
+    auto* stamp = new xpcs_stream::Stamp();
+    stamp->push_ns = now_ns();
+    stamp->n_frames = n;
+    XPCS_TRY(enqueue_batch(S, static_cast<const char*>(frames) + off * fb, n, stamp));
+  }
+  if (ticket) *ticket = (uint64_t)S->frames;
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_stream_poll(xpcs_stream* S, uint64_t ticket, int timeout_ms) {
+  if (!S) return XPCS_EINVAL;
+  xpcs_ctx* ctx = S->ctx;
+  const int64_t t_end = now_ns() + (int64_t)std::max(0, timeout_ms) * 1000000;
+  while (true) {
+    // retire completed tickets in order
+    size_t done = 0;
+    for (; done < S->tickets.size(); ++done) {
+      cudaError_t e = cudaEventQuery(S->tickets[done].second);
+      if (e == cudaErrorNotReady) break;
+      if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+    }
+    for (size_t i = 0; i < done; ++i) S->event_pool.push_back(S->tickets[i].second);
+    if (done) S->tickets.erase(S->tickets.begin(), S->tickets.begin() + done);
+    // tickets are increasing: none pending at or below `ticket` means its frames are in
+    if (S->tickets.empty() || S->tickets.front().first > ticket) return XPCS_OK;
+    if (now_ns() >= t_end) return XPCS_EBUSY;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+extern "C" xpcs_status xpcs_stream_read_g2(xpcs_stream* S, double* g2_host, int64_t* count_host) {
+  if (!S) return XPCS_EINVAL;
+  xpcs_ctx* ctx = S->ctx;
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const long long n = (long long)S->basis->rings->n_q * S->W;
+  if (g2_host) {
+    cudaError_t e = launch_stream_g2(S->d_g2sum, S->d_cnt, n, S->d_g2, S->stream);
+    if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream g2: ") + cudaGetErrorString(e));
+    ctx->launches += 1;
+    XPCS_CUDA(ctx, cudaMemcpyAsync(g2_host, S->d_g2, n * 8, cudaMemcpyDeviceToHost, S->stream));
+  }
+  if (count_host) XPCS_CUDA(ctx, cudaMemcpyAsync(count_host, S->d_cnt, n * 8, cudaMemcpyDeviceToHost, S->stream));
+  XPCS_CUDA(ctx, cudaStreamSynchronize(S->stream));
+  return XPCS_OK;
+}
+
+extern "C" int64_t xpcs_stream_frames(const xpcs_stream* S) { return S ? S->frames : 0; }
+
+extern "C" xpcs_status xpcs_stream_latency(xpcs_stream* S, int reset, double* p50_us, double* p99_us,
+                                           double* max_us, int64_t* n_batches) {
+  if (!S) return XPCS_EINVAL;
+  std::vector<double> lat;
+  std::vector<xpcs_stream::Stamp*> keep;
+  for (auto* st : S->stamps) {
+    const int64_t d = st->done_ns;
+    if (d) {
+      lat.push_back((d - st->push_ns) * 1e-3);
+      if (reset) delete st;
+      else keep.push_back(st);
+    } else {
+      keep.push_back(st);
+    }
+  }
+  S->stamps.swap(keep);
+  std::sort(lat.begin(), lat.end());
+  auto pct = [&](double f) { return lat.empty() ? 0.0 : lat[std::min(lat.size() - 1, (size_t)(f * lat.size()))]; };
+  if (p50_us) *p50_us = pct(0.50);
+  if (p99_us) *p99_us = pct(0.99);
+  if (max_us) *max_us = lat.empty() ? 0.0 : lat.back();
+  if (n_batches) *n_batches = (int64_t)lat.size();
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_stream_close(xpcs_stream* S) {
+  if (!S) return XPCS_EINVAL;
+  stream_free(S);
+  return XPCS_OK;
+}

@@ -57,6 +57,15 @@ _SIGS = {
     "xpcs_encode": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
     "xpcs_g2": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
+    "xpcs_stream_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.POINTER(vp)]),
+    "xpcs_stream_push": (C.c_int, [vp, vp, i64, C.POINTER(C.c_uint64)]),
+    "xpcs_stream_push_device": (C.c_int, [vp, vp, i64, C.POINTER(C.c_uint64)]),
+    "xpcs_stream_poll": (C.c_int, [vp, C.c_uint64, C.c_int]),
+    "xpcs_stream_read_g2": (C.c_int, [vp, vp, vp]),
+    "xpcs_stream_frames": (i64, [vp]),
+    "xpcs_stream_latency": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "xpcs_stream_close": (C.c_int, [vp]),
 }
 
 
@@ -252,3 +261,60 @@ def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None,
 
 def xpcs_g2(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
     ctx.check(_lib.xpcs_g2(ctx.h, _ptr(C_in), n_q, T, _ptr(g2_out), _ptr(count_out)))
+
+
+class Stream:
+    """An xpcs_stream: online encode + two-time row update of every pushed frame."""
+
+    def __init__(self, ctx: Context, basis: Basis, history: int, max_batch: int, dtype="uint16"):
+        h = vp()
+        st = _lib.xpcs_stream_open(ctx.h, basis.h, history, max_batch, _dtype_code(dtype), C.byref(h))
+        if st != XPCS_OK:
+            raise XpcsError(st, _lib.xpcs_last_error(ctx.h).decode())
+        self.ctx, self.basis, self.h, self.W = ctx, basis, h, history
+        self.n_q = basis.rings.n_q
+        ctx._adopt(self)
+
+    def push(self, frames) -> int:
+        """Push frames (host numpy array or device tensor, n x M); returns the ticket."""
+        t = C.c_uint64()
+        n = int(frames.shape[0])
+        on_device = hasattr(frames, "is_cuda") and frames.is_cuda
+        f = _lib.xpcs_stream_push_device if on_device else _lib.xpcs_stream_push
+        self.ctx.check(f(self.h, _ptr(frames), n, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0) -> bool:
+        st = _lib.xpcs_stream_poll(self.h, ticket, timeout_ms)
+        if st == XPCS_EBUSY:
+            return False
+        self.ctx.check(st)
+        return True
+
+    def read_g2(self):
+        g2 = np.empty((self.n_q, self.W))
+        cnt = np.empty((self.n_q, self.W), dtype=np.int64)
+        self.ctx.check(_lib.xpcs_stream_read_g2(self.h, g2.ctypes.data, cnt.ctypes.data))
+        return g2, cnt
+
+    def frames(self) -> int:
+        return int(_lib.xpcs_stream_frames(self.h))
+
+    def latency(self, reset: bool = False) -> dict:
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        n = C.c_int64()
+        self.ctx.check(_lib.xpcs_stream_latency(self.h, 1 if reset else 0, C.byref(a), C.byref(b), C.byref(c),
+                                                C.byref(n)))
+        return {"p50_us": a.value, "p99_us": b.value, "max_us": c.value, "batches": n.value}
+
+    def close(self):
+        if self.h and self.ctx.h:
+            _lib.xpcs_stream_close(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -1,0 +1,139 @@
+"""GPU parity of the online stream (Sec. 2.2, Fig. 1c) against the oracle.
+
+The stream folds every pushed frame's two-time row into g2 sums over lags < W.  The
+reference is the FP64 oracle of the compressed two-time matrix of the same frames from
+the same FP64 basis, averaged along diagonals with lags >= W dropped.  The stream works in
+f32 (sparse encode, k-term dot products), so g2 agrees to 1e-4 of max|g2|; pair counts are
+exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import ring_qmap, speckle_counts
+from tests.gpu_util import rel_errors, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2407_20356_gb300 import xpcs
+
+    return xpcs
+
+
+@pytest.fixture(scope="module")
+def ctx(X):
+    return X.Context(0)
+
+
+def _setup(X, ctx, H, W, n_q, k, T, n_fit, dtype, seed, mean=0.3):
+    torch, dev = torch_cuda()
+    frames = speckle_counts(H, W, n_fit + T, mean, 2e-3, seed, dtype)
+    B, _ = O.fit_basis(frames[:n_fit], k)  # calibration run before acquisition
+    qmap = ring_qmap(H, W, n_q)
+    rings = X.Rings(ctx, torch.from_numpy(qmap).to(dev), H * W, n_q)
+    basis = X.xpcs_basis_import(ctx, rings, B)
+    return frames[n_fit:], B, qmap, rings, basis
+
+
+def _oracle_window_g2(Xs, B, qmap, n_q, Wl):
+    G, s, Mq = O.ring_factors(B, qmap, n_q)
+    C, _ = O.compressed_twotime(O.encode(Xs, B), G, s, Mq)
+    out_g, out_c = [], []
+    for q in range(n_q):
+        g, c = O.windowed_g2(C[q], Wl)
+        out_g.append(g[:Wl])
+        out_c.append(c[:Wl])
+    return np.array(out_g), np.array(out_c)
+
+
+@pytest.mark.parametrize("dtype,k,Wl,sizes", [(np.uint16, 20, 50, (1, 3, 8, 13, 5)),
+                                              (np.uint8, 64, 120, (8,)),
+                                              (np.uint16, 150, 64, (2, 7))])
+def test_stream_g2_matches_oracle(X, ctx, dtype, k, Wl, sizes):
+    H, W, n_q, T = 24, 40, 4, 200
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 250, dtype, 300 + k)
+    st = X.Stream(ctx, basis, Wl, 8, dtype=np.dtype(dtype).name)
+    i, j = 0, 0
+    while i < T:
+        n = min(sizes[j % len(sizes)], T - i)
+        ticket = st.push(np.ascontiguousarray(Xs[i:i + n]))
+        i += n
+        j += 1
+    assert st.poll(ticket, 10000)
+    assert st.frames() == T
+    g2, cnt = st.read_g2()
+    g_ref, c_ref = _oracle_window_g2(Xs, B, qmap, n_q, Wl)
+    np.testing.assert_array_equal(cnt, c_ref)
+    for q in range(n_q):
+        rm, _ = rel_errors(g2[q], g_ref[q])
+        assert rm < 1e-4, (q, rm)
+    lat = st.latency()
+    assert lat["batches"] > 0 and lat["p99_us"] >= lat["p50_us"] > 0
+    st.close()
+
+
+def test_stream_batching_and_device_push_agree(X, ctx):
+    torch, dev = torch_cuda()
+    H, W, n_q, k, T, Wl = 16, 32, 3, 24, 150, 40
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 120, np.uint16, 77)
+    a = X.Stream(ctx, basis, Wl, 1)
+    for t in range(T):
+        a.push(Xs[t:t + 1])
+    b = X.Stream(ctx, basis, Wl, 16)
+    b.push(torch.from_numpy(Xs).to(dev))  # device frames, batches of 16
+    ga, ca = a.read_g2()
+    gb, cb = b.read_g2()
+    np.testing.assert_array_equal(ca, cb)
+    ok = ~np.isnan(ga)
+    np.testing.assert_allclose(gb[ok], ga[ok], rtol=1e-6)
+
+
+def test_stream_matches_offline_twotime(X, ctx):
+    # streamed g2 == offline compressed two-time g2 on the same frames (lags < W)
+    torch, dev = torch_cuda()
+    H, W, n_q, k, T, Wl = 20, 20, 4, 32, 256, 256
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 150, np.uint16, 91)
+    st = X.Stream(ctx, basis, Wl, 32)
+    st.push(Xs)
+    g2s, cs = st.read_g2()
+    A = torch.empty((T, k), dtype=torch.float32, device=dev)
+    X.xpcs_encode(ctx, basis, torch.from_numpy(Xs).to(dev), T, A)
+    g2o = torch.empty((n_q, T), dtype=torch.float64, device=dev)
+    co = torch.empty((n_q, T), dtype=torch.int64, device=dev)
+    X.xpcs_twotime(ctx, basis, A, T, "bf16x3", g2_out=g2o, count_out=co)
+    np.testing.assert_array_equal(cs, co.cpu().numpy())
+    for q in range(n_q):
+        rm, _ = rel_errors(g2s[q], g2o[q].cpu().numpy())
+        assert rm < 1e-4, (q, rm)
+
+
+def test_stream_admission_by_budget(X):
+    # a context whose budget holds one stream: the second open is refused until the
+    # first closes
+    torch, dev = torch_cuda()
+    H, W, n_q, k = 32, 32, 4, 16
+    frames = speckle_counts(H, W, 100, 0.5, 2e-3, 5, np.uint16)
+    B, _ = O.fit_basis(frames, k)
+    probe = X.Context(0)
+    rings = X.Rings(probe, torch.from_numpy(ring_qmap(H, W, n_q)).to(dev), H * W, n_q)
+    basis = X.xpcs_basis_import(probe, rings, B)
+    s1 = X.Stream(probe, basis, 20000, 8)
+    one = probe.device_bytes()
+    s1.close()
+    base = probe.device_bytes()
+    probe.close()
+    ctx = X.Context(0, hbm_budget=base + (one - base) + (one - base) // 2)
+    rings = X.Rings(ctx, torch.from_numpy(ring_qmap(H, W, n_q)).to(dev), H * W, n_q)
+    basis = X.xpcs_basis_import(ctx, rings, B)
+    a = X.Stream(ctx, basis, 20000, 8)
+    with pytest.raises(X.XpcsError) as e:
+        X.Stream(ctx, basis, 20000, 8)
+    assert e.value.status == X.XPCS_EBUSY
+    a.close()
+    b = X.Stream(ctx, basis, 20000, 8)  # admitted once memory is free
+    b.push(frames[:10])
+    g2, cnt = b.read_g2()
+    assert cnt[:, 0].max() > 0
