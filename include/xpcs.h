@@ -55,6 +55,7 @@ typedef struct xpcs_ctx xpcs_ctx;
 typedef struct xpcs_rings xpcs_rings;
 typedef struct xpcs_basis xpcs_basis;
 typedef struct xpcs_stream xpcs_stream;
+typedef struct xpcs_server xpcs_server;
 
 /* ------------------------------------------------------------------ context */
 
@@ -181,12 +182,42 @@ xpcs_status xpcs_stream_poll(xpcs_stream* s, uint64_t ticket, int timeout_ms);
 xpcs_status xpcs_stream_read_g2(xpcs_stream* s, double* g2_host, int64_t* count_host);
 /* Frames pushed so far. */
 int64_t xpcs_stream_frames(const xpcs_stream* s);
-/* Push-to-done latency of completed pushes (host steady clock: from entering the push
- * call to the end of the batch's device work), in microseconds.  reset != 0 forgets the
- * completed ones afterwards. */
+/* Per-frame latency of completed frames, in microseconds (host steady clock): from the
+ * frame's arrival (entering xpcs_stream_push, or its submission to a server) to the end of
+ * its batch's device work.  *n_frames = frames measured.  reset != 0 forgets them. */
 xpcs_status xpcs_stream_latency(xpcs_stream* s, int reset, double* p50_us, double* p99_us, double* max_us,
-                                int64_t* n_batches);
+                                int64_t* n_frames);
 xpcs_status xpcs_stream_close(xpcs_stream* s);
+
+/* ------------------------------------------------------------------ serving several streams
+ * A server owns a scheduler thread for streams opened through it.  xpcs_server_submit
+ * copies frames into the stream's host queue and returns at once; the scheduler takes,
+ * for each stream whose staging buffer is free, every frame that has arrived (up to the
+ * stream's max_batch) and enqueues it on the stream's own CUDA stream, so streams of
+ * different detector sizes overlap on the device and a batch grows while the previous one
+ * runs.  Streams are admitted against the context's device-memory budget.  A stream's
+ * results depend only on its own frames (alone or in a mix they agree up to the f32
+ * rounding of per-batch partial sums).  Streams of a server are used only through the
+ * xpcs_server_* calls; all of them are thread-safe. */
+xpcs_status xpcs_server_create(xpcs_ctx* ctx, xpcs_server** out);
+/* Open a stream (arguments as xpcs_stream_open).  If it does not fit the budget, wait up
+ * to wait_ms for streams to close (0: fail at once); XPCS_EBUSY if it still does not fit. */
+xpcs_status xpcs_server_open(xpcs_server* server, const xpcs_basis* basis, int64_t history, int max_batch,
+                             xpcs_dtype dtype, int wait_ms, xpcs_stream** out);
+/* Queue n host frames; *ticket (nullable) = frames submitted to this stream so far. */
+xpcs_status xpcs_server_submit(xpcs_server* server, xpcs_stream* s, const void* frames_host, int64_t n,
+                               uint64_t* ticket);
+/* XPCS_OK once every frame up to `ticket` is folded in; XPCS_EBUSY after timeout_ms. */
+xpcs_status xpcs_server_poll(xpcs_server* server, xpcs_stream* s, uint64_t ticket, int timeout_ms);
+xpcs_status xpcs_server_read_g2(xpcs_server* server, xpcs_stream* s, double* g2_host, int64_t* count_host);
+xpcs_status xpcs_server_latency(xpcs_server* server, xpcs_stream* s, int reset, double* p50_us, double* p99_us,
+                                double* max_us, int64_t* n_frames);
+/* Finish the stream's queued frames, close it and release its memory to waiting opens. */
+xpcs_status xpcs_server_close(xpcs_server* server, xpcs_stream* s);
+/* Batches the scheduler has enqueued so far. */
+uint64_t xpcs_server_batches(const xpcs_server* server);
+/* Stop the scheduler and close the remaining streams. */
+xpcs_status xpcs_server_destroy(xpcs_server* server);
 
 #ifdef __cplusplus
 }

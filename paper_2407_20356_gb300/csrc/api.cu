@@ -20,7 +20,10 @@ using namespace xpcs;
 namespace xpcs {
 
 xpcs_status fail(xpcs_ctx* ctx, xpcs_status s, const std::string& msg) {
-  if (ctx) ctx->err = msg;
+  if (ctx) {
+    std::lock_guard<std::mutex> lk(ctx->err_mu);
+    ctx->err = msg;
+  }
   return s;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cusolverDn.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -23,6 +24,7 @@ struct xpcs_ctx {
   size_t held = 0;
   bool async = false;
   std::string err;
+  std::mutex err_mu;  // error text may be written from a server's scheduler thread
   int num_sms = 0;
   uint32_t* d_status = nullptr;
   void* scratch = nullptr;
@@ -108,9 +110,8 @@ struct xpcs_stream {
   // per-batch latency stamps: push time and completion time (host steady clock, ns),
   // the latter written by a host function queued behind the batch
   struct Stamp {
-    int64_t push_ns = 0;
+    std::vector<int64_t> arrive_ns;  // one per frame of the batch
     volatile int64_t done_ns = 0;
-    int64_t n_frames = 0;
   };
   std::vector<Stamp*> stamps;
 };
@@ -118,6 +119,11 @@ struct xpcs_stream {
 namespace xpcs {
 
 size_t stream_footprint(const xpcs_basis* B, int64_t W, int max_batch, int elem_bytes);
+int64_t now_ns();
+// Push n host frames through the next staging buffer.  arrive_ns (nullable) gives each
+// frame's arrival time for the latency record.  With block == false the call does nothing
+// and returns XPCS_EBUSY while that buffer's previous copy is still in flight.
+xpcs_status stream_push_host(xpcs_stream* S, const void* frames, int64_t n, const int64_t* arrive_ns, bool block);
 
 xpcs_status fail(xpcs_ctx* ctx, xpcs_status s, const std::string& msg);
 xpcs_status dev_alloc(xpcs_ctx* ctx, void** p, size_t bytes);

@@ -12,12 +12,16 @@
 
 using namespace xpcs;
 
-namespace {
+namespace xpcs {
 
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
       .count();
 }
+
+}  // namespace xpcs
+
+namespace {
 
 void CUDART_CB stamp_done(void* p) { static_cast<xpcs_stream::Stamp*>(p)->done_ns = now_ns(); }
 
@@ -211,25 +215,45 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
 
 }  // namespace
 
+namespace xpcs {
+
+xpcs_status stream_push_host(xpcs_stream* S, const void* frames, int64_t n, const int64_t* arrive_ns, bool block) {
+  xpcs_ctx* ctx = S->ctx;
+  const size_t fb = (size_t)S->basis->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
+  const int i = S->stage_i;
+  if (block) {
+    XPCS_CUDA(ctx, cudaEventSynchronize(S->stage_done[i]));  // the staging buffer is free again
+  } else {
+    const cudaError_t q = cudaEventQuery(S->stage_done[i]);
+    if (q == cudaErrorNotReady) return XPCS_EBUSY;
+    if (q != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream staging: ") + cudaGetErrorString(q));
+  }
+  S->stage_i ^= 1;
+  auto* stamp = new xpcs_stream::Stamp();
+  const int64_t t = now_ns();
+  stamp->arrive_ns.resize(n);
+  for (int64_t f = 0; f < n; ++f) stamp->arrive_ns[f] = arrive_ns ? arrive_ns[f] : t;
+  memcpy(S->h_stage[i], frames, n * fb);
+  cudaError_t e = cudaMemcpyAsync(S->d_frames, S->h_stage[i], n * fb, cudaMemcpyHostToDevice, S->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(S->stage_done[i], S->stream);
+  if (e != cudaSuccess) {
+    delete stamp;
+    return fail(ctx, XPCS_ECUDA, std::string("stream copy: ") + cudaGetErrorString(e));
+  }
+  return enqueue_batch(S, S->d_frames, n, stamp);
+}
+
+}  // namespace xpcs
+
 extern "C" xpcs_status xpcs_stream_push(xpcs_stream* S, const void* frames_host, int64_t n_frames, uint64_t* ticket) {
   if (!S || !frames_host || n_frames < 0) return XPCS_EINVAL;
   xpcs_ctx* ctx = S->ctx;
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
-  const int64_t M = S->basis->rings->M;
-  const size_t fb = (size_t)M * (S->dtype == XPCS_U8 ? 1 : 2);
+  const size_t fb = (size_t)S->basis->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
   const char* src = static_cast<const char*>(frames_host);
   for (int64_t off = 0; off < n_frames; off += S->max_batch) {
     const int64_t n = std::min<int64_t>(S->max_batch, n_frames - off);
-    auto* stamp = new xpcs_stream::Stamp();
-    stamp->push_ns = now_ns();
-    stamp->n_frames = n;
-    const int i = S->stage_i;
-    S->stage_i ^= 1;
-    XPCS_CUDA(ctx, cudaEventSynchronize(S->stage_done[i]));  // the staging buffer is free again
-    memcpy(S->h_stage[i], src + off * fb, n * fb);
-    XPCS_CUDA(ctx, cudaMemcpyAsync(S->d_frames, S->h_stage[i], n * fb, cudaMemcpyHostToDevice, S->stream));
-    XPCS_CUDA(ctx, cudaEventRecord(S->stage_done[i], S->stream));
-    XPCS_TRY(enqueue_batch(S, S->d_frames, n, stamp));
+    XPCS_TRY(stream_push_host(S, src + off * fb, n, nullptr, true));
   }
   if (ticket) *ticket = (uint64_t)S->frames;
   return XPCS_OK;
@@ -244,8 +268,7 @@ extern "C" xpcs_status xpcs_stream_push_device(xpcs_stream* S, const void* frame
   for (int64_t off = 0; off < n_frames; off += S->max_batch) {
     const int64_t n = std::min<int64_t>(S->max_batch, n_frames - off);
     auto* stamp = new xpcs_stream::Stamp();
-    stamp->push_ns = now_ns();
-    stamp->n_frames = n;
+    stamp->arrive_ns.assign(n, now_ns());
     XPCS_TRY(enqueue_batch(S, static_cast<const char*>(frames) + off * fb, n, stamp));
   }
   if (ticket) *ticket = (uint64_t)S->frames;
@@ -299,7 +322,7 @@ extern "C" xpcs_status xpcs_stream_latency(xpcs_stream* S, int reset, double* p5
   for (auto* st : S->stamps) {
     const int64_t d = st->done_ns;
     if (d) {
-      lat.push_back((d - st->push_ns) * 1e-3);
+      for (int64_t a : st->arrive_ns) lat.push_back((d - a) * 1e-3);
       if (reset) delete st;
       else keep.push_back(st);
     } else {
@@ -312,7 +335,7 @@ extern "C" xpcs_status xpcs_stream_latency(xpcs_stream* S, int reset, double* p5
   if (p50_us) *p50_us = pct(0.50);
   if (p99_us) *p99_us = pct(0.99);
   if (max_us) *max_us = lat.empty() ? 0.0 : lat.back();
-  if (n_batches) *n_batches = (int64_t)lat.size();
+  if (n_batches) *n_batches = (int64_t)lat.size();  // frames measured
   return XPCS_OK;
 }
 

@@ -66,6 +66,16 @@ _SIGS = {
     "xpcs_stream_latency": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "xpcs_stream_close": (C.c_int, [vp]),
+    "xpcs_server_create": (C.c_int, [vp, C.POINTER(vp)]),
+    "xpcs_server_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.c_int, C.POINTER(vp)]),
+    "xpcs_server_submit": (C.c_int, [vp, vp, vp, i64, C.POINTER(C.c_uint64)]),
+    "xpcs_server_poll": (C.c_int, [vp, vp, C.c_uint64, C.c_int]),
+    "xpcs_server_read_g2": (C.c_int, [vp, vp, vp, vp]),
+    "xpcs_server_latency": (C.c_int, [vp, vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "xpcs_server_close": (C.c_int, [vp, vp]),
+    "xpcs_server_batches": (C.c_uint64, [vp]),
+    "xpcs_server_destroy": (C.c_int, [vp]),
 }
 
 
@@ -310,6 +320,70 @@ class Stream:
     def close(self):
         if self.h and self.ctx.h:
             _lib.xpcs_stream_close(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """An xpcs_server: a scheduler thread serving several streams with continuous batching."""
+
+    def __init__(self, ctx: Context):
+        h = vp()
+        ctx.check(_lib.xpcs_server_create(ctx.h, C.byref(h)))
+        self.ctx, self.h = ctx, h
+        self.streams = {}
+        ctx._adopt(self)
+
+    def open(self, basis: Basis, history: int, max_batch: int, dtype="uint16", wait_ms: int = 0):
+        """Open a stream; returns its handle (an int key), or raises XpcsError (XPCS_EBUSY)."""
+        h = vp()
+        st = _lib.xpcs_server_open(self.h, basis.h, history, max_batch, _dtype_code(dtype), wait_ms, C.byref(h))
+        if st != XPCS_OK:
+            raise XpcsError(st, _lib.xpcs_last_error(self.ctx.h).decode())
+        self.streams[h.value] = (basis.rings.n_q, history)
+        return h.value
+
+    def submit(self, s: int, frames) -> int:
+        t = C.c_uint64()
+        self.ctx.check(_lib.xpcs_server_submit(self.h, s, _ptr(frames), int(frames.shape[0]), C.byref(t)))
+        return t.value
+
+    def poll(self, s: int, ticket: int, timeout_ms: int = 0) -> bool:
+        st = _lib.xpcs_server_poll(self.h, s, ticket, timeout_ms)
+        if st == XPCS_EBUSY:
+            return False
+        self.ctx.check(st)
+        return True
+
+    def read_g2(self, s: int):
+        n_q, W = self.streams[s]
+        g2 = np.empty((n_q, W))
+        cnt = np.empty((n_q, W), dtype=np.int64)
+        self.ctx.check(_lib.xpcs_server_read_g2(self.h, s, g2.ctypes.data, cnt.ctypes.data))
+        return g2, cnt
+
+    def latency(self, s: int, reset: bool = False) -> dict:
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        n = C.c_int64()
+        self.ctx.check(_lib.xpcs_server_latency(self.h, s, 1 if reset else 0, C.byref(a), C.byref(b), C.byref(c),
+                                                C.byref(n)))
+        return {"p50_us": a.value, "p99_us": b.value, "max_us": c.value, "frames": n.value}
+
+    def close_stream(self, s: int):
+        self.ctx.check(_lib.xpcs_server_close(self.h, s))
+        self.streams.pop(s, None)
+
+    def batches(self) -> int:
+        return int(_lib.xpcs_server_batches(self.h))
+
+    def close(self):
+        if self.h and self.ctx.h:
+            _lib.xpcs_server_destroy(self.h)
         self.h = None
 
     def __del__(self):

@@ -1,0 +1,124 @@
+"""GPU tests of the serving layer: several streams, one scheduler, continuous batching.
+
+Each stream's g2 must be the same alone and in a mix of streams of other detector sizes
+(the f32 partial sums of a batch may round differently when frames are batched
+differently: relative 1e-6), match the oracle (1e-4 of max|g2|), and streams must be
+admitted as device memory frees up.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import ring_qmap, speckle_counts
+from tests.gpu_util import rel_errors, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2407_20356_gb300 import xpcs
+
+    return xpcs
+
+
+def _basis(X, ctx, H, W, n_q, k, seed):
+    torch, dev = torch_cuda()
+    frames = speckle_counts(H, W, 200 + 240, 0.4, 2e-3, seed, np.uint16)
+    B, _ = O.fit_basis(frames[:200], k)
+    qmap = ring_qmap(H, W, n_q)
+    rings = X.Rings(ctx, torch.from_numpy(qmap).to(dev), H * W, n_q)
+    return frames[200:], B, qmap, X.xpcs_basis_import(ctx, rings, B)
+
+
+def _feed(sv, s, frames, chunk):
+    t = 0
+    for i in range(0, len(frames), chunk):
+        t = sv.submit(s, np.ascontiguousarray(frames[i:i + chunk]))
+    return t
+
+
+def test_stream_same_alone_and_in_mix(X):
+    shapes = [(24, 40, 4, 20, 60), (16, 32, 3, 16, 40), (32, 32, 5, 24, 80)]
+    ctx = X.Context(0)
+    data = [_basis(X, ctx, H, W, n_q, k, 500 + i) for i, (H, W, n_q, k, _) in enumerate(shapes)]
+    Wl = [sh[4] for sh in shapes]
+    # stream 0 alone
+    sv = X.Server(ctx)
+    a = sv.open(data[0][3], Wl[0], 8)
+    assert sv.poll(a, _feed(sv, a, data[0][0], 7), 20000)
+    g_alone, c_alone = sv.read_g2(a)
+    sv.close()
+    # all three streams at once, fed from three client threads
+    sv = X.Server(ctx)
+    ids = [sv.open(d[3], w, 8) for d, w in zip(data, Wl)]
+    tickets = [0, 0, 0]
+
+    def client(i):
+        tickets[i] = _feed(sv, ids[i], data[i][0], 3 + 4 * i)
+
+    th = [threading.Thread(target=client, args=(i,)) for i in range(3)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for i in range(3):
+        assert sv.poll(ids[i], tickets[i], 20000)
+    g_mix, c_mix = sv.read_g2(ids[0])
+    np.testing.assert_array_equal(c_mix, c_alone)
+    ok = ~np.isnan(g_alone)
+    np.testing.assert_allclose(g_mix[ok], g_alone[ok], rtol=1e-6)
+    # every stream against the oracle
+    for i, (d, w) in enumerate(zip(data, Wl)):
+        frames, B, qmap, _ = d
+        n_q = shapes[i][2]
+        G, s, Mq = O.ring_factors(B, qmap, n_q)
+        C, _ = O.compressed_twotime(O.encode(frames, B), G, s, Mq)
+        g2, cnt = sv.read_g2(ids[i])
+        for q in range(n_q):
+            gr, cr = O.windowed_g2(C[q], w)
+            np.testing.assert_array_equal(cnt[q], cr[:w])
+            rm, _ = rel_errors(g2[q], gr[:w])
+            assert rm < 1e-4, (i, q, rm)
+        lat = sv.latency(ids[i])
+        assert lat["frames"] == len(frames) and lat["p99_us"] > 0
+    assert sv.batches() < sum(len(d[0]) for d in data)  # frames were batched
+    sv.close()
+
+
+def test_admission_waits_for_memory(X):
+    probe = X.Context(0)
+    frames, B, qmap, basis = _basis(X, probe, 32, 32, 4, 16, 9)
+    sv = X.Server(probe)
+    s = sv.open(basis, 30000, 8)
+    one = probe.device_bytes()
+    sv.close_stream(s)
+    base = probe.device_bytes()
+    sv.close()
+    probe.close()
+    ctx = X.Context(0, hbm_budget=base + 2 * (one - base) + (one - base) // 2)
+    frames, B, qmap, basis = _basis(X, ctx, 32, 32, 4, 16, 9)
+    sv = X.Server(ctx)
+    a = sv.open(basis, 30000, 8)
+    b = sv.open(basis, 30000, 8)
+    with pytest.raises(X.XpcsError) as e:
+        sv.open(basis, 30000, 8, wait_ms=0)
+    assert e.value.status == X.XPCS_EBUSY
+    got = {}
+
+    def opener():
+        got["s"] = sv.open(basis, 30000, 8, wait_ms=20000)  # admitted when memory frees up
+
+    th = threading.Thread(target=opener)
+    th.start()
+    sv.submit(a, frames[:20])
+    sv.close_stream(a)
+    th.join(30)
+    assert "s" in got
+    t = sv.submit(got["s"], frames[:16])
+    assert sv.poll(got["s"], t, 20000)
+    g2, cnt = sv.read_g2(got["s"])
+    assert cnt[0, 0] > 0
+    sv.close()
