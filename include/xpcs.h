@@ -152,6 +152,29 @@ xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A,
  * triangle of C (n_q x T x T float32).  g2_out n_q x T f64, count_out nullable. */
 xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out, int64_t* count_out);
 
+/* ------------------------------------------------------------------ g2 over a stored C, no allocation
+ * The paper has no counterpart to this call: it is a library convenience.
+ * Same arguments, layout and result as xpcs_g2 (up to the order of the f64 partial
+ * sums), but it allocates no device memory while it runs: its partial sums live in one
+ * fixed array of XPCS_G2_NOALLOC_MAX_CELLS x 16 bytes (16 MiB) per device, part of the
+ * library's image, instead of the context's scratch, which xpcs_g2 grows with cudaMalloc.
+ * For callers that must not allocate while they run, e.g. a loop whose HBM is all
+ * handed out under a budget, or one that cannot take the device-wide synchronisation a
+ * cudaFree may imply.
+ *   - n_q * T must not exceed XPCS_G2_NOALLOC_MAX_CELLS; larger calls return
+ *     XPCS_ERANGE (with a message in xpcs_last_error) and launch nothing.
+ *   - The first call on each device does a one-time set-up (finds the array's device
+ *     address and loads the kernels, which the CUDA runtime may do by allocating):
+ *     make it at start-up, before any stream capture and before the caller's
+ *     no-allocation region.  Later calls only launch two kernels on the context's stream.
+ *   - Nothing needs to start at zero: every call overwrites the partial sums it reads.
+ *   - The array is shared by every call on a device: calls that can run at the same time
+ *     (on different CUDA streams or contexts of one device) race on it and give wrong
+ *     results.  Calls on one CUDA stream are ordered and safe. */
+#define XPCS_G2_NOALLOC_MAX_CELLS (1 << 20)
+xpcs_status xpcs_g2_noalloc(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out,
+                            int64_t* count_out);
+
 /* ------------------------------------------------------------------ online stream (Sec. 2.2, Fig. 1c)
  * Online compression with a basis fit before acquisition: every pushed frame is encoded
  * (a_t = x_t V_K, sparse: only nonzero pixels read their basis row, f32), appended to a

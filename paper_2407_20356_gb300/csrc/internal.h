@@ -106,6 +106,9 @@ cudaError_t launch_g2_from_C(const float* C, int n_q, long long T, double* parti
                              long long* cnt_partial, cudaStream_t st);
 cudaError_t launch_g2_from_C_reduce(const double* partial, const long long* cnt_partial, int n_q, long long T,
                                     int row_splits, double* g2, long long* count, cudaStream_t st);
+// Loads the two g2-over-C kernels into the current device's context (lazy module
+// loading would otherwise do it, and may allocate, at their first launch).
+cudaError_t preload_g2_from_C();
 
 // ------------------------------------------------------------------ encode
 

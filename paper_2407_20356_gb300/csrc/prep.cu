@@ -442,4 +442,11 @@ cudaError_t launch_g2_from_C_reduce(const double* partial, const long long* cnt_
   return cudaGetLastError();
 }
 
+cudaError_t preload_g2_from_C() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, g2_from_C_kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncGetAttributes(&a, g2_from_C_reduce_kernel);
+}
+
 }  // namespace xpcs

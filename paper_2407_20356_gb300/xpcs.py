@@ -57,6 +57,7 @@ _SIGS = {
     "xpcs_encode": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
     "xpcs_g2": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
+    "xpcs_g2_noalloc": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_stream_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.POINTER(vp)]),
     "xpcs_stream_push": (C.c_int, [vp, vp, i64, C.POINTER(C.c_uint64)]),
     "xpcs_stream_push_device": (C.c_int, [vp, vp, i64, C.POINTER(C.c_uint64)]),
@@ -271,6 +272,14 @@ def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None,
 
 def xpcs_g2(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
     ctx.check(_lib.xpcs_g2(ctx.h, _ptr(C_in), n_q, T, _ptr(g2_out), _ptr(count_out)))
+
+
+G2_NOALLOC_MAX_CELLS = 1 << 20  # n_q * T limit of xpcs_g2_noalloc (its fixed scratch)
+
+
+def xpcs_g2_noalloc(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
+    """xpcs_g2 with its scratch in a fixed per-device array: allocates no device memory."""
+    ctx.check(_lib.xpcs_g2_noalloc(ctx.h, _ptr(C_in), n_q, T, _ptr(g2_out), _ptr(count_out)))
 
 
 class Stream:

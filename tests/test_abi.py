@@ -43,3 +43,12 @@ def test_binding_declares_the_header_functions():
 
     assert sorted(xpcs.declared_symbols()) == header_functions()
     assert xpcs.xpcs_version() >= 100
+
+
+def test_binding_constants_match_the_header():
+    _ensure_built()
+    from paper_2407_20356_gb300 import xpcs
+
+    src = open(HEADER).read()
+    m = re.search(r"#define\s+XPCS_G2_NOALLOC_MAX_CELLS\s+\(1 << (\d+)\)", src)
+    assert m and xpcs.G2_NOALLOC_MAX_CELLS == 1 << int(m.group(1))
