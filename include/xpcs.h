@@ -197,6 +197,13 @@ xpcs_status xpcs_stream_push(xpcs_stream* s, const void* frames_host, int64_t n_
 /* Push n frames already in device memory (the buffer must stay valid until the ticket
  * completes). */
 xpcs_status xpcs_stream_push_device(xpcs_stream* s, const void* frames, int64_t n_frames, uint64_t* ticket);
+/* As xpcs_stream_push_device, with each frame's arrival time: arrive_ns_host holds
+ * n_frames values of xpcs_clock_ns (e.g. when the detector delivered the frame), and the
+ * latency statistics count from there instead of from the call. */
+xpcs_status xpcs_stream_push_device_at(xpcs_stream* s, const void* frames, int64_t n_frames,
+                                       const int64_t* arrive_ns_host, uint64_t* ticket);
+/* The host steady clock of the latency statistics, in nanoseconds. */
+int64_t xpcs_clock_ns(void);
 /* XPCS_OK once every frame up to `ticket` is folded into the sums; XPCS_EBUSY if not
  * within timeout_ms (0 = just check). */
 xpcs_status xpcs_stream_poll(xpcs_stream* s, uint64_t ticket, int timeout_ms);

@@ -18,7 +18,7 @@
 //   warp 0      TMA producer: 64-wide K chunks of the L and R row blocks, NSTAGE ring
 //   warp 1      TMEM allocator and MMA issuer: 128x128 f32 accumulator, 2 TMEM buffers
 //   warps 2..5  drain: TMEM -> registers -> C store
-//   warps 6..13 TMEM -> skewed shared tile -> diagonal sums
+//   warps 6..13 TMEM -> registers -> per-warp skewed 32x32 blocks -> diagonal sums
 // Any warp may read the TMEM lanes of its quarter (warp id mod 4), so both groups read
 // the accumulator independently; they meet only at the TMEM full/empty barriers, and the
 // C stores of one tile overlap the diagonal pass of another.
@@ -29,10 +29,14 @@
 // C store: C is symmetric, so tile (I, J >= I) is written transposed into the lower
 // triangle, straight from registers and fully coalesced.
 //
-// Skewed tile: element (i, j) of the tile is written to shared row i, column
-// 128 - i + j.  Column c then holds the tile diagonal j - i = c - 128 (c >= 128: upper
-// diagonals 0..127; c < 128: lower diagonals -128..-1).  Cells a row never writes stay
-// zero, so summing a column over a warp-uniform row range gives the diagonal sum.
+// Diagonal sums: a diagonal warp holds 32 tile rows (its lane quarter) x 64 columns and
+// treats them as two 32x32 blocks.  Lane i writes row i of a block rotated by i into the
+// warp's own 32x32 shared buffer, P[i][(j - i) mod 32] = C(i, j), then lane d sums column
+// d of P: rows i < 32 - d hold block diagonal j - i = d, rows i >= 32 - d hold j - i =
+// d - 32.  Both the writes and the reads touch 32 distinct banks.  The warps need no
+// barrier per tile; the eight warps' per-lane sums meet once per work item, added in a
+// fixed order.
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -43,14 +47,15 @@ namespace {
 constexpr int NSTAGE = 3;
 constexpr int CHUNK_BYTES = TILE * KCH * 2;        // one operand chunk: 128 rows x 128 B
 constexpr int STAGE_BYTES = 2 * CHUNK_BYTES;       // L + R
-constexpr int SKEW_LD = 258;                       // floats per skewed row (257 = 1 mod 32)
-constexpr int SKEW_BYTES = TILE * SKEW_LD * 4;
 constexpr int N_DIAG_WARPS = 8;
+constexpr int PRIV_FLOATS = 32 * 32;                   // one warp's rotated 32x32 block
+constexpr int RED_FLOATS = N_DIAG_WARPS * 3 * 32;      // per-warp sums of a work item
+constexpr int DIAG_BYTES = (N_DIAG_WARPS * PRIV_FLOATS + RED_FLOATS) * 4;
 constexpr int GRAM_THREADS = 64 + 4 * 32 + N_DIAG_WARPS * 32;  // producer, MMA, 4 drain, 8 diagonal warps
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + SKEW_BYTES + BAR_BYTES;
+constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + DIAG_BYTES + BAR_BYTES;
 constexpr uint32_t TMEM_COLS = 256;                // two 128-column accumulators
-constexpr int DIAG_BAR = 1;                        // named barrier of the four diagonal warps
+constexpr int DIAG_BAR = 1;                        // named barrier of the eight diagonal warps
 
 // Stores one 32-column chunk of a tile row: element (i, j) of tile (I, J) is C(t1, t2)
 // with t1 = 128 I + i, t2 = 128 J + j, written transposed at [t2][t1] (lower triangle) so
@@ -98,8 +103,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stages = smem;
-  float* skew = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES + SKEW_BYTES);
+  float* diag_smem = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES + DIAG_BYTES);
   uint64_t* full = bars;                    // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;          // [NSTAGE]
   uint64_t* tfull = bars + 2 * NSTAGE;      // [2]
@@ -128,7 +133,6 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     tmem_alloc(tmem_slot, TMEM_COLS);
     tmem_relinquish();
   }
-  for (int i = threadIdx.x; i < TILE * SKEW_LD; i += blockDim.x) skew[i] = 0.f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -285,112 +289,97 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     }
   } else if (p.partials) {
     // ------------------------------------------------------------ diagonal warps (6..13)
-    // Warps dw and dw + 4 share a TMEM lane quarter (warp id mod 4): each copies half of the
-    // quarter's 32 tile rows' columns into the skewed shared tile.  After the eight warps
-    // meet, warp dw reduces skew columns 32 g + lane (lower diagonals, rows
-    // [97 - 32 g, 128)) and 128 + 32 g + lane (upper diagonals, rows [0, 128 - 32 g)),
-    // g = dw mod 4, over every other row starting at dw / 4: together 159 rows per g.
-    // Cells outside a row's band are never written and stay zero, so the warp-uniform
-    // row ranges give exact diagonal sums.
-    const int dw = warp - 6;              // 0..7
-    const int quarter = warp & 3;
-    const int half = dw >> 2;             // column half copied, row parity reduced
-    const int i_row = quarter * 32 + lane;
-    const int g = dw & 3;
-    const float* col_lo = skew + 32 * g + lane;
-    const float* col_hi = skew + TILE + 32 * g + lane;
-    float* dst_row = skew + i_row * SKEW_LD + TILE - i_row + 64 * half;
-    const int lo0 = 97 - 32 * g + half;
-    const int hi1 = TILE - 32 * g;
+    // Warp dw (0..7) covers TMEM lane quarter r = warp mod 4 (tile rows 32 r ..) and
+    // column half h = dw / 4 (blocks b = 2 h, 2 h + 1).  Block b's sums land on tile
+    // diagonals 32 (b - r) + d (rows i < 32 - d) and 32 (b - r - 1) + d (the others), so
+    // the warp keeps three per-lane sums, for e = 2 h - r - 1 + k (k = 0, 1, 2), diagonal
+    // 32 e + lane.
+    const int dw = warp - 6;
+    const int r = warp & 3;
+    const int h = dw >> 2;
+    float* P = diag_smem + dw * PRIV_FLOATS;
+    float* red = diag_smem + N_DIAG_WARPS * PRIV_FLOATS;  // [warp][k][lane]
+    const int i_row = r * 32 + lane;
+    const int lim = 32 - lane;  // rows of P whose column `lane` lies on the block diagonal d = lane
     uint32_t tile = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
       const int4 w = p.items[item];
       const int q = w.x, delta = w.y;
       const float* rq = p.r + (size_t)q * p.T_pad;
-      float acc_lo = 0.f, acc_hi = 0.f;
-      for (int I = w.z; I < w.w; ++I, ++tile) {
+      float acc[3] = {0.f, 0.f, 0.f};
+      for (int I = w.z; I < w.w && ok; ++I, ++tile) {
         const int J = I + delta;
         const uint32_t b = tile & 1, tph = (tile >> 1) & 1;
         const float ri = p.raw ? rq[(size_t)I * TILE + i_row] : 1.f;
-        const bool okw = mbar_wait_warp(&tfull[b], tph, p.status);
-        if (!okw) *abort_flag = 1;
-        named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);  // skew buffer free (previous tile reduced)
-        if (*abort_flag) {
+        if (*abort_flag || !mbar_wait_warp(&tfull[b], tph, p.status)) {  // warp-uniform outcome
+          *abort_flag = 1;
           ok = false;
           break;
         }
         tc_fence_after();
-        {
-          const uint32_t tbase = tmem_base + b * TILE + ((uint32_t)(quarter * 32) << 16) + 64 * half;
-          uint32_t v0[32], v1[32];
-          tmem_ld32(tbase, v0);
-          tmem_ld32(tbase + 32, v1);
+        // one 32-column block at a time; TMEM is released once block 1 is in registers
+        const uint32_t tbase = tmem_base + b * TILE + ((uint32_t)(r * 32) << 16) + 64 * h;
+        const float* rj = rq + (size_t)J * TILE + 64 * h;
+#pragma unroll
+        for (int sb = 0; sb < 2; ++sb) {
+          uint32_t v[32];
+          tmem_ld32(tbase + 32 * sb, v);
           tc_wait_ld();
+          if (sb == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+          }
           if (p.raw) {
-            const float* rj = rq + (size_t)J * TILE + 64 * half;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
+          }
+          __syncwarp();  // the previous block's reads are done
+          {
+            // rotated row: column (j - lane) mod 32, walked with one running offset
+            float* prow = P + lane * 32;
+            int c = (32 - lane) & 31;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              v0[j] = __float_as_uint((__uint_as_float(v0[j]) * ri) * __ldg(rj + j));
-              v1[j] = __float_as_uint((__uint_as_float(v1[j]) * ri) * __ldg(rj + 32 + j));
+              prow[c] = __uint_as_float(v[j]);
+              c = (c + 1) & 31;
             }
           }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            dst_row[j] = __uint_as_float(v0[j]);
-            dst_row[32 + j] = __uint_as_float(v1[j]);
+          __syncwarp();
+          float an = 0.f, aw = 0.f;
+#pragma unroll 8
+          for (int i = 0; i < 32; ++i) {
+            const float x = P[i * 32 + lane];
+            if (i < lim)
+              an += x;
+            else
+              aw += x;
           }
+          acc[sb + 1] += an;  // e = b - r
+          acc[sb] += aw;      // e = b - r - 1
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[b]);
-        named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);  // skew buffer complete
-        float sl[8], sh[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) sl[u] = sh[u] = 0.f;
-        int i = lo0;
-        for (; i + 14 < TILE; i += 16) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) sl[u] += col_lo[(i + 2 * u) * SKEW_LD];
-        }
-        for (; i < TILE; i += 2) sl[0] += col_lo[i * SKEW_LD];
-        for (i = half; i + 14 < hi1; i += 16) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) sh[u] += col_hi[(i + 2 * u) * SKEW_LD];
-        }
-        for (; i < hi1; i += 2) sh[0] += col_hi[i * SKEW_LD];
-#pragma unroll
-        for (int u = 1; u < 8; ++u) {
-          sl[0] += sl[u];
-          sh[0] += sh[u];
-        }
-        acc_lo += sl[0];
-        acc_hi += sh[0];
       }
-      if (!ok) break;
-      // combine the two row parities of each column group through the (free) skew buffer
-      // cells of row 0 outside its band, then restore them to zero
+      // every diagonal warp reaches these barriers once per item, also after an abort
+      // (each of its waits is bounded), so none is left waiting
+#pragma unroll
+      for (int k = 0; k < 3; ++k) red[(dw * 3 + k) * 32 + lane] = acc[k];
       named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
-      float* red = skew;  // row 0, columns 0..127 lie outside row 0's band [128, 256)
-      if (half) {
-        red[32 * g + lane] = acc_lo;
-      }
-      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
-      if (!half) acc_lo += red[32 * g + lane];
-      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
-      if (half) {
-        red[32 * g + lane] = acc_hi;
-      }
-      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
-      if (!half) {
-        acc_hi += red[32 * g + lane];
+      if (ok && !*abort_flag) {
+        // warp dw finishes diagonals 32 (dw - 4) + lane, adding the warps in a fixed order
+        const int e = dw - 4;
+        float sum = 0.f;
+#pragma unroll
+        for (int u = 0; u < N_DIAG_WARPS; ++u) {
+          const int k = e - (2 * (u >> 2) - ((u + 6) & 3) - 1);
+          if (k >= 0 && k < 3) sum += red[(u * 3 + k) * 32 + lane];
+        }
         const int chunk = w.z / p.CH;
         float* slot = p.partials + (((size_t)q * p.nT + delta) * p.maxC + chunk) * DIAG_SLOTS;
-        slot[32 * g + lane] = acc_lo;
-        slot[TILE + 32 * g + lane] = acc_hi;
+        slot[32 * dw + lane] = sum;
       }
-      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
-      if (half) red[32 * g + lane] = 0.f;
+      named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);  // red is free again
+      if (!ok || *abort_flag) break;
     }
   }
 

@@ -4,6 +4,7 @@
 
 #include <mutex>
 #include <string>
+#include <deque>
 #include <vector>
 
 #include "internal.h"
@@ -105,15 +106,23 @@ struct xpcs_stream {
   cudaEvent_t stage_done[2] = {nullptr, nullptr};
   int stage_i = 0;
   int dtype = -1;
-  std::vector<std::pair<uint64_t, cudaEvent_t>> tickets;  // (last frame + 1, event)
-  std::vector<cudaEvent_t> event_pool;
-  // per-batch latency stamps: push time and completion time (host steady clock, ns),
-  // the latter written by a host function queued behind the batch
+  // per-batch latency stamps: arrival and completion times (host steady clock, ns)
   struct Stamp {
     std::vector<int64_t> arrive_ns;  // one per frame of the batch
-    volatile int64_t done_ns = 0;
+    int64_t done_ns = 0;             // 0 while the batch is in flight
   };
+  struct Ticket {
+    uint64_t frames;  // frames pushed up to and including this batch
+    cudaEvent_t ev;   // recorded behind the batch's kernels (timing enabled)
+    Stamp* stamp;
+  };
+  std::deque<Ticket> tickets;
+  std::vector<cudaEvent_t> event_pool;
   std::vector<Stamp*> stamps;
+  // completion times come from CUDA event timing relative to a base event whose host
+  // time is known: done_ns = base_ns + elapsed(base_ev, ev)
+  cudaEvent_t base_ev = nullptr;
+  int64_t base_ns = 0;
 };
 
 namespace xpcs {

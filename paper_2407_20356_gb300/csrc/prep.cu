@@ -16,8 +16,11 @@ constexpr int MAX_RINGS_SMEM = 1024;
 // (exact for counts <= 256) and accumulates S_q(t) = sum of counts and the sum of squares
 // per ring (Eq. 1 denominators and the exactness bound of the f32 Gram).
 // Each warp step covers 64 consecutive sorted positions (2 per lane).  Ring segments
-// start at multiples of 64, so those 64 positions belong to one ring (or its padding):
-// the warp reduces its counts with shuffles and issues one shared atomic per step.
+// start at multiples of 64, so those 64 positions belong to one ring (or its padding),
+// which the first position names: the warp reduces its counts with shuffles and issues
+// one shared atomic per step.  A warp issues the loads of RI_U steps before using any of
+// them, so that enough gathers are in flight to cover the memory latency.
+constexpr int RI_U = 4;
 __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p) {
   __shared__ unsigned long long ssum[MAX_RINGS_SMEM];
   __shared__ unsigned long long ssq[MAX_RINGS_SMEM];
@@ -32,32 +35,49 @@ __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p
   bool too_big = false;
   const uint8_t* x8 = static_cast<const uint8_t*>(p.X) + t * p.M;
   const uint16_t* x16 = static_cast<const uint16_t*>(p.X) + t * p.M;
-  for (long long base = (long long)warp * 64; base < p.Mp; base += 64 * 8) {
-    const long long o = base + 2 * lane;
-    const int2 src = *reinterpret_cast<const int2*>(p.perm + o);
-    unsigned x0 = 0, x1 = 0;
-    if (live) {
-      if (src.x >= 0) x0 = p.dtype == 0 ? (unsigned)x8[src.x] : (unsigned)x16[src.x];
-      if (src.y >= 0) x1 = p.dtype == 0 ? (unsigned)x8[src.y] : (unsigned)x16[src.y];
+  for (long long base = (long long)warp * 64 * RI_U; base < p.Mp; base += 64 * RI_U * 8) {
+    int2 src[RI_U];
+    int qs[RI_U];
+#pragma unroll
+    for (int u = 0; u < RI_U; ++u) {
+      const long long o = base + 64 * u + 2 * lane;
+      const bool in = base + 64 * u < p.Mp;
+      src[u] = in ? *reinterpret_cast<const int2*>(p.perm + o) : make_int2(-1, -1);
+      qs[u] = in ? p.pos_ring[base + 64 * u] : -1;
     }
-    const bool big = (x0 > 256u) | (x1 > 256u);
-    too_big |= big;
-    if (p.Xp) {
-      __nv_bfloat162 v = __floats2bfloat162_rn((float)x0, (float)x1);
-      *reinterpret_cast<__nv_bfloat162*>(p.Xp + t * p.Mp + o) = v;
-    }
-    const int q = __reduce_max_sync(0xffffffffu, max(p.pos_ring[o], p.pos_ring[o + 1]));
-    if (q < 0) continue;
-    if (!__any_sync(0xffffffffu, big)) {
-      const unsigned s = __reduce_add_sync(0xffffffffu, x0 + x1);
-      const unsigned s2 = __reduce_add_sync(0xffffffffu, x0 * x0 + x1 * x1);
-      if (lane == 0 && s) {
-        atomicAdd(&ssum[q], (unsigned long long)s);
-        atomicAdd(&ssq[q], (unsigned long long)s2);
+    unsigned x0[RI_U], x1[RI_U];
+#pragma unroll
+    for (int u = 0; u < RI_U; ++u) {
+      x0[u] = 0;
+      x1[u] = 0;
+      if (live) {
+        if (src[u].x >= 0) x0[u] = p.dtype == 0 ? (unsigned)x8[src[u].x] : (unsigned)x16[src[u].x];
+        if (src[u].y >= 0) x1[u] = p.dtype == 0 ? (unsigned)x8[src[u].y] : (unsigned)x16[src[u].y];
       }
-    } else if (x0 | x1) {
-      atomicAdd(&ssum[q], (unsigned long long)x0 + x1);
-      atomicAdd(&ssq[q], (unsigned long long)x0 * x0 + (unsigned long long)x1 * x1);
+    }
+#pragma unroll
+    for (int u = 0; u < RI_U; ++u) {
+      const long long o = base + 64 * u + 2 * lane;
+      if (base + 64 * u >= p.Mp) break;  // warp-uniform
+      const bool big = (x0[u] > 256u) | (x1[u] > 256u);
+      too_big |= big;
+      if (p.Xp) {
+        __nv_bfloat162 v = __floats2bfloat162_rn((float)x0[u], (float)x1[u]);
+        *reinterpret_cast<__nv_bfloat162*>(p.Xp + t * p.Mp + o) = v;
+      }
+      const int q = qs[u];
+      if (q < 0) continue;
+      if (!__any_sync(0xffffffffu, big)) {
+        const unsigned s = __reduce_add_sync(0xffffffffu, x0[u] + x1[u]);
+        const unsigned s2 = __reduce_add_sync(0xffffffffu, x0[u] * x0[u] + x1[u] * x1[u]);
+        if (lane == 0 && s) {
+          atomicAdd(&ssum[q], (unsigned long long)s);
+          atomicAdd(&ssq[q], (unsigned long long)s2);
+        }
+      } else if (x0[u] | x1[u]) {
+        atomicAdd(&ssum[q], (unsigned long long)x0[u] + x1[u]);
+        atomicAdd(&ssq[q], (unsigned long long)x0[u] * x0[u] + (unsigned long long)x1[u] * x1[u]);
+      }
     }
   }
   if (too_big && p.Xp) set_status(p.status, XPCS_DEV_RANGE);

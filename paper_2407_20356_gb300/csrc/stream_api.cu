@@ -23,7 +23,6 @@ int64_t now_ns() {
 
 namespace {
 
-void CUDART_CB stamp_done(void* p) { static_cast<xpcs_stream::Stamp*>(p)->done_ns = now_ns(); }
 
 int ka_of(int k) { return (k + 31) / 32 * 32; }
 int nqp_of(int n_q) { return (n_q + 11) / 12 * 12; }
@@ -68,9 +67,13 @@ void stream_free(xpcs_stream* S) {
     if (S->h_stage[i]) cudaFreeHost(S->h_stage[i]);
     if (S->stage_done[i]) cudaEventDestroy(S->stage_done[i]);
   }
-  for (auto& t : S->tickets) cudaEventDestroy(t.second);
+  for (auto& t : S->tickets) {
+    cudaEventDestroy(t.ev);
+    if (t.stamp && !t.stamp->done_ns) delete t.stamp;  // not yet handed to `stamps`
+  }
   for (auto e : S->event_pool) cudaEventDestroy(e);
   for (auto st : S->stamps) delete st;
+  if (S->base_ev) cudaEventDestroy(S->base_ev);
   if (S->stream) cudaStreamDestroy(S->stream);
   delete S;
 }
@@ -87,6 +90,22 @@ size_t stream_footprint(const xpcs_basis* B, int64_t W, int max_batch, int elem_
 }
 
 }  // namespace xpcs
+
+namespace {
+
+// Host time of the base event: record it on the idle stream and watch it complete
+// (bounded to one second); completion is seen within the polling interval.
+cudaError_t calibrate_clock(xpcs_stream* S) {
+  cudaError_t e = cudaEventRecord(S->base_ev, S->stream);
+  if (e != cudaSuccess) return e;
+  const int64_t t_end = now_ns() + 1000000000ll;
+  while ((e = cudaEventQuery(S->base_ev)) == cudaErrorNotReady)
+    if (now_ns() > t_end) return cudaErrorNotReady;
+  S->base_ns = now_ns();
+  return e;
+}
+
+}  // namespace
 
 extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int64_t history, int max_batch,
                                         xpcs_dtype dtype, xpcs_stream** out) {
@@ -148,6 +167,8 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_g2sum, 0, z.g2sum, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_cnt, 0, z.cnt, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaEventCreate(&S->base_ev);
+  if (st == XPCS_OK && e == cudaSuccess) e = calibrate_clock(S);
   if (st == XPCS_OK && e != cudaSuccess) st = fail(ctx, XPCS_ECUDA, std::string("stream setup: ") + cudaGetErrorString(e));
   if (st != XPCS_OK) {
     stream_free(S);
@@ -167,8 +188,37 @@ cudaEvent_t take_event(xpcs_stream* S) {
     return e;
   }
   cudaEvent_t e = nullptr;
-  cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
   return e;
+}
+
+// Retire the completed batches at the front of the ticket queue: their completion time
+// from the event timing, their event back to the pool.  A base older than five seconds is
+// replaced by a retired event (keeps the f32 millisecond differences fine-grained).
+xpcs_status retire(xpcs_stream* S) {
+  while (!S->tickets.empty()) {
+    xpcs_stream::Ticket& tk = S->tickets.front();
+    const cudaError_t q = cudaEventQuery(tk.ev);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) return fail(S->ctx, XPCS_ECUDA, std::string("stream: ") + cudaGetErrorString(q));
+    float ms = 0.f;
+    const cudaError_t e = cudaEventElapsedTime(&ms, S->base_ev, tk.ev);
+    if (e != cudaSuccess) return fail(S->ctx, XPCS_ECUDA, std::string("stream timing: ") + cudaGetErrorString(e));
+    const int64_t done = S->base_ns + (int64_t)((double)ms * 1e6);
+    if (tk.stamp) {
+      tk.stamp->done_ns = done > 0 ? done : 1;
+      S->stamps.push_back(tk.stamp);
+    }
+    if (done - S->base_ns > 5000000000ll) {
+      S->event_pool.push_back(S->base_ev);
+      S->base_ev = tk.ev;
+      S->base_ns = done;
+    } else {
+      S->event_pool.push_back(tk.ev);
+    }
+    S->tickets.pop_front();
+  }
+  return XPCS_OK;
 }
 
 // Enqueue one batch whose counts are already on the device.
@@ -198,19 +248,24 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.g2sum = S->d_g2sum;
   s.cnt = S->d_cnt;
   cudaError_t e = launch_stream_step(s, S->stream);
-  if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream step: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    delete stamp;
+    return fail(ctx, XPCS_ECUDA, std::string("stream step: ") + cudaGetErrorString(e));
+  }
   ctx->launches += 4;
   S->frames += n;
-  if (stamp) {
-    e = cudaLaunchHostFunc(S->stream, stamp_done, stamp);
-    if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream stamp: ") + cudaGetErrorString(e));
-    S->stamps.push_back(stamp);
-  }
   cudaEvent_t ev = take_event(S);
+  if (!ev) {
+    delete stamp;
+    return fail(ctx, XPCS_ECUDA, "stream event: cudaEventCreate failed");
+  }
   e = cudaEventRecord(ev, S->stream);
-  if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream event: ") + cudaGetErrorString(e));
-  S->tickets.push_back({(uint64_t)S->frames, ev});
-  return XPCS_OK;
+  if (e != cudaSuccess) {
+    delete stamp;
+    return fail(ctx, XPCS_ECUDA, std::string("stream event: ") + cudaGetErrorString(e));
+  }
+  S->tickets.push_back({(uint64_t)S->frames, ev, stamp});
+  return retire(S);
 }
 
 }  // namespace
@@ -259,38 +314,51 @@ extern "C" xpcs_status xpcs_stream_push(xpcs_stream* S, const void* frames_host,
   return XPCS_OK;
 }
 
-extern "C" xpcs_status xpcs_stream_push_device(xpcs_stream* S, const void* frames, int64_t n_frames,
-                                               uint64_t* ticket) {
+namespace {
+
+xpcs_status push_device(xpcs_stream* S, const void* frames, int64_t n_frames, const int64_t* arrive_ns,
+                        uint64_t* ticket) {
   if (!S || !frames || n_frames < 0) return XPCS_EINVAL;
   xpcs_ctx* ctx = S->ctx;
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const size_t fb = (size_t)S->basis->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
+  const int64_t t = now_ns();
   for (int64_t off = 0; off < n_frames; off += S->max_batch) {
     const int64_t n = std::min<int64_t>(S->max_batch, n_frames - off);
     auto* stamp = new xpcs_stream::Stamp();
-    stamp->arrive_ns.assign(n, now_ns());
+    if (arrive_ns)
+      stamp->arrive_ns.assign(arrive_ns + off, arrive_ns + off + n);
+    else
+      stamp->arrive_ns.assign(n, t);
     XPCS_TRY(enqueue_batch(S, static_cast<const char*>(frames) + off * fb, n, stamp));
   }
   if (ticket) *ticket = (uint64_t)S->frames;
   return XPCS_OK;
 }
 
+}  // namespace
+
+extern "C" xpcs_status xpcs_stream_push_device(xpcs_stream* S, const void* frames, int64_t n_frames,
+                                               uint64_t* ticket) {
+  return push_device(S, frames, n_frames, nullptr, ticket);
+}
+
+extern "C" xpcs_status xpcs_stream_push_device_at(xpcs_stream* S, const void* frames, int64_t n_frames,
+                                                  const int64_t* arrive_ns_host, uint64_t* ticket) {
+  if (!arrive_ns_host) return XPCS_EINVAL;
+  return push_device(S, frames, n_frames, arrive_ns_host, ticket);
+}
+
+extern "C" int64_t xpcs_clock_ns(void) { return now_ns(); }
+
 extern "C" xpcs_status xpcs_stream_poll(xpcs_stream* S, uint64_t ticket, int timeout_ms) {
   if (!S) return XPCS_EINVAL;
   xpcs_ctx* ctx = S->ctx;
   const int64_t t_end = now_ns() + (int64_t)std::max(0, timeout_ms) * 1000000;
   while (true) {
-    // retire completed tickets in order
-    size_t done = 0;
-    for (; done < S->tickets.size(); ++done) {
-      cudaError_t e = cudaEventQuery(S->tickets[done].second);
-      if (e == cudaErrorNotReady) break;
-      if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
-    }
-    for (size_t i = 0; i < done; ++i) S->event_pool.push_back(S->tickets[i].second);
-    if (done) S->tickets.erase(S->tickets.begin(), S->tickets.begin() + done);
+    XPCS_TRY(retire(S));
     // tickets are increasing: none pending at or below `ticket` means its frames are in
-    if (S->tickets.empty() || S->tickets.front().first > ticket) return XPCS_OK;
+    if (S->tickets.empty() || S->tickets.front().frames > ticket) return XPCS_OK;
     if (now_ns() >= t_end) return XPCS_EBUSY;
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
@@ -317,6 +385,7 @@ extern "C" int64_t xpcs_stream_frames(const xpcs_stream* S) { return S ? S->fram
 extern "C" xpcs_status xpcs_stream_latency(xpcs_stream* S, int reset, double* p50_us, double* p99_us,
                                            double* max_us, int64_t* n_batches) {
   if (!S) return XPCS_EINVAL;
+  XPCS_TRY(retire(S));
   std::vector<double> lat;
   std::vector<xpcs_stream::Stamp*> keep;
   for (auto* st : S->stamps) {

@@ -61,6 +61,8 @@ _SIGS = {
     "xpcs_stream_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.POINTER(vp)]),
     "xpcs_stream_push": (C.c_int, [vp, vp, i64, C.POINTER(C.c_uint64)]),
     "xpcs_stream_push_device": (C.c_int, [vp, vp, i64, C.POINTER(C.c_uint64)]),
+    "xpcs_stream_push_device_at": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_uint64)]),
+    "xpcs_clock_ns": (i64, []),
     "xpcs_stream_poll": (C.c_int, [vp, C.c_uint64, C.c_int]),
     "xpcs_stream_read_g2": (C.c_int, [vp, vp, vp]),
     "xpcs_stream_frames": (i64, [vp]),
@@ -274,6 +276,11 @@ def xpcs_g2(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
     ctx.check(_lib.xpcs_g2(ctx.h, _ptr(C_in), n_q, T, _ptr(g2_out), _ptr(count_out)))
 
 
+def clock_ns() -> int:
+    """The library's host steady clock (ns), in which stream latencies are measured."""
+    return int(_lib.xpcs_clock_ns())
+
+
 G2_NOALLOC_MAX_CELLS = 1 << 20  # n_q * T limit of xpcs_g2_noalloc (its fixed scratch)
 
 
@@ -301,6 +308,15 @@ class Stream:
         on_device = hasattr(frames, "is_cuda") and frames.is_cuda
         f = _lib.xpcs_stream_push_device if on_device else _lib.xpcs_stream_push
         self.ctx.check(f(self.h, _ptr(frames), n, C.byref(t)))
+        return t.value
+
+    def push_at(self, frames, arrive_ns) -> int:
+        """Push device frames (n x M) with their arrival times (n int64 values of clock_ns())."""
+        t = C.c_uint64()
+        arr = np.ascontiguousarray(arrive_ns, dtype=np.int64)
+        n = int(frames.shape[0])
+        assert arr.shape == (n,)
+        self.ctx.check(_lib.xpcs_stream_push_device_at(self.h, _ptr(frames), n, arr.ctypes.data, C.byref(t)))
         return t.value
 
     def poll(self, ticket: int, timeout_ms: int = 0) -> bool:

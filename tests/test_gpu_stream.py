@@ -75,6 +75,24 @@ def test_stream_g2_matches_oracle(X, ctx, dtype, k, Wl, sizes):
     st.close()
 
 
+def test_stream_many_rings_and_lag_tiles(X, ctx):
+    # more rings than one row-update ring group (36) and several 128-lag tiles, batches
+    # longer than one window shift (16 frames)
+    H, W, n_q, k, T, Wl = 24, 24, 40, 24, 300, 260
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 200, np.uint16, 404, mean=1.0)
+    st = X.Stream(ctx, basis, Wl, 40)
+    for i, n in ((0, 37), (37, 1), (38, 40), (78, 222)):
+        ticket = st.push(np.ascontiguousarray(Xs[i:i + n]))
+    assert st.poll(ticket, 10000)
+    g2, cnt = st.read_g2()
+    g_ref, c_ref = _oracle_window_g2(Xs, B, qmap, n_q, Wl)
+    np.testing.assert_array_equal(cnt, c_ref)
+    for q in range(n_q):
+        rm, _ = rel_errors(g2[q], g_ref[q])
+        assert rm < 1e-4, (q, rm)
+    st.close()
+
+
 def test_stream_batching_and_device_push_agree(X, ctx):
     torch, dev = torch_cuda()
     H, W, n_q, k, T, Wl = 16, 32, 3, 24, 150, 40
@@ -89,6 +107,33 @@ def test_stream_batching_and_device_push_agree(X, ctx):
     np.testing.assert_array_equal(ca, cb)
     ok = ~np.isnan(ga)
     np.testing.assert_allclose(gb[ok], ga[ok], rtol=1e-6)
+
+
+def test_stream_push_at_counts_latency_from_arrival(X, ctx):
+    # frames stamped 20 ms in the past: every latency includes those 20 ms; results are
+    # those of an unstamped device push
+    torch, dev = torch_cuda()
+    H, W, n_q, k, T, Wl = 16, 16, 2, 16, 64, 32
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 80, np.uint16, 55)
+    Xd = torch.from_numpy(Xs).to(dev)
+    a = X.Stream(ctx, basis, Wl, 8)
+    b = X.Stream(ctx, basis, Wl, 8)
+    a.push(Xd)
+    t0 = X.clock_ns()
+    arrive = t0 - 20_000_000 + np.arange(T, dtype=np.int64) * 1000
+    ticket = b.push_at(Xd, arrive)
+    assert b.poll(ticket, 10000)
+    lat = b.latency(reset=True)
+    assert lat["batches"] == T
+    assert 20_000 - T < lat["p50_us"] <= lat["p99_us"] <= lat["max_us"]
+    assert lat["max_us"] < 20_000 + 10_000_000  # bounded by the poll timeout
+    ga, ca = a.read_g2()
+    gb, cb = b.read_g2()
+    np.testing.assert_array_equal(ca, cb)
+    ok = ~np.isnan(ga)
+    np.testing.assert_array_equal(gb[ok], ga[ok])
+    a.close()
+    b.close()
 
 
 def test_stream_matches_offline_twotime(X, ctx):
