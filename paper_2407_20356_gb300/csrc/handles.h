@@ -85,21 +85,25 @@ struct xpcs_stream {
   const xpcs_basis* basis = nullptr;
   cudaStream_t stream = nullptr;     // own CUDA stream: streams overlap on the device
   int64_t W = 0;                     // history window (lags kept)
-  int64_t cap = 0;                   // ring slots = W + max_batch
+  int64_t cap = 0;                   // ring slots = max(W + max_batch, 256)
   int max_batch = 0;
   int64_t frames = 0;                // frames enqueued so far
   int nblk = 0;                      // pixel slices of the sparse encode
   // device
   void* d_frames = nullptr;          // max_batch x M counts (u16 or u8)
-  float* d_Ah = nullptr;             // cap x k coefficient history
-  float* d_Rh = nullptr;             // cap x n_q  r_q(s) = sqrt(M_q)/S~_q(s), 0 if undefined
+  __nv_bfloat16* d_A2 = nullptr;     // (cap + 128) x 2 kpad coefficient history, bf16 hi | lo
+  float* d_Rh = nullptr;             // (cap + 128) x npad  r_q(s) = sqrt(M_q)/S~_q(s), 0 if undefined
+  unsigned long long* d_vbits = nullptr;  // n_q x vwords  validity bits r_q(s) > 0 per slot
   double* d_g2sum = nullptr;         // n_q x W
   long long* d_cnt = nullptr;        // n_q x W
   float* d_part = nullptr;           // max_batch x nblk x k sparse-encode partials
   float* d_a = nullptr;              // max_batch x k
-  float* d_w = nullptr;              // max_batch x n_q x k   r_q(t) a_t G_q
+  __nv_bfloat16* d_W2 = nullptr;     // (max_batch n_q) x 2 kpad  r_q(t) a_t G_q, bf16 hi | lo
   double* d_g2 = nullptr;            // n_q x W read-out buffer
-  uint32_t* d_status = nullptr;
+  int kpad = 0;                      // k rounded up to 64
+  CUtensorMap tmA, tmW, tmR;         // tensor maps of d_A2, d_W2 (64 x 128 boxes) and d_Rh
+  uint32_t* h_status = nullptr;      // host-mapped status word of the stream's kernels
+  uint32_t* d_status = nullptr;      // its device address
   size_t bytes = 0;
   // host
   void* h_stage[2] = {nullptr, nullptr};  // pinned staging, double-buffered

@@ -133,6 +133,7 @@ cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T
 struct StreamStep {
   const void* X;           // b x M counts (device)
   int dtype;               // 0 u8, 1 u16
+  int vec16;               // X and its rows are 16-byte aligned (vector loads allowed)
   long long M;
   int k, n_q, b;
   long long t0;            // index of the first frame of the batch
@@ -144,13 +145,73 @@ struct StreamStep {
   const long long* Mq;     // n_q
   float* part;             // b x nblk x k
   float* a;                // b x k
-  float* w;                // b x n_q x k
-  float* Ah;               // cap x k
-  float* Rh;               // cap x n_q
+  __nv_bfloat16* W2;       // (max_batch n_q) x 2 kpad: w_q(t) rows, bf16 hi | lo
+  __nv_bfloat16* A2;       // (cap + 128) x 2 kpad: coefficient history, bf16 hi | lo;
+                           // rows cap .. cap + 127 mirror rows 0 .. 127
+  int kpad;                // k rounded up to 64
+  long long w2_rows;       // rows allocated in W2
+  float* Rh;               // (cap + 128) x npad, rows cap .. cap + 127 mirror rows 0 .. 127
+  unsigned long long* vbits;  // n_q x vwords: bit s of ring q = r_q(slot s) > 0, slots
+                              // cap .. cap + 63 mirror slots 0 .. 63
+  long long vwords;
   double* g2sum;           // n_q x W
   long long* cnt;          // n_q x W
+  uint32_t* status;
+  int num_sms;
+  const CUtensorMap* tmA;  // host copies of the tensor maps of A2, W2 and Rh
+  const CUtensorMap* tmW;
+  const CUtensorMap* tmR;
 };
 cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st);
+
+// Row update of a step of at most 64 frames on the tensor cores (see stream_tc.cu).
+// W2 holds the step's w rows in pair order, per ring group rg (36 rings from q0 = 36 rg)
+// n_mt M-tiles of 128 rows starting at row rg n_mt 128; within M-tile mt, lane quarter w
+// (ring residue q mod 4) and lane l:
+//   small steps (b <= 8): mt = f, l = (q - q0) / 4 (lanes 0..8): one frame per M-tile, so
+//     no two lanes of a warp share a ring;
+//   larger steps: mt = qi nfb + fb (nfb = ceil(b / 32)), ring q = q0 + 4 qi + w, frame
+//     f = 32 fb + l: a warp holds 32 consecutive frames of one ring.
+constexpr int W2_SMALL_B = 8;
+struct RowTcParams {
+  long long t0, W, cap;
+  int b, n_q, kpad, n_kc, lt, wst, n_tiles;
+  int n_rg;  // ring groups of 36
+  int n_mt;  // M-tiles per ring group
+  int nfb;   // 32-frame blocks of the step
+  int npad;  // Rh row pitch (n_q rounded up to 4)
+  int qb;    // r values per history row loaded per item (min(36, npad))
+  const float* Rh;
+  const unsigned long long* vbits;  // n_q x vwords validity bits of the ring slots (+ 64 mirrored)
+  long long vwords;
+  double* g2sum;
+  long long* cnt;
+  uint32_t* status;
+};
+int row_update_tc_smem(int n_kc, int lt, int qb, int wst);
+cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
+                                 const RowTcParams& p, int grid, cudaStream_t st);
+// M-tiles per ring group for a step of b frames
+__host__ __device__ inline int w2_mtiles(int b, int n_q) {
+  if (b <= W2_SMALL_B) return b;
+  const int nq4 = ((n_q < 36 ? n_q : 36) + 3) / 4;
+  return nq4 * ((b + 31) / 32);
+}
+// pair-order row of (frame f, ring q) in W2 for a step of b frames
+__host__ __device__ inline int w2_pair_row(int f, int q, int b, int n_q) {
+  const int rg = q / 36, ql = q - 36 * rg;
+  const int base = rg * w2_mtiles(b, n_q) * 128 + (ql % 4) * 32;
+  if (b <= W2_SMALL_B) return base + f * 128 + ql / 4;
+  const int nfb = (b + 31) / 32;
+  return base + ((ql / 4) * nfb + f / 32) * 128 + f % 32;
+}
+// 64-bit words per ring of the validity bits: cap + 64 bits and one spare word
+inline long long stream_vwords(long long cap) { return (cap + 64 + 63) / 64 + 1; }
+// Rh row pitch: n_q rounded up to 4 (16-byte rows for the tensor map)
+__host__ __device__ inline int stream_npad(int n_q) { return (n_q + 3) / 4 * 4; }
+int row_update_lags(int n_q, int kpad);  // lags per tile of the row update (64 or 32)
+cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const RowTcParams& p, int grid,
+                                 cudaStream_t st);
 cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, long long n, double* g2, cudaStream_t st);
 cudaError_t launch_basis_f32(const double* B, long long n, float* B32, cudaStream_t st);
 

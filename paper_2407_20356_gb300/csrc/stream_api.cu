@@ -24,27 +24,39 @@ int64_t now_ns() {
 namespace {
 
 
-int ka_of(int k) { return (k + 31) / 32 * 32; }
-int nqp_of(int n_q) { return (n_q + 11) / 12 * 12; }
+int kpad_of(int k) { return (k + 63) / 64 * 64; }
+// ring slots: the window plus a batch, and at least 256 so that a 128-row history
+// operand starting anywhere in the ring ends before the 128 mirrored rows do
+int64_t ring_cap(int64_t W, int max_batch) { return std::max<int64_t>(W + max_batch, 256); }
+// frames per stream step (one launch of each stream kernel)
+constexpr int STEP_MAX = 64;
+// W2 rows: the pair-ordered M-tiles of every ring group for any step size, plus one
+// spare 128-row box
+int64_t w2_rows(int max_batch, int n_q) {
+  int mt = 0;  // the pair layouts of small and large steps differ: take the largest step need
+  for (int b = 1; b <= std::min(STEP_MAX, max_batch); ++b) mt = std::max(mt, w2_mtiles(b, n_q));
+  return (int64_t)((n_q + 35) / 36) * mt * 128 + 128;
+}
 int nblk_of(int64_t M) { return (int)((M + 4095) / 4096); }
 
 struct Sizes {
-  size_t frames, Ah, Rh, g2sum, cnt, part, a, w, g2, stage;
+  size_t frames, A2, Rh, vbits, g2sum, cnt, part, a, W2, g2, stage;
 };
 
 Sizes stream_sizes(const xpcs_basis* B, int64_t W, int max_batch, int eb) {
   const int64_t M = B->rings->M;
   const int n_q = B->rings->n_q, k = B->k;
-  const int64_t cap = W + max_batch;
+  const int64_t cap = ring_cap(W, max_batch);
   Sizes z;
   z.frames = (size_t)max_batch * M * eb;
-  z.Ah = (size_t)cap * ka_of(k) * 4;
-  z.Rh = (size_t)cap * n_q * 4;
+  z.A2 = (size_t)(cap + 128) * 2 * kpad_of(k) * 2;
+  z.Rh = (size_t)(cap + 128) * stream_npad(n_q) * 4;
+  z.vbits = (size_t)n_q * stream_vwords(cap) * 8;
   z.g2sum = (size_t)n_q * W * 8;
   z.cnt = (size_t)n_q * W * 8;
   z.part = (size_t)max_batch * nblk_of(M) * k * 4;
   z.a = (size_t)max_batch * k * 4;
-  z.w = (size_t)max_batch * nqp_of(n_q) * ka_of(k) * 4;
+  z.W2 = (size_t)w2_rows(max_batch, n_q) * 2 * kpad_of(k) * 2;
   z.g2 = (size_t)n_q * W * 8;
   z.stage = (size_t)max_batch * M * eb;
   return z;
@@ -55,13 +67,15 @@ void stream_free(xpcs_stream* S) {
   if (S->stream) cudaStreamSynchronize(S->stream);
   const Sizes z = stream_sizes(S->basis, S->W, S->max_batch, S->dtype == XPCS_U8 ? 1 : 2);
   dev_free(ctx, S->d_frames, z.frames);
-  dev_free(ctx, S->d_Ah, z.Ah);
+  dev_free(ctx, S->d_A2, z.A2);
   dev_free(ctx, S->d_Rh, z.Rh);
+  dev_free(ctx, S->d_vbits, z.vbits);
   dev_free(ctx, S->d_g2sum, z.g2sum);
   dev_free(ctx, S->d_cnt, z.cnt);
   dev_free(ctx, S->d_part, z.part);
   dev_free(ctx, S->d_a, z.a);
-  dev_free(ctx, S->d_w, z.w);
+  dev_free(ctx, S->d_W2, z.W2);
+  if (S->h_status) cudaFreeHost(S->h_status);
   dev_free(ctx, S->d_g2, z.g2);
   for (int i = 0; i < 2; ++i) {
     if (S->h_stage[i]) cudaFreeHost(S->h_stage[i]);
@@ -84,7 +98,7 @@ namespace xpcs {
 
 size_t stream_footprint(const xpcs_basis* B, int64_t W, int max_batch, int elem_bytes) {
   const Sizes z = stream_sizes(B, W, max_batch, elem_bytes);
-  size_t b = z.frames + z.Ah + z.Rh + z.g2sum + z.cnt + z.part + z.a + z.w + z.g2;
+  size_t b = z.frames + z.A2 + z.Rh + z.vbits + z.g2sum + z.cnt + z.part + z.a + z.W2 + z.g2;
   if (!B->d_B32) b += (size_t)B->rings->M * B->k * 4;  // f32 basis copy made on first use
   return b;
 }
@@ -113,6 +127,8 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
       (dtype != XPCS_U8 && dtype != XPCS_U16))
     return fail(ctx, XPCS_EINVAL, "bad stream_open args");
   *out = nullptr;
+  if (row_update_tc_smem(kpad_of(B->k) / 64, 32, std::min(36, stream_npad(B->rings->n_q)), 2) > 227 * 1024)
+    return fail(ctx, XPCS_ENOTSUP, "stream: too many rings for the row-update tile at this k");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int eb = dtype == XPCS_U8 ? 1 : 2;
   const size_t need = stream_footprint(B, history, max_batch, eb);
@@ -133,7 +149,7 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
   S->ctx = ctx;
   S->basis = B;
   S->W = history;
-  S->cap = history + max_batch;
+  S->cap = ring_cap(history, max_batch);
   S->max_batch = max_batch;
   S->dtype = dtype;
   S->nblk = nblk_of(B->rings->M);
@@ -146,13 +162,14 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
     S->field = static_cast<T>(p);                     \
   }
   XPCS_SALLOC(d_frames, z.frames, void*)
-  XPCS_SALLOC(d_Ah, z.Ah, float*)
+  XPCS_SALLOC(d_A2, z.A2, __nv_bfloat16*)
   XPCS_SALLOC(d_Rh, z.Rh, float*)
+  XPCS_SALLOC(d_vbits, z.vbits, unsigned long long*)
   XPCS_SALLOC(d_g2sum, z.g2sum, double*)
   XPCS_SALLOC(d_cnt, z.cnt, long long*)
   XPCS_SALLOC(d_part, z.part, float*)
   XPCS_SALLOC(d_a, z.a, float*)
-  XPCS_SALLOC(d_w, z.w, float*)
+  XPCS_SALLOC(d_W2, z.W2, __nv_bfloat16*)
   XPCS_SALLOC(d_g2, z.g2, double*)
 #undef XPCS_SALLOC
   cudaError_t e = cudaSuccess;
@@ -162,14 +179,33 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->stage_done[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(S->stage_done[i], S->stream);
   }
-  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_Ah, 0, z.Ah, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_A2, 0, z.A2, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_W2, 0, z.W2, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_status, 4, cudaHostAllocMapped);
+  if (st == XPCS_OK && e == cudaSuccess) {
+    *S->h_status = 0;
+    e = cudaHostGetDevicePointer((void**)&S->d_status, S->h_status, 0);
+  }
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_Rh, 0, z.Rh, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_vbits, 0, z.vbits, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_g2sum, 0, z.g2sum, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_cnt, 0, z.cnt, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaEventCreate(&S->base_ev);
   if (st == XPCS_OK && e == cudaSuccess) e = calibrate_clock(S);
   if (st == XPCS_OK && e != cudaSuccess) st = fail(ctx, XPCS_ECUDA, std::string("stream setup: ") + cudaGetErrorString(e));
+  S->kpad = kpad_of(B->k);
+  if (st == XPCS_OK)
+    st = make_map(ctx, &S->tmA, S->d_A2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * S->kpad, S->cap + 128, 64, 128,
+                  CU_TENSOR_MAP_SWIZZLE_128B);
+  if (st == XPCS_OK)
+    st = make_map(ctx, &S->tmW, S->d_W2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * S->kpad,
+                  w2_rows(max_batch, B->rings->n_q), 64, 128, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (st == XPCS_OK) {
+    const int npad = stream_npad(B->rings->n_q);
+    st = make_map(ctx, &S->tmR, S->d_Rh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, npad, S->cap + 128,
+                  std::min(36, npad), 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+  }
   if (st != XPCS_OK) {
     stream_free(S);
     return st;
@@ -201,6 +237,11 @@ xpcs_status retire(xpcs_stream* S) {
     const cudaError_t q = cudaEventQuery(tk.ev);
     if (q == cudaErrorNotReady) break;
     if (q != cudaSuccess) return fail(S->ctx, XPCS_ECUDA, std::string("stream: ") + cudaGetErrorString(q));
+    if (const uint32_t code = *static_cast<volatile uint32_t*>(S->h_status)) {
+      *S->h_status = 0;
+      return fail(S->ctx, code == XPCS_DEV_TIMEOUT ? XPCS_ETIMEOUT : XPCS_ECUDA,
+                  "stream: a bounded device wait expired (device status " + std::to_string(code) + ")");
+    }
     float ms = 0.f;
     const cudaError_t e = cudaEventElapsedTime(&ms, S->base_ev, tk.ev);
     if (e != cudaSuccess) return fail(S->ctx, XPCS_ECUDA, std::string("stream timing: ") + cudaGetErrorString(e));
@@ -228,6 +269,8 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   StreamStep s{};
   s.X = X;
   s.dtype = S->dtype;
+  s.vec16 = (reinterpret_cast<uintptr_t>(X) % 16 == 0) &&
+            ((size_t)B->rings->M * (S->dtype == XPCS_U8 ? 1 : 2)) % 16 == 0;
   s.M = B->rings->M;
   s.k = B->k;
   s.n_q = B->rings->n_q;
@@ -242,17 +285,35 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.Mq = B->rings->d_Mq;
   s.part = S->d_part;
   s.a = S->d_a;
-  s.w = S->d_w;
-  s.Ah = S->d_Ah;
+  s.W2 = S->d_W2;
+  s.A2 = S->d_A2;
+  s.kpad = S->kpad;
+  s.w2_rows = w2_rows(S->max_batch, B->rings->n_q);
   s.Rh = S->d_Rh;
+  s.vbits = S->d_vbits;
+  s.vwords = stream_vwords(S->cap);
+  s.status = S->d_status;
+  s.num_sms = ctx->num_sms;
+  s.tmA = &S->tmA;
+  s.tmW = &S->tmW;
+  s.tmR = &S->tmR;
   s.g2sum = S->d_g2sum;
   s.cnt = S->d_cnt;
-  cudaError_t e = launch_stream_step(s, S->stream);
+  // steps of at most STEP_MAX frames; the batch completes with its last step
+  const size_t fb = (size_t)B->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
+  cudaError_t e = cudaSuccess;
+  for (int64_t f0 = 0; f0 < n && e == cudaSuccess; f0 += STEP_MAX) {
+    s.X = static_cast<const char*>(X) + f0 * fb;
+    s.vec16 = (reinterpret_cast<uintptr_t>(s.X) % 16 == 0) && fb % 16 == 0;
+    s.b = (int)std::min<int64_t>(STEP_MAX, n - f0);
+    s.t0 = S->frames + f0;
+    e = launch_stream_step(s, S->stream);
+    if (e == cudaSuccess) ctx->launches += 4;
+  }
   if (e != cudaSuccess) {
     delete stamp;
     return fail(ctx, XPCS_ECUDA, std::string("stream step: ") + cudaGetErrorString(e));
   }
-  ctx->launches += 4;
   S->frames += n;
   cudaEvent_t ev = take_event(S);
   if (!ev) {

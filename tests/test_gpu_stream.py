@@ -75,6 +75,28 @@ def test_stream_g2_matches_oracle(X, ctx, dtype, k, Wl, sizes):
     st.close()
 
 
+def test_stream_small_and_large_steps_mixed(X, ctx):
+    # steps of at most 8 frames and larger steps lay out their (frame, ring) pairs
+    # differently; mixing them in one stream, in both orders, must not change g2
+    H, W, n_q, k, T, Wl = 20, 20, 5, 32, 160, 70
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 150, np.uint16, 515)
+    st = X.Stream(ctx, basis, Wl, 12)
+    i, j, sizes = 0, 0, (4, 12, 9, 1, 12, 5)
+    while i < T:
+        n = min(sizes[j % len(sizes)], T - i)
+        ticket = st.push(np.ascontiguousarray(Xs[i:i + n]))
+        i += n
+        j += 1
+    assert st.poll(ticket, 10000)
+    g2, cnt = st.read_g2()
+    g_ref, c_ref = _oracle_window_g2(Xs, B, qmap, n_q, Wl)
+    np.testing.assert_array_equal(cnt, c_ref)
+    for q in range(n_q):
+        rm, _ = rel_errors(g2[q], g_ref[q])
+        assert rm < 1e-4, (q, rm)
+    st.close()
+
+
 def test_stream_many_rings_and_lag_tiles(X, ctx):
     # more rings than one row-update ring group (36) and several 128-lag tiles, batches
     # longer than one window shift (16 frames)
