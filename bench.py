@@ -511,16 +511,22 @@ def run_stream_leg(X, ctx, dev, args, sw=STREAM):
     fps_b1 = run_unpaced(4000, 1)
     st.latency(reset=True)
 
-    # paced: frame j arrives at t0 + j / rate; push every frame that has arrived
+    # paced: frame j arrives at t0 + j / rate.  Continuous batching: whenever fewer than
+    # two batches are in flight, every frame that has arrived (up to max_batch) goes out
+    # as one batch, so the batch grows with the load instead of a queue.
     n_paced = int(sw["rate_hz"] * args.stream_seconds)
     period = 1e9 / sw["rate_hz"]
-    arrive = None
     t0 = X.clock_ns() + 1_000_000
     arrive = (t0 + np.arange(n_paced) * period).astype(np.int64)
     j = 0
     batches = 0
+    inflight = []
     ticket = 0
     while j < n_paced:
+        while inflight and st.poll(inflight[0], 0):
+            inflight.pop(0)
+        if len(inflight) >= 2:
+            continue
         now = X.clock_ns()
         due = min(n_paced, int((now - t0) // period) + 1) if now >= t0 else 0
         if due <= j:
@@ -529,6 +535,7 @@ def run_stream_leg(X, ctx, dev, args, sw=STREAM):
         i = pushed % P
         n = min(n, P - i)
         ticket = st.push_at(pool[i:i + n], arrive[j:j + n])
+        inflight.append(ticket)
         pushed += n
         j += n
         batches += 1
