@@ -82,16 +82,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   return fn;
 }
 
-// 2-D tiled map of a row-major [rows][cols] matrix of 16-bit (or 8-bit) elements,
+// 2-D tiled map of a row-major [rows][cols] matrix (row pitch in bytes; 0 = dense),
 // box = box_cols x box_rows, with the given swizzle.
 xpcs_status make_map(xpcs_ctx* ctx, CUtensorMap* map, const void* base, CUtensorMapDataType dt, int elem_bytes,
-                     uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw) {
+                     uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw,
+                     uint64_t pitch_bytes) {
   auto fn = get_encode_fn();
   if (!fn) return fail(ctx, XPCS_ECUDA, "cuTensorMapEncodeTiled is unavailable");
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((cols * elem_bytes) & 15))
+  const uint64_t pitch = pitch_bytes ? pitch_bytes : cols * (uint64_t)elem_bytes;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 15))
     return fail(ctx, XPCS_ENOTSUP, "tensor map needs 16-byte aligned base and row pitch");
   cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * (uint64_t)elem_bytes};
+  cuuint64_t strides[1] = {pitch};
   cuuint32_t box[2] = {box_cols, box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,

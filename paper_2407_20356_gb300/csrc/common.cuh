@@ -99,6 +99,19 @@ XPCS_DEV void tma_load_2d(void* smem_dst, const void* map, uint64_t* bar, int x,
       : "memory");
 }
 
+// Tiled store of a shared-memory box to global memory (elements outside the tensor are
+// not written), in the issuing thread's bulk group.
+XPCS_DEV void tma_store_2d(const void* map, const void* smem_src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(smem_src)), "r"(x), "r"(y)
+               : "memory");
+}
+XPCS_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the sources of this thread's bulk stores have been read (shared memory reusable)
+XPCS_DEV void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk stores are complete
+XPCS_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // ------------------------------------------------------------------ tcgen05
 
 XPCS_DEV void tmem_alloc(uint32_t* smem_dst, uint32_t ncols) {  // whole warp

@@ -94,14 +94,15 @@ struct xpcs_stream {
   __nv_bfloat16* d_A2 = nullptr;     // (cap + 128) x 2 kpad coefficient history, bf16 hi | lo
   float* d_Rh = nullptr;             // (cap + 128) x npad  r_q(s) = sqrt(M_q)/S~_q(s), 0 if undefined
   unsigned long long* d_vbits = nullptr;  // n_q x vwords  validity bits r_q(s) > 0 per slot
-  double* d_g2sum = nullptr;         // n_q x W
-  long long* d_cnt = nullptr;        // n_q x W
+  double* d_g2sum = nullptr;         // n_q x Wp (W rounded up to 64)
+  long long* d_cnt = nullptr;        // n_q x Wp
   float* d_part = nullptr;           // max_batch x nblk x k sparse-encode partials
   float* d_a = nullptr;              // max_batch x k
   __nv_bfloat16* d_W2 = nullptr;     // (max_batch n_q) x 2 kpad  r_q(t) a_t G_q, bf16 hi | lo
   double* d_g2 = nullptr;            // n_q x W read-out buffer
   int kpad = 0;                      // k rounded up to 64
   CUtensorMap tmA, tmW, tmR;         // tensor maps of d_A2, d_W2 (64 x 128 boxes) and d_Rh
+  CUtensorMap tmG, tmC;              // tensor maps of d_g2sum and d_cnt (row pitch Wp)
   uint32_t* h_status = nullptr;      // host-mapped status word of the stream's kernels
   uint32_t* d_status = nullptr;      // its device address
   size_t bytes = 0;
@@ -145,7 +146,8 @@ xpcs_status ensure_scratch(xpcs_ctx* ctx, size_t need);
 xpcs_status rings_from_host(xpcs_ctx* ctx, const int32_t* qmap_host, int64_t M, int n_q, xpcs_rings** out);
 xpcs_status finish(xpcs_ctx* ctx);
 xpcs_status make_map(xpcs_ctx* ctx, CUtensorMap* map, const void* base, CUtensorMapDataType dt, int elem_bytes,
-                     uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw);
+                     uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw,
+                     uint64_t pitch_bytes = 0);
 
 // Scratch: one growing device buffer per context, carved per call.
 struct Carve {

@@ -138,6 +138,7 @@ struct StreamStep {
   int k, n_q, b;
   long long t0;            // index of the first frame of the batch
   long long W, cap;
+  long long Wp;            // row pitch of g2sum / cnt
   int nblk;
   const float* B32;        // M x k
   const float* G32;        // n_q x k x k
@@ -152,15 +153,17 @@ struct StreamStep {
   long long w2_rows;       // rows allocated in W2
   float* Rh;               // (cap + 128) x npad, rows cap .. cap + 127 mirror rows 0 .. 127
   unsigned long long* vbits;  // n_q x vwords: bit s of ring q = r_q(slot s) > 0, slots
-                              // cap .. cap + 63 mirror slots 0 .. 63
+                              // cap .. cap + 127 mirror slots 0 .. 127
   long long vwords;
-  double* g2sum;           // n_q x W
-  long long* cnt;          // n_q x W
+  double* g2sum;           // n_q x Wp (W rounded up to 64)
+  long long* cnt;          // n_q x Wp
   uint32_t* status;
   int num_sms;
-  const CUtensorMap* tmA;  // host copies of the tensor maps of A2, W2 and Rh
+  const CUtensorMap* tmA;  // host copies of the tensor maps of A2, W2, Rh, g2sum, cnt
   const CUtensorMap* tmW;
   const CUtensorMap* tmR;
+  const CUtensorMap* tmG;
+  const CUtensorMap* tmC;
 };
 cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st);
 
@@ -182,15 +185,17 @@ struct RowTcParams {
   int npad;  // Rh row pitch (n_q rounded up to 4)
   int qb;    // r values per history row loaded per item (min(36, npad))
   const float* Rh;
-  const unsigned long long* vbits;  // n_q x vwords validity bits of the ring slots (+ 64 mirrored)
+  const unsigned long long* vbits;  // n_q x vwords validity bits of the ring slots (+ 128 mirrored)
   long long vwords;
-  double* g2sum;
-  long long* cnt;
+  long long Wp;  // row pitch (elements) of g2sum and cnt: W rounded up to 64
+  int qg2;       // ring rows per g2sum / cnt box: min(36, n_q)
   uint32_t* status;
 };
-int row_update_tc_smem(int n_kc, int lt, int qb, int wst);
+int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2);
+// tensor maps: A2 history, W2 pairs, Rh r values, g2sum and cnt (lt x qg2 boxes)
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
-                                 const RowTcParams& p, int grid, cudaStream_t st);
+                                 const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,
+                                 cudaStream_t st);
 // M-tiles per ring group for a step of b frames
 __host__ __device__ inline int w2_mtiles(int b, int n_q) {
   if (b <= W2_SMALL_B) return b;
@@ -205,14 +210,17 @@ __host__ __device__ inline int w2_pair_row(int f, int q, int b, int n_q) {
   const int nfb = (b + 31) / 32;
   return base + ((ql / 4) * nfb + f / 32) * 128 + f % 32;
 }
-// 64-bit words per ring of the validity bits: cap + 64 bits and one spare word
-inline long long stream_vwords(long long cap) { return (cap + 64 + 63) / 64 + 1; }
+// 64-bit words per ring of the validity bits: cap + 128 bits and two spare words
+inline long long stream_vwords(long long cap) { return (cap + 128 + 63) / 64 + 2; }
 // Rh row pitch: n_q rounded up to 4 (16-byte rows for the tensor map)
 __host__ __device__ inline int stream_npad(int n_q) { return (n_q + 3) / 4 * 4; }
-int row_update_lags(int n_q, int kpad);  // lags per tile of the row update (64 or 32)
+// lags per tile (64 or 32) and w stages (2 or 1) of the row update that fit shared
+// memory; false if none does
+bool row_update_config(int n_q, int kpad, int* lt, int* wst);
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const RowTcParams& p, int grid,
                                  cudaStream_t st);
-cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, long long n, double* g2, cudaStream_t st);
+cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
+                             double* g2, cudaStream_t st);
 cudaError_t launch_basis_f32(const double* B, long long n, float* B32, cudaStream_t st);
 
 // ------------------------------------------------------------------ basis

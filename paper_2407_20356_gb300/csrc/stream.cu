@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
     // validity bit of (q, slot), and of its mirror slot; other frames of the step may
     // touch the same words
     unsigned long long* vb = s.vbits + (size_t)q * s.vwords;
-    for (long long sl = slot; sl >= 0; sl = (sl == slot && slot < 64) ? s.cap + slot : -1) {
+    for (long long sl = slot; sl >= 0; sl = (sl == slot && slot < 128) ? s.cap + slot : -1) {
       const unsigned long long bit = 1ull << (sl & 63);
       if (r > 0.f)
         atomicOr(vb + (sl >> 6), bit);
@@ -207,9 +207,12 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
   }
 }
 
-__global__ void stream_g2_kernel(const double* g2sum, const long long* cnt, long long n, double* g2) {
+__global__ void stream_g2_kernel(const double* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
+                                 double* g2) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) g2[i] = cnt[i] > 0 ? g2sum[i] / (double)cnt[i] : __longlong_as_double(0x7ff8000000000000ll);
+  if (i >= (long long)n_q * W) return;
+  const long long j = i / W * Wp + i % W;
+  g2[i] = cnt[j] > 0 ? g2sum[j] / (double)cnt[j] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 __global__ void basis_f32_kernel(const double* B, long long n, float* B32) {
@@ -240,8 +243,7 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   p.n_q = s.n_q;
   p.kpad = s.kpad;
   p.n_kc = s.kpad / 64;
-  p.lt = row_update_lags(s.n_q, s.kpad);
-  p.wst = 2;
+  if (!row_update_config(s.n_q, s.kpad, &p.lt, &p.wst)) return cudaErrorInvalidConfiguration;
   p.n_tiles = (int)((s.W + p.lt - 1) / p.lt);
   p.n_rg = (s.n_q + 35) / 36;
   p.n_mt = w2_mtiles(s.b, s.n_q);
@@ -251,22 +253,29 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   p.Rh = s.Rh;
   p.vbits = s.vbits;
   p.vwords = s.vwords;
-  p.g2sum = s.g2sum;
-  p.cnt = s.cnt;
+  p.Wp = s.Wp;
+  p.qg2 = std::min(36, s.n_q);
   p.status = s.status;
   const int grid = std::min(p.n_tiles * p.n_rg, s.num_sms);
-  return launch_row_update_tc(*s.tmA, *s.tmW, *s.tmR, p, grid, st);
+  return launch_row_update_tc(*s.tmA, *s.tmW, *s.tmR, *s.tmG, *s.tmC, p, grid, st);
 }
 
-int row_update_lags(int n_q, int kpad) {
-  // 64 lags per tile when the shared-memory layout fits, else 32
-  const int n_kc = kpad / 64;
-  const int qb = std::min(36, stream_npad(n_q));
-  return row_update_tc_smem(n_kc, 64, qb, 2) <= 227 * 1024 ? 64 : 32;
+bool row_update_config(int n_q, int kpad, int* lt, int* wst) {
+  const int n_kc = kpad / 64, qb = std::min(36, stream_npad(n_q)), qg2 = std::min(36, n_q);
+  const int cand[3][2] = {{64, 2}, {32, 2}, {32, 1}};
+  for (const auto& c : cand)
+    if (row_update_tc_smem(n_kc, c[0], qb, c[1], qg2) <= 227 * 1024) {
+      *lt = c[0];
+      *wst = c[1];
+      return true;
+    }
+  return false;
 }
 
-cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, long long n, double* g2, cudaStream_t st) {
-  stream_g2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g2sum, cnt, n, g2);
+cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
+                             double* g2, cudaStream_t st) {
+  const long long n = (long long)n_q * W;
+  stream_g2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g2sum, cnt, n_q, W, Wp, g2);
   return cudaGetLastError();
 }
 

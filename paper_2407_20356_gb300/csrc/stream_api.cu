@@ -38,6 +38,8 @@ int64_t w2_rows(int max_batch, int n_q) {
   return (int64_t)((n_q + 35) / 36) * mt * 128 + 128;
 }
 int nblk_of(int64_t M) { return (int)((M + 4095) / 4096); }
+// row pitch (elements) of the g2 sums and counts: whole 64-lag tiles
+int64_t wpitch(int64_t W) { return (W + 63) / 64 * 64; }
 
 struct Sizes {
   size_t frames, A2, Rh, vbits, g2sum, cnt, part, a, W2, g2, stage;
@@ -52,8 +54,8 @@ Sizes stream_sizes(const xpcs_basis* B, int64_t W, int max_batch, int eb) {
   z.A2 = (size_t)(cap + 128) * 2 * kpad_of(k) * 2;
   z.Rh = (size_t)(cap + 128) * stream_npad(n_q) * 4;
   z.vbits = (size_t)n_q * stream_vwords(cap) * 8;
-  z.g2sum = (size_t)n_q * W * 8;
-  z.cnt = (size_t)n_q * W * 8;
+  z.g2sum = (size_t)n_q * wpitch(W) * 8;
+  z.cnt = (size_t)n_q * wpitch(W) * 8;
   z.part = (size_t)max_batch * nblk_of(M) * k * 4;
   z.a = (size_t)max_batch * k * 4;
   z.W2 = (size_t)w2_rows(max_batch, n_q) * 2 * kpad_of(k) * 2;
@@ -127,8 +129,9 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
       (dtype != XPCS_U8 && dtype != XPCS_U16))
     return fail(ctx, XPCS_EINVAL, "bad stream_open args");
   *out = nullptr;
-  if (row_update_tc_smem(kpad_of(B->k) / 64, 32, std::min(36, stream_npad(B->rings->n_q)), 2) > 227 * 1024)
-    return fail(ctx, XPCS_ENOTSUP, "stream: too many rings for the row-update tile at this k");
+  int lt = 0, wst = 0;
+  if (!row_update_config(B->rings->n_q, kpad_of(B->k), &lt, &wst))
+    return fail(ctx, XPCS_ENOTSUP, "stream: the row-update tile does not fit shared memory at this k");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int eb = dtype == XPCS_U8 ? 1 : 2;
   const size_t need = stream_footprint(B, history, max_batch, eb);
@@ -206,6 +209,14 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
     st = make_map(ctx, &S->tmR, S->d_Rh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, npad, S->cap + 128,
                   std::min(36, npad), 128, CU_TENSOR_MAP_SWIZZLE_NONE);
   }
+  // g2 sums and counts: W x n_q with row pitch Wp, boxes of lt lags x up to 36 rings
+  const int qg2 = std::min(36, B->rings->n_q);
+  if (st == XPCS_OK)
+    st = make_map(ctx, &S->tmG, S->d_g2sum, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, history, B->rings->n_q, lt, qg2,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, (uint64_t)wpitch(history) * 8);
+  if (st == XPCS_OK)
+    st = make_map(ctx, &S->tmC, S->d_cnt, CU_TENSOR_MAP_DATA_TYPE_INT64, 8, history, B->rings->n_q, lt, qg2,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, (uint64_t)wpitch(history) * 8);
   if (st != XPCS_OK) {
     stream_free(S);
     return st;
@@ -277,6 +288,7 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.b = (int)n;
   s.t0 = S->frames;
   s.W = S->W;
+  s.Wp = wpitch(S->W);
   s.cap = S->cap;
   s.nblk = S->nblk;
   s.B32 = B->d_B32;
@@ -297,6 +309,8 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.tmA = &S->tmA;
   s.tmW = &S->tmW;
   s.tmR = &S->tmR;
+  s.tmG = &S->tmG;
+  s.tmC = &S->tmC;
   s.g2sum = S->d_g2sum;
   s.cnt = S->d_cnt;
   // steps of at most STEP_MAX frames; the batch completes with its last step
@@ -429,14 +443,17 @@ extern "C" xpcs_status xpcs_stream_read_g2(xpcs_stream* S, double* g2_host, int6
   if (!S) return XPCS_EINVAL;
   xpcs_ctx* ctx = S->ctx;
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
-  const long long n = (long long)S->basis->rings->n_q * S->W;
+  const int n_q = S->basis->rings->n_q;
+  const long long n = (long long)n_q * S->W;
   if (g2_host) {
-    cudaError_t e = launch_stream_g2(S->d_g2sum, S->d_cnt, n, S->d_g2, S->stream);
+    cudaError_t e = launch_stream_g2(S->d_g2sum, S->d_cnt, n_q, S->W, wpitch(S->W), S->d_g2, S->stream);
     if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream g2: ") + cudaGetErrorString(e));
     ctx->launches += 1;
     XPCS_CUDA(ctx, cudaMemcpyAsync(g2_host, S->d_g2, n * 8, cudaMemcpyDeviceToHost, S->stream));
   }
-  if (count_host) XPCS_CUDA(ctx, cudaMemcpyAsync(count_host, S->d_cnt, n * 8, cudaMemcpyDeviceToHost, S->stream));
+  if (count_host)
+    XPCS_CUDA(ctx, cudaMemcpy2DAsync(count_host, S->W * 8, S->d_cnt, wpitch(S->W) * 8, S->W * 8, n_q,
+                                     cudaMemcpyDeviceToHost, S->stream));
   XPCS_CUDA(ctx, cudaStreamSynchronize(S->stream));
   return XPCS_OK;
 }

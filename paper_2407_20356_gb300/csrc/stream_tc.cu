@@ -39,38 +39,42 @@ constexpr int RT_EPI_BAR = 1;
 constexpr int RT_QG = 36;                      // rings per work item (nine per lane quarter)
 
 struct RtLayout {
-  int n_kc, lt, qb, wst;
+  int n_kc, lt, qb, wst, qg2;
   __host__ __device__ int hist_bytes() const { return 2 * n_kc * RT_CHUNK; }
   __host__ __device__ int w_bytes() const { return wst * 2 * RT_CHUNK; }
+  __host__ __device__ int slice_bytes() const { return (qg2 * lt * 8 + 1023) / 1024 * 1024; }  // one of two
   __host__ __device__ int rs_bytes() const { return RT_ROWS * qb * 4; }
   __host__ __device__ int bins_bytes() const { return RT_QG * (lt + 1) * 4; }
   __host__ __device__ int rot_bytes() const { return 4 * 32 * 32 * 4; }  // a 32x32 block per epilogue warp
+  __host__ __device__ int vw_bytes() const { return RT_QG * 5 * 8; }      // validity words per ring
   __host__ __device__ int smem() const {
-    return 1024 + hist_bytes() + w_bytes() + rs_bytes() + bins_bytes() + rot_bytes() + 256;
+    return 1024 + hist_bytes() + w_bytes() + 2 * slice_bytes() + rs_bytes() + bins_bytes() + rot_bytes() +
+           vw_bytes() + 256;
   }
 };
 
-// 64 validity bits of one ring starting at ring slot o (the bit array mirrors its first
-// 64 slots after slot cap - 1, so a window never wraps)
-XPCS_DEV unsigned long long bits_at(const unsigned long long* vb, long long o) {
-  const long long wi = o >> 6;
-  const int sh = (int)(o & 63);
-  const unsigned long long lo = __ldg(vb + wi);
-  return sh ? (lo >> sh) | (__ldg(vb + wi + 1) << (64 - sh)) : lo;
+// 64 bits of a little-endian bit string held in 64-bit words, starting at bit o
+XPCS_DEV unsigned long long bits64(const unsigned long long* w, int o) {
+  const int wi = o >> 6, sh = o & 63;
+  return sh ? (w[wi] >> sh) | (w[wi + 1] << (64 - sh)) : w[wi];
 }
 
 __global__ void __launch_bounds__(RT_THREADS, 1)
     row_update_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
-                         const __grid_constant__ CUtensorMap tmR, const RowTcParams p) {
+                         const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmG,
+                         const __grid_constant__ CUtensorMap tmC, const RowTcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const RtLayout L{p.n_kc, p.lt, p.qb, p.wst};
+  const RtLayout L{p.n_kc, p.lt, p.qb, p.wst, p.qg2};
   uint8_t* hist = smem;                                       // [hi kc..., lo kc...]
   uint8_t* w_st = smem + L.hist_bytes();                      // [stage][hi, lo]
-  float* rs = reinterpret_cast<float*>(w_st + L.w_bytes());   // [128][qb] r_q of the history rows
+  double* g2s = reinterpret_cast<double*>(w_st + L.w_bytes());                     // [qg2][lt] g2 sums
+  long long* cns = reinterpret_cast<long long*>(w_st + L.w_bytes() + L.slice_bytes());  // [qg2][lt] counts
+  float* rs = reinterpret_cast<float*>(w_st + L.w_bytes() + 2 * L.slice_bytes());  // [128][qb] r of the rows
   float* bins = rs + RT_ROWS * p.qb;                          // [36][lt + 1]
   float* rot = bins + RT_QG * (p.lt + 1);                     // [4][32][32]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(rot) + L.rot_bytes());
+  unsigned long long* vw = reinterpret_cast<unsigned long long*>(rot + 4 * 1024);  // [36][5]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(vw) + L.vw_bytes());
   uint64_t* h_full = bars;        // history + r rows landed
   uint64_t* h_empty = bars + 1;   // MMAs done with the history rows
   uint64_t* r_empty = bars + 2;   // epilogue done with the r rows
@@ -79,7 +83,9 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   uint64_t* tfull = bars + 11;    // [2]
   uint64_t* tempty = bars + 13;   // [2]
   uint64_t* mma_done = bars + 15;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
+  uint64_t* s_full = bars + 16;   // g2sum / cnt slices landed
+  uint64_t* s_empty = bars + 17;  // their store has read them
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 18);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -99,6 +105,8 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       mbar_init(&tempty[b], 4);
     }
     mbar_init(mma_done, 1);
+    mbar_init(s_full, 1);
+    mbar_init(s_empty, 1);
     mbar_fence_init();
     *abort_flag = 0;
   }
@@ -117,7 +125,9 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       tma_prefetch_desc(&tmA);
       tma_prefetch_desc(&tmW);
       tma_prefetch_desc(&tmR);
-      uint32_t item_i = 0, it = 0;
+      tma_prefetch_desc(&tmG);
+      tma_prefetch_desc(&tmC);
+      uint32_t item_i = 0, it = 0, n_slices = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++item_i) {
         const uint32_t par = (item_i & 1) ^ 1;
@@ -153,9 +163,21 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             tma_load_2d(dst + RT_CHUNK, &tmW, &w_full[s], p.kpad + kc * RT_CH, wy);
           }
         }
+        // the item's g2 sums and counts, once the previous item's store has read them
+        if (ok && (*abort_flag || !mbar_wait(s_empty, par, p.status))) {
+          *abort_flag = 1;
+          ok = false;
+        }
+        if (ok) {
+          mbar_arrive_expect_tx(s_full, (uint32_t)(2 * p.qg2 * lt * 8));
+          tma_load_2d(g2s, &tmG, s_full, (int)tau0, rg * RT_QG);
+          tma_load_2d(cns, &tmC, s_full, (int)tau0, rg * RT_QG);
+          ++n_slices;
+        }
       }
       // never leave the CTA with bulk copies in flight
       if (item_i) mbar_wait(h_full, (item_i - 1) & 1, p.status);
+      if (n_slices) mbar_wait(s_full, (n_slices - 1) & 1, p.status);
       for (uint32_t j = (it > (uint32_t)p.wst ? it - p.wst : 0); j < it; ++j)
         mbar_wait(&w_full[j % p.wst], (j / p.wst) & 1, p.status);
     }
@@ -220,8 +242,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     const int w = warp & 3;           // TMEM lane quarter = ring residue
     const int et = threadIdx.x - 64;  // 0..127
     const unsigned long long bmask = p.b == 64 ? ~0ull : ((1ull << p.b) - 1);
-    const long long o_batch = p.t0 % p.cap;  // validity bits of the step's own frames
-    uint32_t item_i = 0, acc_i = 0;
+    uint32_t item_i = 0, acc_i = 0, stores = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++item_i) {
       const int tile = item / p.n_rg, rg = item - tile * p.n_rg;
@@ -232,6 +253,16 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       const int tl_max = (int)min((long long)lt - 1, p.W - 1 - tau0);  // lags that exist
       const int c_min = s_start < 0 ? (int)(-s_start) : 0;              // rows before frame 0
       for (int e = et; e < RT_QG * (lt + 1); e += 128) bins[e] = 0.f;
+      // validity words of the item: for ring ql, words [0, 3) hold the history window
+      // starting at bit o_min (the slot of lag tau0 + lt - 1 at frame t0), words [3, 5)
+      // the step's own frames from bit o_batch
+      const long long o_min = (((s_start % p.cap) + p.cap) % p.cap);
+      const long long o_batch = p.t0 % p.cap;
+      for (int e = et; e < qn * 5; e += 128) {
+        const int ql = e / 5, u = e - ql * 5;
+        const unsigned long long* vb = p.vbits + (size_t)(q0 + ql) * p.vwords;
+        vw[ql * 5 + u] = u < 3 ? __ldg(vb + (o_min >> 6) + u) : __ldg(vb + (o_batch >> 6) + (u - 3));
+      }
       named_bar_sync(RT_EPI_BAR, 128);
       bool good = ok && !__any_sync(0xffffffffu, *abort_flag != 0);  // warp-uniform
       if (good) good = mbar_wait_warp(h_full, item_i & 1, p.status);  // r rows landed
@@ -331,51 +362,51 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(r_empty);  // the r rows may be replaced
       named_bar_sync(RT_EPI_BAR, 128);     // all bins of the item are complete
-      // fold the item's bins into the FP64 sums (one owner per bin).  Pair count of
-      // (q, tau) in this step: frames f < b whose frame t0 + f and history frame
-      // t0 + f - tau are both defined, a popcount of two validity-bit windows.
-      // Loads of four bins are issued before their stores.
+      // fold the item's bins into its g2 sums and counts (loaded by TMA, stored back by
+      // TMA; one owner per bin).  Pair count of (q, tau) in this step: frames f < b whose
+      // frame t0 + f and history frame t0 + f - tau are both defined, a popcount of two
+      // windows of the validity bits.
+      good = ok && !__any_sync(0xffffffffu, *abort_flag != 0);
+      if (good) good = mbar_wait_warp(s_full, item_i & 1, p.status);
+      if (!good) {
+        *abort_flag = 1;
+        ok = false;
+      }
       if (ok) {
-        const int n = qn * lt;
-        for (int e0 = et; e0 < n; e0 += 4 * 128) {
-          double gs[4];
-          long long gc[4];
-          size_t gi[4];
-          int bi[4], cntu[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * 128;
-            cntu[u] = 0;
-            gi[u] = 0;
-            bi[u] = 0;
-            if (e < n) {
-              const int ql = e / lt, tl = e - ql * lt;
-              const long long tau = tau0 + tl;
-              if (tl <= tl_max) {
-                const unsigned long long* vb = p.vbits + (size_t)(q0 + ql) * p.vwords;
-                const unsigned long long mine = bits_at(vb, o_batch) & bmask;
-                const long long o_h = (((p.t0 - tau) % p.cap) + p.cap) % p.cap;
-                cntu[u] = __popcll(mine & bits_at(vb, o_h));
-              }
-              bi[u] = ql * (lt + 1) + tl;
-              gi[u] = (size_t)(q0 + ql) * p.W + (size_t)(tau0 + tl);
-              if (cntu[u]) {
-                gs[u] = p.g2sum[gi[u]];
-                gc[u] = p.cnt[gi[u]];
-              }
-            }
+        const int sh_b = (int)(o_batch & 63);
+        for (int e = et; e < qn * lt; e += 128) {
+          const int ql = e / lt, tl = e - ql * lt;
+          if (tl > tl_max) continue;
+          const unsigned long long* wq = vw + ql * 5;
+          const unsigned long long mine = bits64(wq + 3, sh_b) & bmask;
+          const unsigned long long hist = bits64(wq, (int)(o_min & 63) + (lt - 1 - tl));
+          const int n = __popcll(mine & hist);
+          if (n) {
+            g2s[ql * lt + tl] += (double)bins[ql * (lt + 1) + tl];
+            cns[ql * lt + tl] += n;
           }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (cntu[u]) {
-              p.g2sum[gi[u]] = gs[u] + (double)bins[bi[u]];
-              p.cnt[gi[u]] = gc[u] + cntu[u];
-            }
         }
+        fence_proxy_async_smem();  // the slice writes, visible to the bulk store
+      }
+      if (named_bar_sync_or(RT_EPI_BAR, 128, !ok || *abort_flag)) {
+        if (et == 0 && stores) bulk_wait_all();
+        break;
+      }
+      if (et == 0) {
+        tma_store_2d(&tmG, g2s, (int)tau0, q0);
+        tma_store_2d(&tmC, cns, (int)tau0, q0);
+        bulk_commit();
+        ++stores;
+        bulk_wait_read_all();
+        mbar_arrive(s_empty);  // the slices may be refilled
       }
       // one decision for all four warps (also orders the fold before the next zeroing)
-      if (named_bar_sync_or(RT_EPI_BAR, 128, !ok || *abort_flag)) break;
+      if (named_bar_sync_or(RT_EPI_BAR, 128, !ok || *abort_flag)) {
+        if (et == 0 && stores) bulk_wait_all();
+        break;
+      }
     }
+    if (et == 0 && stores) bulk_wait_all();  // the sums are in global memory before exit
   }
 
   tc_fence_before();
@@ -388,18 +419,19 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
 
 }  // namespace
 
-int row_update_tc_smem(int n_kc, int lt, int qb, int wst) { return RtLayout{n_kc, lt, qb, wst}.smem(); }
+int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2) { return RtLayout{n_kc, lt, qb, wst, qg2}.smem(); }
 
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
-                                 const RowTcParams& p, int grid, cudaStream_t st) {
-  const int smem = row_update_tc_smem(p.n_kc, p.lt, p.qb, p.wst);
+                                 const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,
+                                 cudaStream_t st) {
+  const int smem = row_update_tc_smem(p.n_kc, p.lt, p.qb, p.wst, p.qg2);
   static int attr_bytes = 0;  // the attribute only ever grows
   if (smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(row_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  row_update_tc_kernel<<<grid, RT_THREADS, smem, st>>>(tmA, tmW, tmR, p);
+  row_update_tc_kernel<<<grid, RT_THREADS, smem, st>>>(tmA, tmW, tmR, tmG, tmC, p);
   return cudaGetLastError();
 }
 
