@@ -9,12 +9,14 @@
 // 0x6400 | v is exactly 1024 + v, so one OR and one packed subtract give v.  Counts of
 // 1024 or more are flagged (XPCS_ERANGE).
 //
-// Work item = (frame block m of 128 frames, pixel split s).  Per 64-pixel chunk:
-//   warp 0      TMA: X tile (128 x 64) and the Bcat tile (2kp x 64, 128-byte swizzle)
+// Work item = (group of mb frame blocks of 128 frames, pixel split s); mb = 2 when two
+// accumulators fit TMEM (N <= 256), so each Bcat tile loaded serves 256 frames.  Per
+// 64-pixel chunk:
+//   warp 0      TMA: mb X tiles (128 x 64) and the Bcat tile (2kp x 64, 128-byte swizzle)
 //   warps 2..5  convert X to f16: u16 tiles in place (loaded with the same swizzle the
 //               MMA reads, so the conversion is position-agnostic); u8 tiles into a
 //               separate swizzled buffer
-//   warp 1      MMA into a 128 x 2kp f32 TMEM accumulator (N <= 256 per instruction)
+//   warp 1      MMA into mb 128 x 2kp f32 TMEM accumulators (N <= 256 per instruction)
 // After the split's last chunk warps 2..5 drain TMEM, add the two halves and write the
 // split's partial coefficients; a second kernel sums the splits in a fixed order.
 #include <algorithm>
@@ -32,18 +34,19 @@ constexpr int ENC_THREADS = 64 + 128;
 constexpr int CONV_BYTES = TILE * KCH * 2;  // converted bf16 tile: 16 KB
 
 struct EncLayout {
-  int k, kp, N, nload, ns, raw_bytes, b_bytes, stage_bytes, tmem_cols;
+  int k, kp, N, nload, ns, mb, raw_bytes, b_bytes, stage_bytes, tmem_cols;
   __host__ __device__ EncLayout(int k_, int dtype) {
     k = k_;
     kp = (k_ + 15) / 16 * 16;  // lo half starts at column kp; N = 2 kp is a multiple of 32
     N = 2 * kp;
     nload = (N + 255) / 256;
+    tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
+    mb = 2 * tmem_cols <= 512 ? 2 : 1;        // frame blocks sharing each basis tile
     raw_bytes = dtype == 0 ? TILE * KCH : 0;  // u16 converts in place
     b_bytes = N * 128;
-    stage_bytes = raw_bytes + b_bytes + CONV_BYTES;
+    stage_bytes = mb * (raw_bytes + CONV_BYTES) + b_bytes;
     ns = (200 * 1024) / stage_bytes;
     if (ns > 8) ns = 8;
-    tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
   }
   __host__ __device__ int smem() const { return 1024 + ns * stage_bytes + 256; }
 };
@@ -63,13 +66,17 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   uint64_t* mma_done = bars + 26;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 27);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  auto raw_of = [&](int s) { return smem + s * lay.stage_bytes; };
-  auto b_of = [&](int s) { return smem + s * lay.stage_bytes + lay.raw_bytes; };
-  auto conv_of = [&](int s) { return smem + s * lay.stage_bytes + lay.raw_bytes + lay.b_bytes; };
+  // stage s: [B tile][conv tile 0..mb-1][raw tile 0..mb-1 (u8 only)]; 1024-aligned pieces
+  auto b_of = [&](int s) { return smem + s * lay.stage_bytes; };
+  auto conv_of = [&](int s, int i) { return smem + s * lay.stage_bytes + lay.b_bytes + i * CONV_BYTES; };
+  auto raw_of = [&](int s, int i) {
+    return smem + s * lay.stage_bytes + lay.b_bytes + lay.mb * CONV_BYTES + i * lay.raw_bytes;
+  };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_chunks = (int)(p.px_per_split / KCH);
   const int n_m = p.T_pad / TILE;
+  const int n_mp = (n_m + lay.mb - 1) / lay.mb;  // items: (group of mb frame blocks, pixel split)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < lay.ns; ++s) {
@@ -84,7 +91,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     *abort_flag = 0;
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, lay.tmem_cols);
+    tmem_alloc(tmem_slot, lay.mb * lay.tmem_cols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -98,9 +105,9 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       tma_prefetch_desc(&tmB);
       uint32_t it = 0;
       bool ok = true;
-      const uint32_t tx = (uint32_t)(TILE * KCH * (p.dtype == 0 ? 1 : 2) + lay.b_bytes);
+      const uint32_t tx = (uint32_t)(lay.mb * TILE * KCH * (p.dtype == 0 ? 1 : 2) + lay.b_bytes);
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-        const int m = item % n_m, sp = item / n_m;
+        const int mp = item % n_mp, sp = item / n_mp;
         const long long px0 = (long long)sp * p.px_per_split;
         for (int c = 0; c < n_chunks; ++c, ++it) {
           const uint32_t s = it % lay.ns, ph = (it / lay.ns) & 1;
@@ -111,7 +118,9 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           }
           const int x = (int)(px0 + (long long)c * KCH);
           mbar_arrive_expect_tx(&full[s], tx);
-          tma_load_2d(p.dtype == 0 ? raw_of(s) : conv_of(s), &tmX, &full[s], x, m * TILE);
+          // frame blocks past the end read as zeros (rows beyond T)
+          for (int i = 0; i < lay.mb; ++i)
+            tma_load_2d(p.dtype == 0 ? raw_of(s, i) : conv_of(s, i), &tmX, &full[s], x, (mp * lay.mb + i) * TILE);
           for (int l = 0; l < lay.nload; ++l)
             tma_load_2d(b_of(s) + l * (lay.N / lay.nload) * 128, &tmB, &full[s], x, l * (lay.N / lay.nload));
         }
@@ -141,12 +150,15 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
             break;
           }
           tc_fence_after();
-          const uint64_t ad = smem_desc_sw128(conv_of(s));
-          for (int h = 0; h < nmma; ++h) {
-            const uint64_t bd = smem_desc_sw128(b_of(s) + h * nper * 128);
+          for (int i = 0; i < lay.mb; ++i) {
+            const uint64_t ad = smem_desc_sw128(conv_of(s, i));
+            for (int h = 0; h < nmma; ++h) {
+              const uint64_t bd = smem_desc_sw128(b_of(s) + h * nper * 128);
 #pragma unroll
-            for (int kk = 0; kk < KCH / 16; ++kk)
-              tc_mma_f16(tmem_base + h * nper, ad + 2 * kk, bd + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              for (int kk = 0; kk < KCH / 16; ++kk)
+                tc_mma_f16(tmem_base + i * lay.tmem_cols + h * nper, ad + 2 * kk, bd + 2 * kk, idesc,
+                           (c > 0 || kk > 0) ? 1u : 0u);
+            }
           }
           issued = true;
           tc_commit(&empty[s]);
@@ -167,7 +179,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     uint32_t it = 0, item_i = 0;
     uint32_t over = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++item_i) {
-      const int m = item % n_m, sp = item / n_m;
+      const int mp = item % n_mp, sp = item / n_mp;
       bool ok = true;
       for (int c = 0; c < n_chunks; ++c, ++it) {
         const uint32_t s = it % lay.ns, ph = (it / lay.ns) & 1;
@@ -177,7 +189,8 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           ok = false;
           break;
         }
-        uint8_t* conv = conv_of(s);
+        for (int i = 0; i < lay.mb; ++i) {
+        uint8_t* conv = conv_of(s, i);
         if (p.dtype == 1) {
           // in place: 1024 16-byte chunks, 8 per thread
 #pragma unroll
@@ -195,7 +208,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
             *ptr = make_uint4(w[0], w[1], w[2], w[3]);
           }
         } else {
-          const uint8_t* raw = raw_of(s);
+          const uint8_t* raw = raw_of(s, i);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int unit = u * 128 + ct;
@@ -213,6 +226,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
             *reinterpret_cast<uint4*>(conv + row * 128 + ((ch ^ (row & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
           }
         }
+        }
         fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
         mbar_arrive(&cfull[s]);
       }
@@ -224,15 +238,21 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       }
       tc_fence_after();
       const int row = quarter * 32 + lane;
-      float* dst = p.partials + ((size_t)sp * p.T_pad + (size_t)m * TILE + row) * p.k;
-      for (int j0 = 0; j0 < p.k; j0 += 32) {
-        uint32_t hi[32], lo[32];
-        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
-        tmem_ld32(lane_base + j0, hi);
-        tmem_ld32(lane_base + lay.kp + j0, lo);
-        tc_wait_ld();
-        const int nj = min(32, p.k - j0);
-        for (int j = 0; j < nj; ++j) dst[j0 + j] = __uint_as_float(hi[j]) + __uint_as_float(lo[j]);
+      for (int i = 0; i < lay.mb; ++i) {
+        const int m = mp * lay.mb + i;
+        if (m >= n_m) break;  // warp-uniform
+        float* dst = p.partials + ((size_t)sp * p.T_pad + (size_t)m * TILE + row) * p.k;
+        for (int j0 = 0; j0 < p.k; j0 += 32) {
+          uint32_t hi[32], lo[32];
+          const uint32_t lane_base = tmem_base + i * lay.tmem_cols + ((uint32_t)(quarter * 32) << 16);
+          tmem_ld32(lane_base + j0, hi);
+          tmem_ld32(lane_base + lay.kp + j0, lo);
+          tc_wait_ld();
+          const int nj = min(32, p.k - j0);
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nj) dst[j0 + j] = __uint_as_float(hi[j]) + __uint_as_float(lo[j]);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -245,7 +265,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, lay.tmem_cols);
+    tmem_dealloc(tmem_base, lay.mb * lay.tmem_cols);
   }
 }
 
@@ -263,6 +283,7 @@ __global__ void encode_reduce_kernel(const float* partials, int n_split, long lo
 }  // namespace
 
 int encode_smem_bytes(int k) { return EncLayout(k, 1).smem(); }
+int encode_frame_blocks(int k) { return EncLayout(k, 1).mb; }
 
 cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const EncodeParams& p, int grid,
                           cudaStream_t st) {
@@ -273,7 +294,7 @@ cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const 
     if (e != cudaSuccess) return e;
     attr_bytes = lay.smem();
   }
-  const int n_items = (p.T_pad / TILE) * p.n_split;
+  const int n_items = (p.T_pad / TILE + lay.mb - 1) / lay.mb * p.n_split;
   encode_kernel<<<grid, ENC_THREADS, lay.smem(), st>>>(tmX, tmB, p, n_items);
   return cudaGetLastError();
 }
@@ -322,7 +343,9 @@ extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const voi
   const int k = B->k;
   const int nT = (int)((T + TILE - 1) / TILE);
   const int T_pad = nT * TILE;
-  const int n_split = pick_splits(nT, B->M_pad, ctx->num_sms);
+  const int mb = encode_frame_blocks(k);
+  const int n_mp = (nT + mb - 1) / mb;  // work items: groups of mb frame blocks x pixel splits
+  const int n_split = pick_splits(n_mp, B->M_pad, ctx->num_sms);
   const long long per = ((B->M_pad + n_split - 1) / n_split + KCH - 1) / KCH * KCH;
   Carve c0;
   c0.take<float>((size_t)n_split * T_pad * k);
@@ -345,7 +368,7 @@ extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const voi
   p.partials = partials;
   p.T_pad = T_pad;
   p.status = ctx->d_status;
-  const int n_items = nT * n_split;
+  const int n_items = n_mp * n_split;
   XPCS_LAUNCH(ctx, "encode", 1, launch_encode(tmX, tmB, p, std::min(n_items, ctx->num_sms), ctx->stream));
   XPCS_LAUNCH(ctx, "encode_reduce", 1,
               launch_encode_reduce(partials, n_split, T, T_pad, k, std::ldexp(1.0f, -B->enc_log2), A_out, ctx->stream));

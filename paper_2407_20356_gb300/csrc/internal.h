@@ -125,6 +125,7 @@ struct EncodeParams {
 cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const EncodeParams& p, int grid,
                           cudaStream_t st);
 int encode_smem_bytes(int k);
+int encode_frame_blocks(int k);  // 128-frame blocks sharing each basis tile
 cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float scale,
                                  float* A, cudaStream_t st);
 
