@@ -233,28 +233,39 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   uint4* L = reinterpret_cast<uint4*>(static_cast<T16*>(p.L) + ((size_t)q * p.T_pad + t0) * p.Kc);
   uint4* R = reinterpret_cast<uint4*>(static_cast<T16*>(p.R) + ((size_t)q * p.T_pad + t0) * p.Kc);
   for (int ff = tid >> 3; ff < PREP_FRAMES; ff += 32) {
+    const float* wrow = Ws + ff * lda;
+    const float* arow = As + ff * lda;
     for (int vv = tid & 7; vv < nvec; vv += 8) {
+      // a vector never straddles the hi | lo boundary (piece is a multiple of 64)
+      const bool lo = SPLIT && vv * 8 >= piece;
+      const int jb = vv * 8 - (lo ? piece : 0);
       alignas(16) T16 lv[8];
       alignas(16) T16 rv[8];
+      if (jb + 8 <= k) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int col = vv * 8 + e;
-        const int seg = (SPLIT && col >= piece) ? 1 : 0;
-        const int j = col - seg * piece;
-        float wl = 0.f, ar = 0.f;
-        if (j < k) {
-          const float wv = Ws[ff * lda + j], av = As[ff * lda + j];
-          if (!SPLIT) {
-            wl = wv;
-            ar = av;
+        for (int e = 0; e < 8; ++e) {
+          const float wv = wrow[jb + e], av = arow[jb + e];
+          if (!lo) {
+            lv[e] = to16<T16>(wv);
+            rv[e] = to16<T16>(av);
           } else {
-            const float wh = (float)to16<T16>(wv), ah = (float)to16<T16>(av);
-            wl = seg == 0 ? wh : wv - wh;
-            ar = seg == 0 ? ah : av - ah;
+            lv[e] = to16<T16>(wv - (float)to16<T16>(wv));
+            rv[e] = to16<T16>(av - (float)to16<T16>(av));
           }
         }
-        lv[e] = to16<T16>(wl);
-        rv[e] = to16<T16>(ar);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int j = jb + e;
+          const float wv = j < k ? wrow[j] : 0.f, av = j < k ? arow[j] : 0.f;
+          if (!lo) {
+            lv[e] = to16<T16>(wv);
+            rv[e] = to16<T16>(av);
+          } else {
+            lv[e] = to16<T16>(wv - (float)to16<T16>(wv));
+            rv[e] = to16<T16>(av - (float)to16<T16>(av));
+          }
+        }
       }
       L[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(lv);
       R[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(rv);
