@@ -87,6 +87,14 @@ int xpcs_profile_count(const xpcs_ctx* ctx);
 xpcs_status xpcs_profile_get(xpcs_ctx* ctx, int i, char* name_host, size_t name_cap, double* ms_host,
                              int64_t* launches_host);
 
+/* Failure-detection self test (no counterpart in the paper).  Every device-side wait of
+ * the library is bounded: past its limit the kernel records a timeout and unwinds, and
+ * the host sees XPCS_ETIMEOUT with the context still usable.  This call runs one such
+ * wait that nothing satisfies, for limit_ms (1..1000) milliseconds, and returns what a
+ * real expired wait returns: XPCS_ETIMEOUT (at once in synchronous mode, else from
+ * xpcs_synchronize).  XPCS_EINVAL for a limit out of range. */
+xpcs_status xpcs_selftest_timeout(xpcs_ctx* ctx, int limit_ms);
+
 /* ------------------------------------------------------------------ q-rings (Sec. 2.2)
  * A ring plan fixes which pixels form each q-ring: qmap[p] in [0, n_q) is the ring of
  * pixel p, -1 leaves the pixel out (the q-subsets of Sec. 2.2).  `qmap` is a device

@@ -57,6 +57,7 @@ _SIGS = {
     "xpcs_encode": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
     "xpcs_g2": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
+    "xpcs_selftest_timeout": (C.c_int, [vp, C.c_int]),
     "xpcs_g2_noalloc": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_stream_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.POINTER(vp)]),
     "xpcs_stream_push": (C.c_int, [vp, vp, i64, C.POINTER(C.c_uint64)]),
@@ -274,6 +275,11 @@ def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None,
 
 def xpcs_g2(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
     ctx.check(_lib.xpcs_g2(ctx.h, _ptr(C_in), n_q, T, _ptr(g2_out), _ptr(count_out)))
+
+
+def xpcs_selftest_timeout(ctx: Context, limit_ms: int):
+    """Run a bounded device wait that nothing satisfies; raises XpcsError(XPCS_ETIMEOUT)."""
+    ctx.check(_lib.xpcs_selftest_timeout(ctx.h, limit_ms))
 
 
 def clock_ns() -> int:

@@ -121,3 +121,28 @@ def test_compressed_undefined_frames(X, ctx):
     out = run_compressed(X, ctx, B, A, qmap, n_q, "bf16x3")
     np.testing.assert_array_equal(np.isnan(lower(out["C"])), np.isnan(lower(Cref)))
     _check(out, Cref, n_q, "bf16x3")
+
+
+def test_grouped_sector_masks_uneven_sizes(X, ctx):
+    # ring-plus-sector masks with log-spaced, uneven pixel counts (20 .. 1500 px, 16
+    # masks, pixels outside every mask unused), all in one launch: the compressed path
+    # against the FP64 oracle, and the exact raw path's integer Gram bit for bit
+    from synth import sector_qmap
+    from tests.gpu_util import run_raw
+
+    H, W, T, k = 96, 96, 300, 40
+    qmap = sector_qmap(H, W, n_annuli=4, n_sectors=4, min_px=20, max_px=1500, seed=7)
+    n_q = int(qmap.max()) + 1
+    assert n_q == 16 and (qmap < 0).any()
+    frames = speckle_counts(H, W, T + 200, 0.5, 2e-3, 20356003, np.uint16)
+    B, _ = O.fit_basis(frames[:200], k)
+    Xs = frames[200:]
+    A = O.encode(Xs, B).astype(np.float32).astype(np.float64)
+    G, s, Mq = O.ring_factors(B, qmap, n_q)
+    Cref, _ = O.compressed_twotime(A, G, s, Mq)
+    out = run_compressed(X, ctx, B, A, qmap, n_q, "bf16x3")
+    _check(out, Cref, n_q, "bf16x3")
+    raw = run_raw(X, ctx, Xs, qmap, n_q)
+    for q in range(n_q):
+        Nref = O.raw_gram(Xs, qmap, q)
+        assert np.array_equal(lower(raw["N"][q]), lower(Nref)), q
