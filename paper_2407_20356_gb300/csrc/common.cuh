@@ -195,4 +195,16 @@ XPCS_DEV bool named_bar_sync_or(int id, int nthreads, bool pred) {
 
 XPCS_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Two float32 additions in one instruction (round to nearest, each lane of the pair exact
+// as a scalar add.rn.f32).
+XPCS_DEV unsigned long long add_f32x2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+XPCS_DEV float2 u64_as_float2(unsigned long long x) {
+  return make_float2(__uint_as_float((uint32_t)x), __uint_as_float((uint32_t)(x >> 32)));
+}
+
 }  // namespace xpcs

@@ -29,13 +29,15 @@
 // C store: C is symmetric, so tile (I, J >= I) is written transposed into the lower
 // triangle, straight from registers and fully coalesced.
 //
-// Diagonal sums: a diagonal warp holds 32 tile rows (its lane quarter) x 64 columns and
-// treats them as two 32x32 blocks.  Lane i writes row i of a block rotated by i into the
-// warp's own 32x32 shared buffer, P[i][(j - i) mod 32] = C(i, j), then lane d sums column
-// d of P: rows i < 32 - d hold block diagonal j - i = d, rows i >= 32 - d hold j - i =
-// d - 32.  Both the writes and the reads touch 32 distinct banks.  The warps need no
-// barrier per tile; the eight warps' per-lane sums meet once per work item, added in a
-// fixed order.
+// Diagonal sums: a diagonal warp holds 32 tile rows (its lane quarter) x 64 columns of the
+// accumulator and takes them as two 32x32 blocks.  Lane i stores block element (i, j) at
+// row j - i + 32, column i of the warp's own skewed buffer Q (64 rows of 36 floats): every
+// block diagonal j - i lands on one row, the per-lane base address is fixed and the 32
+// stores use constant offsets, hitting 32 distinct banks (bank 4 j - 3 i mod 32).  Entries
+// no lane ever writes stay zero from the kernel start.  Lane d then adds up rows d and
+// d + 32 (block diagonals d - 32 and d) with 16-byte loads and packed f32x2 adds.  The
+// warps need no barrier per tile; the eight warps' per-lane sums meet once per work item,
+// added in a fixed order.
 
 #include "common.cuh"
 #include "internal.h"
@@ -44,16 +46,21 @@ namespace xpcs {
 
 namespace {
 
-constexpr int NSTAGE = 3;
+#ifndef XPCS_GRAM_NSTAGE
+#define XPCS_GRAM_NSTAGE 3
+#endif
+constexpr int NSTAGE = XPCS_GRAM_NSTAGE;           // operand stages (one K chunk of L and R each)
 constexpr int CHUNK_BYTES = TILE * KCH * 2;        // one operand chunk: 128 rows x 128 B
 constexpr int STAGE_BYTES = 2 * CHUNK_BYTES;       // L + R
 constexpr int N_DIAG_WARPS = 8;
-constexpr int PRIV_FLOATS = 32 * 32;                   // one warp's rotated 32x32 block
+constexpr int Q_ROWS = 64, Q_LD = 36;                  // one warp's skewed buffer (row = j - i + 32)
+constexpr int PRIV_FLOATS = Q_ROWS * Q_LD;
 constexpr int RED_FLOATS = N_DIAG_WARPS * 3 * 32;      // per-warp sums of a work item
 constexpr int DIAG_BYTES = (N_DIAG_WARPS * PRIV_FLOATS + RED_FLOATS) * 4;
 constexpr int GRAM_THREADS = 64 + 4 * 32 + N_DIAG_WARPS * 32;  // producer, MMA, 4 drain, 8 diagonal warps
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + DIAG_BYTES + BAR_BYTES;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 constexpr uint32_t TMEM_COLS = 256;                // two 128-column accumulators
 constexpr int DIAG_BAR = 1;                        // named barrier of the eight diagonal warps
 
@@ -297,10 +304,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     const int dw = warp - 6;
     const int r = warp & 3;
     const int h = dw >> 2;
-    float* P = diag_smem + dw * PRIV_FLOATS;
+    float* Q = diag_smem + dw * PRIV_FLOATS;
     float* red = diag_smem + N_DIAG_WARPS * PRIV_FLOATS;  // [warp][k][lane]
     const int i_row = r * 32 + lane;
-    const int lim = 32 - lane;  // rows of P whose column `lane` lies on the block diagonal d = lane
+    for (int x = lane; x < PRIV_FLOATS; x += 32) Q[x] = 0.f;  // entries never written stay 0
+    float* qw = Q + (32 - lane) * Q_LD + lane;                // block element (lane, j) at qw[Q_LD * j]
     uint32_t tile = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
@@ -335,29 +343,26 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
           }
-          __syncwarp();  // the previous block's reads are done
-          {
-            // rotated row: column (j - lane) mod 32, walked with one running offset
-            float* prow = P + lane * 32;
-            int c = (32 - lane) & 31;
+          __syncwarp();  // the previous block's row sums are read
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              prow[c] = __uint_as_float(v[j]);
-              c = (c + 1) & 31;
-            }
-          }
+          for (int j = 0; j < 32; ++j) qw[Q_LD * j] = __uint_as_float(v[j]);
           __syncwarp();
-          float an = 0.f, aw = 0.f;
-#pragma unroll 8
-          for (int i = 0; i < 32; ++i) {
-            const float x = P[i * 32 + lane];
-            if (i < lim)
-              an += x;
-            else
-              aw += x;
+          // row 32 k + lane holds block diagonal 32 (k - 1) + lane, which is diagonal
+          // e = b - r - 1 + k of the tile grid (acc[sb + k]): 8 x 16-byte loads, two packed
+          // accumulators of depth 8
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const ulonglong2* row = reinterpret_cast<const ulonglong2*>(Q + (32 * k + lane) * Q_LD);
+            ulonglong2 s = row[0];
+#pragma unroll
+            for (int m = 1; m < 8; ++m) {
+              const ulonglong2 x = row[m];
+              s.x = add_f32x2(s.x, x.x);
+              s.y = add_f32x2(s.y, x.y);
+            }
+            const float2 lo = u64_as_float2(s.x), hi = u64_as_float2(s.y);
+            acc[sb + k] += (lo.x + lo.y) + (hi.x + hi.y);
           }
-          acc[sb + 1] += an;  // e = b - r
-          acc[sb] += aw;      // e = b - r - 1
         }
       }
       // every diagonal warp reaches these barriers once per item, also after an abort
