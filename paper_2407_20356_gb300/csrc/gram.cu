@@ -30,14 +30,17 @@
 // triangle, straight from registers and fully coalesced.
 //
 // Diagonal sums: a diagonal warp holds 32 tile rows (its lane quarter) x 64 columns of the
-// accumulator and takes them as two 32x32 blocks.  Lane i stores block element (i, j) at
-// row j - i + 32, column i of the warp's own skewed buffer Q (64 rows of 36 floats): every
-// block diagonal j - i lands on one row, the per-lane base address is fixed and the 32
-// stores use constant offsets, hitting 32 distinct banks (bank 4 j - 3 i mod 32).  Entries
-// no lane ever writes stay zero from the kernel start.  Lane d then adds up rows d and
-// d + 32 (block diagonals d - 32 and d) with 16-byte loads and packed f32x2 adds.  The
-// warps need no barrier per tile; the eight warps' per-lane sums meet once per work item,
-// added in a fixed order.
+// accumulator.  Lane i stores element (i, j) at row j - i + 32, column i of the warp's own
+// skewed buffer Q (96 rows of 36 floats): every diagonal j - i lands on one row, the
+// per-lane base address is fixed and the stores use constant offsets, hitting 32 distinct
+// banks (bank 4 j - 3 i mod 32).  Entries no lane ever writes stay zero from the kernel
+// start.  Lane d then adds up its rows with 16-byte loads and packed f32x2 adds, skipping
+// the 16-byte groups that hold no entry (those lanes issue no shared-memory traffic).  Two
+// schedules, chosen by operand format (each measured faster for its own): with hi/lo
+// operand pieces the whole 64-column strip is stored and rows d, d + 32, d + 64 are read
+// once; with single operands each 32-column block is stored and read (rows d, d + 32) in
+// turn.  The warps need no barrier per tile; the eight warps' per-lane sums meet once per
+// work item, added in a fixed order.
 
 #include "common.cuh"
 #include "internal.h"
@@ -53,16 +56,39 @@ constexpr int NSTAGE = XPCS_GRAM_NSTAGE;           // operand stages (one K chun
 constexpr int CHUNK_BYTES = TILE * KCH * 2;        // one operand chunk: 128 rows x 128 B
 constexpr int STAGE_BYTES = 2 * CHUNK_BYTES;       // L + R
 constexpr int N_DIAG_WARPS = 8;
-constexpr int Q_ROWS = 64, Q_LD = 36;                  // one warp's skewed buffer (row = j - i + 32)
-constexpr int PRIV_FLOATS = Q_ROWS * Q_LD;
+constexpr int Q_LD = 36;                               // skewed buffer row: 32 floats + 4 pad
 constexpr int RED_FLOATS = N_DIAG_WARPS * 3 * 32;      // per-warp sums of a work item
-constexpr int DIAG_BYTES = (N_DIAG_WARPS * PRIV_FLOATS + RED_FLOATS) * 4;
 constexpr int GRAM_THREADS = 64 + 4 * 32 + N_DIAG_WARPS * 32;  // producer, MMA, 4 drain, 8 diagonal warps
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + DIAG_BYTES + BAR_BYTES;
-static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
+// Shared memory of the kernel for one diagonal schedule (STRIP: whole 64-column strip,
+// 96 skewed rows per warp; otherwise one 32-column block at a time, 64 rows).
+template <bool STRIP>
+struct GramSmem {
+  static constexpr int q_rows = STRIP ? 96 : 64;
+  static constexpr int priv = q_rows * Q_LD;  // floats of one warp's skewed buffer
+  static constexpr int diag_bytes = (N_DIAG_WARPS * priv + RED_FLOATS) * 4;
+  static constexpr int bytes = 1024 + NSTAGE * STAGE_BYTES + diag_bytes + BAR_BYTES;
+  static_assert(bytes <= 227 * 1024, "shared memory of one CTA");
+};
 constexpr uint32_t TMEM_COLS = 256;                // two 128-column accumulators
 constexpr int DIAG_BAR = 1;                        // named barrier of the eight diagonal warps
+
+// Sum of one row of a skewed buffer whose entries lie in columns i in [lo, hi); the
+// 16-byte groups outside that range hold zeros and are not read.
+__device__ __forceinline__ float skew_row_sum(const float* Q, int row, int lo, int hi) {
+  const ulonglong2* v = reinterpret_cast<const ulonglong2*>(Q + row * Q_LD);
+  ulonglong2 s = make_ulonglong2(0ull, 0ull);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    if (4 * m + 3 >= lo && 4 * m < hi) {
+      const ulonglong2 x = v[m];
+      s.x = add_f32x2(s.x, x.x);
+      s.y = add_f32x2(s.y, x.y);
+    }
+  }
+  const float2 a = u64_as_float2(s.x), b = u64_as_float2(s.y);
+  return (a.x + a.y) + (b.x + b.y);
+}
 
 // Stores one 32-column chunk of a tile row: element (i, j) of tile (I, J) is C(t1, t2)
 // with t1 = 128 I + i, t2 = 128 J + j, written transposed at [t2][t1] (lower triangle) so
@@ -104,6 +130,7 @@ __device__ __forceinline__ void store_chunk(const GramParams& p, uint32_t (&v)[3
   }
 }
 
+template <bool STRIP>
 __global__ void __launch_bounds__(GRAM_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR,
                const GramParams p) {
@@ -111,7 +138,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stages = smem;
   float* diag_smem = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES + DIAG_BYTES);
+  using SM = GramSmem<STRIP>;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES + SM::diag_bytes);
   uint64_t* full = bars;                    // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;          // [NSTAGE]
   uint64_t* tfull = bars + 2 * NSTAGE;      // [2]
@@ -304,11 +332,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     const int dw = warp - 6;
     const int r = warp & 3;
     const int h = dw >> 2;
-    float* Q = diag_smem + dw * PRIV_FLOATS;
-    float* red = diag_smem + N_DIAG_WARPS * PRIV_FLOATS;  // [warp][k][lane]
+    float* Q = diag_smem + dw * SM::priv;
+    float* red = diag_smem + N_DIAG_WARPS * SM::priv;  // [warp][k][lane]
     const int i_row = r * 32 + lane;
-    for (int x = lane; x < PRIV_FLOATS; x += 32) Q[x] = 0.f;  // entries never written stay 0
-    float* qw = Q + (32 - lane) * Q_LD + lane;                // block element (lane, j) at qw[Q_LD * j]
+    for (int x = lane; x < SM::priv; x += 32) Q[x] = 0.f;  // entries never written stay 0
+    float* qw = Q + (32 - lane) * Q_LD + lane;                // element (lane, j) at qw[Q_LD * j]
     uint32_t tile = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
@@ -326,42 +354,55 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           break;
         }
         tc_fence_after();
-        // one 32-column block at a time; TMEM is released once block 1 is in registers
         const uint32_t tbase = tmem_base + b * TILE + ((uint32_t)(r * 32) << 16) + 64 * h;
         const float* rj = rq + (size_t)J * TILE + 64 * h;
+        if constexpr (STRIP) {
+          // whole strip: row 32 k + lane holds strip diagonal 32 (k - 1) + lane (acc[k])
+          __syncwarp();  // the previous tile's row sums are read
 #pragma unroll
-        for (int sb = 0; sb < 2; ++sb) {
-          uint32_t v[32];
-          tmem_ld32(tbase + 32 * sb, v);
-          tc_wait_ld();
-          if (sb == 1) {
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
-          }
-          if (p.raw) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
-          }
-          __syncwarp();  // the previous block's row sums are read
-#pragma unroll
-          for (int j = 0; j < 32; ++j) qw[Q_LD * j] = __uint_as_float(v[j]);
-          __syncwarp();
-          // row 32 k + lane holds block diagonal 32 (k - 1) + lane, which is diagonal
-          // e = b - r - 1 + k of the tile grid (acc[sb + k]): 8 x 16-byte loads, two packed
-          // accumulators of depth 8
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const ulonglong2* row = reinterpret_cast<const ulonglong2*>(Q + (32 * k + lane) * Q_LD);
-            ulonglong2 s = row[0];
-#pragma unroll
-            for (int m = 1; m < 8; ++m) {
-              const ulonglong2 x = row[m];
-              s.x = add_f32x2(s.x, x.x);
-              s.y = add_f32x2(s.y, x.y);
+          for (int sb = 0; sb < 2; ++sb) {
+            uint32_t v[32];
+            tmem_ld32(tbase + 32 * sb, v);
+            tc_wait_ld();
+            if (sb == 1) {  // TMEM is released once block 1 is in registers
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&tempty[b]);
             }
-            const float2 lo = u64_as_float2(s.x), hi = u64_as_float2(s.y);
-            acc[sb + k] += (lo.x + lo.y) + (hi.x + hi.y);
+            if (p.raw) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) qw[Q_LD * (32 * sb + j)] = __uint_as_float(v[j]);
+          }
+          __syncwarp();
+          acc[0] += skew_row_sum(Q, lane, 32 - lane, 32);
+          acc[1] += skew_row_sum(Q, 32 + lane, 0, 32);
+          acc[2] += skew_row_sum(Q, 64 + lane, 0, 32 - lane);
+        } else {
+          // one 32-column block at a time: row lane holds block diagonal lane - 32 (acc[sb]),
+          // row 32 + lane block diagonal lane (acc[sb + 1])
+#pragma unroll
+          for (int sb = 0; sb < 2; ++sb) {
+            uint32_t v[32];
+            tmem_ld32(tbase + 32 * sb, v);
+            tc_wait_ld();
+            if (sb == 1) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&tempty[b]);
+            }
+            if (p.raw) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
+            }
+            __syncwarp();  // the previous block's row sums are read
+#pragma unroll
+            for (int j = 0; j < 32; ++j) qw[Q_LD * j] = __uint_as_float(v[j]);
+            __syncwarp();
+            acc[sb] += skew_row_sum(Q, lane, 32 - lane, 32);
+            acc[sb + 1] += skew_row_sum(Q, 32 + lane, 0, 32 - lane);
           }
         }
       }
@@ -398,18 +439,27 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
 
 }  // namespace
 
-int gram_smem_bytes() { return SMEM_BYTES; }
+int gram_smem_bytes() { return GramSmem<true>::bytes > GramSmem<false>::bytes ? GramSmem<true>::bytes : GramSmem<false>::bytes; }
 
-cudaError_t launch_gram(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
-                        cudaStream_t st) {
+template <bool STRIP>
+static cudaError_t launch_gram_t(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
+                                 cudaStream_t st) {
+  constexpr int smem = GramSmem<STRIP>::bytes;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<STRIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  gram_tc_kernel<<<grid, GRAM_THREADS, SMEM_BYTES, st>>>(tmL, tmR, p);
+  gram_tc_kernel<STRIP><<<grid, GRAM_THREADS, smem, st>>>(tmL, tmR, p);
   return cudaGetLastError();
+}
+
+// hi/lo operand pieces take the whole-strip diagonal schedule, single operands (and the raw
+// path) the block schedule
+cudaError_t launch_gram(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
+                        cudaStream_t st) {
+  return p.split ? launch_gram_t<true>(tmL, tmR, p, grid, st) : launch_gram_t<false>(tmL, tmR, p, grid, st);
 }
 
 }  // namespace xpcs
