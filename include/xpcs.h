@@ -51,6 +51,21 @@ typedef enum xpcs_precision {
   XPCS_PREC_BF16X3 = 2 /* hi/lo bf16 split, three products: about 2^-16 */
 } xpcs_precision;
 
+/* Normalisation of the two-time correlation, as a per-frame scale r_q(t) with
+ * C_q(t1,t2) = r_q(t1) r_q(t2) N_q(t1,t2) and g2_q(tau) the mean of C_q over the defined
+ * pairs of the tau-th diagonal:
+ *   XPCS_NORM_MEAN  Eq. 1: r = sqrt(M_q) / S_q(t) (per-frame ring mean); frames with
+ *                   S_q(t) <= 0 are undefined (the default of xpcs_twotime{,_raw});
+ *   XPCS_NORM_FROB  Eq. 2 with rows normalised by their Frobenius norm (Sec. 2.1):
+ *                   r = 1 / sqrt(N_q(t,t)), C is the cosine similarity of the ring's
+ *                   frames; frames with N_q(t,t) = 0 are undefined;
+ *   XPCS_NORM_EQ12  Eq. 12 literally: r = sqrt(M_q) / Sbar_q with Sbar_q the mean of
+ *                   S_q(t) over the T frames, so g2 = <I(t) I(t+tau)> / <I>^2 with both
+ *                   averages over frames and ring pixels; every frame is defined.
+ * On the compressed path N~ and S~ take the place of N and S (N~_q(t,t) = a_t G_q a_t^T,
+ * Sbar~_q = abar s_q with abar the mean coefficient row). */
+typedef enum xpcs_norm { XPCS_NORM_MEAN = 0, XPCS_NORM_FROB = 1, XPCS_NORM_EQ12 = 2 } xpcs_norm;
+
 typedef struct xpcs_ctx xpcs_ctx;
 typedef struct xpcs_rings xpcs_rings;
 typedef struct xpcs_basis xpcs_basis;
@@ -120,6 +135,11 @@ xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X
  * int64 (lower triangle), g2_out n_q x T f64, count_out n_q x T int64. */
 xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X, xpcs_dtype dtype, int64_t T,
                              float* C_out, int64_t* N_out, double* g2_out, int64_t* count_out);
+/* xpcs_twotime_raw with a chosen normalisation (xpcs_norm); norm = XPCS_NORM_MEAN is
+ * xpcs_twotime_raw.  N_out is the integer Gram in every mode. */
+xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X, xpcs_dtype dtype,
+                                  int64_t T, xpcs_norm norm, float* C_out, int64_t* N_out, double* g2_out,
+                                  int64_t* count_out);
 
 /* ------------------------------------------------------------------ basis (Eq. 3-6)
  * Fit the encoding matrix V_K (M x k) on n_fit frames F (T x M layout, n_fit rows):
@@ -138,6 +158,14 @@ xpcs_status xpcs_basis_import(xpcs_ctx* ctx, const xpcs_rings* rings, const doub
 xpcs_status xpcs_basis_export(xpcs_ctx* ctx, const xpcs_basis* basis, double* B_host, double* G_host,
                               double* s_host);
 xpcs_status xpcs_basis_rank(const xpcs_basis* basis, int* k);
+/* Rank choice from a fitted spectrum (Sec. 3.1, offline lossy compression): the number of
+ * components whose value in the spectrum is at least `factor` times its smallest value
+ * (the paper's rule uses factor 2).  sigma_host: n values in descending order, as
+ * xpcs_fit_basis returns them; values at or below the numerical-rank cutoff
+ * (sigma^2 <= n * eps * sigma_max^2) are left out, so the minimum is taken over the
+ * numerical rank.  Host-side, no context needed.  Returns K >= 0, or -1 for a null
+ * pointer, n <= 0, factor <= 0 or a spectrum that is not descending. */
+int xpcs_rank_from_spectrum(const double* sigma_host, int n, double factor);
 xpcs_status xpcs_basis_destroy(xpcs_basis* basis);
 
 /* ------------------------------------------------------------------ encode (Eq. 7)
@@ -154,6 +182,11 @@ xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* basis, const void* X, x
  * Outputs nullable as for xpcs_twotime_raw. */
 xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T, xpcs_precision prec,
                          float* C_out, double* g2_out, int64_t* count_out);
+/* xpcs_twotime with a chosen normalisation (xpcs_norm); norm = XPCS_NORM_MEAN is
+ * xpcs_twotime. */
+xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T,
+                              xpcs_precision prec, xpcs_norm norm, float* C_out, double* g2_out,
+                              int64_t* count_out);
 
 /* ------------------------------------------------------------------ g2 over a stored C
  * g2_q(tau) = mean over t of C[q][t+tau][t], NaN entries skipped, from the lower

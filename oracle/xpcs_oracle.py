@@ -34,7 +34,7 @@ __all__ = [
     "compressed_ring_gram", "compressed_ring_sums", "compressed_twotime",
     "decompress", "raw_pair_values", "compressed_pair_values", "g2_eq12",
     "frobenius_twotime", "windowed_g2", "compression_ratio_offline",
-    "compression_ratio_online", "lossless_speedup",
+    "compression_ratio_online", "lossless_speedup", "rank_from_spectrum", "twotime_eq12",
 ]
 
 
@@ -148,6 +148,24 @@ def fit_basis(F: np.ndarray, k: int):
     return B, sigma
 
 
+def rank_from_spectrum(sigma: np.ndarray, factor: float = 2.0) -> int:
+    """Rank choice of Sec. 3.1: how many values of the spectrum are at least `factor`
+    times its smallest value (the paper counts those "twice as large as the minimum").
+
+    The spectrum is the descending list of singular values returned by fit_basis.  Values
+    at or below the numerical-rank cutoff (sigma^2 <= n eps sigma_max^2, the cutoff
+    fit_basis applies to the eigenvalues) are not part of it, so a rank-deficient fit
+    does not make the minimum zero.
+    """
+    s = np.asarray(sigma, dtype=np.float64)
+    n = s.size
+    tol = n * np.finfo(np.float64).eps * max(s[0], 0.0) ** 2
+    kept = s[(s > 0) & (s * s > tol)]
+    if kept.size == 0:
+        return 0
+    return int((kept >= factor * kept.min()).sum())
+
+
 # ---------------------------------------------------------------- compressed path (Eq. 7-10)
 
 def encode(X: np.ndarray, B: np.ndarray) -> np.ndarray:
@@ -249,6 +267,19 @@ def frobenius_twotime(Nq: np.ndarray) -> np.ndarray:
     ok = den > 0
     out[ok] = np.asarray(Nq, dtype=np.float64)[ok] / den[ok]
     return out
+
+
+def twotime_eq12(Nq: np.ndarray, S: np.ndarray, Mq: float) -> np.ndarray:
+    """Two-time form of the literal Eq. 12: M_q N(t1,t2) / Sbar^2, Sbar the ring sum averaged
+    over all T frames.  Its mean along the tau-th diagonal (every pair counts) is
+    <I(q,t) I(q,t+tau)> / <I(q)>^2 with both averages over frames and the ring's pixels.
+    NaN everywhere if Sbar <= 0.
+    """
+    Sbar = float(np.mean(np.asarray(S, dtype=np.float64)))
+    N = np.asarray(Nq, dtype=np.float64)
+    if Sbar <= 0:
+        return np.full(N.shape, np.nan)
+    return float(Mq) * N / (Sbar * Sbar)
 
 
 def windowed_g2(C: np.ndarray, W: int):

@@ -408,6 +408,8 @@ namespace {
 struct RawBuffers {
   __nv_bfloat16* Xp;
   long long* S;
+  long long* S2;  // per-frame sums of squares (Frobenius normalisation only)
+  double* Sbar;   // ring means of S (Eq. 12 normalisation only)
   unsigned long long* sq;
   float* r;
   uint32_t* blk_bad;
@@ -433,6 +435,7 @@ xpcs_status raw_ingest(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_d
   ip.n_q = R->n_q;
   ip.Xp = want_xp ? b.Xp : nullptr;
   ip.S = S;
+  ip.S2 = b.S2;
   ip.sq = b.sq;
   ip.status = ctx->d_status;
   XPCS_LAUNCH(ctx, "ingest", 1, launch_raw_ingest(ip, ctx->stream));
@@ -496,7 +499,14 @@ xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap
 
 extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_dtype dtype,
                                         int64_t T, float* C_out, int64_t* N_out, double* g2_out, int64_t* count_out) {
-  if (!ctx || !R || !X || T <= 0 || R->ctx != ctx || (dtype != XPCS_U8 && dtype != XPCS_U16))
+  return xpcs_twotime_raw_norm(ctx, R, X, dtype, T, XPCS_NORM_MEAN, C_out, N_out, g2_out, count_out);
+}
+
+extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_dtype dtype,
+                                             int64_t T, xpcs_norm norm, float* C_out, int64_t* N_out,
+                                             double* g2_out, int64_t* count_out) {
+  if (!ctx || !R || !X || T <= 0 || R->ctx != ctx || (dtype != XPCS_U8 && dtype != XPCS_U16) || (int)norm < 0 ||
+      (int)norm > 2)
     return fail(ctx, XPCS_EINVAL, "bad twotime_raw args");
   if (T > (1 << 24)) return fail(ctx, XPCS_ENOTSUP, "T too large");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -510,6 +520,8 @@ extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, cons
   auto layout = [&](Carve& c, RawBuffers& b) {
     b.Xp = c.take<__nv_bfloat16>((size_t)T_pad * R->Mp);
     b.S = c.take<long long>((size_t)n_q * T);
+    b.S2 = norm == XPCS_NORM_FROB ? c.take<long long>((size_t)n_q * T) : nullptr;
+    b.Sbar = norm == XPCS_NORM_EQ12 ? c.take<double>(n_q) : nullptr;
     b.sq = c.take<unsigned long long>(n_q);
     b.r = c.take<float>((size_t)n_q * T_pad);
     b.blk_bad = c.take<uint32_t>((size_t)n_q * nT);
@@ -525,8 +537,11 @@ extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, cons
   layout(c1, b);
   if (count_out) b.count = reinterpret_cast<long long*>(count_out);
   XPCS_TRY(raw_ingest(ctx, R, X, dtype, T, T_pad, nT, true, b.S, b));
-  XPCS_LAUNCH(ctx, "raw_scales", 1, launch_raw_scales(b.S, R->d_Mq, n_q, T, T_pad, nT, b.sq, b.r, b.blk_bad, ctx->d_status,
-                                   ctx->stream));
+  if (norm == XPCS_NORM_EQ12)
+    XPCS_LAUNCH(ctx, "ring_mean", 1, launch_ring_mean(b.S, n_q, T, b.Sbar, ctx->stream));
+  XPCS_LAUNCH(ctx, "raw_scales", 1,
+              launch_raw_scales(b.S, b.S2, b.Sbar, (int)norm, R->d_Mq, n_q, T, T_pad, nT, b.sq, b.r, b.blk_bad,
+                                ctx->d_status, ctx->stream));
   CUtensorMap tm;
   XPCS_TRY(make_map(ctx, &tm, b.Xp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, R->Mp, T_pad, KCH, TILE,
                     CU_TENSOR_MAP_SWIZZLE_128B));
@@ -779,11 +794,33 @@ extern "C" xpcs_status xpcs_fit_basis(xpcs_ctx* ctx, const xpcs_rings* R, const 
   return XPCS_OK;
 }
 
+extern "C" int xpcs_rank_from_spectrum(const double* sigma, int n, double factor) {
+  if (!sigma || n <= 0 || !(factor > 0.0)) return -1;
+  for (int i = 1; i < n; ++i)
+    if (!(sigma[i] <= sigma[i - 1])) return -1;  // descending (NaN fails too)
+  const double smax = std::max(sigma[0], 0.0);
+  const double tol = (double)n * 2.220446049250313e-16 * smax * smax;
+  int rank = 0;
+  while (rank < n && sigma[rank] * sigma[rank] > tol && sigma[rank] > 0.0) ++rank;
+  if (rank == 0) return 0;
+  const double cut = factor * sigma[rank - 1];
+  int K = 0;
+  while (K < rank && sigma[K] >= cut) ++K;
+  return K;
+}
+
 // ====================================================================== compressed path
 
 extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const float* A, int64_t T,
                                     xpcs_precision prec, float* C_out, double* g2_out, int64_t* count_out) {
-  if (!ctx || !B || !A || T <= 0 || B->ctx != ctx || (int)prec < 0 || (int)prec > 2)
+  return xpcs_twotime_norm(ctx, B, A, T, prec, XPCS_NORM_MEAN, C_out, g2_out, count_out);
+}
+
+extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, const float* A, int64_t T,
+                                         xpcs_precision prec, xpcs_norm norm, float* C_out, double* g2_out,
+                                         int64_t* count_out) {
+  if (!ctx || !B || !A || T <= 0 || B->ctx != ctx || (int)prec < 0 || (int)prec > 2 || (int)norm < 0 ||
+      (int)norm > 2)
     return fail(ctx, XPCS_EINVAL, "bad twotime args");
   if (T > (1 << 24)) return fail(ctx, XPCS_ENOTSUP, "T too large");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -799,6 +836,7 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   const bool want_cnt = want_g2 || count_out;
   struct Bufs {
     uint16_t *L, *R;
+    double* Sbar;
     float* r;
     uint32_t* blk_bad;
     float* partials;
@@ -808,6 +846,7 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   auto layout = [&](Carve& c) {
     b.L = c.take<uint16_t>((size_t)n_q * T_pad * Kc);
     b.R = c.take<uint16_t>((size_t)n_q * T_pad * Kc);
+    b.Sbar = norm == XPCS_NORM_EQ12 ? c.take<double>(n_q) : nullptr;
     b.r = c.take<float>((size_t)n_q * T_pad);
     b.blk_bad = c.take<uint32_t>((size_t)n_q * nT);
     b.partials = want_g2 ? c.take<float>((size_t)n_q * nT * maxC * DIAG_SLOTS) : nullptr;
@@ -838,6 +877,10 @@ extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const fl
   pp.r = b.r;
   pp.blk_bad = b.blk_bad;
   pp.St = nullptr;
+  pp.norm = (int)norm;
+  pp.Sbar = b.Sbar;
+  if (norm == XPCS_NORM_EQ12)
+    XPCS_LAUNCH(ctx, "coef_mean", 1, launch_coef_mean(A, T, k, B->d_s, n_q, b.Sbar, ctx->stream));
   XPCS_LAUNCH(ctx, "compressed_prep", 1, launch_prep_compressed(pp, ctx->stream));
   const CUtensorMapDataType dt =
       prec == XPCS_PREC_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;

@@ -67,16 +67,24 @@ struct RawIngestParams {
   int n_q;
   __nv_bfloat16* Xp;       // [T_pad][Mp] (nullable when only sums are wanted)
   long long* S;            // [n_q][T]
+  long long* S2;           // nullable [n_q][T] per-frame sum of squared counts
   unsigned long long* sq;  // [n_q] max over frames of sum of squares (atomicMax)
   uint32_t* status;
 };
 cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st);
 
-// r[q][t] = sqrt(Mq)/S (raw int64 sums) and block flags
+// r[q][t] for the chosen normalisation (xpcs_norm) from the raw int64 sums S, the
+// per-frame sums of squares S2 (FROB) or the ring means Sbar (EQ12), and block flags
 // (also flags XPCS_DEV_RANGE when a ring's max sum of squares reaches 2^24)
-cudaError_t launch_raw_scales(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
+cudaError_t launch_raw_scales(const long long* S, const long long* S2, const double* Sbar, int norm,
+                              const long long* Mq, int n_q, long long T, int T_pad, int nT,
                               const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status,
                               cudaStream_t st);
+// Sbar[q] = mean over T frames of S[q][t]
+cudaError_t launch_ring_mean(const long long* S, int n_q, long long T, double* Sbar, cudaStream_t st);
+// Sbar[q] = (column means of A) . s_q, the compressed ring sum averaged over T frames
+cudaError_t launch_coef_mean(const float* A, long long T, int k, const double* s64, int n_q, double* Sbar,
+                             cudaStream_t st);
 
 struct PrepParams {
   const float* A;          // [T][k]
@@ -95,6 +103,8 @@ struct PrepParams {
   float* r;                // [n_q][T_pad]
   uint32_t* blk_bad;        // [n_q][nT]
   double* St;              // nullable [n_q][T] compressed ring sums
+  int norm;                // xpcs_norm
+  const double* Sbar;      // [n_q] mean compressed ring sums (XPCS_NORM_EQ12)
 };
 cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st);
 

@@ -85,14 +85,19 @@ __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p
   if (live) {
     for (int q = threadIdx.x; q < p.n_q; q += blockDim.x) {
       p.S[(size_t)q * p.T + t] = (long long)ssum[q];
+      if (p.S2) p.S2[(size_t)q * p.T + t] = (long long)ssq[q];
       atomicMax(&p.sq[q], ssq[q]);
     }
   }
 }
 
-// r[q][t] = sqrt(M_q) / S_q(t) for defined frames, 0 otherwise; blk_bad marks tiles with
-// an undefined frame inside the series.
-__global__ void raw_scales_kernel(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
+// Per-frame operand scale r[q][t], so that C = r(t1) r(t2) N(t1,t2):
+//   XPCS_NORM_MEAN  r = sqrt(M_q) / S_q(t)          (Eq. 1), undefined if S_q(t) <= 0
+//   XPCS_NORM_FROB  r = 1 / sqrt(sum_p x_{t,p}^2)   (Eq. 2 with Frobenius rows), undefined if 0
+//   XPCS_NORM_EQ12  r = sqrt(M_q) / mean_t S_q(t)   (Eq. 12), every frame defined
+// Undefined frames get r = 0; blk_bad marks tiles with an undefined frame.
+__global__ void raw_scales_kernel(const long long* S, const long long* S2, const double* Sbar, int norm,
+                                  const long long* Mq, int n_q, long long T, int T_pad, int nT,
                                   const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status) {
   const int q = blockIdx.y, I = blockIdx.x;
   if (I == 0 && threadIdx.x == 0 && sq && sq[q] >= (1ull << 24)) set_status(status, XPCS_DEV_RANGE);
@@ -100,15 +105,54 @@ __global__ void raw_scales_kernel(const long long* S, const long long* Mq, int n
   float v = 0.f;
   bool bad = false;
   if (t < T) {
-    const long long s = S[(size_t)q * T + t];
-    if (s > 0)
-      v = (float)(sqrt((double)Mq[q]) / (double)s);
+    double den;
+    if (norm == XPCS_NORM_FROB)
+      den = sqrt((double)S2[(size_t)q * T + t]);
+    else if (norm == XPCS_NORM_EQ12)
+      den = Sbar[q] / sqrt((double)Mq[q]);
+    else
+      den = (double)S[(size_t)q * T + t] / sqrt((double)Mq[q]);
+    if (den > 0.0)
+      v = (float)(1.0 / den);
     else
       bad = true;
   }
   r[(size_t)q * T_pad + t] = v;
   const int any = __syncthreads_or(bad);
   if (threadIdx.x == 0) blk_bad[(size_t)q * nT + I] = (uint32_t)any;
+}
+
+// Sbar[q] = mean over the T frames of the raw ring sums S_q(t) (FP64, fixed order).
+__global__ void __launch_bounds__(256) ring_mean_kernel(const long long* S, long long T, double* Sbar) {
+  __shared__ double red[256];
+  const int q = blockIdx.x;
+  long long acc = 0;  // exact: at most T * M_q * 65535 < 2^63
+  for (long long t = threadIdx.x; t < T; t += blockDim.x) acc += S[(size_t)q * T + t];
+  red[threadIdx.x] = (double)acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) Sbar[q] = red[0] / (double)T;
+}
+
+// Compressed Eq. 12 denominator: S~bar_q = mean_t a_t . s_q = abar . s_q (the ring sum is
+// linear in the coefficients), abar = column means of A in FP64.  One block.
+__global__ void __launch_bounds__(256) coef_mean_kernel(const float* A, long long T, int k, const double* s64,
+                                                        int n_q, double* Sbar) {
+  __shared__ double abar[256];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double acc = 0.0;
+    for (long long t = 0; t < T; ++t) acc += (double)A[t * k + c];
+    abar[c] = acc / (double)T;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n_q; q += blockDim.x) {
+    double d = 0.0;
+    for (int c = 0; c < k; ++c) d += abar[c] * s64[(size_t)q * k + c];
+    Sbar[q] = d;
+  }
 }
 
 // ---------------------------------------------------------------- compressed preparation
@@ -130,8 +174,8 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   extern __shared__ float sm[];
   const int k = p.k;
   const int lda = k + 1;
-  float* As = sm;                          // [64][k+1]  r * a
-  float* Ws = As + PREP_FRAMES * lda;      // [64][k+1]  r * a G_q
+  float* As = sm;                          // [64][k+1]  a
+  float* Ws = As + PREP_FRAMES * lda;      // [64][k+1]  a G_q
   float* Gs = Ws + PREP_FRAMES * lda;      // [k][64]
   const int q = blockIdx.y;
   const long long t0 = (long long)blockIdx.x * PREP_FRAMES;
@@ -178,19 +222,21 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
       if (t < p.T) {
         const double acc = (double)hi + (double)lo;
         if (p.St) p.St[(size_t)q * p.T + t] = acc;
-        if (acc > 0.0)
-          v = (float)(sqrt((double)p.Mq[q]) / acc);
-        else
-          atomicOr(&p.blk_bad[(size_t)q * p.nT + (t >> 7)], 1u);
+        // per-frame scale (xpcs_norm); the Frobenius one needs W and is set below
+        const double den = p.norm == XPCS_NORM_EQ12 ? p.Sbar[q] : acc;
+        if (p.norm != XPCS_NORM_FROB) {
+          if (den > 0.0)
+            v = (float)(sqrt((double)p.Mq[q]) / den);
+          else
+            atomicOr(&p.blk_bad[(size_t)q * p.nT + (t >> 7)], 1u);
+        }
       }
-      p.r[(size_t)q * p.T_pad + t] = v;
+      if (p.norm != XPCS_NORM_FROB) p.r[(size_t)q * p.T_pad + t] = v;
       rs[f] = v;
     }
   }
-  __syncthreads();
-  for (int f = tid >> 6; f < PREP_FRAMES; f += 4)
-    for (int c = tid & 63; c < k; c += 64) As[f * lda + c] *= rs[f];
-  // W = (r a) G_q in 64-column chunks: thread (fl, cg) computes frames fl and fl + 32,
+  // W = a G_q in 64-column chunks (the scale r is applied when the rows are written):
+  // thread (fl, cg) computes frames fl and fl + 32,
   // columns 8 cg .. 8 cg + 7 of the chunk (16 outputs, 4 shared loads per 16 FMAs)
   const int fl = tid & 31, cg = tid >> 5;
   const float* Gq = p.G32 + (size_t)q * k * k;
@@ -227,6 +273,45 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
       }
   }
   __syncthreads();
+  if (p.norm == XPCS_NORM_FROB) {
+    // ||x~_t||^2 over the ring = a_t G_q a_t^T = W_t . a_t, compensated as the ring sums
+    const int f = tid >> 2, part = tid & 3;
+    const float* wrow = Ws + f * lda;
+    const float* arow = As + f * lda;
+    float hi = 0.f, lo = 0.f;
+    for (int c = part; c < k; c += 4) {
+      const float x = wrow[c], y = arow[c];
+      const float prod = x * y;
+      const float perr = fmaf(x, y, -prod);
+      const float sum = hi + prod;
+      const float z = sum - hi;
+      lo += ((hi - (sum - z)) + (prod - z)) + perr;
+      hi = sum;
+    }
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+      const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+      const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+      const float sum = hi + ohi;
+      const float z = sum - hi;
+      lo += ((hi - (sum - z)) + (ohi - z)) + olo;
+      hi = sum;
+    }
+    if (part == 0) {
+      const long long t = t0 + f;
+      float v = 0.f;
+      if (t < p.T) {
+        const double n = (double)hi + (double)lo;
+        if (n > 0.0)
+          v = (float)(1.0 / sqrt(n));
+        else
+          atomicOr(&p.blk_bad[(size_t)q * p.nT + (t >> 7)], 1u);
+      }
+      p.r[(size_t)q * p.T_pad + t] = v;
+      rs[f] = v;
+    }
+    __syncthreads();
+  }
   // rows out: 8 threads per row, 16-byte vectors, coalesced 128-byte segments
   const int nvec = p.Kc / 8;
   const int piece = SPLIT ? p.Kc / 2 : p.Kc;  // split rows are [hi | lo], each `piece` wide
@@ -235,6 +320,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   for (int ff = tid >> 3; ff < PREP_FRAMES; ff += 32) {
     const float* wrow = Ws + ff * lda;
     const float* arow = As + ff * lda;
+    const float rf = rs[ff];
     for (int vv = tid & 7; vv < nvec; vv += 8) {
       // a vector never straddles the hi | lo boundary (piece is a multiple of 64)
       const bool lo = SPLIT && vv * 8 >= piece;
@@ -244,7 +330,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
       if (jb + 8 <= k) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const float wv = wrow[jb + e], av = arow[jb + e];
+          const float wv = rf * wrow[jb + e], av = rf * arow[jb + e];
           if (!lo) {
             lv[e] = to16<T16>(wv);
             rv[e] = to16<T16>(av);
@@ -257,7 +343,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int j = jb + e;
-          const float wv = j < k ? wrow[j] : 0.f, av = j < k ? arow[j] : 0.f;
+          const float wv = j < k ? rf * wrow[j] : 0.f, av = j < k ? rf * arow[j] : 0.f;
           if (!lo) {
             lv[e] = to16<T16>(wv);
             rv[e] = to16<T16>(av);
@@ -407,10 +493,23 @@ cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_raw_scales(const long long* S, const long long* Mq, int n_q, long long T, int T_pad, int nT,
+cudaError_t launch_raw_scales(const long long* S, const long long* S2, const double* Sbar, int norm,
+                              const long long* Mq, int n_q, long long T, int T_pad, int nT,
                               const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status,
                               cudaStream_t st) {
-  raw_scales_kernel<<<dim3(nT, n_q), TILE, 0, st>>>(S, Mq, n_q, T, T_pad, nT, sq, r, blk_bad, status);
+  raw_scales_kernel<<<dim3(nT, n_q), TILE, 0, st>>>(S, S2, Sbar, norm, Mq, n_q, T, T_pad, nT, sq, r, blk_bad,
+                                                     status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ring_mean(const long long* S, int n_q, long long T, double* Sbar, cudaStream_t st) {
+  ring_mean_kernel<<<n_q, 256, 0, st>>>(S, T, Sbar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_mean(const float* A, long long T, int k, const double* s64, int n_q, double* Sbar,
+                             cudaStream_t st) {
+  coef_mean_kernel<<<1, 256, 0, st>>>(A, T, k, s64, n_q, Sbar);
   return cudaGetLastError();
 }
 

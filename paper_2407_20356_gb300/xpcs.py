@@ -28,6 +28,8 @@ STATUS_NAMES = ["XPCS_OK", "XPCS_EINVAL", "XPCS_ENOMEM", "XPCS_ECUDA", "XPCS_ETI
 XPCS_U8, XPCS_U16 = 0, 1
 XPCS_PREC_FP16, XPCS_PREC_BF16, XPCS_PREC_BF16X3 = 0, 1, 2
 PRECISIONS = {"fp16": XPCS_PREC_FP16, "bf16": XPCS_PREC_BF16, "bf16x3": XPCS_PREC_BF16X3}
+XPCS_NORM_MEAN, XPCS_NORM_FROB, XPCS_NORM_EQ12 = 0, 1, 2
+NORMS = {"mean": XPCS_NORM_MEAN, "frob": XPCS_NORM_FROB, "eq12": XPCS_NORM_EQ12}
 
 vp = C.c_void_p
 i64 = C.c_int64
@@ -49,13 +51,16 @@ _SIGS = {
     "xpcs_rings_sizes": (C.c_int, [vp, vp]),
     "xpcs_ring_sums": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     "xpcs_twotime_raw": (C.c_int, [vp, vp, vp, C.c_int, i64, vp, vp, vp, vp]),
+    "xpcs_twotime_raw_norm": (C.c_int, [vp, vp, vp, C.c_int, i64, C.c_int, vp, vp, vp, vp]),
     "xpcs_fit_basis": (C.c_int, [vp, vp, vp, C.c_int, i64, C.c_int, C.POINTER(vp), vp]),
     "xpcs_basis_import": (C.c_int, [vp, vp, vp, C.c_int, C.POINTER(vp)]),
     "xpcs_basis_export": (C.c_int, [vp, vp, vp, vp, vp]),
     "xpcs_basis_rank": (C.c_int, [vp, C.POINTER(C.c_int)]),
+    "xpcs_rank_from_spectrum": (C.c_int, [vp, C.c_int, C.c_double]),
     "xpcs_basis_destroy": (C.c_int, [vp]),
     "xpcs_encode": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
+    "xpcs_twotime_norm": (C.c_int, [vp, vp, vp, i64, C.c_int, C.c_int, vp, vp, vp]),
     "xpcs_g2": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_selftest_timeout": (C.c_int, [vp, C.c_int]),
     "xpcs_g2_noalloc": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
@@ -243,10 +248,22 @@ def xpcs_ring_sums(ctx: Context, rings: Rings, X, T: int, S_out, dtype=None):
     ctx.check(_lib.xpcs_ring_sums(ctx.h, rings.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(S_out)))
 
 
+def _norm_code(norm) -> int:
+    return NORMS[norm] if isinstance(norm, str) else int(norm)
+
+
 def xpcs_twotime_raw(ctx: Context, rings: Rings, X, T: int, C_out=None, N_out=None, g2_out=None, count_out=None,
-                     dtype=None):
+                     dtype=None, norm="mean"):
+    if _norm_code(norm) != XPCS_NORM_MEAN:
+        return xpcs_twotime_raw_norm(ctx, rings, X, T, norm, C_out, N_out, g2_out, count_out, dtype)
     ctx.check(_lib.xpcs_twotime_raw(ctx.h, rings.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(C_out),
                                     _ptr(N_out), _ptr(g2_out), _ptr(count_out)))
+
+
+def xpcs_twotime_raw_norm(ctx: Context, rings: Rings, X, T: int, norm, C_out=None, N_out=None, g2_out=None,
+                          count_out=None, dtype=None):
+    ctx.check(_lib.xpcs_twotime_raw_norm(ctx.h, rings.h, _ptr(X), _dtype_code(dtype or X), T, _norm_code(norm),
+                                         _ptr(C_out), _ptr(N_out), _ptr(g2_out), _ptr(count_out)))
 
 
 def xpcs_fit_basis(ctx: Context, rings: Rings, F, n_fit: int, k: int, sigma_host=None, dtype=None) -> Basis:
@@ -264,13 +281,31 @@ def xpcs_basis_import(ctx: Context, rings: Rings, B_host: np.ndarray) -> Basis:
     return Basis(ctx, rings, h, B_host.shape[1])
 
 
+def xpcs_rank_from_spectrum(sigma, factor: float = 2.0) -> int:
+    """K = number of spectrum values >= factor * the smallest one within the numerical rank."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    K = _lib.xpcs_rank_from_spectrum(sigma.ctypes.data, sigma.size, float(factor))
+    if K < 0:
+        raise XpcsError(XPCS_EINVAL, "xpcs_rank_from_spectrum: bad spectrum or factor")
+    return K
+
+
 def xpcs_encode(ctx: Context, basis: Basis, X, T: int, A_out, dtype=None):
     ctx.check(_lib.xpcs_encode(ctx.h, basis.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(A_out)))
 
 
-def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None, g2_out=None, count_out=None):
+def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None, g2_out=None, count_out=None,
+                 norm="mean"):
+    if _norm_code(norm) != XPCS_NORM_MEAN:
+        return xpcs_twotime_norm(ctx, basis, A, T, prec, norm, C_out, g2_out, count_out)
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     ctx.check(_lib.xpcs_twotime(ctx.h, basis.h, _ptr(A), T, p, _ptr(C_out), _ptr(g2_out), _ptr(count_out)))
+
+
+def xpcs_twotime_norm(ctx: Context, basis: Basis, A, T: int, prec, norm, C_out=None, g2_out=None, count_out=None):
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    ctx.check(_lib.xpcs_twotime_norm(ctx.h, basis.h, _ptr(A), T, p, _norm_code(norm), _ptr(C_out), _ptr(g2_out),
+                                     _ptr(count_out)))
 
 
 def xpcs_g2(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):

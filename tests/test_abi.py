@@ -52,3 +52,27 @@ def test_binding_constants_match_the_header():
     src = open(HEADER).read()
     m = re.search(r"#define\s+XPCS_G2_NOALLOC_MAX_CELLS\s+\(1 << (\d+)\)", src)
     assert m and xpcs.G2_NOALLOC_MAX_CELLS == 1 << int(m.group(1))
+    for name, val in re.findall(r"\b(XPCS_NORM_[A-Z0-9]+)\s*=\s*(\d+)", src):
+        assert getattr(xpcs, name) == int(val), name
+
+
+def test_rank_rule_host_function_matches_the_oracle():
+    # host-side logic behind the ABI (no device work): the rank rule of Sec. 3.1
+    _ensure_built()
+    import numpy as np
+
+    import oracle as O
+    from paper_2407_20356_gb300 import xpcs
+
+    rng = np.random.default_rng(11)
+    spectra = [[8.0, 4.0, 2.5, 2.0, 1.5, 1.0], [3.0, 1.0, 0.0, 0.0], [1.0, 1.0, 1.0], [5.0], [0.0, 0.0]]
+    spectra += [np.sort(rng.exponential(1.0, size=n))[::-1] for n in (2, 17, 300)]
+    for s in spectra:
+        for f in (1.5, 2.0, 3.0):
+            assert xpcs.xpcs_rank_from_spectrum(s, f) == O.rank_from_spectrum(s, f), (s, f)
+    for bad, f in (([1.0, 2.0], 2.0), ([2.0, 1.0], 0.0), ([float("nan"), 1.0], 2.0)):
+        try:
+            xpcs.xpcs_rank_from_spectrum(bad, f)
+        except xpcs.XpcsError:
+            continue
+        raise AssertionError(("accepted", bad, f))

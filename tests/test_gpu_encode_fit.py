@@ -94,6 +94,54 @@ def test_fit_basis_matches_oracle(X, ctx, dtype, n_fit, k):
     np.testing.assert_allclose(sd, sd2, atol=1e-12)
 
 
+def test_spectrum_rank_rule_matches_oracle(X, ctx):
+    # Sec. 3.1 rank choice (values >= 2x the smallest) on the device fit's spectrum equals
+    # the same rule on the oracle's own fit of the same frames
+    torch, dev = torch_cuda()
+    H, W, n_q, n_fit = 40, 40, 5, 300
+    frames = speckle_counts(H, W, n_fit, 0.5, 1e-3, 20356005, np.uint16)
+    rings = _rings(X, ctx, ring_qmap(H, W, n_q), n_q)
+    sig = np.empty(n_fit)
+    X.xpcs_fit_basis(ctx, rings, torch.from_numpy(frames).to(dev), n_fit, 8, sigma_host=sig)
+    _, sref = O.fit_basis(frames, 8)
+    K = X.xpcs_rank_from_spectrum(sig)
+    assert K == O.rank_from_spectrum(sref)
+    assert 1 <= K < n_fit
+
+
+def test_fit_on_calibration_run_then_another_series(X, ctx):
+    # online variant (Sec. 2.3): the basis comes from an earlier run on the same sample and
+    # every frame of the new series is encoded with it; compared with the oracle doing the
+    # same (its own fit of the calibration run, encode of the new series)
+    torch, dev = torch_cuda()
+    H = W = 40
+    n_q, k, T, n_fit = 6, 32, 300, 200
+    calib = speckle_counts(H, W, n_fit, 0.2, 1e-3, 20356105, np.uint16)
+    series = speckle_counts(H, W, T, 0.2, 1e-3, 20356005, np.uint16)
+    qmap = ring_qmap(H, W, n_q)
+    rings = _rings(X, ctx, qmap, n_q)
+    basis = X.xpcs_fit_basis(ctx, rings, torch.from_numpy(calib).to(dev), n_fit, k)
+    Xd = torch.from_numpy(series).to(dev)
+    A = torch.empty((T, k), dtype=torch.float32, device=dev)
+    X.xpcs_encode(ctx, basis, Xd, T, A)
+    C = torch.full((n_q, T, T), float("nan"), dtype=torch.float32, device=dev)
+    g2 = torch.empty((n_q, T), dtype=torch.float64, device=dev)
+    cnt = torch.empty((n_q, T), dtype=torch.int64, device=dev)
+    X.xpcs_twotime(ctx, basis, A, T, "bf16x3", C_out=C, g2_out=g2, count_out=cnt)
+    Bref, _ = O.fit_basis(calib, k)
+    G, s, Mq = O.ring_factors(Bref, qmap, n_q)
+    Cref, _ = O.compressed_twotime(O.encode(series, Bref), G, s, Mq)
+    Ch = C.cpu().numpy()
+    assert np.array_equal(np.isnan(lower(Ch)), np.isnan(lower(Cref)))
+    rm, _ = rel_errors(lower(Ch), lower(Cref))
+    assert rm < 1e-4, rm
+    for q in range(n_q):
+        gref, cref = O.g2_from_twotime(Cref[q])
+        np.testing.assert_array_equal(cnt[q].cpu().numpy(), cref)
+        gm, _ = rel_errors(g2[q].cpu().numpy(), gref)
+        assert gm < 1e-4, (q, gm)
+
+
 def test_fit_rejects_k_above_rank(X, ctx):
     torch, dev = torch_cuda()
     frames = np.zeros((20, 64), dtype=np.uint8)

@@ -284,3 +284,45 @@ def test_paper_compression_ratios_and_speedup():
         assert abs(O.compression_ratio_online(on["M"], K) - cr) / cr < 0.01  # printed rounded
     ls = g["lossless_speedup"]
     assert abs(O.lossless_speedup(ls["N"], ls["M"]) - ls["factor"]) / ls["factor"] < 0.01
+
+
+# ---------------------------------------------------------------- rank rule of Sec. 3.1
+
+def test_rank_rule_hand_spectra():
+    # hand-counted: values >= 2 x the smallest (1.0) are 8, 4, 2.5 and 2 (equality counts)
+    assert O.rank_from_spectrum([8.0, 4.0, 2.5, 2.0, 1.5, 1.0]) == 4
+    assert O.rank_from_spectrum([8.0, 4.0, 2.5, 2.0, 1.5, 1.0], factor=3.0) == 2
+    # a rank-deficient tail is not the minimum: the smallest kept value is 1.0
+    assert O.rank_from_spectrum([3.0, 1.0, 0.0, 0.0]) == 1
+    # a flat spectrum has no component that stands out
+    assert O.rank_from_spectrum([1.0, 1.0, 1.0]) == 0
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_rank_rule_finds_planted_components(seed):
+    # five equal-weight patterns plus white noise: after the fit's row normalisation the
+    # noise singular values spread by about 1.5x (Marchenko-Pastur edges at n/M = 0.05), so
+    # the rule on singular values returns the five planted components, while the same
+    # rule applied to squared values (eigenvalues, spread about 2.3x) would count noise too
+    rng = np.random.default_rng(seed)
+    n, M, r = 60, 1200, 5
+    P = np.linalg.qr(rng.standard_normal((M, r)))[0].T
+    u = rng.standard_normal((n, r))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    F = 50 * u @ P + 0.5 * rng.standard_normal((n, M))
+    _, s = O.fit_basis(F, r)
+    assert O.rank_from_spectrum(s) == r
+    assert int((s * s >= 2 * (s * s).min()).sum()) > r
+
+
+def test_eq12_twotime_diagonals_equal_the_pixel_level_literal_eq12():
+    # Eq. 12 two ways: diagonal means of M_q N / Sbar^2 (Gram form) against the oracle's
+    # pixel-level average of I(t) I(t+tau) over frames and ring pixels divided by <I>^2
+    X, qmap, n_q = _small_speckle(T=40)
+    S = O.ring_sums(X, qmap, n_q)
+    Mq = O.ring_sizes(qmap, n_q)
+    for q in range(n_q):
+        g2, cnt = O.g2_from_twotime(O.twotime_eq12(O.raw_gram(X, qmap, q), S[q], Mq[q]))
+        np.testing.assert_array_equal(cnt, 40 - np.arange(40))
+        for tau in (0, 1, 7, 39):
+            assert abs(g2[tau] - O.g2_eq12(X, qmap, q, tau)) < 1e-12 * abs(g2[tau])
