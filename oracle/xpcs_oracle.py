@@ -150,7 +150,7 @@ def fit_basis(F: np.ndarray, k: int):
 
 def rank_from_spectrum(sigma: np.ndarray, factor: float = 2.0) -> int:
     """Rank choice of Sec. 3.1: how many values of the spectrum are at least `factor`
-    times its smallest value (the paper counts those "twice as large as the minimum").
+    times its smallest value (the paper's count uses a factor of two).
 
     The spectrum is the descending list of singular values returned by fit_basis.  Values
     at or below the numerical-rank cutoff (sigma^2 <= n eps sigma_max^2, the cutoff
