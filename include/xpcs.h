@@ -216,6 +216,30 @@ xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g
 xpcs_status xpcs_g2_noalloc(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out,
                             int64_t* count_out);
 
+/* ------------------------------------------------------------------ downstream analysis (Sec. 3)
+ * Eq. 13 relaxation fit per ring: g2(tau) = B + C exp(-2 tau / t0), unweighted least
+ * squares over the defined lags tau_lo..tau_hi of g2 (n_q x T f64, device; NaN lags are
+ * skipped), t0 searched over [t0_min, t0_max] (variable projection: (B, C) solved for
+ * each t0, the residual minimised over log t0 by a grid and golden-section refinement).
+ * params_out (device, n_q x 4 f64): B, C, t0, rms residual; NaN for a ring with fewer
+ * than three defined lags.  Requires 0 <= tau_lo <= tau_hi < T, 0 < t0_min < t0_max. */
+xpcs_status xpcs_fit_relaxation(xpcs_ctx* ctx, const double* g2, int n_q, int64_t T, int64_t tau_lo,
+                                int64_t tau_hi, double t0_min, double t0_max, double* params_out);
+/* Mean and population standard deviation of a stored two-time matrix per ring (the
+ * spread that Sec. 3.2 takes as the TTC's background level): over the defined values of
+ * the lower triangle strictly below the diagonal, i.e. every unordered pair t1 != t2
+ * once.  C: n_q x T x T f32 as written by the two-time calls; mean_out, std_out (nullable)
+ * device n_q f64; NaN for a ring without defined pairs. */
+xpcs_status xpcs_twotime_stats(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* mean_out,
+                               double* std_out);
+/* Peak visibility (Sec. 3.1) per ring: the largest g2 over lags peak_lo..peak_hi minus the
+ * mean g2 over lags bg_lo..bg_hi (defined lags only; NaN if either window has none).
+ * flag_out (nullable, needs ttc_std): 1 when the visibility exceeds factor x ttc_std[q]
+ * (Sec. 3.2's detectability test, factor 2), else 0.  All arrays device, length n_q. */
+xpcs_status xpcs_peak_visibility(xpcs_ctx* ctx, const double* g2, int n_q, int64_t T, int64_t peak_lo,
+                                 int64_t peak_hi, int64_t bg_lo, int64_t bg_hi, const double* ttc_std,
+                                 double factor, double* vis_out, int32_t* flag_out);
+
 /* ------------------------------------------------------------------ online stream (Sec. 2.2, Fig. 1c)
  * Online compression with a basis fit before acquisition: every pushed frame is encoded
  * (a_t = x_t V_K, sparse: only nonzero pixels read their basis row, f32), appended to a

@@ -35,6 +35,7 @@ __all__ = [
     "decompress", "raw_pair_values", "compressed_pair_values", "g2_eq12",
     "frobenius_twotime", "windowed_g2", "compression_ratio_offline",
     "compression_ratio_online", "lossless_speedup", "rank_from_spectrum", "twotime_eq12",
+    "relaxation_fit", "peak_visibility", "twotime_stats", "detectable",
 ]
 
 
@@ -280,6 +281,71 @@ def twotime_eq12(Nq: np.ndarray, S: np.ndarray, Mq: float) -> np.ndarray:
     if Sbar <= 0:
         return np.full(N.shape, np.nan)
     return float(Mq) * N / (Sbar * Sbar)
+
+
+# ---------------------------------------------------------------- downstream analysis (Sec. 3)
+
+def relaxation_fit(g2: np.ndarray, tau_lo: int, tau_hi: int, t0_min: float, t0_max: float):
+    """Least-squares fit of Eq. 13, g2(tau) = B + C exp(-2 tau / t0), over the defined lags
+    tau_lo..tau_hi (unweighted).
+
+    For a fixed t0 the model is linear in (B, C), solved by lstsq; the residual is then a
+    function of t0 alone, minimised over log t0 in [t0_min, t0_max]: a 2001-point grid, then
+    a bounded scalar minimisation between the grid neighbours of the best point.  Returns
+    (B, C, t0, rms residual); NaNs if fewer than three lags are defined.
+    """
+    from scipy.optimize import minimize_scalar
+
+    tau = np.arange(tau_lo, tau_hi + 1, dtype=np.float64)
+    g = np.asarray(g2, dtype=np.float64)[tau_lo:tau_hi + 1]
+    ok = ~np.isnan(g)
+    tau, g = tau[ok], g[ok]
+    if g.size < 3:
+        return (np.nan,) * 4
+
+    def solve(lt0):
+        e = np.exp(-2.0 * tau / np.exp(lt0))
+        M = np.stack([np.ones_like(e), e], axis=1)
+        coef = np.linalg.lstsq(M, g, rcond=None)[0]
+        r = g - M @ coef
+        return float(r @ r), coef
+
+    grid = np.linspace(np.log(t0_min), np.log(t0_max), 2001)
+    res = np.array([solve(x)[0] for x in grid])
+    i = int(np.argmin(res))
+    lo, hi = grid[max(i - 1, 0)], grid[min(i + 1, grid.size - 1)]
+    best = minimize_scalar(lambda x: solve(x)[0], bounds=(lo, hi), method="bounded",
+                           options={"xatol": 1e-12})
+    lt0 = best.x if best.fun <= res[i] else grid[i]
+    rss, (B, C) = solve(lt0)
+    return float(B), float(C), float(np.exp(lt0)), float(np.sqrt(rss / g.size))
+
+
+def peak_visibility(g2: np.ndarray, pa: int, pb: int, ba: int, bb: int) -> float:
+    """Sec. 3.1: the peak of g2 over lags pa..pb minus its background level, read as the
+    mean of g2 over the lags ba..bb (defined lags only)."""
+    g = np.asarray(g2, dtype=np.float64)
+    return float(np.nanmax(g[pa:pb + 1]) - np.nanmean(g[ba:bb + 1]))
+
+
+def twotime_stats(C: np.ndarray):
+    """Mean and (population) standard deviation of the two-time values C(t1, t2), t1 != t2,
+    over the defined pairs (each unordered pair once), the spread Sec. 3.2 calls the
+    background level of the TTC."""
+    C = np.asarray(C, dtype=np.float64)
+    il = np.tril_indices(C.shape[0], -1)
+    v = C[il]
+    v = v[~np.isnan(v)]
+    if v.size == 0:
+        return np.nan, np.nan
+    m = v.sum() / v.size
+    return float(m), float(np.sqrt(((v - m) ** 2).sum() / v.size))
+
+
+def detectable(visibility: float, ttc_std: float, factor: float = 2.0) -> bool:
+    """Sec. 3.2: a correlation peak counts as detectable when its visibility exceeds
+    `factor` (two) times the standard deviation of the TTC."""
+    return bool(visibility > factor * ttc_std)
 
 
 def windowed_g2(C: np.ndarray, W: int):

@@ -62,6 +62,9 @@ _SIGS = {
     "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
     "xpcs_twotime_norm": (C.c_int, [vp, vp, vp, i64, C.c_int, C.c_int, vp, vp, vp]),
     "xpcs_g2": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
+    "xpcs_fit_relaxation": (C.c_int, [vp, vp, C.c_int, i64, i64, i64, C.c_double, C.c_double, vp]),
+    "xpcs_twotime_stats": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
+    "xpcs_peak_visibility": (C.c_int, [vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, C.c_double, vp, vp]),
     "xpcs_selftest_timeout": (C.c_int, [vp, C.c_int]),
     "xpcs_g2_noalloc": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_stream_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.POINTER(vp)]),
@@ -306,6 +309,22 @@ def xpcs_twotime_norm(ctx: Context, basis: Basis, A, T: int, prec, norm, C_out=N
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     ctx.check(_lib.xpcs_twotime_norm(ctx.h, basis.h, _ptr(A), T, p, _norm_code(norm), _ptr(C_out), _ptr(g2_out),
                                      _ptr(count_out)))
+
+
+def xpcs_fit_relaxation(ctx: Context, g2, n_q: int, T: int, tau_lo: int, tau_hi: int, t0_min: float,
+                        t0_max: float, params_out):
+    ctx.check(_lib.xpcs_fit_relaxation(ctx.h, _ptr(g2), n_q, T, tau_lo, tau_hi, float(t0_min), float(t0_max),
+                                       _ptr(params_out)))
+
+
+def xpcs_twotime_stats(ctx: Context, C_in, n_q: int, T: int, mean_out, std_out=None):
+    ctx.check(_lib.xpcs_twotime_stats(ctx.h, _ptr(C_in), n_q, T, _ptr(mean_out), _ptr(std_out)))
+
+
+def xpcs_peak_visibility(ctx: Context, g2, n_q: int, T: int, peak_lo: int, peak_hi: int, bg_lo: int, bg_hi: int,
+                         vis_out, ttc_std=None, factor: float = 2.0, flag_out=None):
+    ctx.check(_lib.xpcs_peak_visibility(ctx.h, _ptr(g2), n_q, T, peak_lo, peak_hi, bg_lo, bg_hi, _ptr(ttc_std),
+                                        float(factor), _ptr(vis_out), _ptr(flag_out)))
 
 
 def xpcs_g2(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):

@@ -326,3 +326,46 @@ def test_eq12_twotime_diagonals_equal_the_pixel_level_literal_eq12():
         np.testing.assert_array_equal(cnt, 40 - np.arange(40))
         for tau in (0, 1, 7, 39):
             assert abs(g2[tau] - O.g2_eq12(X, qmap, q, tau)) < 1e-12 * abs(g2[tau])
+
+
+# ---------------------------------------------------------------- downstream analysis (Sec. 3)
+
+def test_relaxation_fit_recovers_a_noiseless_eq13_curve():
+    tau = np.arange(400, dtype=np.float64)
+    g2 = 1.0 + 0.3 * np.exp(-2.0 * tau / 50.0)
+    g2[[3, 77, 200]] = np.nan  # undefined lags are skipped
+    B, C, t0, rms = O.relaxation_fit(g2, 1, 399, 1.0, 1e4)
+    assert abs(B - 1.0) < 1e-7 and abs(C - 0.3) < 1e-7 and abs(t0 - 50.0) < 1e-5 and rms < 1e-8
+
+
+def test_relaxation_fit_on_speckle_gives_the_decay_time():
+    # one mode per pixel: g2 - 1 = mean_p exp(-2 Gamma_p tau), so the fitted t0 lies between
+    # the ring's extreme 1/Gamma and near 1/mean(Gamma), with baseline 1 and contrast 1
+    H = W = 64
+    T, n_q, D = 800, 8, 4e-4
+    X = speckle_counts(H, W, T, 2.0, D, 12, np.uint8)
+    qmap = ring_qmap(H, W, n_q)
+    gam = rate_of_pixels(H, W, D)
+    C, _, _, _ = O.raw_twotime(X, qmap, n_q)
+    for q in (1, 2, 3):
+        g2, _ = O.g2_from_twotime(C[q])
+        B, Cc, t0, _ = O.relaxation_fit(g2, 1, 300, 0.5, 1e4)
+        g = gam[O.ring_index(qmap, q)]
+        assert 1 / g.max() < t0 < 1 / g.min(), (q, t0)
+        assert abs(t0 * g.mean() - 1.0) < 0.15, (q, t0)
+        assert abs(B - 1.0) < 0.02 and abs(Cc - 1.0) < 0.05, (q, B, Cc)
+
+
+def test_peak_visibility_and_detectability_hand_example():
+    g2 = np.array([2.0, 1.1, 1.0, 1.02, 0.98, 1.5, 1.3, 1.0, np.nan, 1.0])
+    # peak over lags 4..6 is 1.5; background over lags 7..9 (NaN skipped) is 1.0
+    assert abs(O.peak_visibility(g2, 4, 6, 7, 9) - 0.5) < 1e-15
+    assert O.detectable(0.5, 0.2) and not O.detectable(0.5, 0.3)
+
+
+def test_twotime_stats_hand_example():
+    nan = np.nan
+    C = np.array([[9.0, 1.0, 3.0], [1.0, 9.0, nan], [3.0, nan, 9.0]])
+    # off-diagonal defined pairs: (1,0) = 1 and (2,0) = 3 -> mean 2, std 1
+    m, s = O.twotime_stats(C)
+    assert m == 2.0 and s == 1.0
