@@ -700,6 +700,11 @@ extern "C" xpcs_status xpcs_basis_destroy(xpcs_basis* B) {
   dev_free(ctx, B->d_koff, (size_t)n_q * 4);
   dev_free(ctx, B->d_kch, (size_t)n_q * 4);
   dev_free(ctx, B->d_s32, (size_t)n_q * k * 8);
+  if (B->d_B32) dev_free(ctx, B->d_B32, (size_t)B->rings->M * k * 4);
+  if (B->d_Gpair) {
+    const int kq = (k + 63) / 64 * 64;
+    dev_free(ctx, B->d_Gpair, (size_t)n_q * kq * 2 * kq * 2);
+  }
   delete B;
   return XPCS_OK;
 }
@@ -834,8 +839,23 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   const int Kc = (split ? 2 : 1) * nkp * KCH;
   const bool want_g2 = g2_out != nullptr;
   const bool want_cnt = want_g2 || count_out;
+  // the left operand on the tensor cores when k <= 128 and the scale does not need W
+  // (Eq. 1 and Eq. 12): the CUDA-core pass forms the ring sums, scales and R rows, then A
+  // pieces + G pieces give L; else the CUDA-core kernel forms L as well
+  const int kq = (k + 63) / 64 * 64;
+  const bool use_tc = norm != XPCS_NORM_FROB && kq <= 128;
+  if (use_tc && !B->d_Gpair) {
+    xpcs_basis* Bm = const_cast<xpcs_basis*>(B);
+    void* p = nullptr;
+    const size_t gb = (size_t)n_q * kq * 2 * kq * 2;
+    XPCS_TRY(dev_alloc(ctx, &p, gb));
+    Bm->d_Gpair = static_cast<__nv_bfloat16*>(p);
+    Bm->bytes += gb;
+    XPCS_LAUNCH(ctx, "gram_pieces", 1, launch_gram_pieces(B->d_G, n_q, k, kq, Bm->d_Gpair, ctx->stream));
+  }
   struct Bufs {
     uint16_t *L, *R;
+    __nv_bfloat16* Apair;
     double* Sbar;
     float* r;
     uint32_t* blk_bad;
@@ -846,6 +866,7 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   auto layout = [&](Carve& c) {
     b.L = c.take<uint16_t>((size_t)n_q * T_pad * Kc);
     b.R = c.take<uint16_t>((size_t)n_q * T_pad * Kc);
+    b.Apair = use_tc ? c.take<__nv_bfloat16>((size_t)T_pad * 2 * kq) : nullptr;
     b.Sbar = norm == XPCS_NORM_EQ12 ? c.take<double>(n_q) : nullptr;
     b.r = c.take<float>((size_t)n_q * T_pad);
     b.blk_bad = c.take<uint32_t>((size_t)n_q * nT);
@@ -879,9 +900,26 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   pp.St = nullptr;
   pp.norm = (int)norm;
   pp.Sbar = b.Sbar;
+  pp.skip_L = use_tc ? 1 : 0;
   if (norm == XPCS_NORM_EQ12)
     XPCS_LAUNCH(ctx, "coef_mean", 1, launch_coef_mean(A, T, k, B->d_s, n_q, b.Sbar, ctx->stream));
   XPCS_LAUNCH(ctx, "compressed_prep", 1, launch_prep_compressed(pp, ctx->stream));
+  if (use_tc) {
+    XPCS_LAUNCH(ctx, "coef_pieces", 1, launch_coef_pieces(A, T, k, kq, T_pad, b.Apair, ctx->stream));
+    CUtensorMap tmA, tmG;
+    XPCS_TRY(make_map(ctx, &tmA, b.Apair, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * kq, T_pad, 64, TILE,
+                      CU_TENSOR_MAP_SWIZZLE_128B));
+    XPCS_TRY(make_map(ctx, &tmG, B->d_Gpair, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * kq, (uint64_t)n_q * kq, 64,
+                      kq, CU_TENSOR_MAP_SWIZZLE_128B));
+    CompTcParams cp{};
+    cp.r = b.r;
+    cp.L = b.L;
+    cp.T_pad = T_pad;
+    cp.Kc = Kc;
+    cp.kq = kq;
+    cp.status = ctx->d_status;
+    XPCS_LAUNCH(ctx, "ring_w_tc", 1, launch_ring_w_tc(tmA, tmG, cp, n_q, nT, (int)prec, ctx->stream));
+  }
   const CUtensorMapDataType dt =
       prec == XPCS_PREC_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap tmL, tmR;

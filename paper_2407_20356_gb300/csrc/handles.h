@@ -74,6 +74,8 @@ struct xpcs_basis {
   __half* d_Bcat = nullptr;       // 2kp x M_pad: f16 hi/lo of V^T 2^enc_log2
   int* d_koff = nullptr;          // n_q zeros: K offsets of the compressed operands
   int* d_kch = nullptr;           // n_q x ceil(k/64): K chunks per operand piece
+  __nv_bfloat16* d_Gpair = nullptr;  // n_q kq x 2 kq: bf16 [hi | lo] rows of G_q for the
+                                     // tensor-core left operand (made on first use), kq = ceil64(k)
   int enc_log2 = 0;
   size_t bytes = 0;
 };

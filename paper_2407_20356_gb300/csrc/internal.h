@@ -105,7 +105,26 @@ struct PrepParams {
   double* St;              // nullable [n_q][T] compressed ring sums
   int norm;                // xpcs_norm
   const double* Sbar;      // [n_q] mean compressed ring sums (XPCS_NORM_EQ12)
+  int skip_L;              // 1: ring sums, scales and R rows only (L from the tensor-core kernel)
 };
+
+// Tensor-core left operand L_q(t) = r_q(t) a_t G_q (comp_tc.cu), kq = k rounded up to 64
+// (64 or 128).  A pieces: [T_pad][2 kq] bf16 ([hi | lo]); G pieces: [n_q kq][2 kq] bf16,
+// row (q, n) holding G_q[n][:] as [hi | lo].
+struct CompTcParams {
+  const float* r;          // [n_q][T_pad] scales from the CUDA-core operand pass
+  void* L;                 // [n_q][T_pad][Kc] 16-bit operand rows
+  int T_pad, Kc, kq;
+  uint32_t* status;
+};
+int comp_tc_smem(int kq);
+cudaError_t launch_ring_w_tc(const CUtensorMap& tmA, const CUtensorMap& tmG, const CompTcParams& p, int n_q,
+                             int n_tiles, int prec, cudaStream_t st);
+// [T_pad][2 kq] bf16 hi/lo pieces of the coefficient rows (zero beyond T and k)
+cudaError_t launch_coef_pieces(const float* A, long long T, int k, int kq, int T_pad, __nv_bfloat16* out,
+                               cudaStream_t st);
+// [n_q kq][2 kq] bf16 hi/lo pieces of the ring factors G_q (FP64), zero beyond k
+cudaError_t launch_gram_pieces(const double* G, int n_q, int k, int kq, __nv_bfloat16* out, cudaStream_t st);
 cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st);
 
 cudaError_t launch_counts(const float* r, int n_q, long long T, int T_pad, uint32_t* vbits, int words,

@@ -2,6 +2,8 @@
 // reductions (sm_103a).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -175,12 +177,12 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   const int k = p.k;
   const int lda = k + 1;
   float* As = sm;                          // [64][k+1]  a
-  float* Ws = As + PREP_FRAMES * lda;      // [64][k+1]  a G_q
-  float* Gs = Ws + PREP_FRAMES * lda;      // [k][64]
+  float* rs = As + PREP_FRAMES * lda;      // [64] r of this block's frames
+  float* Ws = rs + PREP_FRAMES;            // [64][k+1]  a G_q  (not allocated with skip_L)
+  float* Gs = Ws + PREP_FRAMES * lda;      // [k][64]           (not allocated with skip_L)
   const int q = blockIdx.y;
   const long long t0 = (long long)blockIdx.x * PREP_FRAMES;
   const int tid = threadIdx.x;
-  float* rs = Gs + k * 64;                 // [64] r of this block's frames
   // A rows: 4 rows per pass, 64 columns per row chunk (coalesced, no integer division)
   for (int f = tid >> 6; f < PREP_FRAMES; f += 4) {
     const long long t = t0 + f;
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   // columns 8 cg .. 8 cg + 7 of the chunk (16 outputs, 4 shared loads per 16 FMAs)
   const int fl = tid & 31, cg = tid >> 5;
   const float* Gq = p.G32 + (size_t)q * k * k;
-  for (int j0 = 0; j0 < k; j0 += 64) {
+  for (int j0 = 0; j0 < (p.skip_L ? 0 : k); j0 += 64) {
     const int nc = min(64, k - j0);
     __syncthreads();
     for (int c = tid >> 6; c < k; c += 4) {
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
       if (jb + 8 <= k) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const float wv = rf * wrow[jb + e], av = rf * arow[jb + e];
+          const float wv = p.skip_L ? 0.f : rf * wrow[jb + e], av = rf * arow[jb + e];
           if (!lo) {
             lv[e] = to16<T16>(wv);
             rv[e] = to16<T16>(av);
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int j = jb + e;
-          const float wv = j < k ? rf * wrow[j] : 0.f, av = j < k ? rf * arow[j] : 0.f;
+          const float wv = (j < k && !p.skip_L) ? rf * wrow[j] : 0.f, av = j < k ? rf * arow[j] : 0.f;
           if (!lo) {
             lv[e] = to16<T16>(wv);
             rv[e] = to16<T16>(av);
@@ -353,9 +355,35 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
           }
         }
       }
-      L[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(lv);
+      if (!p.skip_L) L[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(lv);
       R[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(rv);
     }
+  }
+}
+
+// ---------------------------------------------------------------- tensor-core operand pieces
+__global__ void coef_pieces_kernel(const float* A, long long T, int k, int kq, long long n, __nv_bfloat16* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long t = i / kq;
+    const int c = (int)(i - t * kq);
+    const float a = (t < T && c < k) ? A[t * k + c] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(a);
+    out[t * 2 * kq + c] = hi;
+    out[t * 2 * kq + kq + c] = __float2bfloat16_rn(a - __bfloat162float(hi));
+  }
+}
+
+__global__ void gram_pieces_kernel(const double* G, int n_q, int k, int kq, __nv_bfloat16* out) {
+  const long long n = (long long)n_q * kq * kq;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(i / ((long long)kq * kq));
+    const int rem = (int)(i - (long long)q * kq * kq);
+    const int r = rem / kq, c = rem - r * kq;
+    const double g = (r < k && c < k) ? G[((size_t)q * k + r) * k + c] : 0.0;
+    const __nv_bfloat16 hi = __double2bfloat16(g);
+    const size_t row = ((size_t)q * kq + r) * 2 * kq;
+    out[row + c] = hi;
+    out[row + kq + c] = __double2bfloat16(g - (double)__bfloat162float(hi));
   }
 }
 
@@ -516,7 +544,8 @@ cudaError_t launch_coef_mean(const float* A, long long T, int k, const double* s
 cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(p.blk_bad, 0, (size_t)p.n_q * p.nT * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  const int smem = (2 * PREP_FRAMES * (p.k + 1) + p.k * 64 + PREP_FRAMES) * (int)sizeof(float);
+  const int smem = (p.skip_L ? PREP_FRAMES * (p.k + 1) + PREP_FRAMES
+                              : 2 * PREP_FRAMES * (p.k + 1) + p.k * 64 + PREP_FRAMES) * (int)sizeof(float);
   const dim3 grid(p.T_pad / PREP_FRAMES, p.n_q);
 #define XPCS_PREP_LAUNCH(T16, SPLIT)                                                                  \
   do {                                                                                                \
@@ -536,6 +565,19 @@ cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st) {
   else
     XPCS_PREP_LAUNCH(__nv_bfloat16, true);
 #undef XPCS_PREP_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_pieces(const float* A, long long T, int k, int kq, int T_pad, __nv_bfloat16* out,
+                               cudaStream_t st) {
+  const long long n = (long long)T_pad * kq;
+  coef_pieces_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(A, T, k, kq, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_pieces(const double* G, int n_q, int k, int kq, __nv_bfloat16* out, cudaStream_t st) {
+  const long long n = (long long)n_q * kq * kq;
+  gram_pieces_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(G, n_q, k, kq, out);
   return cudaGetLastError();
 }
 
