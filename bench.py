@@ -40,6 +40,13 @@ GROUPED = dict(H=1024, W=1024, T=20000, dtype="uint16", mean=0.05, D=5e-4, n_q=6
 GROUPED_NAME = ("1024x1024 detector, 64 ring-plus-sector masks of 100..20000 px (246813 masked px, X holds "
                 "those only), T=20000 frames, uint16 Poisson AR(1) speckle mean 0.05 D=5e-4, k=128 basis fit "
                 "on the first 1000 frames; step = encode + two-time with g2 fused (C not stored: 102 GB)")
+# multi-stream serving: four detectors of different sizes at their own rates, 100 q-rings
+# each, coefficient histories capped at 2e5 frames, one server with continuous batching
+SERVING = dict(streams=[dict(H=1536, W=2048, rate_hz=2000.0, k=256, D=1e-4),
+                        dict(H=1024, W=1024, rate_hz=10000.0, k=128, D=4.64e-4),
+                        dict(H=512, W=512, rate_hz=50000.0, k=128, D=2.15e-3),
+                        dict(H=256, W=256, rate_hz=100000.0, k=64, D=1e-2)],
+               n_q=100, history=200000, max_batch=64, mean=0.02, n_fit=1000, pool=64, seed=20356005)
 # online stream: one 1 Mpx detector at 10 kHz, history of 1e5 frames
 STREAM = dict(H=1024, W=1024, dtype="uint16", mean=0.02, D=5e-4, n_q=36, k=128, n_fit=1000, history=100000,
               rate_hz=10000.0, pool=2048, max_batch=64, seed=20356003)
@@ -337,6 +344,11 @@ def run_ours(args, wl):
     if not (args.no_grouped or args.no_host) and args.workload == "c2":
         grouped_res = run_grouped_leg(X, dev, args)
 
+    # ---- multi-stream serving: four detectors at their own rates on one server
+    serving_res = None
+    if not (args.no_serving or args.no_host) and args.workload == "c2":
+        serving_res = run_serving_leg(X, dev, args)
+
     # ---- end to end through the public API from pinned host memory
     if args.no_host:
         if rank == 0:
@@ -466,6 +478,7 @@ def run_ours(args, wl):
         "clocks": sampler.summary() if sampler else None,
         "latency": stream_res,
         "grouped": grouped_res,
+        "serving": serving_res,
     }
     print(json.dumps(line), flush=True)
 
@@ -553,6 +566,110 @@ def run_grouped_leg(X, dev, args, gw=GROUPED):
     ctx.close()
     torch.cuda.empty_cache()
     return out
+
+
+def run_serving_leg(X, dev, args, sv=SERVING):
+    """Multi-stream serving: four streams of different detector sizes on one server.
+
+    Each stream gets its own basis (k per stream, fitted on a 1000-frame calibration run of
+    its detector) and 100 equal-width q-rings, and is opened on one xpcs_server with a
+    2e5-frame history cap and batches of up to 64 frames.  A client thread per stream
+    submits frames in device memory (a detector feeding the GPU directly; cycled from a
+    pool of distinct generated frames, queued by pointer with xpcs_server_submit_device)
+    at the stream's rate for `--serving-seconds`, starting from empty histories; the server's
+    scheduler batches continuously and the streams overlap on the device.  Afterwards each
+    stream is drained.  Reported per stream: target rate, frames submitted and dropped
+    (a client keeps at most about 256 MB of frames outstanding per stream, at least 64;
+    frames that arrive beyond that are dropped and counted), the rate at which the submitted frames were
+    folded in (frames / time until the last one completed), whether the stream kept up
+    (nothing dropped, folded rate within 2 % of the arrival rate), and the per-frame latency
+    (submit to completion) p50/p99."""
+    import threading
+
+    import torch
+    from synth import ring_qmap
+    from synth.speckle import TorchSpeckle
+
+    ctx = X.Context(dev.index or 0)
+    server = X.Server(ctx)
+    n_q, Wl, mb = sv["n_q"], sv["history"], sv["max_batch"]
+    streams = []
+    t0 = time.time()
+    for i, st in enumerate(sv["streams"]):
+        H, W, k = st["H"], st["W"], st["k"]
+        gen = TorchSpeckle(H, W, sv["mean"], st["D"], sv["seed"] + 100 + i, dtype="uint16", device=str(dev))
+        calib = gen.next(sv["n_fit"])
+        rings = X.Rings(ctx, torch.from_numpy(ring_qmap(H, W, n_q)).to(dev), H * W, n_q)
+        basis = X.xpcs_fit_basis(ctx, rings, calib, sv["n_fit"], k)
+        del calib, gen
+        gen = TorchSpeckle(H, W, sv["mean"], st["D"], sv["seed"] + i, dtype="uint16", device=str(dev))
+        pool = gen.next(sv["pool"])  # device frames, read in place by the stream
+        del gen
+        sid = server.open(basis, Wl, mb)
+        streams.append(dict(cfg=st, rings=rings, basis=basis, pool=pool, id=sid, sent=0, dropped=0, ticket=0))
+    torch.cuda.synchronize()
+    t_setup = time.time() - t0
+    secs = args.serving_seconds
+    start = time.perf_counter() + 0.05
+    stop_at = start + secs
+
+    def client(e):
+        # frames arrive at the stream's rate; while more than `cap` submitted frames are not
+        # yet folded in (about 256 MB of frames, at least 64), arriving frames are dropped
+        # and counted, as a detector that outruns its consumer loses them
+        rate, P = e["cfg"]["rate_hz"], e["pool"]
+        cap = max(64, (256 << 20) // (P.shape[1] * 2))
+        e["cap"] = cap
+        while True:
+            now = time.perf_counter()
+            if now >= stop_at:
+                break
+            due = int((now - start) * rate) - (e["sent"] + e["dropped"])
+            if due <= 0:
+                time.sleep(50e-6)
+                continue
+            if e["sent"] > cap and not server.poll(e["id"], e["sent"] - cap, 0):
+                e["dropped"] += due
+                continue
+            o = e["sent"] % P.shape[0]
+            n = min(due, P.shape[0] - o)
+            e["ticket"] = server.submit_device(e["id"], P[o:o + n])
+            e["sent"] += n
+
+    threads = [threading.Thread(target=client, args=(e,)) for e in streams]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    out = []
+    total = 0.0
+    for e in streams:
+        ok = server.poll(e["id"], e["ticket"], 60000) if e["ticket"] else True
+        t_done = time.perf_counter() - start
+        lat = server.latency(e["id"])
+        st = e["cfg"]
+        rate = e["sent"] / t_done if (ok and t_done > 0) else None
+        total += rate or 0.0
+        out.append({"detector": f"{st['H']}x{st['W']}", "k": st["k"], "D": st["D"], "rate_hz": st["rate_hz"],
+                    "frames": e["sent"], "dropped": e["dropped"], "backlog_cap": e.get("cap"), "drained": bool(ok),
+                    "folded_frames_per_s": rate,
+                    "kept_up": bool(e["dropped"] == 0 and rate is not None and rate >= 0.98 * st["rate_hz"]),
+                    "p50_us": lat["p50_us"], "p99_us": lat["p99_us"], "max_us": lat["max_us"],
+                    "history_reached": min(e["sent"], Wl)})
+    res = {"workload": "four uint16 streams (1536x2048 at 2 kHz k=256 D=1e-4, 1024x1024 at 10 kHz k=128 "
+                       "D=4.64e-4, 512x512 at 50 kHz k=128 D=2.15e-3, 256x256 at 100 kHz k=64 D=1e-2), "
+                       "Poisson AR(1) speckle mean 0.02, 100 q-rings each, history cap 200000, batches <= 64, "
+                       "one server, device frames submitted at each stream's rate from empty histories",
+           "seconds": secs, "streams": out, "total_folded_frames_per_s": total,
+           "target_frames_per_s": sum(s_["rate_hz"] for s_ in sv["streams"]), "batches": server.batches(),
+           "setup_s": t_setup}
+    server.close()
+    for e in streams:
+        e["basis"].close()
+        e["rings"].close()
+    ctx.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_stream_leg(X, ctx, dev, args, sw=STREAM):
@@ -682,6 +799,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "small"])
     ap.add_argument("--no-stream", action="store_true", help="skip the online stream leg")
     ap.add_argument("--no-grouped", action="store_true", help="skip the grouped 64-mask leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the multi-stream serving leg")
+    ap.add_argument("--serving-seconds", type=float, default=5.0, help="arrival window of the serving leg")
     ap.add_argument("--stream-seconds", type=float, default=10.0, help="paced part of the stream leg")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -302,6 +302,12 @@ xpcs_status xpcs_server_open(xpcs_server* server, const xpcs_basis* basis, int64
 /* Queue n host frames; *ticket (nullable) = frames submitted to this stream so far. */
 xpcs_status xpcs_server_submit(xpcs_server* server, xpcs_stream* s, const void* frames_host, int64_t n,
                                uint64_t* ticket);
+/* Queue n frames that are already in device memory (a detector feeding the GPU
+ * directly).  Nothing is copied: the stream's kernels read the frames in place, so the
+ * caller keeps them unchanged until the ticket has completed (xpcs_server_poll).  Batches
+ * are taken from one submitted block at a time. */
+xpcs_status xpcs_server_submit_device(xpcs_server* server, xpcs_stream* s, const void* frames_dev, int64_t n,
+                                      uint64_t* ticket);
 /* XPCS_OK once every frame up to `ticket` is folded in; XPCS_EBUSY after timeout_ms. */
 xpcs_status xpcs_server_poll(xpcs_server* server, xpcs_stream* s, uint64_t ticket, int timeout_ms);
 xpcs_status xpcs_server_read_g2(xpcs_server* server, xpcs_stream* s, double* g2_host, int64_t* count_host);

@@ -140,6 +140,11 @@ int64_t now_ns();
 // frame's arrival time for the latency record.  With block == false the call does nothing
 // and returns XPCS_EBUSY while that buffer's previous copy is still in flight.
 xpcs_status stream_push_host(xpcs_stream* S, const void* frames, int64_t n, const int64_t* arrive_ns, bool block);
+// Enqueue n frames that are already in device memory (read by the stream's kernels in place,
+// so they must stay unchanged until the stream has folded them in), with arrival stamps.
+xpcs_status stream_push_device_stamped(xpcs_stream* S, const void* frames, int64_t n, const int64_t* arrive_ns);
+// Batches of the stream still on the device (after retiring the finished ones).
+int stream_inflight(xpcs_stream* S);
 
 xpcs_status fail(xpcs_ctx* ctx, xpcs_status s, const std::string& msg);
 xpcs_status dev_alloc(xpcs_ctx* ctx, void** p, size_t bytes);

@@ -1,6 +1,7 @@
 // Serving layer: several online streams on one GPU, fed by one scheduler thread.
 //
-// Clients submit frames (copied into per-stream host queues) and return at once.  The
+// Clients submit frames (host frames are copied into per-stream host queues; device frames
+// are queued by pointer and read in place) and return at once.  The
 // scheduler loops over the admitted streams; for each one with queued frames whose
 // staging buffer is free it takes every frame that has arrived, up to the stream's batch
 // limit (continuous batching: a batch grows while the previous one is on the device), and
@@ -27,7 +28,8 @@ using namespace xpcs;
 
 struct xpcs_server {
   struct Chunk {
-    std::vector<char> data;
+    std::vector<char> data;        // host frames (copied at submit)
+    const char* dev = nullptr;     // or frames in device memory, read in place
     std::vector<int64_t> arrive;
     int64_t n = 0, off = 0;  // frames in the chunk, frames already taken
   };
@@ -75,21 +77,69 @@ void worker_loop(xpcs_server* sv) {
       xpcs_server::Slot* sl = sv->slots[(rr + u) % ns];
       if (sl->queued == 0) continue;
       xpcs_stream* s = sl->s;
-      const int64_t n = std::min<int64_t>(sl->queued, s->max_batch);
       const size_t fb = frame_bytes(s);
-      // gather the batch: the first n queued frames
-      sl->gather.resize(n * fb);
-      sl->gather_arrive.resize(n);
-      int64_t got = 0;
-      for (auto& c : sl->q) {
-        const int64_t take = std::min(n - got, c.n - c.off);
-        memcpy(sl->gather.data() + got * fb, c.data.data() + c.off * fb, take * fb);
-        std::copy(c.arrive.begin() + c.off, c.arrive.begin() + c.off + take, sl->gather_arrive.begin() + got);
-        got += take;
-        if (got == n) break;
-      }
+      const xpcs_server::Chunk& c0 = sl->q.front();
+      int64_t n = std::min<int64_t>(sl->queued, s->max_batch);
       xpcs_status st;
-      {
+      if (c0.dev) {
+        // continuous batching: while two batches of this stream are on the device, frames
+        // keep queueing and the next batch grows (the host path gets the same back-pressure
+        // from its staging buffers)
+        {
+          std::lock_guard<std::mutex> sg(sl->mu);
+          if (stream_inflight(s) >= 2) continue;
+        }
+        // device frames: within one submitted block the batch is read in place; a batch
+        // spanning blocks (continuous batching of small submissions) is gathered into the
+        // stream's device staging buffer by copies on the stream's own CUDA stream, ordered
+        // after its previous kernels
+        struct Piece {
+          const char* src;
+          int64_t n;
+        };
+        std::vector<Piece> pieces;
+        sl->gather_arrive.clear();
+        int64_t got = 0;
+        for (auto& c : sl->q) {
+          if (!c.dev || got == n) break;
+          const int64_t take = std::min(n - got, c.n - c.off);
+          pieces.push_back({c.dev + c.off * fb, take});
+          sl->gather_arrive.insert(sl->gather_arrive.end(), c.arrive.begin() + c.off, c.arrive.begin() + c.off + take);
+          got += take;
+        }
+        n = got;
+        std::lock_guard<std::mutex> sg(sl->mu);
+        lk.unlock();
+        if (pieces.size() == 1) {
+          st = stream_push_device_stamped(s, pieces[0].src, n, sl->gather_arrive.data());
+        } else {
+          st = XPCS_OK;
+          int64_t at = 0;
+          for (const Piece& pc : pieces) {
+            if (cudaMemcpyAsync(static_cast<char*>(s->d_frames) + at * fb, pc.src, pc.n * fb, cudaMemcpyDeviceToDevice,
+                                s->stream) != cudaSuccess) {
+              st = fail(s->ctx, XPCS_ECUDA, "server device gather failed");
+              break;
+            }
+            at += pc.n;
+          }
+          if (st == XPCS_OK) st = stream_push_device_stamped(s, s->d_frames, n, sl->gather_arrive.data());
+        }
+        lk.lock();
+      } else {
+        // host frames: gather the first n queued host frames (up to the next device chunk)
+        sl->gather.resize(n * fb);
+        sl->gather_arrive.resize(n);
+        int64_t got = 0;
+        for (auto& c : sl->q) {
+          if (c.dev) break;
+          const int64_t take = std::min(n - got, c.n - c.off);
+          memcpy(sl->gather.data() + got * fb, c.data.data() + c.off * fb, take * fb);
+          std::copy(c.arrive.begin() + c.off, c.arrive.begin() + c.off + take, sl->gather_arrive.begin() + got);
+          got += take;
+          if (got == n) break;
+        }
+        n = got;
         std::lock_guard<std::mutex> sg(sl->mu);
         lk.unlock();
         st = stream_push_host(s, sl->gather.data(), n, sl->gather_arrive.data(), false);
@@ -165,6 +215,24 @@ extern "C" xpcs_status xpcs_server_submit(xpcs_server* sv, xpcs_stream* s, const
   const size_t fb = frame_bytes(s);
   c.data.resize(n * fb);
   memcpy(c.data.data(), frames_host, n * fb);
+  c.arrive.assign(n, now_ns());
+  c.n = n;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  xpcs_server::Slot* sl = find_slot(sv, s);
+  if (!sl || sl->closing) return XPCS_EINVAL;
+  if (n) sl->q.push_back(std::move(c));
+  sl->queued += n;
+  sl->submitted += n;
+  if (ticket) *ticket = sl->submitted;
+  sv->cv_work.notify_one();
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_server_submit_device(xpcs_server* sv, xpcs_stream* s, const void* frames_dev, int64_t n,
+                                                 uint64_t* ticket) {
+  if (!sv || !s || !frames_dev || n < 0) return XPCS_EINVAL;
+  xpcs_server::Chunk c;
+  c.dev = static_cast<const char*>(frames_dev);
   c.arrive.assign(n, now_ns());
   c.n = n;
   std::lock_guard<std::mutex> lk(sv->mu);

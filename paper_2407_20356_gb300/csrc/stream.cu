@@ -244,7 +244,9 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   p.kpad = s.kpad;
   p.n_kc = s.kpad / 64;
   if (!row_update_config(s.n_q, s.kpad, &p.lt, &p.wst)) return cudaErrorInvalidConfiguration;
-  p.n_tiles = (int)((s.W + p.lt - 1) / p.lt);
+  // lags up to the window, and no further than the step's last frame: a pair (t, t - tau)
+  // of this step exists only for tau <= t0 + b - 1, so a young history skips the rest
+  p.n_tiles = (int)((std::min<long long>(s.W, s.t0 + s.b) + p.lt - 1) / p.lt);
   p.n_rg = (s.n_q + 35) / 36;
   p.n_mt = w2_mtiles(s.b, s.n_q);
   p.nfb = (s.b + 31) / 32;

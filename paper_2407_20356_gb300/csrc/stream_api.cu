@@ -413,6 +413,19 @@ xpcs_status push_device(xpcs_stream* S, const void* frames, int64_t n_frames, co
 
 }  // namespace
 
+namespace xpcs {
+
+xpcs_status stream_push_device_stamped(xpcs_stream* S, const void* frames, int64_t n, const int64_t* arrive_ns) {
+  return push_device(S, frames, n, arrive_ns, nullptr);
+}
+
+int stream_inflight(xpcs_stream* S) {
+  if (retire(S) != XPCS_OK) return 0;  // the next push reports the error
+  return (int)S->tickets.size();
+}
+
+}  // namespace xpcs
+
 extern "C" xpcs_status xpcs_stream_push_device(xpcs_stream* S, const void* frames, int64_t n_frames,
                                                uint64_t* ticket) {
   return push_device(S, frames, n_frames, nullptr, ticket);

@@ -81,6 +81,7 @@ _SIGS = {
     "xpcs_server_create": (C.c_int, [vp, C.POINTER(vp)]),
     "xpcs_server_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.c_int, C.POINTER(vp)]),
     "xpcs_server_submit": (C.c_int, [vp, vp, vp, i64, C.POINTER(C.c_uint64)]),
+    "xpcs_server_submit_device": (C.c_int, [vp, vp, vp, i64, C.POINTER(C.c_uint64)]),
     "xpcs_server_poll": (C.c_int, [vp, vp, C.c_uint64, C.c_int]),
     "xpcs_server_read_g2": (C.c_int, [vp, vp, vp, vp]),
     "xpcs_server_latency": (C.c_int, [vp, vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -436,6 +437,12 @@ class Server:
     def submit(self, s: int, frames) -> int:
         t = C.c_uint64()
         self.ctx.check(_lib.xpcs_server_submit(self.h, s, _ptr(frames), int(frames.shape[0]), C.byref(t)))
+        return t.value
+
+    def submit_device(self, s: int, frames) -> int:
+        """Queue device frames by pointer; they must stay unchanged until the ticket completes."""
+        t = C.c_uint64()
+        self.ctx.check(_lib.xpcs_server_submit_device(self.h, s, _ptr(frames), int(frames.shape[0]), C.byref(t)))
         return t.value
 
     def poll(self, s: int, ticket: int, timeout_ms: int = 0) -> bool:
