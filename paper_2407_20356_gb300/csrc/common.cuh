@@ -207,4 +207,23 @@ XPCS_DEV float2 u64_as_float2(unsigned long long x) {
   return make_float2(__uint_as_float((uint32_t)x), __uint_as_float((uint32_t)(x >> 32)));
 }
 
+// Sum of one row (32 floats, 16-byte aligned, row pitch LD floats) of a skewed buffer
+// whose entries lie in columns [lo, hi); the 16-byte groups outside that range hold zeros
+// and are not read (lanes that skip a group issue no shared-memory traffic for it).
+template <int LD>
+XPCS_DEV float skew_row_sum(const float* Q, int row, int lo, int hi) {
+  const ulonglong2* v = reinterpret_cast<const ulonglong2*>(Q + row * LD);
+  ulonglong2 s = make_ulonglong2(0ull, 0ull);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    if (4 * m + 3 >= lo && 4 * m < hi) {
+      const ulonglong2 x = v[m];
+      s.x = add_f32x2(s.x, x.x);
+      s.y = add_f32x2(s.y, x.y);
+    }
+  }
+  const float2 a = u64_as_float2(s.x), b = u64_as_float2(s.y);
+  return (a.x + a.y) + (b.x + b.y);
+}
+
 }  // namespace xpcs

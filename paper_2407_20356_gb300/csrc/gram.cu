@@ -73,23 +73,6 @@ struct GramSmem {
 constexpr uint32_t TMEM_COLS = 256;                // two 128-column accumulators
 constexpr int DIAG_BAR = 1;                        // named barrier of the eight diagonal warps
 
-// Sum of one row of a skewed buffer whose entries lie in columns i in [lo, hi); the
-// 16-byte groups outside that range hold zeros and are not read.
-__device__ __forceinline__ float skew_row_sum(const float* Q, int row, int lo, int hi) {
-  const ulonglong2* v = reinterpret_cast<const ulonglong2*>(Q + row * Q_LD);
-  ulonglong2 s = make_ulonglong2(0ull, 0ull);
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    if (4 * m + 3 >= lo && 4 * m < hi) {
-      const ulonglong2 x = v[m];
-      s.x = add_f32x2(s.x, x.x);
-      s.y = add_f32x2(s.y, x.y);
-    }
-  }
-  const float2 a = u64_as_float2(s.x), b = u64_as_float2(s.y);
-  return (a.x + a.y) + (b.x + b.y);
-}
-
 // Stores one 32-column chunk of a tile row: element (i, j) of tile (I, J) is C(t1, t2)
 // with t1 = 128 I + i, t2 = 128 J + j, written transposed at [t2][t1] (lower triangle) so
 // that for a fixed j the warp's 32 lanes write 32 consecutive values.  Raw mode also
@@ -377,9 +360,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
             for (int j = 0; j < 32; ++j) qw[Q_LD * (32 * sb + j)] = __uint_as_float(v[j]);
           }
           __syncwarp();
-          acc[0] += skew_row_sum(Q, lane, 32 - lane, 32);
-          acc[1] += skew_row_sum(Q, 32 + lane, 0, 32);
-          acc[2] += skew_row_sum(Q, 64 + lane, 0, 32 - lane);
+          acc[0] += skew_row_sum<Q_LD>(Q, lane, 32 - lane, 32);
+          acc[1] += skew_row_sum<Q_LD>(Q, 32 + lane, 0, 32);
+          acc[2] += skew_row_sum<Q_LD>(Q, 64 + lane, 0, 32 - lane);
         } else {
           // one 32-column block at a time: row lane holds block diagonal lane - 32 (acc[sb]),
           // row 32 + lane block diagonal lane (acc[sb + 1])
@@ -401,8 +384,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
 #pragma unroll
             for (int j = 0; j < 32; ++j) qw[Q_LD * j] = __uint_as_float(v[j]);
             __syncwarp();
-            acc[sb] += skew_row_sum(Q, lane, 32 - lane, 32);
-            acc[sb + 1] += skew_row_sum(Q, 32 + lane, 0, 32 - lane);
+            acc[sb] += skew_row_sum<Q_LD>(Q, lane, 32 - lane, 32);
+            acc[sb + 1] += skew_row_sum<Q_LD>(Q, 32 + lane, 0, 32 - lane);
           }
         }
       }

@@ -209,6 +209,7 @@ constexpr int W2_SMALL_B = 8;
 struct RowTcParams {
   long long t0, W, cap;
   int b, n_q, kpad, n_kc, lt, wst, n_tiles;
+  int skew;                // 1: diagonal sums of the large-step epilogue through skewed buffers
   int n_rg;  // ring groups of 36
   int n_mt;  // M-tiles per ring group
   int nfb;   // 32-frame blocks of the step
@@ -221,7 +222,7 @@ struct RowTcParams {
   int qg2;       // ring rows per g2sum / cnt box: min(36, n_q)
   uint32_t* status;
 };
-int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2);
+int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2, int skew);
 // tensor maps: A2 history, W2 pairs, Rh r values, g2sum and cnt (lt x qg2 boxes)
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
                                  const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,
@@ -246,7 +247,7 @@ inline long long stream_vwords(long long cap) { return (cap + 128 + 63) / 64 + 2
 __host__ __device__ inline int stream_npad(int n_q) { return (n_q + 3) / 4 * 4; }
 // lags per tile (64 or 32) and w stages (2 or 1) of the row update that fit shared
 // memory; false if none does
-bool row_update_config(int n_q, int kpad, int* lt, int* wst);
+bool row_update_config(int n_q, int kpad, int* lt, int* wst, int* skew);
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const RowTcParams& p, int grid,
                                  cudaStream_t st);
 cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, int n_q, long long W, long long Wp,

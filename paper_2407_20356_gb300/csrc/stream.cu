@@ -243,7 +243,7 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   p.n_q = s.n_q;
   p.kpad = s.kpad;
   p.n_kc = s.kpad / 64;
-  if (!row_update_config(s.n_q, s.kpad, &p.lt, &p.wst)) return cudaErrorInvalidConfiguration;
+  if (!row_update_config(s.n_q, s.kpad, &p.lt, &p.wst, &p.skew)) return cudaErrorInvalidConfiguration;
   // lags up to the window, and no further than the step's last frame: a pair (t, t - tau)
   // of this step exists only for tau <= t0 + b - 1, so a young history skips the rest
   p.n_tiles = (int)((std::min<long long>(s.W, s.t0 + s.b) + p.lt - 1) / p.lt);
@@ -262,13 +262,15 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   return launch_row_update_tc(*s.tmA, *s.tmW, *s.tmR, *s.tmG, *s.tmC, p, grid, st);
 }
 
-bool row_update_config(int n_q, int kpad, int* lt, int* wst) {
+// Largest lag tile that fits, the skewed-buffer epilogue preferred at each tile size.
+bool row_update_config(int n_q, int kpad, int* lt, int* wst, int* skew) {
   const int n_kc = kpad / 64, qb = std::min(36, stream_npad(n_q)), qg2 = std::min(36, n_q);
-  const int cand[3][2] = {{64, 2}, {32, 2}, {32, 1}};
+  const int cand[7][3] = {{64, 2, 1}, {64, 1, 1}, {64, 2, 0}, {32, 2, 1}, {32, 2, 0}, {32, 1, 1}, {32, 1, 0}};
   for (const auto& c : cand)
-    if (row_update_tc_smem(n_kc, c[0], qb, c[1], qg2) <= 227 * 1024) {
+    if (row_update_tc_smem(n_kc, c[0], qb, c[1], qg2, c[2]) <= 227 * 1024) {
       *lt = c[0];
       *wst = c[1];
+      *skew = c[2];
       return true;
     }
   return false;

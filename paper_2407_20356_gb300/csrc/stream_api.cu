@@ -129,8 +129,8 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
       (dtype != XPCS_U8 && dtype != XPCS_U16))
     return fail(ctx, XPCS_EINVAL, "bad stream_open args");
   *out = nullptr;
-  int lt = 0, wst = 0;
-  if (!row_update_config(B->rings->n_q, kpad_of(B->k), &lt, &wst))
+  int lt = 0, wst = 0, skew = 0;
+  if (!row_update_config(B->rings->n_q, kpad_of(B->k), &lt, &wst, &skew))
     return fail(ctx, XPCS_ENOTSUP, "stream: the row-update tile does not fit shared memory at this k");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int eb = dtype == XPCS_U8 ? 1 : 2;

@@ -37,15 +37,17 @@ constexpr int RT_CHUNK = RT_ROWS * RT_CH * 2;  // 16 KB: one operand chunk
 constexpr int RT_THREADS = 192;
 constexpr int RT_EPI_BAR = 1;
 constexpr int RT_QG = 36;                      // rings per work item (nine per lane quarter)
+constexpr int RT_QROWS = 64, RT_QLD = 36;      // skewed buffer of one epilogue warp (row j - i + 32)
 
 struct RtLayout {
-  int n_kc, lt, qb, wst, qg2;
+  int n_kc, lt, qb, wst, qg2, skew;
   __host__ __device__ int hist_bytes() const { return 2 * n_kc * RT_CHUNK; }
   __host__ __device__ int w_bytes() const { return wst * 2 * RT_CHUNK; }
   __host__ __device__ int slice_bytes() const { return (qg2 * lt * 8 + 1023) / 1024 * 1024; }  // one of two
   __host__ __device__ int rs_bytes() const { return RT_ROWS * qb * 4; }
   __host__ __device__ int bins_bytes() const { return RT_QG * (lt + 1) * 4; }
-  __host__ __device__ int rot_bytes() const { return 4 * 32 * 32 * 4; }  // a 32x32 block per epilogue warp
+  // per epilogue warp: a skewed buffer (64 rows of 36 floats) or a rotated 32x32 block
+  __host__ __device__ int rot_bytes() const { return skew ? 4 * RT_QROWS * RT_QLD * 4 : 4 * 32 * 32 * 4; }
   __host__ __device__ int vw_bytes() const { return RT_QG * 5 * 8; }      // validity words per ring
   __host__ __device__ int smem() const {
     return 1024 + hist_bytes() + w_bytes() + 2 * slice_bytes() + rs_bytes() + bins_bytes() + rot_bytes() +
@@ -59,21 +61,22 @@ XPCS_DEV unsigned long long bits64(const unsigned long long* w, int o) {
   return sh ? (w[wi] >> sh) | (w[wi + 1] << (64 - sh)) : w[wi];
 }
 
+template <bool SKEW>
 __global__ void __launch_bounds__(RT_THREADS, 1)
     row_update_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
                          const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmG,
                          const __grid_constant__ CUtensorMap tmC, const RowTcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const RtLayout L{p.n_kc, p.lt, p.qb, p.wst, p.qg2};
+  const RtLayout L{p.n_kc, p.lt, p.qb, p.wst, p.qg2, SKEW ? 1 : 0};
   uint8_t* hist = smem;                                       // [hi kc..., lo kc...]
   uint8_t* w_st = smem + L.hist_bytes();                      // [stage][hi, lo]
   double* g2s = reinterpret_cast<double*>(w_st + L.w_bytes());                     // [qg2][lt] g2 sums
   long long* cns = reinterpret_cast<long long*>(w_st + L.w_bytes() + L.slice_bytes());  // [qg2][lt] counts
   float* rs = reinterpret_cast<float*>(w_st + L.w_bytes() + 2 * L.slice_bytes());  // [128][qb] r of the rows
   float* bins = rs + RT_ROWS * p.qb;                          // [36][lt + 1]
-  float* rot = bins + RT_QG * (p.lt + 1);                     // [4][32][32]
-  unsigned long long* vw = reinterpret_cast<unsigned long long*>(rot + 4 * 1024);  // [36][5]
+  float* rot = bins + RT_QG * (p.lt + 1);                     // [4][64][36] skewed or [4][32][32] rotated
+  unsigned long long* vw = reinterpret_cast<unsigned long long*>(reinterpret_cast<uint8_t*>(rot) + L.rot_bytes());
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(vw) + L.vw_bytes());
   uint64_t* h_full = bars;        // history + r rows landed
   uint64_t* h_empty = bars + 1;   // MMAs done with the history rows
@@ -242,6 +245,11 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     const int w = warp & 3;           // TMEM lane quarter = ring residue
     const int et = threadIdx.x - 64;  // 0..127
     const unsigned long long bmask = p.b == 64 ? ~0ull : ((1ull << p.b) - 1);
+    if constexpr (SKEW) {  // entries of the skewed buffer no lane writes stay zero
+      float* Q = rot + w * (RT_QROWS * RT_QLD);
+      for (int x = lane; x < RT_QROWS * RT_QLD; x += 32) Q[x] = 0.f;
+      __syncwarp();
+    }
     uint32_t item_i = 0, acc_i = 0, stores = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++item_i) {
@@ -315,8 +323,43 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         const int c_lo = __reduce_min_sync(0xffffffffu, c_a);
         const int c_hi = __reduce_max_sync(0xffffffffu, c_b);
         if (ok && c_lo <= c_hi) {
-          float* P = rot + w * 1024;
           float* brow = bins + ql * (lt + 1);
+          if constexpr (SKEW) {
+            // C(f, c) r_q(s_c) of each 32 x 32 block, zero outside the kept lags, stored at
+            // row j - i + 32 of the warp's skewed buffer (constant offsets from a per-lane
+            // base); row lane then holds block diagonal lane - 32 and row 32 + lane block
+            // diagonal lane, summed with 16-byte loads
+            float* Q = rot + w * (RT_QROWS * RT_QLD);
+            float* qw = Q + (32 - lane) * RT_QLD + lane;
+#pragma unroll 1
+            for (int c32 = c_lo >> 5; c32 <= (c_hi >> 5); ++c32) {
+              uint32_t v[32];
+              tmem_ld32(tmem_base + buf * RT_ROWS + ((uint32_t)(w * 32) << 16) + c32 * 32, v);
+              tc_wait_ld();
+              const int cb = c32 * 32;
+              const bool full = __all_sync(0xffffffffu, c_a <= cb && c_b >= cb + 31);  // no lane masks
+              const float* rc = rs + (size_t)cb * p.qb + ql;  // r of column cb + jj: rc[jj qb]
+              __syncwarp();  // the previous block's row sums are read
+              if (full) {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) qw[RT_QLD * jj] = __uint_as_float(v[jj]) * rc[jj * p.qb];
+              } else {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                  const int c = cb + jj;
+                  qw[RT_QLD * jj] = (c >= c_a && c <= c_b) ? __uint_as_float(v[jj]) * rc[jj * p.qb] : 0.f;
+                }
+              }
+              __syncwarp();
+              const float an = skew_row_sum<RT_QLD>(Q, 32 + lane, 0, 32 - lane);
+              const float aw = skew_row_sum<RT_QLD>(Q, lane, 32 - lane, 32);
+              const int T0 = f0 + lt - 1 - cb;
+              const int bn = T0 - lane, bw = T0 - lane + 32;
+              if (bn >= 0 && bn < lt) brow[bn] += an;
+              if (bw >= 0 && bw < lt) brow[bw] += aw;
+            }
+          } else {
+          float* P = rot + w * 1024;
 #pragma unroll 1
           for (int c32 = c_lo >> 5; c32 <= (c_hi >> 5); ++c32) {
             uint32_t v[32];
@@ -352,6 +395,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             const int bn = T0 - lane, bw = T0 - lane + 32;
             if (bn >= 0 && bn < lt) brow[bn] += an;
             if (bw >= 0 && bw < lt) brow[bw] += aw;
+          }
           }
         }
         }
@@ -419,20 +463,30 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
 
 }  // namespace
 
-int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2) { return RtLayout{n_kc, lt, qb, wst, qg2}.smem(); }
+int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2, int skew) {
+  return RtLayout{n_kc, lt, qb, wst, qg2, skew}.smem();
+}
+
+template <bool SKEW>
+static cudaError_t launch_rt(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
+                             const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,
+                             cudaStream_t st) {
+  const int smem = row_update_tc_smem(p.n_kc, p.lt, p.qb, p.wst, p.qg2, SKEW ? 1 : 0);
+  static int attr_bytes = 0;  // the attribute only ever grows
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(row_update_tc_kernel<SKEW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  row_update_tc_kernel<SKEW><<<grid, RT_THREADS, smem, st>>>(tmA, tmW, tmR, tmG, tmC, p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
                                  const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,
                                  cudaStream_t st) {
-  const int smem = row_update_tc_smem(p.n_kc, p.lt, p.qb, p.wst, p.qg2);
-  static int attr_bytes = 0;  // the attribute only ever grows
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(row_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes = smem;
-  }
-  row_update_tc_kernel<<<grid, RT_THREADS, smem, st>>>(tmA, tmW, tmR, tmG, tmC, p);
-  return cudaGetLastError();
+  return p.skew ? launch_rt<true>(tmA, tmW, tmR, tmG, tmC, p, grid, st)
+                : launch_rt<false>(tmA, tmW, tmR, tmG, tmC, p, grid, st);
 }
 
 }  // namespace xpcs
