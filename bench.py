@@ -317,6 +317,16 @@ def run_ours(args, wl):
         sampler.stop()
     ms = max_over_ranks(ms, world, dev)
 
+    # ---- the same step captured once as a CUDA graph and replayed (one launch per step)
+    X.xpcs_capture_begin(ctx)
+    step()
+    graph = X.xpcs_capture_end(ctx)
+    graph_ms, graph_launches, _ = timed(graph.launch, args.steps, args.warmup)
+    graph_ms = max_over_ranks(graph_ms, world, dev)
+    graph_res = {"ms_per_step": graph_ms, "frames_per_s": world * T / (graph_ms * 1e-3),
+                 "kernels_per_step": graph.kernels(), "gpu_launches": graph_launches}
+    graph.close()
+
     # ---- raw exact path on the same frames (the comparison of the metric)
     raw_ms = None
     if not args.no_raw:
@@ -476,6 +486,7 @@ def run_ours(args, wl):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": sampler.summary() if sampler else None,
+        "cuda_graph": graph_res,
         "latency": stream_res,
         "grouped": grouped_res,
         "serving": serving_res,
@@ -542,6 +553,21 @@ def run_grouped_leg(X, dev, args, gw=GROUPED):
     prof = ctx.profile()
     ctx.profile_enable(False)
     kern = {k_: v[0] / max(1, v[1]) for k_, v in prof.items()}
+    # the same step as one CUDA graph (all masks' encode and two-time kernels, one launch)
+    X.xpcs_capture_begin(ctx)
+    step()
+    graph = X.xpcs_capture_end(ctx)
+    for _ in range(3):
+        graph.launch()
+    ctx.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        graph.launch()
+    e1.record(stream)
+    ctx.synchronize()
+    graph_ms = e0.elapsed_time(e1) / K
+    graph_kernels = graph.kernels()
+    graph.close()
     sizes = np.bincount(qmap[qmap >= 0], minlength=n_q)
     nT = (T + 127) // 128
     flops = 2.0 * n_q * k * T * (T + 1) / 2  # one product over the upper triangle
@@ -553,6 +579,8 @@ def run_grouped_leg(X, dev, args, gw=GROUPED):
         "workload": GROUPED_NAME, "frames_per_s": T / (ms * 1e-3), "ms_per_step": ms, "steps": K, "warmup": 3,
         "masks": n_q, "mask_px": {"min": int(sizes.min()), "max": int(sizes.max()), "total": int(sizes.sum())},
         "tiles_per_step": int(n_q * nT * (nT + 1) // 2), "kernels_ms": kern, "gpu_launches": launches,
+        "cuda_graph": {"ms_per_step": graph_ms, "frames_per_s": T / (graph_ms * 1e-3),
+                       "kernels_per_step": graph_kernels},
         "roofline": {"bound": "tensor", "kernel": "twotime_gram", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "peak_source": pk["source"] + (" sustained" if pk["bf16_tflops_sustained"] else ""),

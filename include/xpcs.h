@@ -71,6 +71,7 @@ typedef struct xpcs_rings xpcs_rings;
 typedef struct xpcs_basis xpcs_basis;
 typedef struct xpcs_stream xpcs_stream;
 typedef struct xpcs_server xpcs_server;
+typedef struct xpcs_graph xpcs_graph;
 
 /* ------------------------------------------------------------------ context */
 
@@ -239,6 +240,25 @@ xpcs_status xpcs_twotime_stats(xpcs_ctx* ctx, const float* C, int n_q, int64_t T
 xpcs_status xpcs_peak_visibility(xpcs_ctx* ctx, const double* g2, int n_q, int64_t T, int64_t peak_lo,
                                  int64_t peak_hi, int64_t bg_lo, int64_t bg_hi, const double* ttc_std,
                                  double factor, double* vis_out, int32_t* flag_out);
+
+/* ------------------------------------------------------------------ CUDA-graph capture
+ * xpcs_capture_begin records the following library calls made on ctx (encode, two-time,
+ * g2, analysis: everything that runs on the context's stream) instead of running them;
+ * xpcs_capture_end instantiates them as one graph that xpcs_graph_launch replays with a
+ * single launch on the context's stream (asynchronously if the context is, else waiting
+ * for it).  During the capture the context runs asynchronously and profiling must be off.
+ * The graph refers to the buffers the captured calls used, so while any graph of the
+ * context exists, calls that would move or rewrite the context's scratch, its cached
+ * two-time work items or a basis's first-use copies fail with XPCS_EBUSY: run each call
+ * once, at its largest size, before capturing it.  Streams and servers are not captured.
+ * A failed capture leaves the context usable and returns XPCS_ECUDA (or the failing
+ * call's status). */
+xpcs_status xpcs_capture_begin(xpcs_ctx* ctx);
+xpcs_status xpcs_capture_end(xpcs_ctx* ctx, xpcs_graph** out);
+xpcs_status xpcs_graph_launch(xpcs_ctx* ctx, const xpcs_graph* graph);
+/* Library kernels in the graph (added to xpcs_launch_count at every launch). */
+uint64_t xpcs_graph_kernels(const xpcs_graph* graph);
+xpcs_status xpcs_graph_destroy(xpcs_graph* graph);
 
 /* ------------------------------------------------------------------ online stream (Sec. 2.2, Fig. 1c)
  * Online compression with a basis fit before acquisition: every pushed frame is encoded

@@ -50,6 +50,10 @@ void dev_free(xpcs_ctx* ctx, void* p, size_t bytes) {
 
 xpcs_status ensure_scratch(xpcs_ctx* ctx, size_t need) {
   if (need <= ctx->scratch_cap) return XPCS_OK;
+  if (ctx->capturing || ctx->graphs > 0)
+    return fail(ctx, XPCS_EBUSY,
+                "the context's scratch cannot grow during a capture or while captured graphs exist: run the "
+                "largest call once before capturing");
   XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   dev_free(ctx, ctx->scratch, ctx->scratch_cap);
   ctx->scratch = nullptr;
@@ -151,6 +155,10 @@ std::vector<int4> make_items(int n_q, int nT, int CH) {
 // Device copy of the work items for (n_q, nT, CH), rebuilt only when they change.
 xpcs_status cached_items(xpcs_ctx* ctx, int n_q, int nT, int CH, int4** d_items, int* n_items) {
   if (ctx->items_key[0] != n_q || ctx->items_key[1] != nT || ctx->items_key[2] != CH) {
+    if (ctx->capturing || ctx->graphs > 0)
+      return fail(ctx, XPCS_EBUSY,
+                  "two-time work items of another shape cannot be built during a capture or while captured "
+                  "graphs exist: run the call once before capturing");
     const std::vector<int4> items = make_items(n_q, nT, CH);
     const size_t bytes = items.size() * sizeof(int4);
     if (bytes > ctx->items_bytes) {
@@ -845,6 +853,8 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   const int kq = (k + 63) / 64 * 64;
   const bool use_tc = norm != XPCS_NORM_FROB && kq <= 128;
   if (use_tc && !B->d_Gpair) {
+    if (ctx->capturing)
+      return fail(ctx, XPCS_EBUSY, "run the two-time call once before capturing it (basis pieces are made on first use)");
     xpcs_basis* Bm = const_cast<xpcs_basis*>(B);
     void* p = nullptr;
     const size_t gb = (size_t)n_q * kq * 2 * kq * 2;

@@ -39,6 +39,13 @@ struct xpcs_ctx {
   bool prof = false;
   std::vector<xpcs_prof_entry> prof_entries;
   std::vector<cudaEvent_t> event_pool;
+  // CUDA-graph capture of the context's stream: while capturing, and while graphs made
+  // from it exist, nothing the captured work refers to (scratch, work items, lazily made
+  // basis copies) may move or change
+  bool capturing = false;
+  bool async_before_capture = false;
+  uint64_t launches_at_capture = 0;
+  int graphs = 0;
 };
 
 struct xpcs_rings {

@@ -66,6 +66,11 @@ _SIGS = {
     "xpcs_twotime_stats": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_peak_visibility": (C.c_int, [vp, vp, C.c_int, i64, i64, i64, i64, i64, vp, C.c_double, vp, vp]),
     "xpcs_selftest_timeout": (C.c_int, [vp, C.c_int]),
+    "xpcs_capture_begin": (C.c_int, [vp]),
+    "xpcs_capture_end": (C.c_int, [vp, C.POINTER(vp)]),
+    "xpcs_graph_launch": (C.c_int, [vp, vp]),
+    "xpcs_graph_kernels": (C.c_uint64, [vp]),
+    "xpcs_graph_destroy": (C.c_int, [vp]),
     "xpcs_g2_noalloc": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_stream_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.POINTER(vp)]),
     "xpcs_stream_push": (C.c_int, [vp, vp, i64, C.POINTER(C.c_uint64)]),
@@ -310,6 +315,41 @@ def xpcs_twotime_norm(ctx: Context, basis: Basis, A, T: int, prec, norm, C_out=N
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     ctx.check(_lib.xpcs_twotime_norm(ctx.h, basis.h, _ptr(A), T, p, _norm_code(norm), _ptr(C_out), _ptr(g2_out),
                                      _ptr(count_out)))
+
+
+class Graph:
+    """A captured sequence of library calls on a context (xpcs_capture_begin/end)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        ctx._adopt(self)
+
+    def launch(self):
+        self.ctx.check(_lib.xpcs_graph_launch(self.ctx.h, self.h))
+
+    def kernels(self) -> int:
+        return int(_lib.xpcs_graph_kernels(self.h))
+
+    def close(self):
+        if self.h and self.ctx.h:
+            _lib.xpcs_graph_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def xpcs_capture_begin(ctx: Context):
+    ctx.check(_lib.xpcs_capture_begin(ctx.h))
+
+
+def xpcs_capture_end(ctx: Context) -> Graph:
+    h = vp()
+    ctx.check(_lib.xpcs_capture_end(ctx.h, C.byref(h)))
+    return Graph(ctx, h)
 
 
 def xpcs_fit_relaxation(ctx: Context, g2, n_q: int, T: int, tau_lo: int, tau_hi: int, t0_min: float,
