@@ -183,6 +183,16 @@ xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* basis, const void* X, x
  * Outputs nullable as for xpcs_twotime_raw. */
 xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T, xpcs_precision prec,
                          float* C_out, double* g2_out, int64_t* count_out);
+/* Autotuner of xpcs_twotime for one workload shape (rings, frames, precision, whether C
+ * is stored): times each candidate configuration of the two-time kernel (tiles per work
+ * item 4, 8, 16 or 32 along a tile diagonal; diagonal sums by whole 64-column strips or by
+ * 32-column blocks) on these very arguments, `reps` timed calls each after one untimed
+ * call, keeps the fastest in the context for later calls of that shape, and runs it once
+ * more so the outputs are its own.  tiles_out, strip_out, ms_out (host, nullable): the
+ * choice and its time per call.  Not during a capture. */
+xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T,
+                                  xpcs_precision prec, float* C_out, double* g2_out, int64_t* count_out, int reps,
+                                  int* tiles_out, int* strip_out, double* ms_out);
 /* xpcs_twotime with a chosen normalisation (xpcs_norm); norm = XPCS_NORM_MEAN is
  * xpcs_twotime. */
 xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T,

@@ -485,6 +485,16 @@ extern "C" xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* R, const 
 namespace {
 
 // Shared tail of both two-time paths: the Gram launch, pair counts and g2.
+// Two-time configuration for a workload shape: the autotuner's choice if there is one, else
+// CHUNK_TILES tiles per work item and the whole-strip diagonal schedule for hi/lo operand
+// pieces (the faster one there when measured), the block schedule otherwise.
+std::pair<int, int> gram_tune_for(xpcs_ctx* ctx, uint64_t key, int split) {
+  if (ctx->tune_forced) return ctx->tune_force;
+  const auto it = ctx->gram_tune.find(key);
+  if (it != ctx->gram_tune.end()) return it->second;
+  return {CHUNK_TILES, split};
+}
+
 xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap& tmR, GramParams gp, int n_q,
                         int64_t T, int T_pad, int nT, int maxC, uint32_t* vbits, long long* count,
                         double* g2_out) {
@@ -521,7 +531,8 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   const int n_q = R->n_q;
   const int nT = (int)((T + TILE - 1) / TILE);
   const int T_pad = nT * TILE;
-  const int CH = CHUNK_TILES;
+  const std::pair<int, int> tune = gram_tune_for(ctx, gram_tune_key(n_q, nT, 1, 0, 1, C_out || N_out), 0);
+  const int CH = tune.first;
   const int maxC = (nT + CH - 1) / CH;
   const bool want_g2 = g2_out != nullptr;
   const bool want_cnt = want_g2 || count_out;
@@ -565,6 +576,7 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   gp.fmt = 1;
   gp.split = 0;
   gp.raw = 1;
+  gp.strip = tune.second;
   gp.r = b.r;
   gp.blk_bad = b.blk_bad;
   gp.C = C_out;
@@ -840,9 +852,11 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   const int n_q = B->rings->n_q, k = B->k;
   const int nT = (int)((T + TILE - 1) / TILE);
   const int T_pad = nT * TILE;
-  const int CH = CHUNK_TILES;
-  const int maxC = (nT + CH - 1) / CH;
   const bool split = prec == XPCS_PREC_BF16X3;
+  const std::pair<int, int> tune = gram_tune_for(
+      ctx, gram_tune_key(n_q, nT, prec == XPCS_PREC_FP16 ? 0 : 1, split ? 1 : 0, 0, C_out != nullptr), split ? 1 : 0);
+  const int CH = tune.first;
+  const int maxC = (nT + CH - 1) / CH;
   const int nkp = (k + KCH - 1) / KCH;           // 64-wide chunks per operand piece
   const int Kc = (split ? 2 : 1) * nkp * KCH;
   const bool want_g2 = g2_out != nullptr;
@@ -947,6 +961,7 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   gp.fmt = prec == XPCS_PREC_FP16 ? 0 : 1;
   gp.split = split ? 1 : 0;
   gp.raw = 0;
+  gp.strip = tune.second;
   gp.r = b.r;
   gp.blk_bad = b.blk_bad;
   gp.C = C_out;

@@ -438,11 +438,11 @@ static cudaError_t launch_gram_t(const CUtensorMap& tmL, const CUtensorMap& tmR,
   return cudaGetLastError();
 }
 
-// hi/lo operand pieces take the whole-strip diagonal schedule, single operands (and the raw
-// path) the block schedule
+// the diagonal schedule is a parameter (chosen per call: the whole-strip schedule for hi/lo
+// operand pieces and the block schedule otherwise unless an autotuned choice says otherwise)
 cudaError_t launch_gram(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
                         cudaStream_t st) {
-  return p.split ? launch_gram_t<true>(tmL, tmR, p, grid, st) : launch_gram_t<false>(tmL, tmR, p, grid, st);
+  return p.strip ? launch_gram_t<true>(tmL, tmR, p, grid, st) : launch_gram_t<false>(tmL, tmR, p, grid, st);
 }
 
 }  // namespace xpcs

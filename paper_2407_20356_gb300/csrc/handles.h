@@ -2,6 +2,7 @@
 #pragma once
 #include <cusolverDn.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <deque>
@@ -42,6 +43,11 @@ struct xpcs_ctx {
   // CUDA-graph capture of the context's stream: while capturing, and while graphs made
   // from it exist, nothing the captured work refers to (scratch, work items, lazily made
   // basis copies) may move or change
+  // two-time configuration per workload shape (key from gram_tune_key), set by the
+  // autotuner; `forced` overrides everything while the autotuner times a candidate
+  std::map<uint64_t, std::pair<int, int>> gram_tune;  // key -> (tiles per work item, strip)
+  bool tune_forced = false;
+  std::pair<int, int> tune_force{0, 0};
   bool capturing = false;
   bool async_before_capture = false;
   uint64_t launches_at_capture = 0;
@@ -162,6 +168,12 @@ xpcs_status finish(xpcs_ctx* ctx);
 xpcs_status make_map(xpcs_ctx* ctx, CUtensorMap* map, const void* base, CUtensorMapDataType dt, int elem_bytes,
                      uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw,
                      uint64_t pitch_bytes = 0);
+
+// Key of a two-time workload shape in the context's tuning table.
+inline uint64_t gram_tune_key(int n_q, int nT, int fmt, int split, int raw, bool C) {
+  return ((uint64_t)n_q << 40) | ((uint64_t)nT << 16) | ((uint64_t)fmt << 4) | ((uint64_t)split << 3) |
+         ((uint64_t)raw << 2) | (C ? 2u : 0u);
+}
 
 // Scratch: one growing device buffer per context, carved per call.
 struct Carve {

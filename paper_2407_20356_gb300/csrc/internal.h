@@ -23,7 +23,7 @@ enum : uint32_t {
 constexpr int TILE = 128;        // frames per tile side
 constexpr int KCH = 64;          // 16-bit K elements per pipeline chunk (128 bytes)
 constexpr int DIAG_SLOTS = 256;  // local diagonal slots per (ring, tile-diagonal, chunk)
-constexpr int CHUNK_TILES = 8;   // tiles per work item along a tile diagonal
+constexpr int CHUNK_TILES = 8;   // default tiles per work item along a tile diagonal
 
 // ------------------------------------------------------------------ Gram kernel
 
@@ -42,6 +42,7 @@ struct GramParams {
   int split;               // 1: operand rows are [hi | lo] pieces of k_chunks chunks each;
                            //    C = L_hi R_hi + L_lo R_hi + L_hi R_lo
   int raw;                 // 1: C = acc * r(t1) * r(t2); 0: operands already scaled
+  int strip;               // diagonal schedule: 1 whole 64-column strips, 0 32-column blocks
   const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined
   const uint32_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
   float* C;                // nullable [n_q][T][T]

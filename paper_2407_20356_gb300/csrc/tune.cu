@@ -1,0 +1,81 @@
+// Autotuner of the compressed two-time call.
+//
+// The two-time kernel has two run-time choices for a workload shape: the length of a work
+// item (tiles along one tile diagonal whose diagonal sums meet once: 4, 8, 16 or 32; it
+// trades load balance across the SMs against the number of partial-sum slots and per-item
+// overheads) and the schedule of the diagonal sums (whole 64-column strips or 32-column
+// blocks; the kernel is instantiated for both).  xpcs_autotune_twotime times every
+// candidate on the caller's own inputs and outputs (CUDA events on the context's stream,
+// after one untimed run per candidate that builds its work items), keeps the fastest in
+// the context's table for the shape (rings, tiles, operand format, whether C is stored),
+// and finally runs it, so the outputs are those of the chosen configuration.  Later
+// two-time calls of that shape use it.
+#include <string>
+
+#include "handles.h"
+#include "internal.h"
+
+using namespace xpcs;
+
+extern "C" xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const float* A, int64_t T,
+                                             xpcs_precision prec, float* C_out, double* g2_out, int64_t* count_out,
+                                             int reps, int* tiles_out, int* strip_out, double* ms_out) {
+  if (!ctx || !B || !A || T <= 0 || B->ctx != ctx || (int)prec < 0 || (int)prec > 2 || reps < 1 || reps > 100)
+    return fail(ctx, XPCS_EINVAL, "bad autotune_twotime args");
+  if (ctx->capturing) return fail(ctx, XPCS_EINVAL, "autotuning cannot run during a capture");
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int n_q = B->rings->n_q;
+  const int nT = (int)((T + TILE - 1) / TILE);
+  const bool split = prec == XPCS_PREC_BF16X3;
+  const uint64_t key = gram_tune_key(n_q, nT, prec == XPCS_PREC_FP16 ? 0 : 1, split ? 1 : 0, 0, C_out != nullptr);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  XPCS_CUDA(ctx, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, XPCS_ECUDA, "autotune: event creation failed");
+  }
+  const bool async = ctx->async, prof = ctx->prof;
+  ctx->async = true;  // back-to-back calls; the events bound the timed runs
+  ctx->prof = false;
+  std::pair<int, int> best{0, 0};
+  double best_ms = 1e300;
+  xpcs_status st = XPCS_OK;
+  const int tiles[4] = {4, 8, 16, 32};
+  for (int strip = 0; strip < 2 && st == XPCS_OK; ++strip) {
+    for (int ti = 0; ti < 4 && st == XPCS_OK; ++ti) {
+      ctx->tune_forced = true;
+      ctx->tune_force = {tiles[ti], strip};
+      st = xpcs_twotime(ctx, B, A, T, prec, C_out, g2_out, count_out);  // untimed: builds the work items
+      if (st != XPCS_OK) break;
+      cudaEventRecord(e0, ctx->stream);
+      for (int r = 0; r < reps && st == XPCS_OK; ++r) st = xpcs_twotime(ctx, B, A, T, prec, C_out, g2_out, count_out);
+      cudaEventRecord(e1, ctx->stream);
+      if (st != XPCS_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = fail(ctx, XPCS_ECUDA, "autotune: event wait failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / reps < best_ms) {
+        best_ms = ms / reps;
+        best = ctx->tune_force;
+      }
+    }
+  }
+  ctx->tune_forced = false;
+  if (st == XPCS_OK) {
+    ctx->gram_tune[key] = best;
+    st = xpcs_twotime(ctx, B, A, T, prec, C_out, g2_out, count_out);  // outputs of the chosen configuration
+  }
+  if (st == XPCS_OK) st = xpcs_synchronize(ctx);
+  ctx->async = async;
+  ctx->prof = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != XPCS_OK) return st;
+  if (tiles_out) *tiles_out = best.first;
+  if (strip_out) *strip_out = best.second;
+  if (ms_out) *ms_out = best_ms;
+  return XPCS_OK;
+}

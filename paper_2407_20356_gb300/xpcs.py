@@ -61,6 +61,8 @@ _SIGS = {
     "xpcs_encode": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
     "xpcs_twotime_norm": (C.c_int, [vp, vp, vp, i64, C.c_int, C.c_int, vp, vp, vp]),
+    "xpcs_autotune_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp, C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "xpcs_g2": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_fit_relaxation": (C.c_int, [vp, vp, C.c_int, i64, i64, i64, C.c_double, C.c_double, vp]),
     "xpcs_twotime_stats": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
@@ -309,6 +311,16 @@ def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None,
         return xpcs_twotime_norm(ctx, basis, A, T, prec, norm, C_out, g2_out, count_out)
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     ctx.check(_lib.xpcs_twotime(ctx.h, basis.h, _ptr(A), T, p, _ptr(C_out), _ptr(g2_out), _ptr(count_out)))
+
+
+def xpcs_autotune_twotime(ctx: Context, basis: Basis, A, T: int, prec="bf16x3", C_out=None, g2_out=None,
+                          count_out=None, reps: int = 2) -> dict:
+    """Time the two-time kernel's configurations on these arguments, keep the fastest."""
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    tiles, strip, ms = C.c_int(), C.c_int(), C.c_double()
+    ctx.check(_lib.xpcs_autotune_twotime(ctx.h, basis.h, _ptr(A), T, p, _ptr(C_out), _ptr(g2_out), _ptr(count_out),
+                                         reps, C.byref(tiles), C.byref(strip), C.byref(ms)))
+    return {"tiles_per_item": tiles.value, "strip": bool(strip.value), "ms": ms.value}
 
 
 def xpcs_twotime_norm(ctx: Context, basis: Basis, A, T: int, prec, norm, C_out=None, g2_out=None, count_out=None):

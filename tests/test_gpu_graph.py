@@ -87,3 +87,30 @@ def test_capture_refuses_profiling(X):
     assert e.value.status == X.XPCS_EINVAL
     ctx.profile_enable(False)
     ctx.close()
+
+
+def test_autotuned_configuration_gives_the_same_results(X):
+    # the tuned configuration only changes how the work is split and scheduled: C is
+    # bit-identical, counts exact, g2 equal up to the order of its f32 partial sums
+    torch, dev, ctx, rings, basis, Xd = _setup(X, T=700)
+    T, n_q, k = Xd.shape[0], 4, 24
+    A = torch.empty((T, k), dtype=torch.float32, device=dev)
+    X.xpcs_encode(ctx, basis, Xd, T, A)
+    outs = []
+    for tune in (False, True):
+        C = torch.full((n_q, T, T), float("nan"), dtype=torch.float32, device=dev)
+        g2 = torch.empty((n_q, T), dtype=torch.float64, device=dev)
+        cnt = torch.empty((n_q, T), dtype=torch.int64, device=dev)
+        if tune:
+            got = X.xpcs_autotune_twotime(ctx, basis, A, T, "bf16x3", C_out=C, g2_out=g2, count_out=cnt, reps=1)
+            assert got["tiles_per_item"] in (4, 8, 16, 32) and got["ms"] > 0
+        else:
+            X.xpcs_twotime(ctx, basis, A, T, "bf16x3", C_out=C, g2_out=g2, count_out=cnt)
+        ctx.synchronize()
+        outs.append((C, g2, cnt))
+    (C0, g0, c0), (C1, g1, c1) = outs
+    assert torch.equal(C0.isnan(), C1.isnan()) and torch.equal(C0[~C0.isnan()], C1[~C1.isnan()])
+    assert torch.equal(c0, c1)
+    ok = ~g0.isnan()
+    assert torch.allclose(g1[ok], g0[ok], rtol=1e-5, atol=0)
+    ctx.close()
