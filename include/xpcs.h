@@ -187,8 +187,9 @@ xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A,
  * is stored): times each candidate configuration of the two-time kernel (tiles per work
  * item 4, 8, 16 or 32 along a tile diagonal; diagonal sums by whole 64-column strips or by
  * 32-column blocks) on these very arguments, `reps` timed calls each after one untimed
- * call, keeps the fastest in the context for later calls of that shape, and runs it once
- * more so the outputs are its own.  tiles_out, strip_out, ms_out (host, nullable): the
+ * call, keeps the fastest in the context for later calls of that shape (the default, 8
+ * tiles with strips for hi/lo operands, unless another is at least 3 % faster), and runs
+ * it once more so the outputs are its own.  tiles_out, strip_out, ms_out (host, nullable): the
  * choice and its time per call.  Not during a capture. */
 xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T,
                                   xpcs_precision prec, float* C_out, double* g2_out, int64_t* count_out, int reps,
@@ -307,6 +308,18 @@ xpcs_status xpcs_stream_poll(xpcs_stream* s, uint64_t ticket, int timeout_ms);
 xpcs_status xpcs_stream_read_g2(xpcs_stream* s, double* g2_host, int64_t* count_host);
 /* Frames pushed so far. */
 int64_t xpcs_stream_frames(const xpcs_stream* s);
+/* Checkpoint / resume of a stream's state: the coefficient history, ring-factor rows,
+ * validity bits, g2 sums, pair counts and frame count (everything else is per-step
+ * scratch), after a header with the stream's shape and a hash of the basis's ring
+ * factors.  xpcs_stream_checkpoint waits for the stream's queued batches and copies the
+ * state into host_buf (at least xpcs_stream_checkpoint_size bytes).  xpcs_stream_restore
+ * takes a checkpoint into a stream opened with the same basis, history, max_batch and
+ * dtype to which no frame has been pushed yet, which then continues where the
+ * checkpointed one stopped; other shapes or bases give XPCS_EINVAL.  Latency records are
+ * not part of the state. */
+xpcs_status xpcs_stream_checkpoint_size(const xpcs_stream* stream, size_t* bytes);
+xpcs_status xpcs_stream_checkpoint(xpcs_stream* stream, void* host_buf, size_t bytes);
+xpcs_status xpcs_stream_restore(xpcs_stream* stream, const void* host_buf, size_t bytes);
 /* Per-frame latency of completed frames, in microseconds (host steady clock): from the
  * frame's arrival (entering xpcs_stream_push, or its submission to a server) to the end of
  * its batch's device work.  *n_frames = frames measured.  reset != 0 forgets them. */

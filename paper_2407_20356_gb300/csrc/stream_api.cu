@@ -504,3 +504,129 @@ extern "C" xpcs_status xpcs_stream_close(xpcs_stream* S) {
   stream_free(S);
   return XPCS_OK;
 }
+
+// ====================================================================== checkpoint / resume
+//
+// A checkpoint is a header followed by the stream's state: the coefficient history ring
+// (bf16 hi | lo rows), the ring-factor rows r_q(s), the validity bits, the g2 sums and the
+// pair counts, each as stored on the device.  Everything else a stream holds is per-step
+// scratch.  The header records the shape (k, n_q, M, W, ring slots, dtype), the frame
+// count and a hash of the basis's ring factors (FNV-1a over G_q and s_q), so a checkpoint
+// is restored only into a stream of the same shape and basis.
+
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t k, n_q, dtype;
+  int64_t M, W, cap, frames;
+  uint64_t basis_hash;
+  uint64_t bytes[5];  // A2, Rh, vbits, g2sum, cnt
+};
+
+constexpr char CKPT_MAGIC[8] = {'X', 'P', 'C', 'S', 'C', 'K', 'P', 'T'};
+
+xpcs_status basis_hash(xpcs_stream* S, uint64_t* h) {
+  const xpcs_basis* B = S->basis;
+  const int n_q = B->rings->n_q, k = B->k;
+  std::vector<double> buf((size_t)n_q * k * k + (size_t)n_q * k);
+  XPCS_CUDA(S->ctx, cudaMemcpy(buf.data(), B->d_G, (size_t)n_q * k * k * 8, cudaMemcpyDeviceToHost));
+  XPCS_CUDA(S->ctx, cudaMemcpy(buf.data() + (size_t)n_q * k * k, B->d_s, (size_t)n_q * k * 8, cudaMemcpyDeviceToHost));
+  uint64_t x = 1469598103934665603ull;
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(buf.data());
+  for (size_t i = 0; i < buf.size() * 8; ++i) x = (x ^ p[i]) * 1099511628211ull;
+  *h = x;
+  return XPCS_OK;
+}
+
+void ckpt_parts(xpcs_stream* S, void* ptr[5], uint64_t bytes[5]) {
+  const Sizes z = stream_sizes(S->basis, S->W, S->max_batch, S->dtype == XPCS_U8 ? 1 : 2);
+  ptr[0] = S->d_A2;
+  ptr[1] = S->d_Rh;
+  ptr[2] = S->d_vbits;
+  ptr[3] = S->d_g2sum;
+  ptr[4] = S->d_cnt;
+  bytes[0] = z.A2;
+  bytes[1] = z.Rh;
+  bytes[2] = z.vbits;
+  bytes[3] = z.g2sum;
+  bytes[4] = z.cnt;
+}
+
+}  // namespace
+
+extern "C" xpcs_status xpcs_stream_checkpoint_size(const xpcs_stream* S, size_t* bytes) {
+  if (!S || !bytes) return XPCS_EINVAL;
+  void* ptr[5];
+  uint64_t b[5];
+  ckpt_parts(const_cast<xpcs_stream*>(S), ptr, b);
+  *bytes = sizeof(CkptHeader) + b[0] + b[1] + b[2] + b[3] + b[4];
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_stream_checkpoint(xpcs_stream* S, void* host_buf, size_t bytes) {
+  if (!S || !host_buf) return XPCS_EINVAL;
+  xpcs_ctx* ctx = S->ctx;
+  size_t need = 0;
+  xpcs_stream_checkpoint_size(S, &need);
+  if (bytes < need) return fail(ctx, XPCS_EINVAL, "checkpoint buffer too small: need " + std::to_string(need));
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  XPCS_CUDA(ctx, cudaStreamSynchronize(S->stream));  // every queued batch folded in
+  XPCS_TRY(retire(S));
+  CkptHeader h{};
+  memcpy(h.magic, CKPT_MAGIC, 8);
+  h.version = 1;
+  h.k = S->basis->k;
+  h.n_q = S->basis->rings->n_q;
+  h.dtype = S->dtype;
+  h.M = S->basis->rings->M;
+  h.W = S->W;
+  h.cap = S->cap;
+  h.frames = S->frames;
+  XPCS_TRY(basis_hash(S, &h.basis_hash));
+  void* ptr[5];
+  ckpt_parts(S, ptr, h.bytes);
+  char* out = static_cast<char*>(host_buf);
+  memcpy(out, &h, sizeof(h));
+  size_t off = sizeof(h);
+  for (int i = 0; i < 5; ++i) {
+    XPCS_CUDA(ctx, cudaMemcpy(out + off, ptr[i], h.bytes[i], cudaMemcpyDeviceToHost));
+    off += h.bytes[i];
+  }
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_stream_restore(xpcs_stream* S, const void* host_buf, size_t bytes) {
+  if (!S || !host_buf || bytes < sizeof(CkptHeader)) return XPCS_EINVAL;
+  xpcs_ctx* ctx = S->ctx;
+  CkptHeader h;
+  memcpy(&h, host_buf, sizeof(h));
+  if (memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != 1) return fail(ctx, XPCS_EINVAL, "not a stream checkpoint");
+  if (S->frames != 0) return fail(ctx, XPCS_EINVAL, "restore needs a freshly opened stream");
+  if (h.k != S->basis->k || h.n_q != S->basis->rings->n_q || h.dtype != S->dtype || h.M != S->basis->rings->M ||
+      h.W != S->W || h.cap != S->cap)
+    return fail(ctx, XPCS_EINVAL, "checkpoint of a stream with another shape (k, rings, pixels, history, batch)");
+  void* ptr[5];
+  uint64_t b[5];
+  ckpt_parts(S, ptr, b);
+  size_t need = sizeof(h);
+  for (int i = 0; i < 5; ++i) {
+    if (b[i] != h.bytes[i]) return fail(ctx, XPCS_EINVAL, "checkpoint layout does not match the stream");
+    need += b[i];
+  }
+  if (bytes < need) return fail(ctx, XPCS_EINVAL, "checkpoint truncated");
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  uint64_t hb = 0;
+  XPCS_TRY(basis_hash(S, &hb));
+  if (hb != h.basis_hash) return fail(ctx, XPCS_EINVAL, "checkpoint made with another basis");
+  XPCS_CUDA(ctx, cudaStreamSynchronize(S->stream));
+  const char* in = static_cast<const char*>(host_buf);
+  size_t off = sizeof(h);
+  for (int i = 0; i < 5; ++i) {
+    XPCS_CUDA(ctx, cudaMemcpy(ptr[i], in + off, b[i], cudaMemcpyHostToDevice));
+    off += b[i];
+  }
+  S->frames = h.frames;
+  return XPCS_OK;
+}

@@ -9,7 +9,9 @@
 // after one untimed run per candidate that builds its work items), keeps the fastest in
 // the context's table for the shape (rings, tiles, operand format, whether C is stored),
 // and finally runs it, so the outputs are those of the chosen configuration.  Later
-// two-time calls of that shape use it.
+// two-time calls of that shape use it.  A candidate replaces the default (8 tiles; strips
+// for hi/lo operand pieces, blocks otherwise) only when it is at least 3 % faster, so
+// timing noise does not flip the choice.
 #include <string>
 
 #include "handles.h"
@@ -37,8 +39,9 @@ extern "C" xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* B,
   const bool async = ctx->async, prof = ctx->prof;
   ctx->async = true;  // back-to-back calls; the events bound the timed runs
   ctx->prof = false;
-  std::pair<int, int> best{0, 0};
-  double best_ms = 1e300;
+  const std::pair<int, int> dflt{CHUNK_TILES, split ? 1 : 0};
+  std::pair<int, int> best = dflt;
+  double best_ms = 1e300, dflt_ms = 1e300;
   xpcs_status st = XPCS_OK;
   const int tiles[4] = {4, 8, 16, 32};
   for (int strip = 0; strip < 2 && st == XPCS_OK; ++strip) {
@@ -57,6 +60,7 @@ extern "C" xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* B,
       }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
+      if (ctx->tune_force == dflt) dflt_ms = ms / reps;
       if (ms / reps < best_ms) {
         best_ms = ms / reps;
         best = ctx->tune_force;
@@ -64,6 +68,10 @@ extern "C" xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* B,
     }
   }
   ctx->tune_forced = false;
+  if (st == XPCS_OK && best != dflt && best_ms > 0.97 * dflt_ms) {  // not clearly faster than the default
+    best = dflt;
+    best_ms = dflt_ms;
+  }
   if (st == XPCS_OK) {
     ctx->gram_tune[key] = best;
     st = xpcs_twotime(ctx, B, A, T, prec, C_out, g2_out, count_out);  // outputs of the chosen configuration

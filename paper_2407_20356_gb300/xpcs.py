@@ -85,6 +85,9 @@ _SIGS = {
     "xpcs_stream_latency": (C.c_int, [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "xpcs_stream_close": (C.c_int, [vp]),
+    "xpcs_stream_checkpoint_size": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+    "xpcs_stream_checkpoint": (C.c_int, [vp, vp, C.c_size_t]),
+    "xpcs_stream_restore": (C.c_int, [vp, vp, C.c_size_t]),
     "xpcs_server_create": (C.c_int, [vp, C.POINTER(vp)]),
     "xpcs_server_open": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.c_int, C.POINTER(vp)]),
     "xpcs_server_submit": (C.c_int, [vp, vp, vp, i64, C.POINTER(C.c_uint64)]),
@@ -454,6 +457,19 @@ class Stream:
         self.ctx.check(_lib.xpcs_stream_latency(self.h, 1 if reset else 0, C.byref(a), C.byref(b), C.byref(c),
                                                 C.byref(n)))
         return {"p50_us": a.value, "p99_us": b.value, "max_us": c.value, "batches": n.value}
+
+    def checkpoint(self) -> np.ndarray:
+        """The stream's state as bytes (waits for its queued batches)."""
+        n = C.c_size_t()
+        self.ctx.check(_lib.xpcs_stream_checkpoint_size(self.h, C.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self.ctx.check(_lib.xpcs_stream_checkpoint(self.h, buf.ctypes.data, n.value))
+        return buf
+
+    def restore(self, buf: np.ndarray):
+        """Continue from a checkpoint (this stream must be fresh, same basis and shape)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self.ctx.check(_lib.xpcs_stream_restore(self.h, buf.ctypes.data, buf.size))
 
     def close(self):
         if self.h and self.ctx.h:

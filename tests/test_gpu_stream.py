@@ -204,3 +204,40 @@ def test_stream_admission_by_budget(X):
     b.push(frames[:10])
     g2, cnt = b.read_g2()
     assert cnt[:, 0].max() > 0
+
+
+def test_stream_checkpoint_and_resume(X, ctx):
+    # a stream checkpointed mid-series and resumed in a fresh stream ends with the same
+    # bytes as one that ran through (same batches), and both match the oracle
+    H, W, n_q, k, T, Wl = 16, 32, 3, 24, 200, 60
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 120, np.uint16, 88)
+    full = X.Stream(ctx, basis, Wl, 8)
+    for i in range(0, T, 8):
+        full.push(Xs[i:i + 8])
+    first = X.Stream(ctx, basis, Wl, 8)
+    for i in range(0, 96, 8):
+        first.push(Xs[i:i + 8])
+    ck = first.checkpoint()
+    first.close()
+    resumed = X.Stream(ctx, basis, Wl, 8)
+    resumed.restore(ck)
+    assert resumed.frames() == 96
+    for i in range(96, T, 8):
+        resumed.push(Xs[i:i + 8])
+    gf, cf = full.read_g2()
+    gr, cr = resumed.read_g2()
+    np.testing.assert_array_equal(cr, cf)
+    assert np.array_equal(np.isnan(gr), np.isnan(gf)) and np.array_equal(gr[~np.isnan(gr)], gf[~np.isnan(gf)])
+    g_ref, c_ref = _oracle_window_g2(Xs, B, qmap, n_q, Wl)
+    np.testing.assert_array_equal(cr, c_ref)
+    for q in range(n_q):
+        rm, _ = rel_errors(gr[q], g_ref[q])
+        assert rm < 1e-4, (q, rm)
+    # a checkpoint only goes into a fresh stream of the same shape
+    with pytest.raises(X.XpcsError) as e:
+        resumed.restore(ck)
+    assert e.value.status == X.XPCS_EINVAL
+    other = X.Stream(ctx, basis, Wl + 1, 8)
+    with pytest.raises(X.XpcsError) as e:
+        other.restore(ck)
+    assert e.value.status == X.XPCS_EINVAL
