@@ -545,7 +545,7 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
     b.r = c.take<float>((size_t)n_q * T_pad);
     b.blk_bad = c.take<uint32_t>((size_t)n_q * nT);
     b.partials = want_g2 ? c.take<float>((size_t)n_q * nT * maxC * DIAG_SLOTS) : nullptr;
-    b.vbits = c.take<uint32_t>((size_t)n_q * (T_pad / 32));
+    b.vbits = c.take<uint32_t>((size_t)n_q * (T_pad / 32) + n_q);  // + per-ring flags
     b.count = (want_cnt && !count_out) ? c.take<long long>((size_t)n_q * T) : nullptr;
   };
   RawBuffers b{};
@@ -895,7 +895,7 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
     b.r = c.take<float>((size_t)n_q * T_pad);
     b.blk_bad = c.take<uint32_t>((size_t)n_q * nT);
     b.partials = want_g2 ? c.take<float>((size_t)n_q * nT * maxC * DIAG_SLOTS) : nullptr;
-    b.vbits = c.take<uint32_t>((size_t)n_q * (T_pad / 32));
+    b.vbits = c.take<uint32_t>((size_t)n_q * (T_pad / 32) + n_q);  // + per-ring flags
     b.count = (want_cnt && !count_out) ? c.take<long long>((size_t)n_q * T) : nullptr;
   };
   Carve c0;

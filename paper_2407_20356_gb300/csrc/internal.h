@@ -128,6 +128,7 @@ cudaError_t launch_coef_pieces(const float* A, long long T, int k, int kq, int T
 cudaError_t launch_gram_pieces(const double* G, int n_q, int k, int kq, __nv_bfloat16* out, cudaStream_t st);
 cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st);
 
+// validity bits (vbits: n_q x words, followed by n_q per-ring flags) and pair counts
 cudaError_t launch_counts(const float* r, int n_q, long long T, int T_pad, uint32_t* vbits, int words,
                           long long* count, cudaStream_t st);
 cudaError_t launch_g2_finalize(const float* partials, const long long* count, int n_q, long long T, int nT,

@@ -388,7 +388,10 @@ __global__ void gram_pieces_kernel(const double* G, int n_q, int k, int kq, __nv
 }
 
 // ---------------------------------------------------------------- pair counts
-__global__ void vbits_kernel(const float* r, int n_q, int T_pad, int words, uint32_t* vbits) {
+// Validity bits of every ring (bit t: r_q(t) > 0), and ring_gap[q] != 0 when ring q has an
+// undefined frame among t < T (ring_gap zeroed by the launcher).
+__global__ void vbits_kernel(const float* r, int n_q, long long T, int T_pad, int words, uint32_t* vbits,
+                             uint32_t* ring_gap) {
   const long long gw = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (gw >= (long long)n_q * words) return;
@@ -396,15 +399,25 @@ __global__ void vbits_kernel(const float* r, int n_q, int T_pad, int words, uint
   const long long t = (long long)w * 32 + lane;
   const bool v = (t < T_pad) && r[(size_t)q * T_pad + t] > 0.f;
   const uint32_t m = __ballot_sync(0xffffffffu, v);
-  if (lane == 0) vbits[(size_t)q * words + w] = m;
+  const uint32_t real = __ballot_sync(0xffffffffu, t < T);  // frames of the series in this word
+  if (lane == 0) {
+    vbits[(size_t)q * words + w] = m;
+    if ((m & real) != real) atomicOr(&ring_gap[q], 1u);
+  }
 }
 
-// count_q(tau) = number of t with frames t and t+tau both defined.
-__global__ void counts_kernel(const uint32_t* vbits, int n_q, long long T, int words, long long* count) {
+// count_q(tau) = number of t with frames t and t+tau both defined (T - tau when every frame
+// of the ring is defined).
+__global__ void counts_kernel(const uint32_t* vbits, const uint32_t* ring_gap, int n_q, long long T, int words,
+                              long long* count) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long long)n_q * T) return;
   const int q = (int)(gid / T);
   const long long tau = gid % T;
+  if (!ring_gap[q]) {
+    count[gid] = T - tau;
+    return;
+  }
   const uint32_t* v = vbits + (size_t)q * words;
   const int ws = (int)(tau >> 5), s = (int)(tau & 31);
   long long c = 0;
@@ -425,18 +438,19 @@ __global__ void g2_finalize_kernel(const float* partials, const long long* count
   const int q = (int)(gid / T);
   const long long tau = gid % T;
   const int d1 = (int)(tau / TILE), e1 = (int)(tau % TILE);
-  double sum = 0.0;
+  double s1 = 0.0, s2 = 0.0;  // two independent chains, added in a fixed order
   {
     const int nC = (nT - d1 + CH - 1) / CH;
     const float* base = partials + ((size_t)q * nT + d1) * maxC * DIAG_SLOTS;
-    for (int c = 0; c < nC; ++c) sum += (double)base[(size_t)c * DIAG_SLOTS + TILE + e1];
+    for (int c = 0; c < nC; ++c) s1 += (double)base[(size_t)c * DIAG_SLOTS + TILE + e1];
   }
   const int d2 = d1 + 1;
   if (d2 < nT) {
     const int nC = (nT - d2 + CH - 1) / CH;
     const float* base = partials + ((size_t)q * nT + d2) * maxC * DIAG_SLOTS;
-    for (int c = 0; c < nC; ++c) sum += (double)base[(size_t)c * DIAG_SLOTS + e1];
+    for (int c = 0; c < nC; ++c) s2 += (double)base[(size_t)c * DIAG_SLOTS + e1];
   }
+  const double sum = s1 + s2;
   const long long n = count[gid];
   g2[gid] = n > 0 ? sum / (double)n : __longlong_as_double(0x7ff8000000000000ll);
 }
@@ -584,11 +598,13 @@ cudaError_t launch_gram_pieces(const double* G, int n_q, int k, int kq, __nv_bfl
 cudaError_t launch_counts(const float* r, int n_q, long long T, int T_pad, uint32_t* vbits, int words,
                           long long* count, cudaStream_t st) {
   const long long nw = (long long)n_q * words;
-  vbits_kernel<<<(unsigned)((nw + 7) / 8), 256, 0, st>>>(r, n_q, T_pad, words, vbits);
-  cudaError_t e = cudaGetLastError();
+  uint32_t* ring_gap = vbits + nw;  // n_q flags after the bits
+  cudaError_t e = cudaMemsetAsync(ring_gap, 0, (size_t)n_q * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
+  vbits_kernel<<<(unsigned)((nw + 7) / 8), 256, 0, st>>>(r, n_q, T, T_pad, words, vbits, ring_gap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const long long n = (long long)n_q * T;
-  counts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vbits, n_q, T, words, count);
+  counts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vbits, ring_gap, n_q, T, words, count);
   return cudaGetLastError();
 }
 
