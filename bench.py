@@ -821,6 +821,45 @@ def run_stream_leg(X, ctx, dev, args, sw=STREAM):
     return out
 
 
+def stream_capture(mode, path):
+    """A short stream run for profiling one single-frame step at the full history.
+
+    make: fit the basis of the online-stream workload, fill a stream with history + 64
+    frames, and save the basis and a checkpoint under `path`.  run: import that basis,
+    restore the checkpoint into a fresh stream and push three single frames, each waited
+    for, so a profiler sees about twenty launches before them.  Prints no bench line."""
+    import torch
+    from paper_2407_20356_gb300 import xpcs as X
+    from synth import ring_qmap
+    from synth.speckle import TorchSpeckle
+
+    sw = STREAM
+    dev = torch.device("cuda", 0)
+    H, W, n_q, k, Wl = sw["H"], sw["W"], sw["n_q"], sw["k"], sw["history"]
+    ctx = X.Context(0)
+    rings = X.Rings(ctx, torch.from_numpy(ring_qmap(H, W, n_q)).to(dev), H * W, n_q)
+    f_basis, f_ckpt = os.path.join(path, "stream_basis.npy"), os.path.join(path, "stream_ckpt.bin")
+    if mode == "make":
+        gen = TorchSpeckle(H, W, sw["mean"], sw["D"], sw["seed"] + 100, dtype=sw["dtype"], device=str(dev))
+        np.save(f_basis, X.xpcs_fit_basis(ctx, rings, gen.next(sw["n_fit"]), sw["n_fit"], k).export()[0])
+    basis = X.xpcs_basis_import(ctx, rings, np.load(f_basis))
+    pool = TorchSpeckle(H, W, sw["mean"], sw["D"], sw["seed"], dtype=sw["dtype"], device=str(dev)).next(64)
+    st = X.Stream(ctx, basis, Wl, 64, dtype=sw["dtype"])
+    if mode == "make":
+        t = 0
+        for _ in range(0, Wl + 64, 64):
+            t = st.push(pool)
+        assert st.poll(t, 600000)
+        st.checkpoint().tofile(f_ckpt)
+    else:
+        st.restore(np.fromfile(f_ckpt, dtype=np.uint8))
+        for j in range(3):
+            assert st.poll(st.push(pool[j:j + 1]), 60000)
+    print(f"stream capture {mode}: {st.frames()} frames", file=sys.stderr)
+    st.close()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -837,7 +876,14 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the multi-stream serving leg")
     ap.add_argument("--serving-seconds", type=float, default=5.0, help="arrival window of the serving leg")
     ap.add_argument("--stream-seconds", type=float, default=10.0, help="paced part of the stream leg")
+    ap.add_argument("--stream-capture", choices=["make", "run"],
+                    help="profiling aid, no bench line: make = fill the online stream and checkpoint it; "
+                         "run = restore it and push three single frames")
+    ap.add_argument("--capture-dir", default="/tmp", help="where --stream-capture keeps its basis and checkpoint")
     args = ap.parse_args()
+    if args.stream_capture:
+        stream_capture(args.stream_capture, args.capture_dir)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     wl = dict(WORKLOAD if args.workload == "c2" else SMALL)

@@ -283,7 +283,9 @@ xpcs_status xpcs_graph_destroy(xpcs_graph* graph);
 
 /* Open a stream on `basis` for frames of `dtype`, keeping `history` lags, with batches
  * of up to `max_batch` frames.  XPCS_EBUSY if its device memory does not fit the
- * context's budget now (retry once other streams close). */
+ * context's budget now (retry once other streams close); XPCS_ENOTSUP if no row-update
+ * lag tile for 64-frame steps fits shared memory at this k and ring count.  `basis` must
+ * stay alive while frames are pushed; closing the stream does not read it. */
 xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t history, int max_batch,
                              xpcs_dtype dtype, xpcs_stream** out);
 /* Push n frames (n x M counts in host memory).  The frames are copied before the call

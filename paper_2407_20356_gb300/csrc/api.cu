@@ -595,6 +595,8 @@ xpcs_status basis_alloc(xpcs_ctx* ctx, const xpcs_rings* R, int k, xpcs_basis** 
   auto* B = new xpcs_basis();
   B->ctx = ctx;
   B->rings = R;
+  B->n_q = R->n_q;
+  B->M = R->M;
   B->k = k;
   B->kp = (k + 15) / 16 * 16;
   B->M_pad = (R->M + 63) / 64 * 64;
@@ -711,8 +713,8 @@ extern "C" xpcs_status xpcs_basis_destroy(xpcs_basis* B) {
   if (!B) return XPCS_EINVAL;
   xpcs_ctx* ctx = B->ctx;
   cudaStreamSynchronize(ctx->stream);
-  const int n_q = B->rings->n_q, k = B->k;
-  dev_free(ctx, B->d_B, (size_t)B->rings->M * k * 8);
+  const int n_q = B->n_q, k = B->k;
+  dev_free(ctx, B->d_B, (size_t)B->M * k * 8);
   dev_free(ctx, B->d_G, (size_t)n_q * k * k * 8);
   dev_free(ctx, B->d_s, (size_t)n_q * k * 8);
   dev_free(ctx, B->d_G32, (size_t)n_q * k * k * 4);
@@ -720,7 +722,7 @@ extern "C" xpcs_status xpcs_basis_destroy(xpcs_basis* B) {
   dev_free(ctx, B->d_koff, (size_t)n_q * 4);
   dev_free(ctx, B->d_kch, (size_t)n_q * 4);
   dev_free(ctx, B->d_s32, (size_t)n_q * k * 8);
-  if (B->d_B32) dev_free(ctx, B->d_B32, (size_t)B->rings->M * k * 4);
+  if (B->d_B32) dev_free(ctx, B->d_B32, (size_t)B->M * k * 4);
   if (B->d_Gpair) {
     const int kq = (k + 63) / 64 * 64;
     dev_free(ctx, B->d_Gpair, (size_t)n_q * kq * 2 * kq * 2);

@@ -158,6 +158,14 @@ XPCS_DEV void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "memory");
 }
 
+// 32 lanes x 4 consecutive 32-bit columns.
+XPCS_DEV void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+}
+
 // Shared-memory matrix descriptor for a K-major operand tile stored with the 128-byte
 // swizzle: rows of 128 bytes, 8-row core groups 1024 bytes apart (tile base 1024-aligned).
 XPCS_DEV uint64_t smem_desc_sw128(const void* tile) {

@@ -76,6 +76,8 @@ struct xpcs_basis {
   const xpcs_rings* rings = nullptr;
   int k = 0;
   int kp = 0;                     // k rounded up to 16: lo half of Bcat starts at row kp
+  int n_q = 0;                    // copies of the ring plan's shape: destroying the basis
+  int64_t M = 0;                  // never reads the ring plan, which may be gone by then
   int64_t M_pad = 0;
   double* d_B = nullptr;          // M x k
   double* d_G = nullptr;          // n_q x k x k
@@ -102,6 +104,8 @@ struct xpcs_stream {
   int64_t W = 0;                     // history window (lags kept)
   int64_t cap = 0;                   // ring slots = max(W + max_batch, 256)
   int max_batch = 0;
+  int64_t M = 0;                     // copies of the basis's shape, so that closing the
+  int n_q = 0, k = 0;                // stream never reads the basis (which may be gone)
   int64_t frames = 0;                // frames enqueued so far
   int nblk = 0;                      // pixel slices of the sparse encode
   // device
@@ -117,7 +121,8 @@ struct xpcs_stream {
   double* d_g2 = nullptr;            // n_q x W read-out buffer
   int kpad = 0;                      // k rounded up to 64
   CUtensorMap tmA, tmW, tmR;         // tensor maps of d_A2, d_W2 (64 x 128 boxes) and d_Rh
-  CUtensorMap tmG, tmC;              // tensor maps of d_g2sum and d_cnt (row pitch Wp)
+  // tensor maps of d_g2sum and d_cnt (row pitch Wp), one per row-update lag tile RT_LTS[i]
+  CUtensorMap tmG[xpcs::RT_N_LT], tmC[xpcs::RT_N_LT];
   uint32_t* h_status = nullptr;      // host-mapped status word of the stream's kernels
   uint32_t* d_status = nullptr;      // its device address
   size_t bytes = 0;

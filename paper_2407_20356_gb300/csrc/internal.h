@@ -194,24 +194,24 @@ struct StreamStep {
   const CUtensorMap* tmA;  // host copies of the tensor maps of A2, W2, Rh, g2sum, cnt
   const CUtensorMap* tmW;
   const CUtensorMap* tmR;
-  const CUtensorMap* tmG;
-  const CUtensorMap* tmC;
+  const CUtensorMap* tmG;  // [RT_N_LT]: one per lag tile of RT_LTS
+  const CUtensorMap* tmC;  // [RT_N_LT]
 };
 cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st);
 
 // Row update of a step of at most 64 frames on the tensor cores (see stream_tc.cu).
 // W2 holds the step's w rows in pair order, per ring group rg (36 rings from q0 = 36 rg)
-// n_mt M-tiles of 128 rows starting at row rg n_mt 128; within M-tile mt, lane quarter w
-// (ring residue q mod 4) and lane l:
-//   small steps (b <= 8): mt = f, l = (q - q0) / 4 (lanes 0..8): one frame per M-tile, so
-//     no two lanes of a warp share a ring;
-//   larger steps: mt = qi nfb + fb (nfb = ceil(b / 32)), ring q = q0 + 4 qi + w, frame
-//     f = 32 fb + l: a warp holds 32 consecutive frames of one ring.
+// n_mt M-tiles of 128 rows starting at row rg n_mt 128; within M-tile mt:
+//   small steps (b <= 8): mt = f, row ql = q - q0 (rows 0..35): one frame per tile, its
+//     36 rings as the N operand of an MMA whose M operand is the history;
+//   larger steps: mt = qi nfb + fb (nfb = ceil(b / 32)), lane quarter w = ring residue
+//     q mod 4, lane l: ring q = q0 + 4 qi + w, frame f = 32 fb + l: a warp holds 32
+//     consecutive frames of one ring.
 constexpr int W2_SMALL_B = 8;
 struct RowTcParams {
   long long t0, W, cap;
   int b, n_q, kpad, n_kc, lt, wst, n_tiles;
-  int skew;                // 1: diagonal sums of the large-step epilogue through skewed buffers
+  int epi;                 // epilogue: 0 rotated blocks, 1 skewed buffers, 2 steps of <= W2_SMALL_B frames
   int n_rg;  // ring groups of 36
   int n_mt;  // M-tiles per ring group
   int nfb;   // 32-frame blocks of the step
@@ -224,7 +224,7 @@ struct RowTcParams {
   int qg2;       // ring rows per g2sum / cnt box: min(36, n_q)
   uint32_t* status;
 };
-int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2, int skew);
+int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2, int epi);
 // tensor maps: A2 history, W2 pairs, Rh r values, g2sum and cnt (lt x qg2 boxes)
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
                                  const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,
@@ -238,20 +238,28 @@ __host__ __device__ inline int w2_mtiles(int b, int n_q) {
 // pair-order row of (frame f, ring q) in W2 for a step of b frames
 __host__ __device__ inline int w2_pair_row(int f, int q, int b, int n_q) {
   const int rg = q / 36, ql = q - 36 * rg;
-  const int base = rg * w2_mtiles(b, n_q) * 128 + (ql % 4) * 32;
-  if (b <= W2_SMALL_B) return base + f * 128 + ql / 4;
+  const int base = rg * w2_mtiles(b, n_q) * 128;
+  if (b <= W2_SMALL_B) return base + f * 128 + ql;
   const int nfb = (b + 31) / 32;
-  return base + ((ql / 4) * nfb + f / 32) * 128 + f % 32;
+  return base + (ql % 4) * 32 + ((ql / 4) * nfb + f / 32) * 128 + f % 32;
 }
 // 64-bit words per ring of the validity bits: cap + 128 bits and two spare words
 inline long long stream_vwords(long long cap) { return (cap + 128 + 63) / 64 + 2; }
 // Rh row pitch: n_q rounded up to 4 (16-byte rows for the tensor map)
 __host__ __device__ inline int stream_npad(int n_q) { return (n_q + 3) / 4 * 4; }
-// lags per tile (64 or 32) and w stages (2 or 1) of the row update that fit shared
-// memory; false if none does
-bool row_update_config(int n_q, int kpad, int* lt, int* wst, int* skew);
-cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const RowTcParams& p, int grid,
-                                 cudaStream_t st);
+// Lag tiles of the row update: a step of b frames takes the longest tile with
+// lt + b - 1 <= 128 (its history rows fit one operand) that fits shared memory, so a
+// single-frame step covers 128 lags per work item.  One g2-sum / count tensor map per tile.
+constexpr int RT_N_LT = 5;
+constexpr int RT_LTS[RT_N_LT] = {128, 120, 96, 64, 32};
+inline int rt_lt_index(int lt) {
+  for (int i = 0; i < RT_N_LT; ++i)
+    if (RT_LTS[i] == lt) return i;
+  return -1;
+}
+// lag tile, w stages (2 or 1) and epilogue mode of the row update for steps of b frames;
+// false if nothing fits shared memory
+bool row_update_config(int n_q, int kpad, int b, int* lt, int* wst, int* epi);
 cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
                              double* g2, cudaStream_t st);
 cudaError_t launch_basis_f32(const double* B, long long n, float* B32, cudaStream_t st);

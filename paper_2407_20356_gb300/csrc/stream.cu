@@ -114,19 +114,42 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
   }
 }
 
-__global__ void stream_reduce_kernel(const StreamStep s) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= s.b * s.k) return;
-  const int fi = gid / s.k, j = gid % s.k;
-  const float* src = s.part + (size_t)fi * s.nblk * s.k + j;
-  float a8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int b = 0;
-  for (; b + 8 <= s.nblk; b += 8) {
+// a_t[j] = sum of the nblk slice partials of frame t.  Block = 32 (frame, column) pairs x
+// 8 slice groups: group g sums slices g, g + 8, g + 16, ... (32 loads in flight per thread,
+// each warp reading 32 consecutive columns), then group 0 adds the eight group sums in
+// order.  The order is fixed by nblk alone (deterministic, the same for every batching).
+constexpr int RD_GROUPS = 8;
+__global__ void __launch_bounds__(256) stream_reduce_kernel(const StreamStep s) {
+  __shared__ float red[RD_GROUPS][32];
+  const int jj = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const long long col = (long long)blockIdx.x * 32 + jj;  // (frame, column) = (col / k, col mod k)
+  const bool live = col < (long long)s.b * s.k;
+  float acc = 0.f;
+  if (live) {
+    const int fi = (int)(col / s.k), j = (int)(col - (long long)fi * s.k);
+    const float* src = s.part + (size_t)fi * s.nblk * s.k + j;
+    const size_t stride = (size_t)RD_GROUPS * s.k;  // between a group's consecutive slices
+    float a4[4] = {0.f, 0.f, 0.f, 0.f};
+    int blk = g;
+    for (; blk + 31 * RD_GROUPS < s.nblk; blk += 32 * RD_GROUPS) {
+      float x[32];
+      const float* p0 = src + (size_t)blk * s.k;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a8[u] += src[(size_t)(b + u) * s.k];
+      for (int u = 0; u < 32; ++u) x[u] = p0[u * stride];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) a4[u & 3] += x[u];
+    }
+    for (; blk < s.nblk; blk += RD_GROUPS) a4[0] += src[(size_t)blk * s.k];
+    acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
   }
-  for (; b < s.nblk; ++b) a8[0] += src[(size_t)b * s.k];
-  s.a[gid] = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
+  red[g][jj] = acc;
+  __syncthreads();
+  if (g == 0 && live) {
+    float a = red[0][jj];
+#pragma unroll
+    for (int gg = 1; gg < RD_GROUPS; ++gg) a += red[gg][jj];
+    s.a[col] = a;
+  }
 }
 
 // --------------------------------------------------------------------------- 2. factors
@@ -179,6 +202,15 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
     if (j < k && r > 0.f) {
       float v4[4] = {0.f, 0.f, 0.f, 0.f};
       int c = 0;
+      // 32 loads of G_q in flight at a time (a one-frame step has only n_q blocks); chain
+      // u takes rows u, u + 4, u + 8, ... in order
+      for (; c + 32 <= k; c += 32) {
+        float g[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) g[u] = Gq[(size_t)(c + u) * k + j];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) v4[u & 3] = fmaf(as[c + u], g[u], v4[u & 3]);
+      }
       for (; c + 4 <= k; c += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) v4[u] = fmaf(as[c + u], Gq[(size_t)(c + u) * k + j], v4[u]);
@@ -229,7 +261,7 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   sparse_encode_kernel<<<dim3(s.nblk, s.b), 256, 0, st>>>(s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  stream_reduce_kernel<<<(s.b * s.k + 255) / 256, 256, 0, st>>>(s);
+  stream_reduce_kernel<<<(s.b * s.k + 31) / 32, 256, 0, st>>>(s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   frame_factors_kernel<<<dim3(s.b, s.n_q), 128, 0, st>>>(s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -243,7 +275,8 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   p.n_q = s.n_q;
   p.kpad = s.kpad;
   p.n_kc = s.kpad / 64;
-  if (!row_update_config(s.n_q, s.kpad, &p.lt, &p.wst, &p.skew)) return cudaErrorInvalidConfiguration;
+  if (!row_update_config(s.n_q, s.kpad, s.b, &p.lt, &p.wst, &p.epi)) return cudaErrorInvalidConfiguration;
+  const int li = rt_lt_index(p.lt);
   // lags up to the window, and no further than the step's last frame: a pair (t, t - tau)
   // of this step exists only for tau <= t0 + b - 1, so a young history skips the rest
   p.n_tiles = (int)((std::min<long long>(s.W, s.t0 + s.b) + p.lt - 1) / p.lt);
@@ -259,20 +292,30 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   p.qg2 = std::min(36, s.n_q);
   p.status = s.status;
   const int grid = std::min(p.n_tiles * p.n_rg, s.num_sms);
-  return launch_row_update_tc(*s.tmA, *s.tmW, *s.tmR, *s.tmG, *s.tmC, p, grid, st);
+  return launch_row_update_tc(*s.tmA, *s.tmW, *s.tmR, s.tmG[li], s.tmC[li], p, grid, st);
 }
 
-// Largest lag tile that fits, the skewed-buffer epilogue preferred at each tile size.
-bool row_update_config(int n_q, int kpad, int* lt, int* wst, int* skew) {
+// Longest lag tile whose history rows fit one operand and whose layout fits shared memory.
+// Steps of at most W2_SMALL_B frames take the small-step epilogue (no diagonal buffers);
+// larger steps prefer the skewed-buffer epilogue, then two w stages.
+bool row_update_config(int n_q, int kpad, int b, int* lt, int* wst, int* epi) {
   const int n_kc = kpad / 64, qb = std::min(36, stream_npad(n_q)), qg2 = std::min(36, n_q);
-  const int cand[7][3] = {{64, 2, 1}, {64, 1, 1}, {64, 2, 0}, {32, 2, 1}, {32, 2, 0}, {32, 1, 1}, {32, 1, 0}};
-  for (const auto& c : cand)
-    if (row_update_tc_smem(n_kc, c[0], qb, c[1], qg2, c[2]) <= 227 * 1024) {
-      *lt = c[0];
-      *wst = c[1];
-      *skew = c[2];
-      return true;
+  const int small_modes[2][2] = {{2, 2}, {1, 2}};  // {wst, epi}
+  const int large_modes[4][2] = {{2, 1}, {1, 1}, {2, 0}, {1, 0}};
+  for (int i = 0; i < RT_N_LT; ++i) {
+    const int l = RT_LTS[i];
+    if (l + b - 1 > 128) continue;
+    const int n_modes = b <= W2_SMALL_B ? 2 : 4;
+    for (int m = 0; m < n_modes; ++m) {
+      const int* c = b <= W2_SMALL_B ? small_modes[m] : large_modes[m];
+      if (row_update_tc_smem(n_kc, l, qb, c[0], qg2, c[1]) <= 227 * 1024) {
+        *lt = l;
+        *wst = c[0];
+        *epi = c[1];
+        return true;
+      }
     }
+  }
   return false;
 }
 

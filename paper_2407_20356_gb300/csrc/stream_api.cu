@@ -45,9 +45,7 @@ struct Sizes {
   size_t frames, A2, Rh, vbits, g2sum, cnt, part, a, W2, g2, stage;
 };
 
-Sizes stream_sizes(const xpcs_basis* B, int64_t W, int max_batch, int eb) {
-  const int64_t M = B->rings->M;
-  const int n_q = B->rings->n_q, k = B->k;
+Sizes stream_sizes(int64_t M, int n_q, int k, int64_t W, int max_batch, int eb) {
   const int64_t cap = ring_cap(W, max_batch);
   Sizes z;
   z.frames = (size_t)max_batch * M * eb;
@@ -67,7 +65,7 @@ Sizes stream_sizes(const xpcs_basis* B, int64_t W, int max_batch, int eb) {
 void stream_free(xpcs_stream* S) {
   xpcs_ctx* ctx = S->ctx;
   if (S->stream) cudaStreamSynchronize(S->stream);
-  const Sizes z = stream_sizes(S->basis, S->W, S->max_batch, S->dtype == XPCS_U8 ? 1 : 2);
+  const Sizes z = stream_sizes(S->M, S->n_q, S->k, S->W, S->max_batch, S->dtype == XPCS_U8 ? 1 : 2);
   dev_free(ctx, S->d_frames, z.frames);
   dev_free(ctx, S->d_A2, z.A2);
   dev_free(ctx, S->d_Rh, z.Rh);
@@ -99,7 +97,7 @@ void stream_free(xpcs_stream* S) {
 namespace xpcs {
 
 size_t stream_footprint(const xpcs_basis* B, int64_t W, int max_batch, int elem_bytes) {
-  const Sizes z = stream_sizes(B, W, max_batch, elem_bytes);
+  const Sizes z = stream_sizes(B->M, B->n_q, B->k, W, max_batch, elem_bytes);
   size_t b = z.frames + z.A2 + z.Rh + z.vbits + z.g2sum + z.cnt + z.part + z.a + z.W2 + z.g2;
   if (!B->d_B32) b += (size_t)B->rings->M * B->k * 4;  // f32 basis copy made on first use
   return b;
@@ -129,8 +127,8 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
       (dtype != XPCS_U8 && dtype != XPCS_U16))
     return fail(ctx, XPCS_EINVAL, "bad stream_open args");
   *out = nullptr;
-  int lt = 0, wst = 0, skew = 0;
-  if (!row_update_config(B->rings->n_q, kpad_of(B->k), &lt, &wst, &skew))
+  int lt = 0, wst = 0, epi = 0;  // steps of up to 64 frames: the largest a push is cut into
+  if (!row_update_config(B->rings->n_q, kpad_of(B->k), 64, &lt, &wst, &epi))
     return fail(ctx, XPCS_ENOTSUP, "stream: the row-update tile does not fit shared memory at this k");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int eb = dtype == XPCS_U8 ? 1 : 2;
@@ -155,8 +153,11 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
   S->cap = ring_cap(history, max_batch);
   S->max_batch = max_batch;
   S->dtype = dtype;
-  S->nblk = nblk_of(B->rings->M);
-  const Sizes z = stream_sizes(B, history, max_batch, eb);
+  S->M = B->M;
+  S->n_q = B->n_q;
+  S->k = B->k;
+  S->nblk = nblk_of(B->M);
+  const Sizes z = stream_sizes(S->M, S->n_q, S->k, history, max_batch, eb);
   xpcs_status st = XPCS_OK;
   void* p = nullptr;
 #define XPCS_SALLOC(field, bytes, T)                  \
@@ -209,14 +210,16 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
     st = make_map(ctx, &S->tmR, S->d_Rh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, npad, S->cap + 128,
                   std::min(36, npad), 128, CU_TENSOR_MAP_SWIZZLE_NONE);
   }
-  // g2 sums and counts: W x n_q with row pitch Wp, boxes of lt lags x up to 36 rings
+  // g2 sums and counts: W x n_q with row pitch Wp, boxes of lt lags x up to 36 rings for
+  // every lag tile a step may take
   const int qg2 = std::min(36, B->rings->n_q);
-  if (st == XPCS_OK)
-    st = make_map(ctx, &S->tmG, S->d_g2sum, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, history, B->rings->n_q, lt, qg2,
-                  CU_TENSOR_MAP_SWIZZLE_NONE, (uint64_t)wpitch(history) * 8);
-  if (st == XPCS_OK)
-    st = make_map(ctx, &S->tmC, S->d_cnt, CU_TENSOR_MAP_DATA_TYPE_INT64, 8, history, B->rings->n_q, lt, qg2,
-                  CU_TENSOR_MAP_SWIZZLE_NONE, (uint64_t)wpitch(history) * 8);
+  for (int i = 0; i < RT_N_LT && st == XPCS_OK; ++i) {
+    st = make_map(ctx, &S->tmG[i], S->d_g2sum, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, history, B->rings->n_q,
+                  RT_LTS[i], qg2, CU_TENSOR_MAP_SWIZZLE_NONE, (uint64_t)wpitch(history) * 8);
+    if (st == XPCS_OK)
+      st = make_map(ctx, &S->tmC[i], S->d_cnt, CU_TENSOR_MAP_DATA_TYPE_INT64, 8, history, B->rings->n_q,
+                    RT_LTS[i], qg2, CU_TENSOR_MAP_SWIZZLE_NONE, (uint64_t)wpitch(history) * 8);
+  }
   if (st != XPCS_OK) {
     stream_free(S);
     return st;
@@ -309,8 +312,8 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.tmA = &S->tmA;
   s.tmW = &S->tmW;
   s.tmR = &S->tmR;
-  s.tmG = &S->tmG;
-  s.tmC = &S->tmC;
+  s.tmG = S->tmG;
+  s.tmC = S->tmC;
   s.g2sum = S->d_g2sum;
   s.cnt = S->d_cnt;
   // steps of at most STEP_MAX frames; the batch completes with its last step
@@ -541,7 +544,7 @@ xpcs_status basis_hash(xpcs_stream* S, uint64_t* h) {
 }
 
 void ckpt_parts(xpcs_stream* S, void* ptr[5], uint64_t bytes[5]) {
-  const Sizes z = stream_sizes(S->basis, S->W, S->max_batch, S->dtype == XPCS_U8 ? 1 : 2);
+  const Sizes z = stream_sizes(S->M, S->n_q, S->k, S->W, S->max_batch, S->dtype == XPCS_U8 ? 1 : 2);
   ptr[0] = S->d_A2;
   ptr[1] = S->d_Rh;
   ptr[2] = S->d_vbits;

@@ -5,21 +5,23 @@
 // summed into lag bins g2sum_q[tau] (count_q[tau] += 1 for defined pairs).
 //
 // Work item = (tile of LT consecutive lags tau0 .., group of up to 36 rings).  All its
-// pairs use history rows s in [t0 - tau0 - LT + 1, t0 + b - 1 - tau0], fewer than 128
-// rows: one 128-row operand.  The other operand holds the (frame, ring) pairs of the
-// group, 128 per M-tile, laid out by the frame-factors kernel so that ring q sits in
-// TMEM lane quarter q mod 4 (one epilogue warp per quarter): M-tile mt, lane quarter w,
-// lane l holds pair idx = 32 mt + l of the list (f, q) with q = q0 + 4 (idx / b) + w,
-// f = idx mod b.  One GEMM per M-tile,
-//     D[pair][c] = w_q(t0 + f) . a_{s_start + c},   c = 0..127,
-// with both operands as bf16 hi/lo pieces of the f32 values (hi.hi + lo.hi + hi.lo,
-// f32 accumulation: about 2^-16 relative per product).  In the epilogue a thread owns one
-// pair and walks its columns: column c is lag tau0 + tl with tl = f + LT - 1 - c, so the
-// thread adds D r_q(s) to bin (q, tl) when 0 <= tl < LT, tau < W, s >= 0 and both r are
-// positive.  Lanes of a warp hold distinct pairs and warps hold disjoint rings, so at any
-// column the 128 threads update distinct bins: no atomics and no barriers, and every
-// bin's additions come in a fixed order.  The bins are added to the FP64 sums once per
-// work item.
+// pairs use history rows s in [t0 - tau0 - LT + 1, t0 + b - 1 - tau0], at most 128 rows
+// (LT + b - 1 <= 128; the host picks the longest such tile that fits shared memory): one
+// 128-row operand.  The other operand holds the (frame, ring) pairs of the group, laid out
+// by the frame-factors kernel.  Both operands are bf16 hi/lo pieces of the f32 values
+// (hi.hi + lo.hi + hi.lo, f32 accumulation: about 2^-16 relative per product).  Column or
+// row c of the history operand is lag tau0 + tl with tl = f + LT - 1 - c for frame f; a
+// pair adds D r_q(s) to bin (q, tl) when 0 <= tl < LT, tau < W and s >= 0 (undefined
+// frames have r = 0).
+//
+// Large steps (b > 8): M-tiles of 128 pairs, ring q in TMEM lane quarter q mod 4 (one
+// epilogue warp per quarter), lane = frame; D[pair][c] = w_q(t0 + f) . a_{s_start + c}.
+// A warp sums the diagonals of each 32 x 32 block (through a skewed or rotated buffer)
+// into its ring's bins.  Small steps (b <= 8): one frame per M-tile and the history as
+// the M operand, D[c][ring] (N = 48 >= 36 rings): the thread holding TMEM lane c owns lag
+// tl of every ring, so all 128 lanes work and within a frame no two threads share a bin
+// (a barrier separates frames).  Either way every bin's additions come in a fixed order,
+// with no atomics, and the bins are added to the FP64 sums once per work item.
 //
 // Warps: 0 TMA producer (history rows + their r values once per item, pair chunks
 // through a ring of stages), 1 TMEM owner and MMA issuer (two 128-column accumulators),
@@ -39,16 +41,25 @@ constexpr int RT_EPI_BAR = 1;
 constexpr int RT_QG = 36;                      // rings per work item (nine per lane quarter)
 constexpr int RT_QROWS = 64, RT_QLD = 36;      // skewed buffer of one epilogue warp (row j - i + 32)
 
+// Epilogue modes: RT_ROT rotates each 32 x 32 block, RT_SKEW sums block diagonals through
+// skewed buffers, RT_SMALL serves steps of at most W2_SMALL_B frames only (their pairs go
+// straight into the lag bins), so it needs neither buffer and has room for longer lag tiles.
+constexpr int RT_ROT = 0, RT_SKEW = 1, RT_SMALL = 2;
+constexpr int RT_SMALL_N = 48;  // MMA N of a small step: its 36 ring pairs, rounded up to 16
+constexpr int RT_VW = 6;  // validity words per ring: 4 of the history window, 2 of the step
+
 struct RtLayout {
-  int n_kc, lt, qb, wst, qg2, skew;
+  int n_kc, lt, qb, wst, qg2, epi;
   __host__ __device__ int hist_bytes() const { return 2 * n_kc * RT_CHUNK; }
   __host__ __device__ int w_bytes() const { return wst * 2 * RT_CHUNK; }
   __host__ __device__ int slice_bytes() const { return (qg2 * lt * 8 + 1023) / 1024 * 1024; }  // one of two
   __host__ __device__ int rs_bytes() const { return RT_ROWS * qb * 4; }
   __host__ __device__ int bins_bytes() const { return RT_QG * (lt + 1) * 4; }
   // per epilogue warp: a skewed buffer (64 rows of 36 floats) or a rotated 32x32 block
-  __host__ __device__ int rot_bytes() const { return skew ? 4 * RT_QROWS * RT_QLD * 4 : 4 * 32 * 32 * 4; }
-  __host__ __device__ int vw_bytes() const { return RT_QG * 5 * 8; }      // validity words per ring
+  __host__ __device__ int rot_bytes() const {
+    return epi == RT_SKEW ? 4 * RT_QROWS * RT_QLD * 4 : epi == RT_ROT ? 4 * 32 * 32 * 4 : 0;
+  }
+  __host__ __device__ int vw_bytes() const { return RT_QG * RT_VW * 8; }
   __host__ __device__ int smem() const {
     return 1024 + hist_bytes() + w_bytes() + 2 * slice_bytes() + rs_bytes() + bins_bytes() + rot_bytes() +
            vw_bytes() + 256;
@@ -61,21 +72,21 @@ XPCS_DEV unsigned long long bits64(const unsigned long long* w, int o) {
   return sh ? (w[wi] >> sh) | (w[wi + 1] << (64 - sh)) : w[wi];
 }
 
-template <bool SKEW>
+template <int EPI>
 __global__ void __launch_bounds__(RT_THREADS, 1)
     row_update_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
                          const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmG,
                          const __grid_constant__ CUtensorMap tmC, const RowTcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const RtLayout L{p.n_kc, p.lt, p.qb, p.wst, p.qg2, SKEW ? 1 : 0};
+  const RtLayout L{p.n_kc, p.lt, p.qb, p.wst, p.qg2, EPI};
   uint8_t* hist = smem;                                       // [hi kc..., lo kc...]
   uint8_t* w_st = smem + L.hist_bytes();                      // [stage][hi, lo]
   double* g2s = reinterpret_cast<double*>(w_st + L.w_bytes());                     // [qg2][lt] g2 sums
   long long* cns = reinterpret_cast<long long*>(w_st + L.w_bytes() + L.slice_bytes());  // [qg2][lt] counts
   float* rs = reinterpret_cast<float*>(w_st + L.w_bytes() + 2 * L.slice_bytes());  // [128][qb] r of the rows
   float* bins = rs + RT_ROWS * p.qb;                          // [36][lt + 1]
-  float* rot = bins + RT_QG * (p.lt + 1);                     // [4][64][36] skewed or [4][32][32] rotated
+  float* rot = bins + RT_QG * (p.lt + 1);                     // [4][64][36] skewed, [4][32][32] rotated or none
   unsigned long long* vw = reinterpret_cast<unsigned long long*>(reinterpret_cast<uint8_t*>(rot) + L.rot_bytes());
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(vw) + L.vw_bytes());
   uint64_t* h_full = bars;        // history + r rows landed
@@ -188,8 +199,10 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      // history rows used by the step: lt + b - 1 (N a multiple of 16)
-      const uint32_t idesc = idesc_f16(1, RT_ROWS, min(RT_ROWS, (lt + p.b - 1 + 15) / 16 * 16));
+      // large steps: M = pairs, N = the lt + b - 1 history rows used (a multiple of 16);
+      // small steps: M = the 128 history rows, N = the 36 ring pairs of a frame (48)
+      const uint32_t idesc = EPI == RT_SMALL ? idesc_f16(1, RT_ROWS, RT_SMALL_N)
+                                             : idesc_f16(1, RT_ROWS, min(RT_ROWS, (lt + p.b - 1 + 15) / 16 * 16));
       uint32_t item_i = 0, it = 0, acc_i = 0;
       bool ok = true, issued = false;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++item_i) {
@@ -221,9 +234,15 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             const uint64_t hlo = smem_desc_sw128(hist + (p.n_kc + kc) * RT_CHUNK);
 #pragma unroll
             for (int kk = 0; kk < RT_CH / 16; ++kk) {  // 16 elements = 32 B per MMA
-              tc_mma_f16(d, whi + 2 * kk, hhi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-              tc_mma_f16(d, wlo + 2 * kk, hhi + 2 * kk, idesc, 1u);
-              tc_mma_f16(d, whi + 2 * kk, hlo + 2 * kk, idesc, 1u);
+              if constexpr (EPI == RT_SMALL) {  // D[history row][pair]
+                tc_mma_f16(d, hhi + 2 * kk, whi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc_mma_f16(d, hhi + 2 * kk, wlo + 2 * kk, idesc, 1u);
+                tc_mma_f16(d, hlo + 2 * kk, whi + 2 * kk, idesc, 1u);
+              } else {  // D[pair][history row]
+                tc_mma_f16(d, whi + 2 * kk, hhi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc_mma_f16(d, wlo + 2 * kk, hhi + 2 * kk, idesc, 1u);
+                tc_mma_f16(d, whi + 2 * kk, hlo + 2 * kk, idesc, 1u);
+              }
             }
             tc_commit(&w_empty[s]);
             issued = true;
@@ -245,7 +264,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     const int w = warp & 3;           // TMEM lane quarter = ring residue
     const int et = threadIdx.x - 64;  // 0..127
     const unsigned long long bmask = p.b == 64 ? ~0ull : ((1ull << p.b) - 1);
-    if constexpr (SKEW) {  // entries of the skewed buffer no lane writes stay zero
+    if constexpr (EPI == RT_SKEW) {  // entries of the skewed buffer no lane writes stay zero
       float* Q = rot + w * (RT_QROWS * RT_QLD);
       for (int x = lane; x < RT_QROWS * RT_QLD; x += 32) Q[x] = 0.f;
       __syncwarp();
@@ -261,15 +280,15 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       const int tl_max = (int)min((long long)lt - 1, p.W - 1 - tau0);  // lags that exist
       const int c_min = s_start < 0 ? (int)(-s_start) : 0;              // rows before frame 0
       for (int e = et; e < RT_QG * (lt + 1); e += 128) bins[e] = 0.f;
-      // validity words of the item: for ring ql, words [0, 3) hold the history window
-      // starting at bit o_min (the slot of lag tau0 + lt - 1 at frame t0), words [3, 5)
-      // the step's own frames from bit o_batch
+      // validity words of the item: for ring ql, words [0, 4) hold the history window
+      // starting at bit o_min (the slot of lag tau0 + lt - 1 at frame t0; the fold reads
+      // up to bit 63 + lt + 63 < 256), words [4, 6) the step's own frames from bit o_batch
       const long long o_min = (((s_start % p.cap) + p.cap) % p.cap);
       const long long o_batch = p.t0 % p.cap;
-      for (int e = et; e < qn * 5; e += 128) {
-        const int ql = e / 5, u = e - ql * 5;
+      for (int e = et; e < qn * RT_VW; e += 128) {
+        const int ql = e / RT_VW, u = e - ql * RT_VW;
         const unsigned long long* vb = p.vbits + (size_t)(q0 + ql) * p.vwords;
-        vw[ql * 5 + u] = u < 3 ? __ldg(vb + (o_min >> 6) + u) : __ldg(vb + (o_batch >> 6) + (u - 3));
+        vw[ql * RT_VW + u] = u < 4 ? __ldg(vb + (o_min >> 6) + u) : __ldg(vb + (o_batch >> 6) + (u - 4));
       }
       named_bar_sync(RT_EPI_BAR, 128);
       bool good = ok && !__any_sync(0xffffffffu, *abort_flag != 0);  // warp-uniform
@@ -290,27 +309,37 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         // Column c of frame f is lag tl = f + lt - 1 - c, kept when 0 <= tl <= tl_max and
         // the row exists (c >= c_min).  Undefined frames contribute zeros (r = 0 in both
         // factors); pair counts come from the validity bits in the fold.
-        if (p.b <= W2_SMALL_B) {
-          // one frame per M-tile, lane l < 9 holds ring q0 + 4 l + w: the lanes' bins are
-          // disjoint, so each thread adds its columns straight into its ring's bins
-          const int f = mt, ql = 4 * lane + w;
-          const bool pair_ok = lane < 9 && ql < qn;
+        if constexpr (EPI == RT_SMALL) {
+          // D[c][ql] = history row c . w_{q0+ql}(t0 + f): the thread holding TMEM lane c
+          // owns lag tl = f + lt - 1 - c of every ring, so within a frame no two threads
+          // share a bin; it adds D r_q(s_c) for rings ql < qn (r from its own row of rs)
+          const int f = mt, c = 32 * w + lane;
           const int c_a = max(f + lt - 1 - tl_max, c_min), c_b = min(f + lt - 1, RT_ROWS - 1);
-          if (ok && c_a <= c_b && __any_sync(0xffffffffu, pair_ok)) {
-            float* brow = bins + (pair_ok ? ql : 0) * (lt + 1) + f + lt - 1;  // bin of column c: brow[-c]
-            const float* rcol = rs + (pair_ok ? ql : 0);                      // r of column c: rcol[c qb]
-#pragma unroll 1
-            for (int c32 = c_a >> 5; c32 <= (c_b >> 5); ++c32) {
-              uint32_t v[32];
-              tmem_ld32(tmem_base + buf * RT_ROWS + ((uint32_t)(w * 32) << 16) + c32 * 32, v);
-              tc_wait_ld();
-              if (pair_ok) {
+          const uint32_t tb = tmem_base + buf * RT_ROWS + ((uint32_t)(w * 32) << 16);
+          uint32_t v[32], v4[4];
+          tmem_ld32(tb, v);
+          if (qn > 32) tmem_ld4(tb + 32, v4);  // qn is the same for the whole CTA
+          tc_wait_ld();
+          if (ok && c >= c_a && c <= c_b) {
+            float* bc = bins + (f + lt - 1 - c);  // bin (ql, tl): bc[ql (lt + 1)]
+            const float4* r4 = reinterpret_cast<const float4*>(rs + c * p.qb);
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                  const int c = c32 * 32 + jj;
-                  if (c >= c_a && c <= c_b) brow[-c] = fmaf(__uint_as_float(v[jj]), rcol[c * p.qb], brow[-c]);
-                }
+            for (int g = 0; g < 8; ++g) {
+              if (4 * g < qn) {
+                const float4 r = r4[g];
+                const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  if (4 * g + u < qn)
+                    bc[(4 * g + u) * (lt + 1)] = fmaf(__uint_as_float(v[4 * g + u]), rv[u], bc[(4 * g + u) * (lt + 1)]);
               }
+            }
+            if (qn > 32) {
+              const float4 r = r4[8];
+              const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (32 + u < qn) bc[(32 + u) * (lt + 1)] = fmaf(__uint_as_float(v4[u]), rv[u], bc[(32 + u) * (lt + 1)]);
             }
           }
         } else {
@@ -324,7 +353,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         const int c_hi = __reduce_max_sync(0xffffffffu, c_b);
         if (ok && c_lo <= c_hi) {
           float* brow = bins + ql * (lt + 1);
-          if constexpr (SKEW) {
+          if constexpr (EPI == RT_SKEW) {
             // C(f, c) r_q(s_c) of each 32 x 32 block, zero outside the kept lags, stored at
             // row j - i + 32 of the warp's skewed buffer (constant offsets from a per-lane
             // base); row lane then holds block diagonal lane - 32 and row 32 + lane block
@@ -402,6 +431,8 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
+        // small steps: thread c of frame f and thread c + 1 of frame f + 1 share a bin
+        if (EPI == RT_SMALL && mt + 1 < p.n_mt) named_bar_sync(RT_EPI_BAR, 128);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(r_empty);  // the r rows may be replaced
@@ -417,17 +448,20 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         ok = false;
       }
       if (ok) {
+        // thread et takes lag tl = et mod lt of rings et / lt, et / lt + tpl, ...; the
+        // history bits of its lag start at the same offset in every ring's words
         const int sh_b = (int)(o_batch & 63);
-        for (int e = et; e < qn * lt; e += 128) {
-          const int ql = e / lt, tl = e - ql * lt;
-          if (tl > tl_max) continue;
-          const unsigned long long* wq = vw + ql * 5;
-          const unsigned long long mine = bits64(wq + 3, sh_b) & bmask;
-          const unsigned long long hist = bits64(wq, (int)(o_min & 63) + (lt - 1 - tl));
-          const int n = __popcll(mine & hist);
-          if (n) {
-            g2s[ql * lt + tl] += (double)bins[ql * (lt + 1) + tl];
-            cns[ql * lt + tl] += n;
+        const int tpl = RT_ROWS / lt, tl = et % lt, ql0 = et / lt;
+        if (ql0 < tpl && tl <= tl_max) {
+          const int o = (int)(o_min & 63) + (lt - 1 - tl);
+          for (int ql = ql0; ql < qn; ql += tpl) {
+            const unsigned long long* wq = vw + ql * RT_VW;
+            const unsigned long long mine = bits64(wq + 4, sh_b) & bmask;
+            const int n = __popcll(mine & bits64(wq, o));
+            if (n) {
+              g2s[ql * lt + tl] += (double)bins[ql * (lt + 1) + tl];
+              cns[ql * lt + tl] += n;
+            }
           }
         }
         fence_proxy_async_smem();  // the slice writes, visible to the bulk store
@@ -463,30 +497,40 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
 
 }  // namespace
 
-int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2, int skew) {
-  return RtLayout{n_kc, lt, qb, wst, qg2, skew}.smem();
+int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2, int epi) {
+  return RtLayout{n_kc, lt, qb, wst, qg2, epi}.smem();
 }
 
-template <bool SKEW>
+template <int EPI>
 static cudaError_t launch_rt(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
                              const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,
                              cudaStream_t st) {
-  const int smem = row_update_tc_smem(p.n_kc, p.lt, p.qb, p.wst, p.qg2, SKEW ? 1 : 0);
+  const int smem = row_update_tc_smem(p.n_kc, p.lt, p.qb, p.wst, p.qg2, EPI);
   static int attr_bytes = 0;  // the attribute only ever grows
   if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(row_update_tc_kernel<SKEW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(row_update_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  row_update_tc_kernel<SKEW><<<grid, RT_THREADS, smem, st>>>(tmA, tmW, tmR, tmG, tmC, p);
+  row_update_tc_kernel<EPI><<<grid, RT_THREADS, smem, st>>>(tmA, tmW, tmR, tmG, tmC, p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
                                  const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,
                                  cudaStream_t st) {
-  return p.skew ? launch_rt<true>(tmA, tmW, tmR, tmG, tmC, p, grid, st)
-                : launch_rt<false>(tmA, tmW, tmR, tmG, tmC, p, grid, st);
+  // the lag tile and the history rows it needs must fit one 128-row operand, and the
+  // small-step mode has no buffers for the larger steps' epilogue
+  if (p.lt < 2 || (p.lt & 1) || p.lt + p.b - 1 > RT_ROWS || (p.epi == RT_SMALL) != (p.b <= W2_SMALL_B))
+    return cudaErrorInvalidValue;
+  switch (p.epi) {
+    case RT_SKEW:
+      return launch_rt<RT_SKEW>(tmA, tmW, tmR, tmG, tmC, p, grid, st);
+    case RT_SMALL:
+      return launch_rt<RT_SMALL>(tmA, tmW, tmR, tmG, tmC, p, grid, st);
+    default:
+      return launch_rt<RT_ROT>(tmA, tmW, tmR, tmG, tmC, p, grid, st);
+  }
 }
 
 }  // namespace xpcs

@@ -160,10 +160,13 @@ class Context:
         if st != XPCS_OK:
             raise XpcsError(st, _lib.xpcs_last_error(self.h).decode())
 
+    _CLOSE_ORDER = {"Server": 0, "Graph": 1, "Stream": 2, "Basis": 3, "Rings": 4}
+
     def close(self):
-        """Destroy the context after every handle created on it (handles first)."""
+        """Destroy the context after every handle created on it, each handle before the
+        ones it uses: servers and graphs, then streams, bases and ring plans."""
         if self.h:
-            for ch in list(self._children):
+            for ch in sorted(self._children, key=lambda c: self._CLOSE_ORDER.get(type(c).__name__, 0)):
                 ch.close()
             _lib.xpcs_destroy(self.h)
             self.h = None

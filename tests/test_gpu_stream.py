@@ -115,6 +115,35 @@ def test_stream_many_rings_and_lag_tiles(X, ctx):
     st.close()
 
 
+@pytest.mark.parametrize("k,sizes", [(128, (9, 1, 12, 40, 3)), (256, (1, 9, 64, 5))])
+def test_stream_lag_tiles_and_epilogues(X, ctx, k, sizes):
+    # the row update picks its lag tile from the step size (128 lags for one frame, 120 up
+    # to 9, 96 up to 33, else 64 or 32) and its epilogue from what fits shared memory: at
+    # 36 rings these steps reach the small-step, rotated-block and skewed-buffer epilogues
+    # at k = 128 and k = 256; a window of 300 lags leaves a ragged last tile at every size.
+    # 1600 pixels and a 600-frame calibration keep k = 256 well below the data's rank, so
+    # no ring's compressed sum S~ comes near zero (on a 576-pixel detector one ring's
+    # S~ nearly cancels and its lag-0 g2 reaches 4e5, amplifying f32 rounding the same way
+    # for every batching)
+    H, W, n_q, T, Wl = 40, 40, 36, 420, 300
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 600, np.uint16, 606 + k, mean=1.0)
+    st = X.Stream(ctx, basis, Wl, 64)
+    i, j = 0, 0
+    while i < T:
+        n = min(sizes[j % len(sizes)], T - i)
+        ticket = st.push(np.ascontiguousarray(Xs[i:i + n]))
+        i += n
+        j += 1
+    assert st.poll(ticket, 10000)
+    g2, cnt = st.read_g2()
+    g_ref, c_ref = _oracle_window_g2(Xs, B, qmap, n_q, Wl)
+    np.testing.assert_array_equal(cnt, c_ref)
+    for q in range(n_q):
+        rm, _ = rel_errors(g2[q], g_ref[q])
+        assert rm < 1e-4, (q, rm)
+    st.close()
+
+
 def test_stream_batching_and_device_push_agree(X, ctx):
     torch, dev = torch_cuda()
     H, W, n_q, k, T, Wl = 16, 32, 3, 24, 150, 40
