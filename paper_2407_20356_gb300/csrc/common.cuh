@@ -166,6 +166,20 @@ XPCS_DEV void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
                : "memory");
 }
 
+// Running sum held as an f32 pair (hi, lo), value hi + lo: add x with Knuth's TwoSum
+// (s + e = hi + x exactly, no precondition on magnitudes), fold e into lo, then
+// renormalise with a second TwoSum so that |lo| <= ulp(hi) / 2.  Each addition loses only
+// the rounding of lo (about 2^-48 of the sum), with f32 operations only.
+XPCS_DEV float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+XPCS_DEV float2 f32pair_add(float2 acc, float x) {
+  const float2 t = two_sum(acc.x, x);
+  return two_sum(t.x, __fadd_rn(acc.y, t.y));
+}
+
 // Shared-memory matrix descriptor for a K-major operand tile stored with the 128-byte
 // swizzle: rows of 128 bytes, 8-row core groups 1024 bytes apart (tile base 1024-aligned).
 XPCS_DEV uint64_t smem_desc_sw128(const void* tile) {

@@ -113,7 +113,7 @@ struct xpcs_stream {
   __nv_bfloat16* d_A2 = nullptr;     // (cap + 128) x 2 kpad coefficient history, bf16 hi | lo
   float* d_Rh = nullptr;             // (cap + 128) x npad  r_q(s) = sqrt(M_q)/S~_q(s), 0 if undefined
   unsigned long long* d_vbits = nullptr;  // n_q x vwords  validity bits r_q(s) > 0 per slot
-  double* d_g2sum = nullptr;         // n_q x Wp (W rounded up to 64)
+  float2* d_g2sum = nullptr;         // n_q x Wp (W rounded up to 64): sums as f32 pairs (hi, lo)
   long long* d_cnt = nullptr;        // n_q x Wp
   float* d_part = nullptr;           // max_batch x nblk x k sparse-encode partials
   float* d_a = nullptr;              // max_batch x k

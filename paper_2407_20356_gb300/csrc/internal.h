@@ -187,7 +187,7 @@ struct StreamStep {
   unsigned long long* vbits;  // n_q x vwords: bit s of ring q = r_q(slot s) > 0, slots
                               // cap .. cap + 127 mirror slots 0 .. 127
   long long vwords;
-  double* g2sum;           // n_q x Wp (W rounded up to 64)
+  float2* g2sum;           // n_q x Wp (W rounded up to 64): running sums as f32 pairs (hi, lo)
   long long* cnt;          // n_q x Wp
   uint32_t* status;
   int num_sms;
@@ -260,7 +260,7 @@ inline int rt_lt_index(int lt) {
 // lag tile, w stages (2 or 1) and epilogue mode of the row update for steps of b frames;
 // false if nothing fits shared memory
 bool row_update_config(int n_q, int kpad, int b, int* lt, int* wst, int* epi);
-cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
+cudaError_t launch_stream_g2(const float2* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
                              double* g2, cudaStream_t st);
 cudaError_t launch_basis_f32(const double* B, long long n, float* B32, cudaStream_t st);
 

@@ -239,12 +239,14 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
   }
 }
 
-__global__ void stream_g2_kernel(const double* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
+// g2 = (hi + lo) / count of each lag bin (f32 pair sums, added in FP64); NaN without pairs
+__global__ void stream_g2_kernel(const float2* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
                                  double* g2) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)n_q * W) return;
   const long long j = i / W * Wp + i % W;
-  g2[i] = cnt[j] > 0 ? g2sum[j] / (double)cnt[j] : __longlong_as_double(0x7ff8000000000000ll);
+  const float2 v = g2sum[j];
+  g2[i] = cnt[j] > 0 ? ((double)v.x + (double)v.y) / (double)cnt[j] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 __global__ void basis_f32_kernel(const double* B, long long n, float* B32) {
@@ -319,7 +321,7 @@ bool row_update_config(int n_q, int kpad, int b, int* lt, int* wst, int* epi) {
   return false;
 }
 
-cudaError_t launch_stream_g2(const double* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
+cudaError_t launch_stream_g2(const float2* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
                              double* g2, cudaStream_t st) {
   const long long n = (long long)n_q * W;
   stream_g2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g2sum, cnt, n_q, W, Wp, g2);

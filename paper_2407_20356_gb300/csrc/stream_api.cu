@@ -169,7 +169,7 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
   XPCS_SALLOC(d_A2, z.A2, __nv_bfloat16*)
   XPCS_SALLOC(d_Rh, z.Rh, float*)
   XPCS_SALLOC(d_vbits, z.vbits, unsigned long long*)
-  XPCS_SALLOC(d_g2sum, z.g2sum, double*)
+  XPCS_SALLOC(d_g2sum, z.g2sum, float2*)
   XPCS_SALLOC(d_cnt, z.cnt, long long*)
   XPCS_SALLOC(d_part, z.part, float*)
   XPCS_SALLOC(d_a, z.a, float*)
@@ -214,6 +214,7 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
   // every lag tile a step may take
   const int qg2 = std::min(36, B->rings->n_q);
   for (int i = 0; i < RT_N_LT && st == XPCS_OK; ++i) {
+    // 8-byte elements (f32 pairs; the copies are bitwise)
     st = make_map(ctx, &S->tmG[i], S->d_g2sum, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, history, B->rings->n_q,
                   RT_LTS[i], qg2, CU_TENSOR_MAP_SWIZZLE_NONE, (uint64_t)wpitch(history) * 8);
     if (st == XPCS_OK)
@@ -529,6 +530,7 @@ struct CkptHeader {
 };
 
 constexpr char CKPT_MAGIC[8] = {'X', 'P', 'C', 'S', 'C', 'K', 'P', 'T'};
+constexpr uint32_t CKPT_VERSION = 2;  // 2: g2 sums stored as f32 pairs (1: FP64)
 
 xpcs_status basis_hash(xpcs_stream* S, uint64_t* h) {
   const xpcs_basis* B = S->basis;
@@ -579,7 +581,7 @@ extern "C" xpcs_status xpcs_stream_checkpoint(xpcs_stream* S, void* host_buf, si
   XPCS_TRY(retire(S));
   CkptHeader h{};
   memcpy(h.magic, CKPT_MAGIC, 8);
-  h.version = 1;
+  h.version = CKPT_VERSION;
   h.k = S->basis->k;
   h.n_q = S->basis->rings->n_q;
   h.dtype = S->dtype;
@@ -605,7 +607,7 @@ extern "C" xpcs_status xpcs_stream_restore(xpcs_stream* S, const void* host_buf,
   xpcs_ctx* ctx = S->ctx;
   CkptHeader h;
   memcpy(&h, host_buf, sizeof(h));
-  if (memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != 1) return fail(ctx, XPCS_EINVAL, "not a stream checkpoint");
+  if (memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != CKPT_VERSION) return fail(ctx, XPCS_EINVAL, "not a stream checkpoint");
   if (S->frames != 0) return fail(ctx, XPCS_EINVAL, "restore needs a freshly opened stream");
   if (h.k != S->basis->k || h.n_q != S->basis->rings->n_q || h.dtype != S->dtype || h.M != S->basis->rings->M ||
       h.W != S->W || h.cap != S->cap)

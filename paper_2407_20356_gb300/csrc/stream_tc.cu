@@ -21,7 +21,9 @@
 // the M operand, D[c][ring] (N = 48 >= 36 rings): the thread holding TMEM lane c owns lag
 // tl of every ring, so all 128 lanes work and within a frame no two threads share a bin
 // (a barrier separates frames).  Either way every bin's additions come in a fixed order,
-// with no atomics, and the bins are added to the FP64 sums once per work item.
+// with no atomics, and the bins are added to the running sums once per work item.  The
+// sums are f32 pairs (hi, lo) updated by TwoSum: no FP64 arithmetic, which is slow on this
+// part, and about 2^-48 relative rounding per addition.
 //
 // Warps: 0 TMA producer (history rows + their r values once per item, pair chunks
 // through a ring of stages), 1 TMEM owner and MMA issuer (two 128-column accumulators),
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   const RtLayout L{p.n_kc, p.lt, p.qb, p.wst, p.qg2, EPI};
   uint8_t* hist = smem;                                       // [hi kc..., lo kc...]
   uint8_t* w_st = smem + L.hist_bytes();                      // [stage][hi, lo]
-  double* g2s = reinterpret_cast<double*>(w_st + L.w_bytes());                     // [qg2][lt] g2 sums
+  double* g2s = reinterpret_cast<double*>(w_st + L.w_bytes());                     // [qg2][lt] g2 sums (f32 pairs)
   long long* cns = reinterpret_cast<long long*>(w_st + L.w_bytes() + L.slice_bytes());  // [qg2][lt] counts
   float* rs = reinterpret_cast<float*>(w_st + L.w_bytes() + 2 * L.slice_bytes());  // [128][qb] r of the rows
   float* bins = rs + RT_ROWS * p.qb;                          // [36][lt + 1]
@@ -459,7 +461,8 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             const unsigned long long mine = bits64(wq + 4, sh_b) & bmask;
             const int n = __popcll(mine & bits64(wq, o));
             if (n) {
-              g2s[ql * lt + tl] += (double)bins[ql * (lt + 1) + tl];
+              float2* acc = reinterpret_cast<float2*>(g2s) + ql * lt + tl;
+              *acc = f32pair_add(*acc, bins[ql * (lt + 1) + tl]);
               cns[ql * lt + tl] += n;
             }
           }
