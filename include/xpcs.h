@@ -279,7 +279,8 @@ xpcs_status xpcs_graph_destroy(xpcs_graph* graph);
  * tau = 0 .. history-1 (C itself is not stored).  xpcs_stream_read_g2 returns
  * g2_q(tau) = mean over t of C_q(t, t - tau) for every pushed frame t, and the pair count.
  * Work runs on the stream's own CUDA stream, so several streams overlap on the device.
- * Destroy streams before their basis and context. */
+ * Push only while the basis is alive; destroy streams before their context (closing a
+ * stream does not read its basis, and a basis does not read its ring plan). */
 
 /* Open a stream on `basis` for frames of `dtype`, keeping `history` lags, with batches
  * of up to `max_batch` frames.  XPCS_EBUSY if its device memory does not fit the
