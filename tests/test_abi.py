@@ -76,3 +76,41 @@ def test_rank_rule_host_function_matches_the_oracle():
         except xpcs.XpcsError:
             continue
         raise AssertionError(("accepted", bad, f))
+
+
+def test_context_closes_handles_before_the_handles_they_use(monkeypatch):
+    # Host logic only: a context built without the device, fake handles named like the
+    # binding's classes, and a stub in place of the library's context destroy.  Each
+    # handle must be closed before the ones it was made from (server and graph before
+    # stream, stream before basis, basis before ring plan), whatever order they were
+    # created in, and the context itself last.
+    _ensure_built()
+    import weakref
+
+    from paper_2407_20356_gb300 import xpcs as X
+
+    order = []
+
+    class _Lib:
+        def xpcs_destroy(self, h):
+            order.append("Context")
+
+    monkeypatch.setattr(X, "_lib", _Lib())
+
+    def fake(name):
+        def close(self):
+            order.append(name)
+
+        return type(name, (), {"close": close})()
+
+    ctx = X.Context.__new__(X.Context)
+    ctx.h = object()
+    ctx._children = weakref.WeakSet()
+    kids = [fake(n) for n in ("Rings", "Basis", "Stream", "Graph", "Server", "Stream", "Rings")]
+    for k in kids:
+        ctx._adopt(k)
+    ctx.close()
+    rank = {"Server": 0, "Graph": 1, "Stream": 2, "Basis": 3, "Rings": 4}
+    assert order[-1] == "Context" and len(order) == len(kids) + 1
+    assert [rank[n] for n in order[:-1]] == sorted(rank[n] for n in order[:-1])
+    assert ctx.h is None
