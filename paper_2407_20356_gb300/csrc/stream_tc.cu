@@ -325,24 +325,26 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
           if (ok && c >= c_a && c <= c_b) {
             float* bc = bins + (f + lt - 1 - c);  // bin (ql, tl): bc[ql (lt + 1)]
             const float4* r4 = reinterpret_cast<const float4*>(rs + c * p.qb);
+            // all bins first, then the products, then all stores (distinct rings' bins
+            // never alias, which the compiler cannot prove)
+            float bv[RT_QG];
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
+            for (int q = 0; q < RT_QG; ++q)
+              if (q < qn) bv[q] = bc[q * (lt + 1)];
+#pragma unroll
+            for (int g = 0; g < RT_QG / 4; ++g) {
               if (4 * g < qn) {
                 const float4 r = r4[g];
                 const float rv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                   if (4 * g + u < qn)
-                    bc[(4 * g + u) * (lt + 1)] = fmaf(__uint_as_float(v[4 * g + u]), rv[u], bc[(4 * g + u) * (lt + 1)]);
+                    bv[4 * g + u] = fmaf(__uint_as_float(g < 8 ? v[4 * g + u] : v4[u]), rv[u], bv[4 * g + u]);
               }
             }
-            if (qn > 32) {
-              const float4 r = r4[8];
-              const float rv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-              for (int u = 0; u < 4; ++u)
-                if (32 + u < qn) bc[(32 + u) * (lt + 1)] = fmaf(__uint_as_float(v4[u]), rv[u], bc[(32 + u) * (lt + 1)]);
-            }
+            for (int q = 0; q < RT_QG; ++q)
+              if (q < qn) bc[q * (lt + 1)] = bv[q];
           }
         } else {
         // this warp holds ring q0 + ql for frames f0 .. f0 + 31 (lane = frame offset)
@@ -456,13 +458,43 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         const int tpl = RT_ROWS / lt, tl = et % lt, ql0 = et / lt;
         if (ql0 < tpl && tl <= tl_max) {
           const int o = (int)(o_min & 63) + (lt - 1 - tl);
-          for (int ql = ql0; ql < qn; ql += tpl) {
+          float2* g2p = reinterpret_cast<float2*>(g2s);
+          int ql = ql0;
+          // six rings at a time: all loads, then the sums, then all stores, so the shared
+          // memory round trips of the six overlap (the bins, sums and counts of distinct
+          // rings never alias, which the compiler cannot prove)
+          for (; ql + 5 * tpl < qn; ql += 6 * tpl) {
+            int n[6];
+            float bv[6];
+            float2 acc[6];
+            long long cn[6];
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+              const int q = ql + u * tpl;
+              const unsigned long long* wq = vw + q * RT_VW;
+              n[u] = __popcll(bits64(wq + 4, sh_b) & bmask & bits64(wq, o));
+              bv[u] = bins[q * (lt + 1) + tl];
+              acc[u] = g2p[q * lt + tl];
+              cn[u] = cns[q * lt + tl];
+            }
+#pragma unroll
+            for (int u = 0; u < 6; ++u)
+              if (n[u]) {
+                acc[u] = f32pair_add(acc[u], bv[u]);
+                cn[u] += n[u];
+              }
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+              const int q = ql + u * tpl;
+              g2p[q * lt + tl] = acc[u];
+              cns[q * lt + tl] = cn[u];
+            }
+          }
+          for (; ql < qn; ql += tpl) {
             const unsigned long long* wq = vw + ql * RT_VW;
-            const unsigned long long mine = bits64(wq + 4, sh_b) & bmask;
-            const int n = __popcll(mine & bits64(wq, o));
+            const int n = __popcll(bits64(wq + 4, sh_b) & bmask & bits64(wq, o));
             if (n) {
-              float2* acc = reinterpret_cast<float2*>(g2s) + ql * lt + tl;
-              *acc = f32pair_add(*acc, bins[ql * (lt + 1) + tl]);
+              g2p[ql * lt + tl] = f32pair_add(g2p[ql * lt + tl], bins[ql * (lt + 1) + tl]);
               cns[ql * lt + tl] += n;
             }
           }
