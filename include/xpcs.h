@@ -307,7 +307,8 @@ int64_t xpcs_clock_ns(void);
  * within timeout_ms (0 = just check). */
 xpcs_status xpcs_stream_poll(xpcs_stream* s, uint64_t ticket, int timeout_ms);
 /* g2_host (nullable): n_q x history f64; count_host (nullable): n_q x history int64.
- * Waits for the stream's pending work. */
+ * Waits for the stream's pending work.  The running sums behind g2 are f32 pairs
+ * (hi + lo, about 2^-48 relative rounding per addition), divided by the count in FP64. */
 xpcs_status xpcs_stream_read_g2(xpcs_stream* s, double* g2_host, int64_t* count_host);
 /* Frames pushed so far. */
 int64_t xpcs_stream_frames(const xpcs_stream* s);
@@ -318,8 +319,9 @@ int64_t xpcs_stream_frames(const xpcs_stream* s);
  * state into host_buf (at least xpcs_stream_checkpoint_size bytes).  xpcs_stream_restore
  * takes a checkpoint into a stream opened with the same basis, history, max_batch and
  * dtype to which no frame has been pushed yet, which then continues where the
- * checkpointed one stopped; other shapes or bases give XPCS_EINVAL.  Latency records are
- * not part of the state. */
+ * checkpointed one stopped; other shapes or bases give XPCS_EINVAL, as do checkpoints of
+ * format version 1 (FP64 sums; this build writes version 2).  Latency records are not
+ * part of the state. */
 xpcs_status xpcs_stream_checkpoint_size(const xpcs_stream* stream, size_t* bytes);
 xpcs_status xpcs_stream_checkpoint(xpcs_stream* stream, void* host_buf, size_t bytes);
 xpcs_status xpcs_stream_restore(xpcs_stream* stream, const void* host_buf, size_t bytes);
