@@ -369,3 +369,47 @@ def test_twotime_stats_hand_example():
     # off-diagonal defined pairs: (1,0) = 1 and (2,0) = 3 -> mean 2, std 1
     m, s = O.twotime_stats(C)
     assert m == 2.0 and s == 1.0
+
+
+# ---------------------------------------------------------------- per-pair values (sampled parity)
+
+def test_raw_pair_values_hand_example():
+    # ring 0 = pixels {0, 2, 3} (M_q = 3), ring 1 = pixel {1}, pixel 4 outside every ring;
+    # ring 0's rows: (2, 0, 1), (1, 3, 2), (0, 0, 0) with sums 3, 6, 0
+    qmap = np.array([0, 1, 0, 0, -1], dtype=np.int32)
+    X = np.array([[2, 7, 0, 1, 9],
+                  [1, 0, 3, 2, 9],
+                  [0, 5, 0, 0, 9]], dtype=np.uint16)
+    N, C = O.raw_pair_values(X, qmap, 0, np.array([0, 0, 1, 2]), np.array([1, 0, 1, 0]))
+    assert N.tolist() == [4, 5, 14, 0]
+    np.testing.assert_allclose(C[:3], [3 * 4 / (3 * 6), 3 * 5 / (3 * 3), 3 * 14 / (6 * 6)], rtol=1e-15)
+    assert np.isnan(C[3])  # a dark frame: the pair is undefined
+    # a one-pixel ring: C = x_a x_b / (x_a x_b) = 1 whenever both counts are nonzero
+    N1, C1 = O.raw_pair_values(X, qmap, 1, np.array([0, 0]), np.array([2, 1]))
+    assert N1.tolist() == [35, 0] and C1[0] == 1.0 and np.isnan(C1[1])
+
+
+def test_pair_values_agree_with_the_whole_matrix_and_reduce_to_raw_with_a_lossless_basis():
+    # per-pair values against the whole-matrix oracle (raw) and, with the identity as a
+    # lossless basis (A = X, G_q = diag(ring mask), s_q = ring mask), compressed = raw
+    rng = np.random.default_rng(20356041)
+    T, M, n_q = 12, 20, 3
+    X = rng.poisson(1.5, (T, M)).astype(np.uint16)
+    X[4] = 0
+    qmap = (np.arange(M) % n_q).astype(np.int32)
+    qmap[M - 1] = -1
+    t1 = rng.integers(0, T, 40)
+    t2 = rng.integers(0, T, 40)
+    Cm = O.raw_twotime(X, qmap, n_q)[0]
+    B = np.eye(M)
+    G, s, Mq = O.ring_factors(B, qmap, n_q)
+    A = O.encode(X, B)
+    for q in range(n_q):
+        _, Cr = O.raw_pair_values(X, qmap, q, t1, t2)
+        np.testing.assert_array_equal(np.isnan(Cr), np.isnan(Cm[q][t1, t2]))
+        ok = ~np.isnan(Cr)
+        np.testing.assert_allclose(Cr[ok], Cm[q][t1, t2][ok], rtol=1e-14)
+        Cc = O.compressed_pair_values(A, G[q], s[q], Mq[q], t1, t2)
+        np.testing.assert_array_equal(np.isnan(Cc), np.isnan(Cr))
+        np.testing.assert_allclose(Cc[ok], Cr[ok], rtol=1e-13)
+    assert np.isnan(Cr[(t1 == 4) | (t2 == 4)]).all()
