@@ -107,3 +107,34 @@ def test_scaled_ring_sums_are_caught(monkeypatch, scale):
     orig = OX.ring_sums
     _patch(monkeypatch, "ring_sums", lambda X, qmap, n_q: (orig(X, qmap, n_q) * scale).astype(np.int64))
     assert _fails(*ALL_PINS)
+
+
+PAIR_PINS = (
+    P.test_raw_pair_values_hand_example,
+    P.test_pair_values_agree_with_the_whole_matrix_and_reduce_to_raw_with_a_lossless_basis,
+)
+
+
+def test_pair_values_without_ring_size_are_caught(monkeypatch):
+    orig = OX.raw_pair_values
+
+    def bad(X, qmap, q, t1, t2):
+        N, C = orig(X, qmap, q, t1, t2)
+        return N, C / max(1, OX.ring_index(qmap, q).size)  # M_q dropped
+
+    _patch(monkeypatch, "raw_pair_values", bad)
+    assert _fails(*PAIR_PINS)
+
+
+def test_compressed_pair_values_with_swapped_frames_in_one_sum_are_caught(monkeypatch):
+    def bad(A, Gq, sq, Mq, t1, t2):
+        A = np.asarray(A, dtype=np.float64)
+        out = np.empty(len(t1))
+        for i, (a, b) in enumerate(zip(t1, t2)):
+            n = A[a] @ Gq @ A[b]
+            sa, sb = A[a] @ sq, A[a] @ sq  # the second frame's ring sum taken from the first
+            out[i] = Mq * n / (sa * sb) if (sa > 0 and sb > 0) else np.nan
+        return out
+
+    _patch(monkeypatch, "compressed_pair_values", bad)
+    assert _fails(*PAIR_PINS)
