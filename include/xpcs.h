@@ -289,6 +289,14 @@ xpcs_status xpcs_graph_destroy(xpcs_graph* graph);
  * stay alive while frames are pushed; closing the stream does not read it. */
 xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t history, int max_batch,
                              xpcs_dtype dtype, xpcs_stream** out);
+/* The row-update configuration a stream step of b frames takes for n_q rings and a k-term
+ * basis (host-side, no context or device needed): *lags = the lag tile (the longest of
+ * 128, 120, 96, 64, 32 with lags + b - 1 <= 128 whose layout fits shared memory),
+ * *w_stages = pair-operand stages (1 or 2), *epilogue = 0 rotated blocks, 1 skewed
+ * buffers, 2 the small-step form (exactly when b <= 8), *smem_bytes = dynamic shared
+ * memory of the launch.  Outputs are nullable.  XPCS_EINVAL unless 1 <= n_q <= 1024,
+ * 1 <= k <= 256 and 1 <= b <= 64; XPCS_ENOTSUP if nothing fits. */
+xpcs_status xpcs_stream_row_tile(int n_q, int k, int b, int* lags, int* w_stages, int* epilogue, int* smem_bytes);
 /* Push n frames (n x M counts in host memory).  The frames are copied before the call
  * returns, so the caller may reuse its buffer.  *ticket (nullable) = frames pushed so far;
  * pass it to xpcs_stream_poll. */

@@ -321,6 +321,25 @@ bool row_update_config(int n_q, int kpad, int b, int* lt, int* wst, int* epi) {
   return false;
 }
 
+}  // namespace xpcs
+
+extern "C" xpcs_status xpcs_stream_row_tile(int n_q, int k, int b, int* lags, int* w_stages, int* epilogue,
+                                            int* smem_bytes) {
+  if (n_q < 1 || n_q > 1024 || k < 1 || k > 256 || b < 1 || b > 64) return XPCS_EINVAL;
+  const int kpad = (k + 63) / 64 * 64;
+  int lt = 0, wst = 0, epi = 0;
+  if (!xpcs::row_update_config(n_q, kpad, b, &lt, &wst, &epi)) return XPCS_ENOTSUP;
+  if (lags) *lags = lt;
+  if (w_stages) *w_stages = wst;
+  if (epilogue) *epilogue = epi;
+  if (smem_bytes)
+    *smem_bytes = xpcs::row_update_tc_smem(kpad / 64, lt, std::min(36, xpcs::stream_npad(n_q)), wst,
+                                           std::min(36, n_q), epi);
+  return XPCS_OK;
+}
+
+namespace xpcs {
+
 cudaError_t launch_stream_g2(const float2* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
                              double* g2, cudaStream_t st) {
   const long long n = (long long)n_q * W;

@@ -57,6 +57,7 @@ _SIGS = {
     "xpcs_basis_export": (C.c_int, [vp, vp, vp, vp, vp]),
     "xpcs_basis_rank": (C.c_int, [vp, C.POINTER(C.c_int)]),
     "xpcs_rank_from_spectrum": (C.c_int, [vp, C.c_int, C.c_double]),
+    "xpcs_stream_row_tile": (C.c_int, [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]),
     "xpcs_basis_destroy": (C.c_int, [vp]),
     "xpcs_encode": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
@@ -305,6 +306,15 @@ def xpcs_rank_from_spectrum(sigma, factor: float = 2.0) -> int:
     if K < 0:
         raise XpcsError(XPCS_EINVAL, "xpcs_rank_from_spectrum: bad spectrum or factor")
     return K
+
+
+def xpcs_stream_row_tile(n_q: int, k: int, b: int) -> dict:
+    """Row-update configuration of a stream step of b frames (host-side, no device)."""
+    out = [C.c_int() for _ in range(4)]
+    st = _lib.xpcs_stream_row_tile(n_q, k, b, *[C.byref(o) for o in out])
+    if st != XPCS_OK:
+        raise XpcsError(st, "xpcs_stream_row_tile")
+    return dict(zip(("lags", "w_stages", "epilogue", "smem_bytes"), (o.value for o in out)))
 
 
 def xpcs_encode(ctx: Context, basis: Basis, X, T: int, A_out, dtype=None):

@@ -114,3 +114,30 @@ def test_context_closes_handles_before_the_handles_they_use(monkeypatch):
     assert order[-1] == "Context" and len(order) == len(kids) + 1
     assert [rank[n] for n in order[:-1]] == sorted(rank[n] for n in order[:-1])
     assert ctx.h is None
+
+
+def test_stream_row_tile_choice_by_step_size():
+    # Host-side selection of the stream row update's lag tile and epilogue: every step of
+    # 1..64 frames gets a tile whose history rows fit one 128-row operand and a layout that
+    # fits 227 KB of shared memory, the small-step epilogue exactly for steps of <= 8
+    # frames, and the longest listed tile for the shapes the benchmarks run.
+    _ensure_built()
+    from paper_2407_20356_gb300 import xpcs as X
+
+    for n_q, k in ((36, 128), (100, 256), (100, 128), (100, 64), (4, 20), (40, 24), (5, 150), (36, 150)):
+        for b in range(1, 65):
+            t = X.xpcs_stream_row_tile(n_q, k, b)
+            assert t["lags"] in (128, 120, 96, 64, 32) and t["lags"] + b - 1 <= 128, (n_q, k, b, t)
+            assert 0 < t["smem_bytes"] <= 227 * 1024 and t["w_stages"] in (1, 2), (n_q, k, b, t)
+            assert (t["epilogue"] == 2) == (b <= 8), (n_q, k, b, t)
+    expect = {(36, 128, 1): 128, (36, 128, 8): 120, (36, 128, 9): 120, (36, 128, 33): 96, (36, 128, 34): 64,
+              (36, 128, 64): 64, (100, 256, 1): 64, (100, 256, 9): 32, (100, 64, 1): 128, (100, 64, 64): 64}
+    for (n_q, k, b), lags in expect.items():
+        assert X.xpcs_stream_row_tile(n_q, k, b)["lags"] == lags, (n_q, k, b)
+    for bad in ((0, 128, 1), (36, 0, 1), (36, 257, 1), (36, 128, 0), (36, 128, 65), (1025, 64, 1)):
+        try:
+            X.xpcs_stream_row_tile(*bad)
+        except X.XpcsError as e:
+            assert e.status == X.XPCS_EINVAL
+        else:
+            raise AssertionError(bad)
