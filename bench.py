@@ -40,6 +40,9 @@ GROUPED = dict(H=1024, W=1024, T=20000, dtype="uint16", mean=0.05, D=5e-4, n_q=6
 GROUPED_NAME = ("1024x1024 detector, 64 ring-plus-sector masks of 100..20000 px (246813 masked px, X holds "
                 "those only), T=20000 frames, uint16 Poisson AR(1) speckle mean 0.05 D=5e-4, k=128 basis fit "
                 "on the first 1000 frames; step = encode + two-time with g2 fused (C not stored: 102 GB)")
+# smaller case of the grouped kernels for profiler captures (X and the operands exceed L2)
+GROUPED_SMALL = dict(H=512, W=512, T=4096, dtype="uint16", mean=0.05, D=5e-4, n_q=64, min_px=100, max_px=3000,
+                     k=128, n_fit=500, seed=20356013)
 # multi-stream serving: four detectors of different sizes at their own rates, 100 q-rings
 # each, coefficient histories capped at 2e5 frames, one server with continuous batching
 SERVING = dict(streams=[dict(H=1536, W=2048, rate_hz=2000.0, k=256, D=1e-4),
@@ -152,6 +155,15 @@ def max_over_ranks(x, world, device):
     return float(t.item())
 
 
+def T_pad_of(T):
+    return (T + 127) // 128 * 128
+
+
+def rings_padded(rings):
+    """Row length of the raw path's ring-sorted operand: every ring padded to 64 pixels."""
+    return int(sum(max(1, (int(m) + 63) // 64) * 64 for m in rings.sizes()))
+
+
 # ---------------------------------------------------------------- oracle timing (CPU)
 
 def oracle_cpu(frames_host, qmap, wl, n_rings_sample=1, enc_frames=None):
@@ -228,8 +240,8 @@ def run_reference(args, wl):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "impl": "CPU FP64 oracle (numpy)"},
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: oracle encode of 200 frames scaled to T=10000, plus oracle "
-                                   "two-time + g2 of one ring at T=10000 scaled to 36 rings",
+                         "sample": "extrapolated: per step, oracle encode of 200 frames scaled to T=10000, "
+                                   "plus oracle two-time + g2 of one ring at T=10000 scaled to 36 rings",
                          "wall_s": wall},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -330,14 +342,55 @@ def run_ours(args, wl):
                  "kernels_per_step": graph.kernels(), "gpu_launches": graph_launches}
     graph.close()
 
+    # ---- g2 over the stored C of the last step (the standalone xpcs_g2 call): HBM-bound,
+    # it reads the lower triangle once (C = 14.4 GB, far larger than L2)
+    g2s = torch.empty_like(g2)
+    cs = torch.empty_like(cnt)
+    g2c_ms, _, g2c_prof = timed(lambda: X.xpcs_g2(ctx, C, n_q, T, g2s, cs), max(1, min(args.steps, 5)), 3,
+                                profile=True)
+    pk = peaks()
+    g2c_bytes = n_q * T * (T + 1) // 2 * 4 + n_q * T * 16  # lower triangle read + g2 and counts written
+    g2c_kern = {k_: v[0] / max(1, v[1]) for k_, v in g2c_prof.items()}
+    g2c_k = g2c_kern.get("g2_from_C")
+    g2_res = {"ms_per_call": g2c_ms, "kernels_ms": g2c_kern,
+              "roofline": {"bound": "hbm", "kernel": "g2_from_C", "algorithmic_bytes": g2c_bytes,
+                           "bytes_model": "lower triangle of C read once (float32) + g2 and counts written",
+                           "achieved": g2c_bytes / (g2c_k * 1e-3) / 1e9 if g2c_k else None,
+                           "peak": pk["hbm_gbs"], "unit": "GB/s",
+                           "frac": g2c_bytes / (g2c_k * 1e-3) / 1e9 / pk["hbm_gbs"] if g2c_k else None,
+                           "peak_source": pk["source"]}}
+    del g2s, cs
+
     # ---- raw exact path on the same frames (the comparison of the metric)
     raw_ms = None
+    raw_res = None
     if not args.no_raw:
         def raw_step():
             X.xpcs_twotime_raw(ctx, rings, Xd, T, C_out=C, g2_out=g2, count_out=cnt)
 
+        raw_tuned = X.xpcs_autotune_twotime_raw(ctx, rings, Xd, T, C_out=C, g2_out=g2, count_out=cnt, reps=1)
         raw_ms, _, raw_prof = timed(raw_step, max(1, min(args.steps, 3)), 1, profile=True)
         raw_ms = max_over_ranks(raw_ms, world, dev)
+        raw_kern = {k_: v[0] / max(1, v[1]) for k_, v in raw_prof.items()}
+        Mq_sum = int(np.asarray(rings.sizes()).sum())
+        raw_flops = 2.0 * Mq_sum * T * (T + 1) / 2  # exact Gram over the upper triangle, all ring pixels
+        rg = raw_kern.get("twotime_gram")
+        rpeak = pk["bf16_tflops_sustained"] or pk["bf16_tflops"]
+        ing = raw_kern.get("ingest")
+        ing_bytes = T * M * 2 + T_pad_of(T) * rings_padded(rings) * 2  # X read (uint16) + bf16 operand written
+        raw_res = {
+            "frames_per_s": world * T / (raw_ms * 1e-3), "ms_per_step": raw_ms, "kernels_ms": raw_kern,
+            "autotuned": raw_tuned,
+            "roofline": {"bound": "tensor", "kernel": "twotime_gram", "flops": raw_flops,
+                         "flops_model": "2 sum_q M_q T(T+1)/2 (bf16 operands, exact integer Gram)",
+                         "achieved": raw_flops / (rg * 1e-3) / 1e12 if rg else None, "peak": rpeak,
+                         "unit": "TFLOP/s", "frac": raw_flops / (rg * 1e-3) / 1e12 / rpeak if rg else None,
+                         "peak_source": pk["source"] + (" sustained" if pk["bf16_tflops_sustained"] else "")},
+            "ingest_roofline": {"bound": "hbm", "kernel": "ingest", "algorithmic_bytes": ing_bytes,
+                                "bytes_model": "X read once (uint16) + ring-sorted bf16 operand written",
+                                "achieved": ing_bytes / (ing * 1e-3) / 1e9 if ing else None, "peak": pk["hbm_gbs"],
+                                "unit": "GB/s", "frac": ing_bytes / (ing * 1e-3) / 1e9 / pk["hbm_gbs"] if ing else None},
+        }
 
     # ---- other precision modes: time and error
     variants = {}
@@ -362,6 +415,11 @@ def run_ours(args, wl):
     if not (args.no_serving or args.no_host) and args.workload == "c2":
         serving_res = run_serving_leg(X, dev, args)
 
+    # ---- the small raw workload, timed in full beside the oracle
+    c1_res = None
+    if not args.no_host and rank == 0:
+        c1_res = run_c1_leg(X, dev, args)
+
     # ---- end to end through the public API from pinned host memory
     if args.no_host:
         if rank == 0:
@@ -376,8 +434,10 @@ def run_ours(args, wl):
     cnth = torch.empty((n_q, T), dtype=torch.int64, pin_memory=True)
 
     def e2e_step():
-        Xd.copy_(Xh, non_blocking=True)
-        step()
+        # frames from pinned host memory: the library copies them in blocks on two copy
+        # streams while it encodes the blocks already on the device
+        X.xpcs_encode_host(ctx, basis, Xh, T, A)
+        X.xpcs_twotime(ctx, basis, A, T, prec, C_out=C, g2_out=g2, count_out=cnt)
         g2h.copy_(g2, non_blocking=True)
         cnth.copy_(cnt, non_blocking=True)
 
@@ -467,33 +527,40 @@ def run_ours(args, wl):
     value = world * T / (ms * 1e-3)
     h2d = T * M * 2
     d2h = n_q * T * 16
+    # the long objects first and the metric's own figures (latency, raw path, speed-up,
+    # error) last, so that a reader keeping only the end of the line still has them
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "precision": prec, "l2": "inputs larger than L2 (X = 5.24 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "raw_path": {"frames_per_s": (world * T / (raw_ms * 1e-3)) if raw_ms else None, "ms_per_step": raw_ms,
-                     "kernels_ms": {k_: v[0] / max(1, v[1]) for k_, v in raw_prof.items()} if raw_ms else None},
-        "speedup_vs_raw": (raw_ms / ms) if raw_ms else None,
-        "error_vs_fp64_oracle": result["errs"],
-        "precision_variants_ms": {p: v["ms_per_step"] for p, v in variants.items()},
-        "kernels_ms": {k_: v[0] / max(1, v[1]) for k_, v in prof.items()},
-        "setup_s": {"generate": t_gen, "fit_basis_gpu": t_fit},
-        "roofline": roofline,
-        "cpu_baseline": {"value": result["cpu_fps"], "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": "oracle FP64 encode of all 10000 frames + two-time and g2 of ring 0 at T=10000, "
-                                   "scaled x36 rings (BLAS multithreaded, reductions single-threaded)",
-                         "seconds": result["cpu_s"]},
-        "e2e": {"value": world * T / (e2e_ms * 1e-3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": launches,
-        "clocks": sampler.summary() if sampler else None,
-        "autotuned": tuned,
-        "cuda_graph": graph_res,
-        "latency": stream_res,
         "grouped": grouped_res,
         "serving": serving_res,
+        "cuda_graph": graph_res,
+        "autotuned": tuned,
+        "setup_s": {"generate": t_gen, "fit_basis_gpu": t_fit},
+        "kernels_ms": {k_: v[0] / max(1, v[1]) for k_, v in prof.items()},
+        "precision_variants_ms": {p: v["ms_per_step"] for p, v in variants.items()},
+        "xpcs_g2": g2_res,
+        "c1_raw": c1_res,
+        "roofline": roofline,
+        "cpu_baseline": {"value": result["cpu_fps"], "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "extrapolated: oracle FP64 encode of all 10000 frames + two-time and g2 of ring 0 "
+                                   "at T=10000 timed, the two-time scaled x36 rings (BLAS multithreaded, "
+                                   "reductions single-threaded)",
+                         "seconds": result["cpu_s"]},
+        "e2e": {"value": world * T / (e2e_ms * 1e-3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "h2d_gbs_over_step": h2d / (e2e_ms * 1e-3) / 1e9,
+                "path": "xpcs_encode_host (copies of 256 MB blocks on two copy streams overlapped with the "
+                        "encode) + xpcs_twotime + g2/count read back"},
+        "gpu_launches": launches,
+        "clocks": sampler.summary() if sampler else None,
+        "error_vs_fp64_oracle": result["errs"],
+        "raw_path": raw_res,
+        "speedup_vs_raw": (raw_ms / ms) if raw_ms else None,
+        "latency": stream_res,
     }
     print(json.dumps(line), flush=True)
 
@@ -581,6 +648,47 @@ def run_grouped_leg(X, dev, args, gw=GROUPED):
     pk = peaks()
     peak = pk["bf16_tflops_sustained"] or pk["bf16_tflops"]
     achieved = flops / (gram_ms * 1e-3) / 1e12 if gram_ms else None
+    # every precision of the g2-only two-time: time (autotuned per precision) and the error
+    # of g2 against the FP64 oracle of the same coefficients on the smallest and the largest
+    # mask (whole g2 at the full T)
+    import oracle as O
+
+    g2h = {}
+    per_prec = {}
+    for p in ("bf16x3", "fp16", "bf16"):
+        tp = X.xpcs_autotune_twotime(ctx, basis, A, T, p, g2_out=g2, count_out=cnt, reps=1)
+        for _ in range(2):
+            X.xpcs_twotime(ctx, basis, A, T, p, g2_out=g2, count_out=cnt)
+        ctx.synchronize()
+        ctx.profile_enable(True)
+        e0.record(stream)
+        for _ in range(K):
+            X.xpcs_twotime(ctx, basis, A, T, p, g2_out=g2, count_out=cnt)
+        e1.record(stream)
+        ctx.synchronize()
+        kp = {k_: v[0] / max(1, v[1]) for k_, v in ctx.profile().items()}
+        ctx.profile_enable(False)
+        gm = kp.get("twotime_gram")
+        g2h[p] = g2.cpu().numpy()
+        per_prec[p] = {"twotime_ms": e0.elapsed_time(e1) / K, "gram_ms": gm, "autotuned": tp,
+                       "gram_tflops_one_product": flops / (gm * 1e-3) / 1e12 if gm else None,
+                       "frac_of_peak_one_product": flops / (gm * 1e-3) / 1e12 / peak if gm else None}
+    Ah = A.cpu().numpy().astype(np.float64)
+    _, Gh, sh = basis.export()
+    for p in per_prec:
+        per_prec[p]["g2_rel_max"] = {}
+    for m in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        Sq = Ah @ sh[m]
+        Cq = O.twotime_from_gram(O.compressed_ring_gram(Ah, Gh[m]), Sq, Sq, sizes[m])
+        gref, _ = O.g2_from_twotime(Cq)
+        del Cq
+        okr = ~np.isnan(gref)
+        for p in per_prec:
+            gg = g2h[p][m]
+            ok = okr & ~np.isnan(gg)
+            per_prec[p]["g2_rel_max"][f"mask{m}_{int(sizes[m])}px"] = float(
+                np.abs(gg[ok] - gref[ok]).max() / np.abs(gref[ok]).max())
+    del Ah
     out = {
         "workload": GROUPED_NAME, "frames_per_s": T / (ms * 1e-3), "ms_per_step": ms, "steps": K, "warmup": 3,
         "masks": n_q, "mask_px": {"min": int(sizes.min()), "max": int(sizes.max()), "total": int(sizes.sum())},
@@ -594,6 +702,9 @@ def run_grouped_leg(X, dev, args, gw=GROUPED):
                      "flops_model": "2 n_q k T(T+1)/2 (one bf16 product; bf16x3 issues three)"},
         "setup_s": {"generate": t_gen, "fit_basis_gpu": t_fit},
         "precision": "bf16x3", "l2": "inputs larger than L2 (X = %.2f GB)" % (T * M * 2 / 1e9),
+        "precisions": per_prec,
+        "precision_note": "g2 error vs the FP64 oracle of the same coefficients (target 1e-3); the cheapest "
+                          "precision within it is the caller's choice",
     }
     del Xd, A
     basis.close()
@@ -601,6 +712,61 @@ def run_grouped_leg(X, dev, args, gw=GROUPED):
     ctx.close()
     torch.cuda.empty_cache()
     return out
+
+
+C1 = dict(H=64, W=64, T=500, n_q=8, mean=0.1, D=1e-3, seed=20356001)
+C1_NAME = ("64x64 detector, T=500 frames, uint8 Poisson AR(1) speckle mean 0.1 D=1e-3, 8 q-rings; "
+           "raw path: exact integer Gram N, C, g2 and counts")
+
+
+def run_c1_leg(X, dev, args, w=C1):
+    """The small raw workload timed in full on the GPU and on the oracle, with bit-exactness."""
+    import torch
+
+    import oracle as O
+    from synth import ring_qmap, speckle_counts
+
+    H, W, T, n_q = w["H"], w["W"], w["T"], w["n_q"]
+    frames = speckle_counts(H, W, T, w["mean"], w["D"], w["seed"], np.uint8)
+    qmap = ring_qmap(H, W, n_q)
+    stream = torch.cuda.current_stream(dev)
+    ctx = X.Context(dev.index or 0, 0, stream.cuda_stream)
+    rings = X.Rings(ctx, torch.from_numpy(qmap).to(dev), H * W, n_q)
+    Xd = torch.from_numpy(frames).to(dev)
+    C = torch.empty((n_q, T, T), dtype=torch.float32, device=dev)
+    N = torch.empty((n_q, T, T), dtype=torch.int64, device=dev)
+    g2 = torch.empty((n_q, T), dtype=torch.float64, device=dev)
+    cnt = torch.empty((n_q, T), dtype=torch.int64, device=dev)
+    ctx.set_async(True)
+
+    def call():
+        X.xpcs_twotime_raw(ctx, rings, Xd, T, C_out=C, N_out=N, g2_out=g2, count_out=cnt)
+
+    for _ in range(3):
+        call()
+    ctx.synchronize()
+    K = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        call()
+    e1.record(stream)
+    ctx.synchronize()
+    gpu_ms = e0.elapsed_time(e1) / K
+    t0 = time.perf_counter()
+    Cref, Nref, _, _ = O.raw_twotime(frames, qmap, n_q)
+    gref = [O.g2_from_twotime(Cref[q]) for q in range(n_q)]
+    t_or = time.perf_counter() - t0
+    il = np.tril_indices(T)
+    Nh, gh = N.cpu().numpy(), g2.cpu().numpy()
+    exact = all(np.array_equal(Nh[q][il], Nref[q][il]) for q in range(n_q))
+    gerr = max(float(np.nanmax(np.abs(gh[q] - gref[q][0]) / np.nanmax(np.abs(gref[q][0])))) for q in range(n_q))
+    rings.close()
+    ctx.close()
+    return {"workload": C1_NAME, "gpu": {"ms_per_step": gpu_ms, "frames_per_s": T / (gpu_ms * 1e-3), "steps": K},
+            "oracle": {"seconds": t_or, "frames_per_s": T / t_or, "cores": os.cpu_count(),
+                       "sample": "the whole workload (all 8 rings at T=500), not extrapolated"},
+            "N_bit_exact": bool(exact), "g2_rel_max": gerr}
 
 
 def run_serving_leg(X, dev, args, sv=SERVING):
@@ -860,6 +1026,102 @@ def stream_capture(mode, path):
     ctx.close()
 
 
+def profile_leg(args):
+    """Profiling aid, no bench line: run one leg alone so that a profiler sees few launches.
+
+    raw: the exact raw path (ingest, integer Gram with C, g2 and counts) on the chosen
+    workload, `--steps` calls after `--warmup`; grouped: the grouped masks' encode and
+    g2-only two-time (bf16x3) on the small grouped case.  Prints a short JSON line of
+    event-timed milliseconds per call."""
+    import torch
+    from paper_2407_20356_gb300 import xpcs as X
+    from synth import ring_qmap
+    from synth.speckle import TorchSpeckle
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    out = {"leg": args.leg, "workload": args.workload}
+    if args.leg == "raw":
+        wl = dict(WORKLOAD if args.workload == "c2" else SMALL)
+        H, W, T, n_q = wl["H"], wl["W"], wl["T"], wl["n_q"]
+        gen = TorchSpeckle(H, W, wl["mean"], wl["D"], wl["seed"], dtype=wl["dtype"], device=str(dev))
+        Xd = torch.empty((T, H * W), dtype=torch.uint16, device=dev)
+        for i in range(0, T, 1000):
+            Xd[i:i + 1000].copy_(gen.next(min(1000, T - i)))
+        del gen
+        ctx = X.Context(0, 0, stream.cuda_stream)
+        rings = X.Rings(ctx, torch.from_numpy(ring_qmap(H, W, n_q)).to(dev), H * W, n_q)
+        C = torch.empty((n_q, T, T), dtype=torch.float32, device=dev)
+        g2 = torch.empty((n_q, T), dtype=torch.float64, device=dev)
+        cnt = torch.empty((n_q, T), dtype=torch.int64, device=dev)
+
+        def call():
+            X.xpcs_twotime_raw(ctx, rings, Xd, T, C_out=C, g2_out=g2, count_out=cnt)
+
+        flops = 2.0 * H * W * T * (T + 1) / 2
+    else:
+        gw = dict(GROUPED_SMALL)
+        from synth import sector_qmap
+
+        H, W, T, n_q, k = gw["H"], gw["W"], gw["T"], gw["n_q"], gw["k"]
+        qfull = sector_qmap(H, W, n_annuli=8, n_sectors=8, min_px=gw["min_px"], max_px=gw["max_px"],
+                            seed=gw["seed"])
+        pix = np.flatnonzero(qfull >= 0)
+        M = (pix.size + 7) // 8 * 8
+        qmap = np.full(M, -1, dtype=np.int32)
+        qmap[:pix.size] = qfull[pix]
+        gen = TorchSpeckle(H, W, gw["mean"], gw["D"], gw["seed"], dtype=gw["dtype"], device=str(dev))
+        Xd = torch.zeros((T, M), dtype=torch.uint16, device=dev)
+        pix_d = torch.from_numpy(pix.astype(np.int64)).to(dev)
+        for i in range(0, T, 1000):
+            Xd[i:i + 1000, :pix.size].copy_(gen.next(min(1000, T - i)).index_select(1, pix_d))
+        del gen
+        ctx = X.Context(0, 0, stream.cuda_stream)
+        rings = X.Rings(ctx, torch.from_numpy(qmap).to(dev), M, n_q)
+        basis = X.xpcs_fit_basis(ctx, rings, Xd, gw["n_fit"], k)
+        A = torch.empty((T, k), dtype=torch.float32, device=dev)
+        g2 = torch.empty((n_q, T), dtype=torch.float64, device=dev)
+        cnt = torch.empty((n_q, T), dtype=torch.int64, device=dev)
+        X.xpcs_encode(ctx, basis, Xd, T, A)
+
+        def call():
+            X.xpcs_twotime(ctx, basis, A, T, args.prec, g2_out=g2, count_out=cnt)
+
+        flops = 2.0 * n_q * k * T * (T + 1) / 2
+        out["masks_px"] = int(pix.size)
+    ctx.set_async(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed():
+        for _ in range(args.warmup):
+            call()
+        ctx.synchronize()
+        ctx.profile_enable(True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            call()
+        e1.record(stream)
+        ctx.synchronize()
+        kern = {k_: v[0] / max(1, v[1]) for k_, v in ctx.profile().items()}
+        ctx.profile_enable(False)
+        return e0.elapsed_time(e1) / args.steps, kern
+
+    if args.sweep:  # every (tiles per item, schedule) of the two-time kernel
+        sweep = {}
+        for sched in X.SCHEDULES:
+            for tiles in (1, 2, 4, 8, 16, 32):
+                ctx.twotime_config(tiles, sched)
+                _, kern = timed()
+                sweep[f"{sched}/{tiles}"] = kern.get("twotime_gram")
+        ctx.twotime_config(0)
+        out["gram_ms_by_config"] = sweep
+    out["ms_per_call"], out["kernels_ms"] = timed()
+    gm = out["kernels_ms"].get("twotime_gram")
+    out["gram_tflops_one_product"] = flops / (gm * 1e-3) / 1e12 if gm else None
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -880,9 +1142,17 @@ def main():
                     help="profiling aid, no bench line: make = fill the online stream and checkpoint it; "
                          "run = restore it and push three single frames")
     ap.add_argument("--capture-dir", default="/tmp", help="where --stream-capture keeps its basis and checkpoint")
+    ap.add_argument("--sweep", action="store_true",
+                    help="with --leg: also time the two-time kernel in every configuration")
+    ap.add_argument("--leg", choices=["raw", "grouped"],
+                    help="profiling aid, no bench line: run only the raw path (on --workload) or the grouped "
+                         "g2-only two-time (small grouped case) and print its event-timed call time")
     args = ap.parse_args()
     if args.stream_capture:
         stream_capture(args.stream_capture, args.capture_dir)
+        return
+    if args.leg:
+        profile_leg(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -66,6 +66,25 @@ typedef enum xpcs_precision {
  * Sbar~_q = abar s_q with abar the mean coefficient row). */
 typedef enum xpcs_norm { XPCS_NORM_MEAN = 0, XPCS_NORM_FROB = 1, XPCS_NORM_EQ12 = 2 } xpcs_norm;
 
+/* Per-frame ring sums in the denominators of the compressed path (Eq. 1 read with the
+ * compressed Gram of Eq. 10 in the numerator):
+ *   XPCS_QMEAN_COMPRESSED  S~_q(t) = a_t s_q, the ring sum of the decompressed frame
+ *                          (consistent with Eq. 8; the default); lossy bases can make it
+ *                          <= 0, which leaves the frame undefined;
+ *   XPCS_QMEAN_EXACT_RAW   S_q(t), the exact ring sum of the raw frame, captured when the
+ *                          frames are encoded (xpcs_encode_sums, or a stream opened with
+ *                          this option); only frames without photons in a ring are then
+ *                          undefined there. */
+typedef enum xpcs_qmean { XPCS_QMEAN_COMPRESSED = 0, XPCS_QMEAN_EXACT_RAW = 1 } xpcs_qmean;
+
+/* Options of the compressed calls.  Zero-initialised it is { XPCS_PREC_FP16,
+ * XPCS_NORM_MEAN, XPCS_QMEAN_COMPRESSED }. */
+typedef struct xpcs_options {
+  int precision; /* xpcs_precision */
+  int norm;      /* xpcs_norm */
+  int qmean;     /* xpcs_qmean */
+} xpcs_options;
+
 typedef struct xpcs_ctx xpcs_ctx;
 typedef struct xpcs_rings xpcs_rings;
 typedef struct xpcs_basis xpcs_basis;
@@ -106,10 +125,20 @@ xpcs_status xpcs_profile_get(xpcs_ctx* ctx, int i, char* name_host, size_t name_
 /* Failure-detection self test (no counterpart in the paper).  Every device-side wait of
  * the library is bounded: past its limit the kernel records a timeout and unwinds, and
  * the host sees XPCS_ETIMEOUT with the context still usable.  This call runs one such
- * wait that nothing satisfies, for limit_ms (1..1000) milliseconds, and returns what a
- * real expired wait returns: XPCS_ETIMEOUT (at once in synchronous mode, else from
- * xpcs_synchronize).  XPCS_EINVAL for a limit out of range. */
+ * wait that nothing satisfies, for limit_ms (1..1000) milliseconds, or with limit_ms = 0
+ * through the library's own bounded wait with the context's limit (xpcs_set_timeout; at
+ * most 10 s for this call), and returns what a real expired wait returns: XPCS_ETIMEOUT
+ * (at once in synchronous mode, else from xpcs_synchronize).  XPCS_EINVAL for a limit
+ * out of range. */
 xpcs_status xpcs_selftest_timeout(xpcs_ctx* ctx, int limit_ms);
+/* Limit of the bounded device-side waits (no counterpart in the paper) of the kernels this
+ * context launches, and of the streams opened on it after this
+ * call (a stream keeps the limit it was opened with): 1..600000 ms, or 0 for the default
+ * of 2000 ms.  A wait that runs past it ends its kernel with XPCS_ETIMEOUT.  Waits for the
+ * context's queued work first; XPCS_EBUSY during a capture. */
+xpcs_status xpcs_set_timeout(xpcs_ctx* ctx, int timeout_ms);
+/* The context's current limit in milliseconds (-1 for a null context). */
+int xpcs_get_timeout(const xpcs_ctx* ctx);
 
 /* ------------------------------------------------------------------ q-rings (Sec. 2.2)
  * A ring plan fixes which pixels form each q-ring: qmap[p] in [0, n_q) is the ring of
@@ -176,6 +205,21 @@ xpcs_status xpcs_basis_destroy(xpcs_basis* basis);
 xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* basis, const void* X, xpcs_dtype dtype, int64_t T,
                         float* A_out);
 
+/* xpcs_encode of frames in HOST memory (X_host, T x M counts, best pinned), with the
+ * host-to-device copy overlapped with the encode: the frames move in blocks of about 256 MB
+ * through three device staging buffers (context scratch), the copies alternating between
+ * two copy streams, and each block is encoded on the context's stream as soon as it has
+ * landed.  A_out is a device T x k float32 array as for xpcs_encode.  Returns once the
+ * encode is done (unless the context is asynchronous; the host buffer must then stay
+ * unchanged until xpcs_synchronize).  XPCS_EBUSY during a capture. */
+xpcs_status xpcs_encode_host(xpcs_ctx* ctx, const xpcs_basis* basis, const void* X_host, xpcs_dtype dtype, int64_t T,
+                             float* A_out);
+/* xpcs_encode that also captures the exact ring sums of the raw frames for the option
+ * XPCS_QMEAN_EXACT_RAW: S_out n_q x T int64 (device), S_q(t) = sum of X[t][p] over the
+ * pixels p of ring q of the basis's ring plan (as xpcs_ring_sums; one more pass over X). */
+xpcs_status xpcs_encode_sums(xpcs_ctx* ctx, const xpcs_basis* basis, const void* X, xpcs_dtype dtype, int64_t T,
+                             float* A_out, int64_t* S_out);
+
 /* ------------------------------------------------------------------ compressed path (Eq. 8-10)
  * Two-time correlation from coefficients only (no decompression):
  *   N~_q = A G_q A^T, S~_q(t) = a_t s_q, C~_q = M_q N~_q / (S~_q(t1) S~_q(t2)),
@@ -184,25 +228,52 @@ xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* basis, const void* X, x
 xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T, xpcs_precision prec,
                          float* C_out, double* g2_out, int64_t* count_out);
 /* Autotuner of xpcs_twotime for one workload shape (rings, frames, precision, whether C
- * is stored): times each candidate configuration of the two-time kernel (tiles per work
- * item 4, 8, 16 or 32 along a tile diagonal; diagonal sums by whole 64-column strips or by
- * 32-column blocks) on these very arguments, `reps` timed calls each after one untimed
- * call, keeps the fastest in the context for later calls of that shape (the default, 8
- * tiles with strips for hi/lo operands, unless another is at least 3 % faster), and runs
- * it once more so the outputs are its own.  tiles_out, strip_out, ms_out (host, nullable): the
- * choice and its time per call.  Not during a capture. */
+ * is stored): times each candidate configuration of the two-time kernel on these very
+ * arguments, `reps` timed calls each after one untimed call, keeps the fastest in the
+ * context for later calls of that shape, and runs it once more so the outputs are its
+ * own.  Candidates: tiles per work item (1, 2, 4, 8, 16 or 32 along a tile diagonal) x schedule
+ * (0: diagonal sums by 32-column blocks, 1: by whole 64-column strips, 2: tile pairs, one
+ * N = 256 MMA for tiles (I, J) and (I, J + 1), block schedule).  The default stays unless
+ * another candidate is at least 3 % faster: 8 tiles with strips for hi/lo operands (bf16x3)
+ * and blocks otherwise when C is stored; 4 tiles with tile pairs for g2 only (C not
+ * stored, where all tiles of a work item accumulate into one accumulator).
+ * tiles_out, sched_out, ms_out (host, nullable): the choice and its time per call.  Not
+ * during a capture. */
 xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T,
                                   xpcs_precision prec, float* C_out, double* g2_out, int64_t* count_out, int reps,
-                                  int* tiles_out, int* strip_out, double* ms_out);
+                                  int* tiles_out, int* sched_out, double* ms_out);
+/* Fix the two-time configuration of this context's calls (xpcs_twotime*, xpcs_twotime_raw*)
+ * instead of the tuned or default one: `tiles` per work item (1..64) and `schedule` (0, 1
+ * or 2 as for the autotuner).  tiles = 0 returns to the automatic choice.  The results of
+ * every configuration agree up to the f32 rounding order of the g2 partial sums (the raw
+ * integer Gram and C are bit-identical).  XPCS_EINVAL for values out of range. */
+xpcs_status xpcs_twotime_config(xpcs_ctx* ctx, int tiles, int schedule);
+/* The same autotuner for xpcs_twotime_raw (arguments as that call's); the raw default is
+ * 4 tiles per work item with tile pairs. */
+xpcs_status xpcs_autotune_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X, xpcs_dtype dtype,
+                                      int64_t T, float* C_out, int64_t* N_out, double* g2_out, int64_t* count_out,
+                                      int reps, int* tiles_out, int* sched_out, double* ms_out);
 /* xpcs_twotime with a chosen normalisation (xpcs_norm); norm = XPCS_NORM_MEAN is
  * xpcs_twotime. */
 xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T,
                               xpcs_precision prec, xpcs_norm norm, float* C_out, double* g2_out,
                               int64_t* count_out);
 
+/* xpcs_twotime with every option: opt (host, NULL = defaults) gives the precision, the
+ * normalisation and the ring sums of the denominators.  With qmean = XPCS_QMEAN_EXACT_RAW,
+ * S_raw (device, n_q x T int64: the exact ring sums of the raw frames of A, from
+ * xpcs_encode_sums or xpcs_ring_sums) replaces a_t s_q in Eq. 1 (and its mean in Eq. 12);
+ * otherwise S_raw is not read and may be NULL.  XPCS_EINVAL for EXACT_RAW without S_raw or
+ * with the Frobenius normalisation (which uses no ring sums). */
+xpcs_status xpcs_twotime_opts(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A, int64_t T,
+                              const xpcs_options* opt, const int64_t* S_raw, float* C_out, double* g2_out,
+                              int64_t* count_out);
+
 /* ------------------------------------------------------------------ g2 over a stored C
  * g2_q(tau) = mean over t of C[q][t+tau][t], NaN entries skipped, from the lower
- * triangle of C (n_q x T x T float32).  g2_out n_q x T f64, count_out nullable. */
+ * triangle of C (n_q x T x T float32).  g2_out n_q x T f64, count_out nullable.
+ * n_q above XPCS_G2_MAX_RINGS returns XPCS_ERANGE. */
+#define XPCS_G2_MAX_RINGS 65535
 xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out, int64_t* count_out);
 
 /* ------------------------------------------------------------------ g2 over a stored C, no allocation
@@ -214,12 +285,16 @@ xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g
  * For callers that must not allocate while they run, e.g. a loop whose HBM is all
  * handed out under a budget, or one that cannot take the device-wide synchronisation a
  * cudaFree may imply.
- *   - n_q * T must not exceed XPCS_G2_NOALLOC_MAX_CELLS; larger calls return
- *     XPCS_ERANGE (with a message in xpcs_last_error) and launch nothing.
+ *   - n_q * T must not exceed XPCS_G2_NOALLOC_MAX_CELLS, nor n_q XPCS_G2_MAX_RINGS;
+ *     larger calls return XPCS_ERANGE (with a message in xpcs_last_error) and launch
+ *     nothing.
  *   - The first call on each device does a one-time set-up (finds the array's device
  *     address and loads the kernels, which the CUDA runtime may do by allocating):
  *     make it at start-up, before any stream capture and before the caller's
  *     no-allocation region.  Later calls only launch two kernels on the context's stream.
+ *     The array's address found at set-up belongs to the device's primary context and is
+ *     kept for the life of the process: after cudaDeviceReset, or from a context other
+ *     than the primary one, do not call this entry point.
  *   - Nothing needs to start at zero: every call overwrites the partial sums it reads.
  *   - The array is shared by every call on a device: calls that can run at the same time
  *     (on different CUDA streams or contexts of one device) race on it and give wrong
@@ -289,6 +364,12 @@ xpcs_status xpcs_graph_destroy(xpcs_graph* graph);
  * stay alive while frames are pushed; closing the stream does not read it. */
 xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t history, int max_batch,
                              xpcs_dtype dtype, xpcs_stream** out);
+/* xpcs_stream_open with options: of opt (host, NULL = defaults) only qmean is used (a
+ * stream always computes Eq. 1 in bf16x3).  With XPCS_QMEAN_EXACT_RAW every pushed frame's
+ * exact ring sums, added up from its nonzero pixels during the sparse encode, replace
+ * a_t s_q in the denominators. */
+xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t history, int max_batch,
+                                  xpcs_dtype dtype, const xpcs_options* opt, xpcs_stream** out);
 /* The row-update configuration a stream step of b frames takes for n_q rings and a k-term
  * basis (host-side, no context or device needed): *lags = the lag tile (the longest of
  * 128, 120, 96, 64, 32 with lags + b - 1 <= 128 whose layout fits shared memory),

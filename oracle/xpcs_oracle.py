@@ -31,7 +31,7 @@ import numpy as np
 __all__ = [
     "ring_index", "ring_sizes", "ring_sums", "raw_gram", "twotime_from_gram",
     "g2_from_twotime", "raw_twotime", "fit_basis", "encode", "ring_factors",
-    "compressed_ring_gram", "compressed_ring_sums", "compressed_twotime",
+    "compressed_ring_gram", "compressed_ring_sums", "compressed_twotime", "compressed_twotime_exact_sums",
     "decompress", "raw_pair_values", "compressed_pair_values", "g2_eq12",
     "frobenius_twotime", "windowed_g2", "compression_ratio_offline",
     "compression_ratio_online", "lossless_speedup", "rank_from_spectrum", "twotime_eq12",
@@ -218,6 +218,19 @@ def compressed_twotime(A: np.ndarray, G: np.ndarray, s: np.ndarray, Mq: np.ndarr
     for q in range(n_q):
         C[q] = twotime_from_gram(compressed_ring_gram(A, G[q]), St[q], St[q], Mq[q])
     return C, St
+
+
+def compressed_twotime_exact_sums(A: np.ndarray, G: np.ndarray, S: np.ndarray, Mq: np.ndarray) -> np.ndarray:
+    """Compressed two-time correlation with the exact ring sums of the raw frames in the
+    denominators: C_q = M_q N~_q(t1,t2) / (S_q(t1) S_q(t2)), with N~_q = a G_q a^T (Eq. 10)
+    and S_q(t) = sum of the ring's raw counts (the Eq. 1 means, captured when the frames are
+    encoded) instead of S~_q = a s_q.  Shape [n_q, T, T]; pairs with S <= 0 are NaN."""
+    n_q = G.shape[0]
+    T = np.asarray(A).shape[0]
+    C = np.empty((n_q, T, T))
+    for q in range(n_q):
+        C[q] = twotime_from_gram(compressed_ring_gram(A, G[q]), S[q], S[q], Mq[q])
+    return C
 
 
 # ---------------------------------------------------------------- sampled values (large sizes)

@@ -1,4 +1,4 @@
-"""Build the CUDA library libxpcs.so (sm_103a) and the C oracle in-tree.
+"""Build the CUDA library libxpcs.so (sm_103a) in-tree.
 
 Every translation unit is compiled in parallel with nvcc for sm_103a only, then linked
 into ``paper_2407_20356_gb300/lib/libxpcs.so``.  No torch types cross the library's ABI.

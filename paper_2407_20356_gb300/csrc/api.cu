@@ -139,27 +139,48 @@ void ProfScope::done() {
 
 namespace {
 
-// Work items of the two-time kernel: (q, delta, I0, I1), tiles (I, I+delta) of one tile
-// diagonal, CH tiles per item; ordered ring by ring, chunk by chunk, delta ascending.
-std::vector<int4> make_items(int n_q, int nT, int CH) {
+// Work items of the two-time kernel: (q, delta, I0, I1), the tiles (I, I+delta) of one
+// tile diagonal (with tile pairs also (I, I+delta+1); delta then runs over even values),
+// CH tiles per item.  Order, ring by ring: items of full length first, then the shorter
+// ones at the triangle's edge, so that items launched together also finish together;
+// within each group items come in blocks of consecutive e = I0 + delta (the R row block of
+// the item's first tile), all chunks c = I0 / CH of a block together.  Items with the same
+// c read the same L row blocks at every step and items with the same e the same R row
+// blocks, so the items that a persistent grid of `grid` CTAs runs at one time share their
+// operand panels in L2.
+std::vector<int4> make_items(int n_q, int nT, int CH, int pairs, int grid) {
+  const int step = pairs ? 2 : 1;
+  const int nC = (nT + CH - 1) / CH;
+  // e-block width: about `grid` items per block over all chunks
+  const int eb = std::max(step, (grid * step + nC - 1) / nC);
   std::vector<int4> items;
-  for (int q = 0; q < n_q; ++q)
-    for (int c = 0; c * CH < nT; ++c)
-      for (int d = 0; d < nT; ++d) {
+  std::vector<std::pair<long long, int4>> ring;
+  for (int q = 0; q < n_q; ++q) {
+    ring.clear();
+    for (int c = 0; c < nC; ++c)
+      for (int d = 0; d < nT; d += step) {
         const int I0 = c * CH, I1 = std::min(c * CH + CH, nT - d);
-        if (I0 < I1) items.push_back(make_int4(q, d, I0, I1));
+        if (I0 >= I1) continue;
+        const int e = I0 + d;
+        const long long full = (I1 - I0 == CH) ? 0 : 1;
+        const long long key = ((full * (nT / eb + 1) + e / eb) * (long long)nC + c) * (nT + 1) + e;
+        ring.push_back({key, make_int4(q, d, I0, I1)});
       }
+    std::sort(ring.begin(), ring.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (const auto& kv : ring) items.push_back(kv.second);
+  }
   return items;
 }
 
 // Device copy of the work items for (n_q, nT, CH), rebuilt only when they change.
-xpcs_status cached_items(xpcs_ctx* ctx, int n_q, int nT, int CH, int4** d_items, int* n_items) {
-  if (ctx->items_key[0] != n_q || ctx->items_key[1] != nT || ctx->items_key[2] != CH) {
+xpcs_status cached_items(xpcs_ctx* ctx, int n_q, int nT, int CH, int pairs, int4** d_items, int* n_items) {
+  if (ctx->items_key[0] != n_q || ctx->items_key[1] != nT || ctx->items_key[2] != CH ||
+      ctx->items_key[3] != pairs) {
     if (ctx->capturing || ctx->graphs > 0)
       return fail(ctx, XPCS_EBUSY,
                   "two-time work items of another shape cannot be built during a capture or while captured "
                   "graphs exist: run the call once before capturing");
-    const std::vector<int4> items = make_items(n_q, nT, CH);
+    const std::vector<int4> items = make_items(n_q, nT, CH, pairs, ctx->num_sms);
     const size_t bytes = items.size() * sizeof(int4);
     if (bytes > ctx->items_bytes) {
       XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -178,6 +199,7 @@ xpcs_status cached_items(xpcs_ctx* ctx, int n_q, int nT, int CH, int4** d_items,
     ctx->items_key[0] = n_q;
     ctx->items_key[1] = nT;
     ctx->items_key[2] = CH;
+    ctx->items_key[3] = pairs;
   }
   *d_items = ctx->d_items;
   *n_items = (int)ctx->items_n;
@@ -233,6 +255,15 @@ extern "C" xpcs_status xpcs_destroy(xpcs_ctx* ctx) {
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   xpcs_profile_enable(ctx, 0);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->copy_stream[i]) {
+      cudaStreamSynchronize(ctx->copy_stream[i]);
+      cudaStreamDestroy(ctx->copy_stream[i]);
+    }
+  for (int i = 0; i < 3; ++i) {
+    if (ctx->ev_loaded[i]) cudaEventDestroy(ctx->ev_loaded[i]);
+    if (ctx->ev_free[i]) cudaEventDestroy(ctx->ev_free[i]);
+  }
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return XPCS_OK;
@@ -416,9 +447,8 @@ namespace {
 struct RawBuffers {
   __nv_bfloat16* Xp;
   long long* S;
-  long long* S2;  // per-frame sums of squares (Frobenius normalisation only)
+  long long* S2;  // per-frame sums of squares (the exactness bound; Frobenius scales)
   double* Sbar;   // ring means of S (Eq. 12 normalisation only)
-  unsigned long long* sq;
   float* r;
   uint32_t* blk_bad;
   float* partials;
@@ -430,7 +460,6 @@ struct RawBuffers {
 // Ingest (ring-sorted bf16 copy + ring sums) and the per-frame factors of Eq. 1.
 xpcs_status raw_ingest(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_dtype dtype, int64_t T, int T_pad,
                        int nT, bool want_xp, long long* S, RawBuffers& b) {
-  XPCS_CUDA(ctx, cudaMemsetAsync(b.sq, 0, R->n_q * sizeof(unsigned long long), ctx->stream));
   RawIngestParams ip{};
   ip.X = X;
   ip.dtype = dtype;
@@ -444,7 +473,6 @@ xpcs_status raw_ingest(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_d
   ip.Xp = want_xp ? b.Xp : nullptr;
   ip.S = S;
   ip.S2 = b.S2;
-  ip.sq = b.sq;
   ip.status = ctx->d_status;
   XPCS_LAUNCH(ctx, "ingest", 1, launch_raw_ingest(ip, ctx->stream));
   return XPCS_OK;
@@ -456,15 +484,8 @@ extern "C" xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* R, const 
                                       int64_t T, int64_t* S_out) {
   if (!ctx || !R || !X || !S_out || T <= 0 || R->ctx != ctx) return fail(ctx, XPCS_EINVAL, "bad ring_sums args");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
-  Carve c;
-  c.take<unsigned long long>(R->n_q);
-  XPCS_TRY(ensure_scratch(ctx, c.off));
-  c = Carve{0, static_cast<char*>(ctx->scratch)};
-  RawBuffers b{};
-  b.sq = c.take<unsigned long long>(R->n_q);
   // ring sums only: the ingest kernel covers exactly T frames
   RawIngestParams ip{};
-  XPCS_CUDA(ctx, cudaMemsetAsync(b.sq, 0, R->n_q * sizeof(unsigned long long), ctx->stream));
   ip.X = X;
   ip.dtype = dtype;
   ip.T = T;
@@ -476,7 +497,7 @@ extern "C" xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* R, const 
   ip.n_q = R->n_q;
   ip.Xp = nullptr;
   ip.S = reinterpret_cast<long long*>(S_out);
-  ip.sq = b.sq;
+  ip.S2 = nullptr;
   ip.status = ctx->d_status;
   XPCS_LAUNCH(ctx, "ingest", 1, launch_raw_ingest(ip, ctx->stream));
   return finish(ctx);
@@ -484,23 +505,25 @@ extern "C" xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* R, const 
 
 namespace {
 
-// Shared tail of both two-time paths: the Gram launch, pair counts and g2.
-// Two-time configuration for a workload shape: the autotuner's choice if there is one, else
-// CHUNK_TILES tiles per work item and the whole-strip diagonal schedule for hi/lo operand
-// pieces (the faster one there when measured), the block schedule otherwise.
-std::pair<int, int> gram_tune_for(xpcs_ctx* ctx, uint64_t key, int split) {
+// Two-time configuration for a workload shape, (tiles per work item, schedule) with
+// schedule 0 = 32-column diagonal blocks, 1 = whole 64-column strips, 2 = tile pairs (N =
+// 256 MMAs, block schedule): the autotuner's choice if there is one, else the given default.
+std::pair<int, int> gram_tune_for(xpcs_ctx* ctx, uint64_t key, std::pair<int, int> dflt) {
   if (ctx->tune_forced) return ctx->tune_force;
+  if (ctx->user_config.first > 0) return ctx->user_config;
   const auto it = ctx->gram_tune.find(key);
   if (it != ctx->gram_tune.end()) return it->second;
-  return {CHUNK_TILES, split};
+  return dflt;
 }
+
+// Shared tail of both two-time paths: the Gram launch, pair counts and g2.
 
 xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap& tmR, GramParams gp, int n_q,
                         int64_t T, int T_pad, int nT, int maxC, uint32_t* vbits, long long* count,
                         double* g2_out) {
   int4* d_items = nullptr;
   int n_items = 0;
-  XPCS_TRY(cached_items(ctx, n_q, nT, gp.CH, &d_items, &n_items));
+  XPCS_TRY(cached_items(ctx, n_q, nT, gp.CH, gp.pairs, &d_items, &n_items));
   gp.items = d_items;
   gp.n_items = n_items;
   const int grid = std::min<int>(gp.n_items, ctx->num_sms);
@@ -514,6 +537,14 @@ xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap
 }
 
 }  // namespace
+
+extern "C" xpcs_status xpcs_twotime_config(xpcs_ctx* ctx, int tiles, int schedule) {
+  if (!ctx) return XPCS_EINVAL;
+  if (tiles < 0 || tiles > 64 || schedule < 0 || schedule > 2)
+    return fail(ctx, XPCS_EINVAL, "twotime_config: tiles must be 0..64 and schedule 0..2");
+  ctx->user_config = {tiles, schedule};
+  return XPCS_OK;
+}
 
 extern "C" xpcs_status xpcs_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* R, const void* X, xpcs_dtype dtype,
                                         int64_t T, float* C_out, int64_t* N_out, double* g2_out, int64_t* count_out) {
@@ -531,7 +562,8 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   const int n_q = R->n_q;
   const int nT = (int)((T + TILE - 1) / TILE);
   const int T_pad = nT * TILE;
-  const std::pair<int, int> tune = gram_tune_for(ctx, gram_tune_key(n_q, nT, 1, 0, 1, C_out || N_out), 0);
+  const std::pair<int, int> tune =
+      gram_tune_for(ctx, gram_tune_key(n_q, nT, 1, 0, 1, C_out || N_out), gram_default_raw());
   const int CH = tune.first;
   const int maxC = (nT + CH - 1) / CH;
   const bool want_g2 = g2_out != nullptr;
@@ -539,9 +571,8 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   auto layout = [&](Carve& c, RawBuffers& b) {
     b.Xp = c.take<__nv_bfloat16>((size_t)T_pad * R->Mp);
     b.S = c.take<long long>((size_t)n_q * T);
-    b.S2 = norm == XPCS_NORM_FROB ? c.take<long long>((size_t)n_q * T) : nullptr;
+    b.S2 = c.take<long long>((size_t)n_q * T);
     b.Sbar = norm == XPCS_NORM_EQ12 ? c.take<double>(n_q) : nullptr;
-    b.sq = c.take<unsigned long long>(n_q);
     b.r = c.take<float>((size_t)n_q * T_pad);
     b.blk_bad = c.take<uint32_t>((size_t)n_q * nT);
     b.partials = want_g2 ? c.take<float>((size_t)n_q * nT * maxC * DIAG_SLOTS) : nullptr;
@@ -559,11 +590,14 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   if (norm == XPCS_NORM_EQ12)
     XPCS_LAUNCH(ctx, "ring_mean", 1, launch_ring_mean(b.S, n_q, T, b.Sbar, ctx->stream));
   XPCS_LAUNCH(ctx, "raw_scales", 1,
-              launch_raw_scales(b.S, b.S2, b.Sbar, (int)norm, R->d_Mq, n_q, T, T_pad, nT, b.sq, b.r, b.blk_bad,
+              launch_raw_scales(b.S, b.S2, b.Sbar, (int)norm, R->d_Mq, n_q, T, T_pad, nT, b.r, b.blk_bad,
                                 ctx->d_status, ctx->stream));
-  CUtensorMap tm;
+  const int pairs = tune.second == 2;
+  CUtensorMap tm, tmR;
   XPCS_TRY(make_map(ctx, &tm, b.Xp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, R->Mp, T_pad, KCH, TILE,
                     CU_TENSOR_MAP_SWIZZLE_128B));
+  XPCS_TRY(make_map(ctx, &tmR, b.Xp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, R->Mp, T_pad, KCH,
+                    pairs ? 2 * TILE : TILE, CU_TENSOR_MAP_SWIZZLE_128B));
   GramParams gp{};
   gp.T = (int)T;
   gp.nT = nT;
@@ -576,14 +610,16 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   gp.fmt = 1;
   gp.split = 0;
   gp.raw = 1;
-  gp.strip = tune.second;
+  gp.strip = tune.second == 1;
+  gp.pairs = pairs;
+  gp.merge = 0;
   gp.r = b.r;
   gp.blk_bad = b.blk_bad;
   gp.C = C_out;
   gp.Nout = reinterpret_cast<long long*>(N_out);
   gp.partials = b.partials;
   gp.status = ctx->d_status;
-  XPCS_TRY(run_twotime(ctx, tm, tm, gp, n_q, T, T_pad, nT, maxC, b.vbits, want_cnt ? b.count : nullptr, g2_out));
+  XPCS_TRY(run_twotime(ctx, tm, tmR, gp, n_q, T, T_pad, nT, maxC, b.vbits, want_cnt ? b.count : nullptr, g2_out));
   return finish(ctx);
 }
 
@@ -840,23 +876,40 @@ extern "C" int xpcs_rank_from_spectrum(const double* sigma, int n, double factor
 
 extern "C" xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* B, const float* A, int64_t T,
                                     xpcs_precision prec, float* C_out, double* g2_out, int64_t* count_out) {
-  return xpcs_twotime_norm(ctx, B, A, T, prec, XPCS_NORM_MEAN, C_out, g2_out, count_out);
+  const xpcs_options o{(int)prec, XPCS_NORM_MEAN, XPCS_QMEAN_COMPRESSED};
+  return xpcs_twotime_opts(ctx, B, A, T, &o, nullptr, C_out, g2_out, count_out);
 }
 
 extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, const float* A, int64_t T,
                                          xpcs_precision prec, xpcs_norm norm, float* C_out, double* g2_out,
                                          int64_t* count_out) {
+  const xpcs_options o{(int)prec, (int)norm, XPCS_QMEAN_COMPRESSED};
+  return xpcs_twotime_opts(ctx, B, A, T, &o, nullptr, C_out, g2_out, count_out);
+}
+
+extern "C" xpcs_status xpcs_twotime_opts(xpcs_ctx* ctx, const xpcs_basis* B, const float* A, int64_t T,
+                                         const xpcs_options* opt, const int64_t* S_raw, float* C_out,
+                                         double* g2_out, int64_t* count_out) {
+  const xpcs_options o = opt ? *opt : xpcs_options{0, 0, 0};
+  const xpcs_precision prec = (xpcs_precision)o.precision;
+  const xpcs_norm norm = (xpcs_norm)o.norm;
   if (!ctx || !B || !A || T <= 0 || B->ctx != ctx || (int)prec < 0 || (int)prec > 2 || (int)norm < 0 ||
-      (int)norm > 2)
+      (int)norm > 2 || o.qmean < 0 || o.qmean > 1)
     return fail(ctx, XPCS_EINVAL, "bad twotime args");
+  const bool exact = o.qmean == XPCS_QMEAN_EXACT_RAW;
+  if (exact && (!S_raw || norm == XPCS_NORM_FROB))
+    return fail(ctx, XPCS_EINVAL, "qmean EXACT_RAW needs the raw ring sums S_raw and a ring-sum normalisation");
+  const long long* S_exact = exact ? reinterpret_cast<const long long*>(S_raw) : nullptr;
   if (T > (1 << 24)) return fail(ctx, XPCS_ENOTSUP, "T too large");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int n_q = B->rings->n_q, k = B->k;
   const int nT = (int)((T + TILE - 1) / TILE);
   const int T_pad = nT * TILE;
   const bool split = prec == XPCS_PREC_BF16X3;
-  const std::pair<int, int> tune = gram_tune_for(
-      ctx, gram_tune_key(n_q, nT, prec == XPCS_PREC_FP16 ? 0 : 1, split ? 1 : 0, 0, C_out != nullptr), split ? 1 : 0);
+  const bool merge = C_out == nullptr && g2_out != nullptr;  // g2 only: one diagonal pass per item
+  const std::pair<int, int> tune =
+      gram_tune_for(ctx, gram_tune_key(n_q, nT, prec == XPCS_PREC_FP16 ? 0 : 1, split ? 1 : 0, 0, C_out != nullptr),
+                    gram_default_compressed(split, merge));
   const int CH = tune.first;
   const int maxC = (nT + CH - 1) / CH;
   const int nkp = (k + KCH - 1) / KCH;           // 64-wide chunks per operand piece
@@ -926,9 +979,14 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   pp.St = nullptr;
   pp.norm = (int)norm;
   pp.Sbar = b.Sbar;
+  pp.S_exact = S_exact;
   pp.skip_L = use_tc ? 1 : 0;
-  if (norm == XPCS_NORM_EQ12)
-    XPCS_LAUNCH(ctx, "coef_mean", 1, launch_coef_mean(A, T, k, B->d_s, n_q, b.Sbar, ctx->stream));
+  if (norm == XPCS_NORM_EQ12) {
+    if (S_exact)  // mean of the exact ring sums
+      XPCS_LAUNCH(ctx, "ring_mean", 1, launch_ring_mean(S_exact, n_q, T, b.Sbar, ctx->stream));
+    else
+      XPCS_LAUNCH(ctx, "coef_mean", 1, launch_coef_mean(A, T, k, B->d_s, n_q, b.Sbar, ctx->stream));
+  }
   XPCS_LAUNCH(ctx, "compressed_prep", 1, launch_prep_compressed(pp, ctx->stream));
   if (use_tc) {
     XPCS_LAUNCH(ctx, "coef_pieces", 1, launch_coef_pieces(A, T, k, kq, T_pad, b.Apair, ctx->stream));
@@ -948,9 +1006,11 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   }
   const CUtensorMapDataType dt =
       prec == XPCS_PREC_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const int pairs = tune.second == 2;
   CUtensorMap tmL, tmR;
   XPCS_TRY(make_map(ctx, &tmL, b.L, dt, 2, Kc, (uint64_t)n_q * T_pad, KCH, TILE, CU_TENSOR_MAP_SWIZZLE_128B));
-  XPCS_TRY(make_map(ctx, &tmR, b.R, dt, 2, Kc, (uint64_t)n_q * T_pad, KCH, TILE, CU_TENSOR_MAP_SWIZZLE_128B));
+  XPCS_TRY(make_map(ctx, &tmR, b.R, dt, 2, Kc, (uint64_t)n_q * T_pad, KCH, pairs ? 2 * TILE : TILE,
+                    CU_TENSOR_MAP_SWIZZLE_128B));
   GramParams gp{};
   gp.T = (int)T;
   gp.nT = nT;
@@ -963,7 +1023,9 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
   gp.fmt = prec == XPCS_PREC_FP16 ? 0 : 1;
   gp.split = split ? 1 : 0;
   gp.raw = 0;
-  gp.strip = tune.second;
+  gp.strip = tune.second == 1;
+  gp.pairs = pairs;
+  gp.merge = merge ? 1 : 0;
   gp.r = b.r;
   gp.blk_bad = b.blk_bad;
   gp.C = C_out;
@@ -979,11 +1041,12 @@ extern "C" xpcs_status xpcs_twotime_norm(xpcs_ctx* ctx, const xpcs_basis* B, con
 extern "C" xpcs_status xpcs_g2(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out,
                                int64_t* count_out) {
   if (!ctx || !C || !g2_out || n_q <= 0 || T <= 0) return fail(ctx, XPCS_EINVAL, "bad g2 args");
+  if (n_q > XPCS_G2_MAX_RINGS)
+    return fail(ctx, XPCS_ERANGE,
+                "xpcs_g2: n_q = " + std::to_string(n_q) + " rings exceeds the limit of " +
+                    std::to_string(XPCS_G2_MAX_RINGS));
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
-  const int64_t lag_blocks = (T + TILE - 1) / TILE;
-  const int64_t blocks = lag_blocks * n_q;
-  const int target = 8 * ctx->num_sms;
-  const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, (target + blocks - 1) / blocks));
+  const int splits = g2_from_C_splits(T, n_q, ctx->num_sms);
   Carve c0;
   c0.take<double>((size_t)splits * n_q * T);
   c0.take<long long>((size_t)splits * n_q * T);

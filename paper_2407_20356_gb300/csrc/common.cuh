@@ -1,8 +1,10 @@
 // Shared device helpers for the sm_103a kernels: mbarriers, TMA, tcgen05 (TMEM + MMA).
 //
-// All waits are bounded: a wait that does not complete within XPCS_WAIT_NS nanoseconds
-// of %globaltimer records an error code in the kernel's status word and returns false,
-// and the caller unwinds (frees its TMEM and exits) instead of spinning forever.
+// All waits are bounded: a wait that does not complete within its limit (nanoseconds of
+// %globaltimer) records an error code in the kernel's status word and returns false, and
+// the caller unwinds (frees its TMEM and exits) instead of spinning forever.  The limit is
+// the context's (or stream's) setting, a u64 stored 8 bytes after the status word; 0
+// there, or no status word, means XPCS_WAIT_NS.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -62,14 +64,32 @@ XPCS_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait until the phase with the given parity has completed. Bounded by XPCS_WAIT_NS.
+// Bounded-wait limit of the kernel whose status word is `status` (see above).
+XPCS_DEV uint64_t wait_limit_ns(const uint32_t* status) {
+  if (status) {
+    const uint64_t v = *reinterpret_cast<const volatile uint64_t*>(status + 2);
+    if (v) return v;
+  }
+  return XPCS_WAIT_NS;
+}
+
+// Wait until the phase with the given parity has completed, within the kernel's limit.
+// Every limit is at least 1 ms, so the limit word (device or host-mapped memory) is read
+// only once a wait has already lasted that long: short waits never touch it.
 XPCS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
+  uint64_t limit = 1000000ull;  // 1 ms, until the real limit is read
+  bool have_limit = false;
   while (true) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > XPCS_WAIT_NS) {
+    const uint64_t dt = globaltimer() - t0;
+    if (dt > limit && !have_limit) {
+      limit = wait_limit_ns(status);
+      have_limit = true;
+    }
+    if (dt > limit) {
       set_status(status, XPCS_DEV_TIMEOUT);
       return false;
     }

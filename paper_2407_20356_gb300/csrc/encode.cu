@@ -332,14 +332,19 @@ static int pick_splits(int n_m, long long M_pad, int num_sms) {
   return best;
 }
 
-extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const void* X, xpcs_dtype dtype, int64_t T,
-                                   float* A_out) {
-  if (!ctx || !B || !X || !A_out || T <= 0 || B->ctx != ctx || (dtype != XPCS_U8 && dtype != XPCS_U16))
-    return fail(ctx, XPCS_EINVAL, "bad encode args");
-  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+// Partial-sum floats an encode of T frames needs (its pixel splits x padded frames x k).
+static size_t encode_partials(const xpcs_basis* B, int64_t T, int num_sms) {
+  const int nT = (int)((T + TILE - 1) / TILE);
+  const int n_mp = (nT + encode_frame_blocks(B->k) - 1) / encode_frame_blocks(B->k);
+  return (size_t)pick_splits(n_mp, B->M_pad, num_sms) * nT * TILE * B->k;
+}
+
+// Enqueue the encode of T frames X (device) into A_out on the context's stream, with
+// `partials` (encode_partials floats) as its split-K scratch.
+static xpcs_status enqueue_encode(xpcs_ctx* ctx, const xpcs_basis* B, const void* X, xpcs_dtype dtype, int64_t T,
+                                  float* A_out, float* partials) {
   const int64_t M = B->rings->M;
   const int eb = dtype == XPCS_U8 ? 1 : 2;
-  if ((M * eb) % 16) return fail(ctx, XPCS_ENOTSUP, "encode needs M*elem_bytes to be a multiple of 16");
   const int k = B->k;
   const int nT = (int)((T + TILE - 1) / TILE);
   const int T_pad = nT * TILE;
@@ -347,11 +352,6 @@ extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const voi
   const int n_mp = (nT + mb - 1) / mb;  // work items: groups of mb frame blocks x pixel splits
   const int n_split = pick_splits(n_mp, B->M_pad, ctx->num_sms);
   const long long per = ((B->M_pad + n_split - 1) / n_split + KCH - 1) / KCH * KCH;
-  Carve c0;
-  c0.take<float>((size_t)n_split * T_pad * k);
-  XPCS_TRY(ensure_scratch(ctx, c0.off));
-  Carve c{0, static_cast<char*>(ctx->scratch)};
-  float* partials = c.take<float>((size_t)n_split * T_pad * k);
   CUtensorMap tmX, tmB;
   XPCS_TRY(make_map(ctx, &tmX, X, dtype == XPCS_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
                     eb, M, T, KCH, TILE, dtype == XPCS_U8 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B));
@@ -372,5 +372,92 @@ extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const voi
   XPCS_LAUNCH(ctx, "encode", 1, launch_encode(tmX, tmB, p, std::min(n_items, ctx->num_sms), ctx->stream));
   XPCS_LAUNCH(ctx, "encode_reduce", 1,
               launch_encode_reduce(partials, n_split, T, T_pad, k, std::ldexp(1.0f, -B->enc_log2), A_out, ctx->stream));
+  return XPCS_OK;
+}
+
+static xpcs_status encode_args(xpcs_ctx* ctx, const xpcs_basis* B, const void* X, xpcs_dtype dtype, int64_t T,
+                               float* A_out) {
+  if (!ctx || !B || !X || !A_out || T <= 0 || B->ctx != ctx || (dtype != XPCS_U8 && dtype != XPCS_U16))
+    return fail(ctx, XPCS_EINVAL, "bad encode args");
+  if ((B->rings->M * (dtype == XPCS_U8 ? 1 : 2)) % 16)
+    return fail(ctx, XPCS_ENOTSUP, "encode needs M*elem_bytes to be a multiple of 16");
+  return XPCS_OK;
+}
+
+extern "C" xpcs_status xpcs_encode(xpcs_ctx* ctx, const xpcs_basis* B, const void* X, xpcs_dtype dtype, int64_t T,
+                                   float* A_out) {
+  XPCS_TRY(encode_args(ctx, B, X, dtype, T, A_out));
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  Carve c0;
+  c0.take<float>(encode_partials(B, T, ctx->num_sms));
+  XPCS_TRY(ensure_scratch(ctx, c0.off));
+  Carve c{0, static_cast<char*>(ctx->scratch)};
+  float* partials = c.take<float>(encode_partials(B, T, ctx->num_sms));
+  XPCS_TRY(enqueue_encode(ctx, B, X, dtype, T, A_out, partials));
   return finish(ctx);
+}
+
+// Encode of frames in host memory with the host-to-device copy overlapped: the frames go
+// in blocks of ENC_HOST_BLOCK frames through ENC_HOST_BUFS device staging buffers, the
+// copies alternating between two copy streams (so two copy engines can run at once), and
+// each block is encoded on the context's stream as soon as it has landed while the next
+// blocks are copied.  A buffer is refilled only after the encode that read it is done.
+// The frames should be in pinned memory (pageable memory is copied synchronously).
+constexpr int ENC_HOST_BUFS = 3;
+
+extern "C" xpcs_status xpcs_encode_host(xpcs_ctx* ctx, const xpcs_basis* B, const void* X_host, xpcs_dtype dtype,
+                                        int64_t T, float* A_out) {
+  XPCS_TRY(encode_args(ctx, B, X_host, dtype, T, A_out));
+  if (ctx->capturing) return fail(ctx, XPCS_EBUSY, "xpcs_encode_host cannot be captured");
+  XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t fb = (size_t)B->rings->M * (dtype == XPCS_U8 ? 1 : 2);  // bytes per frame
+  // blocks of about 256 MB, a multiple of 128 frames
+  const int64_t blk = std::max<int64_t>(TILE, std::min<int64_t>(T, ((256ll << 20) / (int64_t)fb) / TILE * TILE));
+  const size_t part = encode_partials(B, blk, ctx->num_sms);
+  Carve c0;
+  for (int i = 0; i < ENC_HOST_BUFS; ++i) c0.take<char>((size_t)blk * fb);
+  c0.take<float>(part);
+  XPCS_TRY(ensure_scratch(ctx, c0.off));
+  Carve c{0, static_cast<char*>(ctx->scratch)};
+  char* stage[ENC_HOST_BUFS];
+  for (int i = 0; i < ENC_HOST_BUFS; ++i) stage[i] = c.take<char>((size_t)blk * fb);
+  float* partials = c.take<float>(part);
+  if (!ctx->copy_stream[0]) {
+    for (int i = 0; i < 2; ++i)
+      XPCS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream[i], cudaStreamNonBlocking));
+    for (int i = 0; i < ENC_HOST_BUFS; ++i) {
+      XPCS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_loaded[i], cudaEventDisableTiming));
+      XPCS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_free[i], cudaEventDisableTiming));
+    }
+  }
+  // the staging buffers are scratch: earlier work on the context's stream may still use it
+  XPCS_CUDA(ctx, cudaEventRecord(ctx->ev_free[0], ctx->stream));
+  for (int i = 1; i < ENC_HOST_BUFS; ++i) XPCS_CUDA(ctx, cudaEventRecord(ctx->ev_free[i], ctx->stream));
+  const char* src = static_cast<const char*>(X_host);
+  for (int64_t t0 = 0, i = 0; t0 < T; t0 += blk, ++i) {
+    const int64_t n = std::min(blk, T - t0);
+    const int buf = (int)(i % ENC_HOST_BUFS);
+    cudaStream_t cs = ctx->copy_stream[i % 2];
+    XPCS_CUDA(ctx, cudaStreamWaitEvent(cs, ctx->ev_free[buf], 0));
+    XPCS_CUDA(ctx, cudaMemcpyAsync(stage[buf], src + (size_t)t0 * fb, (size_t)n * fb, cudaMemcpyHostToDevice, cs));
+    XPCS_CUDA(ctx, cudaEventRecord(ctx->ev_loaded[buf], cs));
+    XPCS_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_loaded[buf], 0));
+    XPCS_TRY(enqueue_encode(ctx, B, stage[buf], dtype, n, A_out + (size_t)t0 * B->k, partials));
+    XPCS_CUDA(ctx, cudaEventRecord(ctx->ev_free[buf], ctx->stream));
+  }
+  return finish(ctx);
+}
+
+// Encode plus the exact ring sums of the raw frames (the XPCS_QMEAN_EXACT_RAW option): the
+// encode, then the ring-sum pass of the raw path over the same frames, both on the
+// context's stream; waits once at the end unless the context is asynchronous.
+extern "C" xpcs_status xpcs_encode_sums(xpcs_ctx* ctx, const xpcs_basis* B, const void* X, xpcs_dtype dtype,
+                                        int64_t T, float* A_out, int64_t* S_out) {
+  if (!ctx || !B || !S_out) return fail(ctx, XPCS_EINVAL, "bad encode_sums args");
+  const bool async = ctx->async;
+  ctx->async = true;
+  xpcs_status st = xpcs_encode(ctx, B, X, dtype, T, A_out);
+  if (st == XPCS_OK) st = xpcs_ring_sums(ctx, B->rings, X, dtype, T, S_out);
+  ctx->async = async;
+  return st == XPCS_OK ? finish(ctx) : st;
 }

@@ -11,7 +11,10 @@
 // loads the two kernels into the context, either of which the runtime may do by
 // allocating); make that first call at start-up, before any stream capture and before
 // the point from which the caller must not allocate.  Every later call on that device
-// only launches two kernels.
+// only launches two kernels.  The address found at set-up belongs to the device's primary
+// context and is kept for the life of the process: a caller that resets the device
+// (cudaDeviceReset) or runs the library in another context of it must not call this
+// entry point afterwards.
 //
 // Nothing in the array has to start at zero: the first kernel writes every partial sum
 // the second one reads, for every call.  The array is shared by all calls on a device,
@@ -65,6 +68,10 @@ xpcs_status setup(xpcs_ctx* ctx, void** out) {
 extern "C" xpcs_status xpcs_g2_noalloc(xpcs_ctx* ctx, const float* C, int n_q, int64_t T, double* g2_out,
                                        int64_t* count_out) {
   if (!ctx || !C || !g2_out || n_q <= 0 || T <= 0) return fail(ctx, XPCS_EINVAL, "bad g2 args");
+  if (n_q > XPCS_G2_MAX_RINGS)
+    return fail(ctx, XPCS_ERANGE,
+                "xpcs_g2_noalloc: n_q = " + std::to_string(n_q) + " rings exceeds the limit of " +
+                    std::to_string(XPCS_G2_MAX_RINGS));
   if (T > XPCS_G2_NOALLOC_MAX_CELLS || (int64_t)n_q * T > XPCS_G2_NOALLOC_MAX_CELLS)
     return fail(ctx, XPCS_ERANGE,
                 "xpcs_g2_noalloc: n_q * T = " + std::to_string((int64_t)n_q * T) + " exceeds its fixed scratch of " +
@@ -73,10 +80,8 @@ extern "C" xpcs_status xpcs_g2_noalloc(xpcs_ctx* ctx, const float* C, int n_q, i
   void* base = nullptr;
   XPCS_TRY(setup(ctx, &base));
   const int64_t cells = (int64_t)n_q * T;
-  // row splits as in xpcs_g2 (about 8 blocks per SM), capped by what the array holds
-  const int64_t blocks = (T + TILE - 1) / TILE * n_q;
-  const int64_t target = 8 * (int64_t)ctx->num_sms;
-  int64_t splits = std::max<int64_t>(1, std::min<int64_t>(64, (target + blocks - 1) / blocks));
+  // row splits as in xpcs_g2, capped by what the array holds
+  int64_t splits = g2_from_C_splits(T, n_q, ctx->num_sms);
   splits = std::min<int64_t>(splits, XPCS_G2_NOALLOC_MAX_CELLS / cells);
   double* part = static_cast<double*>(base);
   long long* cpart = reinterpret_cast<long long*>(static_cast<char*>(base) + (size_t)splits * cells * sizeof(double));

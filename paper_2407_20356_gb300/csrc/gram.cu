@@ -16,15 +16,29 @@
 //
 // Structure (one CTA per SM, persistent over work items):
 //   warp 0      TMA producer: 64-wide K chunks of the L and R row blocks, NSTAGE ring
-//   warp 1      TMEM allocator and MMA issuer: 128x128 f32 accumulator, 2 TMEM buffers
+//   warp 1      TMEM allocator and MMA issuer: f32 accumulators, 2 TMEM buffers
 //   warps 2..5  drain: TMEM -> registers -> C store
 //   warps 6..13 TMEM -> registers -> per-warp skewed 32x32 blocks -> diagonal sums
 // Any warp may read the TMEM lanes of its quarter (warp id mod 4), so both groups read
 // the accumulator independently; they meet only at the TMEM full/empty barriers, and the
 // C stores of one tile overlap the diagonal pass of another.
 //
-// Work item = (q, delta, I0, I1): the tiles (I, I+delta) for I in [I0, I1) of one tile
-// diagonal.  Its diagonal sums go to one partial slot; no atomics, deterministic.
+// Tile pairs (NP = 2): one MMA of N = 256 multiplies the 128 L rows of block I with the
+// 256 R rows of blocks J and J + 1, so one L chunk in shared memory serves two tiles and a
+// stage carries 1.5 operand panels per tile instead of 2; the accumulator holds tile
+// (I, J) in columns 0..127 and tile (I, J + 1) in columns 128..255.  A work item then runs
+// along two neighbouring tile diagonals, delta (even) and delta + 1; where J + 1 is past
+// the last tile block the MMA is issued with N = 128 and the second half is not used.
+//
+// Work item = (q, delta, I0, I1): the tiles (I, I+delta) (and (I, I+delta+1) for pairs)
+// for I in [I0, I1).  The diagonal sums of each tile diagonal of an item go to one partial
+// slot; no atomics, deterministic.
+//
+// Merged items (compressed path, g2 only, C not stored): every tile of an item lies on one
+// tile diagonal, and element (i, j) of each of them belongs to lag 128 delta + j - i, so
+// the diagonal sums of the item are the diagonal sums of the SUM of its tiles.  The MMAs
+// of all its tiles then accumulate into one TMEM accumulator and the diagonal pass runs
+// once per item instead of once per tile.
 //
 // C store: C is symmetric, so tile (I, J >= I) is written transposed into the lower
 // triangle, straight from registers and fully coalesced.
@@ -49,35 +63,41 @@ namespace xpcs {
 
 namespace {
 
-#ifndef XPCS_GRAM_NSTAGE
-#define XPCS_GRAM_NSTAGE 3
-#endif
-constexpr int NSTAGE = XPCS_GRAM_NSTAGE;           // operand stages (one K chunk of L and R each)
-constexpr int CHUNK_BYTES = TILE * KCH * 2;        // one operand chunk: 128 rows x 128 B
-constexpr int STAGE_BYTES = 2 * CHUNK_BYTES;       // L + R
 constexpr int N_DIAG_WARPS = 8;
 constexpr int Q_LD = 36;                               // skewed buffer row: 32 floats + 4 pad
-constexpr int RED_FLOATS = N_DIAG_WARPS * 3 * 32;      // per-warp sums of a work item
 constexpr int GRAM_THREADS = 64 + 4 * 32 + N_DIAG_WARPS * 32;  // producer, MMA, 4 drain, 8 diagonal warps
 constexpr int BAR_BYTES = 256;
-// Shared memory of the kernel for one diagonal schedule (STRIP: whole 64-column strip,
-// 96 skewed rows per warp; otherwise one 32-column block at a time, 64 rows).
-template <bool STRIP>
-struct GramSmem {
+constexpr int SMEM_MAX = 227 * 1024;
+constexpr int DIAG_BAR = 1;                        // named barrier of the eight diagonal warps
+
+// Shared-memory layout and pipeline depth of one configuration: STRIP = whole 64-column
+// strips (96 skewed rows per diagonal warp) or one 32-column block at a time (64 rows);
+// NP = tiles per accumulator (1, or 2 for tile pairs).  As many operand stages as fit,
+// at most four.
+template <bool STRIP, int NP>
+struct GramCfg {
   static constexpr int q_rows = STRIP ? 96 : 64;
   static constexpr int priv = q_rows * Q_LD;  // floats of one warp's skewed buffer
-  static constexpr int diag_bytes = (N_DIAG_WARPS * priv + RED_FLOATS) * 4;
-  static constexpr int bytes = 1024 + NSTAGE * STAGE_BYTES + diag_bytes + BAR_BYTES;
-  static_assert(bytes <= 227 * 1024, "shared memory of one CTA");
+  static constexpr int red_floats = NP * N_DIAG_WARPS * 3 * 32;  // per-warp sums of a work item
+  static constexpr int diag_bytes = (N_DIAG_WARPS * priv + red_floats) * 4;
+  static constexpr int chunk_l = TILE * KCH * 2;       // L chunk: 128 rows x 128 B
+  static constexpr int chunk_r = NP * TILE * KCH * 2;  // R chunk: 128 NP rows x 128 B
+  static constexpr int stage_bytes = chunk_l + chunk_r;
+  static constexpr int fixed = 1024 + diag_bytes + BAR_BYTES;
+  static constexpr int fit = (SMEM_MAX - fixed) / stage_bytes;
+  static constexpr int nstage = fit > 4 ? 4 : fit;
+  static constexpr int bytes = fixed + nstage * stage_bytes;
+  static constexpr uint32_t tmem_cols = 2 * NP * TILE;  // two accumulators
+  static_assert(nstage >= 3, "at least three operand stages");
+  static_assert(bytes <= SMEM_MAX, "shared memory of one CTA");
+  static_assert(tmem_cols == 256 || tmem_cols == 512, "TMEM allocation is a power of two");
 };
-constexpr uint32_t TMEM_COLS = 256;                // two 128-column accumulators
-constexpr int DIAG_BAR = 1;                        // named barrier of the eight diagonal warps
 
 // Stores one 32-column chunk of a tile row: element (i, j) of tile (I, J) is C(t1, t2)
 // with t1 = 128 I + i, t2 = 128 J + j, written transposed at [t2][t1] (lower triangle) so
 // that for a fixed j the warp's 32 lanes write 32 consecutive values.  Raw mode also
 // writes the exact integer Gram N and scales the accumulator by r(t1) r(t2).
-__device__ __forceinline__ void store_chunk(const GramParams& p, uint32_t (&v)[32], int q, int I, int J, int col0,
+__device__ __forceinline__ void store_chunk(const GramParams& p, uint32_t (&v)[32], int q, int J, int col0,
                                             long long t1, float ri, const float* rq, bool bad, bool interior) {
   const long long T = p.T;
   const float* rj = rq + (size_t)J * TILE + col0;
@@ -113,16 +133,27 @@ __device__ __forceinline__ void store_chunk(const GramParams& p, uint32_t (&v)[3
   }
 }
 
-template <bool STRIP>
+// Tiles of work item w that share one accumulator ("unit" u): one tile (pair) per unit,
+// or the whole item when merged.
+struct UnitRange {
+  int I_begin, I_end;
+};
+__device__ __forceinline__ UnitRange unit_range(const GramParams& p, const int4& w, int u) {
+  return p.merge ? UnitRange{w.z, w.w} : UnitRange{w.z + u, w.z + u + 1};
+}
+__device__ __forceinline__ int units_of(const GramParams& p, const int4& w) { return p.merge ? 1 : w.w - w.z; }
+
+template <bool STRIP, int NP>
 __global__ void __launch_bounds__(GRAM_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR,
                const GramParams p) {
+  using CF = GramCfg<STRIP, NP>;
+  constexpr int NSTAGE = CF::nstage;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stages = smem;
-  float* diag_smem = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);
-  using SM = GramSmem<STRIP>;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES + SM::diag_bytes);
+  float* diag_smem = reinterpret_cast<float*>(smem + NSTAGE * CF::stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * CF::stage_bytes + CF::diag_bytes);
   uint64_t* full = bars;                    // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;          // [NSTAGE]
   uint64_t* tfull = bars + 2 * NSTAGE;      // [2]
@@ -148,7 +179,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     *abort_flag = 0;
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_alloc(tmem_slot, CF::tmem_cols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -181,10 +212,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
             }
             // split: chunk 2 kc holds the hi pieces of K-block kc, chunk 2 kc + 1 the lo pieces
             const int x = koff + (p.split ? ((c & 1) * nk + (c >> 1)) * KCH : c * KCH);
-            uint8_t* st = stages + s * STAGE_BYTES;
-            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            uint8_t* st = stages + s * CF::stage_bytes;
+            mbar_arrive_expect_tx(&full[s], CF::stage_bytes);
             tma_load_2d(st, &tmL, &full[s], x, rowbase + I * TILE);
-            tma_load_2d(st + CHUNK_BYTES, &tmR, &full[s], x, rowbase + J * TILE);
+            // NP x 128 rows of R (rows past the matrix are filled with zeros)
+            tma_load_2d(st + CF::chunk_l, &tmR, &full[s], x, rowbase + J * TILE);
           }
         }
       }
@@ -196,58 +228,67 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_f16(p.fmt, TILE, TILE);
-      uint32_t it = 0, tile = 0;
+      const uint32_t idesc1 = idesc_f16(p.fmt, TILE, TILE);
+      const uint32_t idesc2 = idesc_f16(p.fmt, TILE, NP * TILE);
+      uint32_t it = 0, unit = 0;
       bool ok = true, issued = false;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const int4 w = p.items[item];
         const int nk = p.k_chunks[w.x];
         const int nc = p.split ? 2 * nk : nk;
-        for (int I = w.z; I < w.w && ok; ++I, ++tile) {
-          const uint32_t b = tile & 1, tph = (tile >> 1) & 1;
+        const int n_units = units_of(p, w);
+        for (int u = 0; u < n_units && ok; ++u, ++unit) {
+          const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
           if (*abort_flag || !mbar_wait(&tempty[b], tph ^ 1, p.status)) {
             *abort_flag = 1;
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t d = tmem_base + b * TILE;
-          for (int c = 0; c < nc; ++c, ++it) {
-            const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
-            if (*abort_flag || !mbar_wait(&full[s], ph, p.status)) {
-              *abort_flag = 1;
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint8_t* st = stages + s * STAGE_BYTES;
-            const uint64_t ad = smem_desc_sw128(st);
-            const uint64_t bd = smem_desc_sw128(st + CHUNK_BYTES);
-            if (!p.split) {
-#pragma unroll
-              for (int kk = 0; kk < KCH / 16; ++kk)  // 16 elements = 32 B per MMA
-                tc_mma_f16(d, ad + 2 * kk, bd + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-              tc_commit(&empty[s]);
-            } else if ((c & 1) == 0) {
-              // hi pieces: L_hi R_hi now; the stage stays until the lo pieces arrive
-#pragma unroll
-              for (int kk = 0; kk < KCH / 16; ++kk)
-                tc_mma_f16(d, ad + 2 * kk, bd + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-            } else {
-              // lo pieces: L_lo R_hi and L_hi R_lo with the previous stage's hi pieces
-              const uint32_t sp = (it - 1) % NSTAGE;
-              const uint8_t* sth = stages + sp * STAGE_BYTES;
-              const uint64_t adh = smem_desc_sw128(sth);
-              const uint64_t bdh = smem_desc_sw128(sth + CHUNK_BYTES);
-#pragma unroll
-              for (int kk = 0; kk < KCH / 16; ++kk) {
-                tc_mma_f16(d, ad + 2 * kk, bdh + 2 * kk, idesc, 1u);
-                tc_mma_f16(d, adh + 2 * kk, bd + 2 * kk, idesc, 1u);
+          const uint32_t d = tmem_base + b * (NP * TILE);
+          const UnitRange ur = unit_range(p, w, u);
+          bool first = true;  // the unit's first MMA overwrites the accumulator
+          for (int I = ur.I_begin; I < ur.I_end && ok; ++I) {
+            // tile pair when the second tile exists, else N = 128 (first half only)
+            const uint32_t idesc = (NP == 2 && I + w.y + 1 < p.nT) ? idesc2 : idesc1;
+            for (int c = 0; c < nc; ++c, ++it) {
+              const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
+              if (*abort_flag || !mbar_wait(&full[s], ph, p.status)) {
+                *abort_flag = 1;
+                ok = false;
+                break;
               }
-              tc_commit(&empty[sp]);
-              tc_commit(&empty[s]);
+              tc_fence_after();
+              const uint8_t* st = stages + s * CF::stage_bytes;
+              const uint64_t ad = smem_desc_sw128(st);
+              const uint64_t bd = smem_desc_sw128(st + CF::chunk_l);
+              if (!p.split) {
+#pragma unroll
+                for (int kk = 0; kk < KCH / 16; ++kk)  // 16 elements = 32 B per MMA
+                  tc_mma_f16(d, ad + 2 * kk, bd + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
+                tc_commit(&empty[s]);
+              } else if ((c & 1) == 0) {
+                // hi pieces: L_hi R_hi now; the stage stays until the lo pieces arrive
+#pragma unroll
+                for (int kk = 0; kk < KCH / 16; ++kk)
+                  tc_mma_f16(d, ad + 2 * kk, bd + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
+              } else {
+                // lo pieces: L_lo R_hi and L_hi R_lo with the previous stage's hi pieces
+                const uint32_t sp = (it - 1) % NSTAGE;
+                const uint8_t* sth = stages + sp * CF::stage_bytes;
+                const uint64_t adh = smem_desc_sw128(sth);
+                const uint64_t bdh = smem_desc_sw128(sth + CF::chunk_l);
+#pragma unroll
+                for (int kk = 0; kk < KCH / 16; ++kk) {
+                  tc_mma_f16(d, ad + 2 * kk, bdh + 2 * kk, idesc, 1u);
+                  tc_mma_f16(d, adh + 2 * kk, bd + 2 * kk, idesc, 1u);
+                }
+                tc_commit(&empty[sp]);
+                tc_commit(&empty[s]);
+              }
+              first = false;
+              issued = true;
             }
-            issued = true;
           }
           if (!ok) break;
           tc_commit(&tfull[b]);
@@ -263,25 +304,32 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     // ------------------------------------------------------------ drain warps (2..5)
     // One warp per TMEM lane quarter: thread = tile row i.  TMEM -> registers -> C store,
     // transposed into the lower triangle: for a fixed column j the warp's 32 lanes write
-    // 32 consecutive floats of output row t2.
+    // 32 consecutive floats of output row t2.  (Merged units store no C: nothing to do.)
     const int quarter = warp & 3;
     const int i_row = quarter * 32 + lane;
     const long long T = p.T;
-    const bool work = p.C || p.Nout;
-    uint32_t tile = 0;
+    const bool work = (p.C || p.Nout) && !p.merge;
+    uint32_t unit = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
       const int4 w = p.items[item];
       const int q = w.x, delta = w.y;
       const float* rq = p.r + (size_t)q * p.T_pad;
-      for (int I = w.z; I < w.w; ++I, ++tile) {
-        const int J = I + delta;
-        const uint32_t b = tile & 1, tph = (tile >> 1) & 1;
+      const int n_units = units_of(p, w);
+      for (int u = 0; u < n_units; ++u, ++unit) {
+        const int I = unit_range(p, w, u).I_begin;
+        const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
         // per-tile metadata first, so its load latency overlaps the wait for the MMA
         const long long t1 = (long long)I * TILE + i_row;
         const float ri = rq[t1];
-        const bool bad = p.blk_bad[(size_t)q * p.nT + I] | p.blk_bad[(size_t)q * p.nT + J];
-        const bool interior = !bad && (long long)(I + 1) * TILE <= T && (long long)(J + 1) * TILE <= T;
+        const int nh = (NP == 2 && I + delta + 1 < p.nT) ? 2 : 1;
+        bool bad[NP], interior[NP];
+#pragma unroll
+        for (int h2 = 0; h2 < NP; ++h2) {
+          const int J = I + delta + h2;
+          bad[h2] = h2 < nh && (p.blk_bad[(size_t)q * p.nT + I] | p.blk_bad[(size_t)q * p.nT + J]);
+          interior[h2] = !bad[h2] && (long long)(I + 1) * TILE <= T && (long long)(J + 1) * TILE <= T;
+        }
         if (!mbar_wait_warp(&tfull[b], tph, p.status)) {  // warp-uniform outcome
           *abort_flag = 1;
           ok = false;
@@ -289,15 +337,20 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
         }
         tc_fence_after();
         if (work) {
-          const uint32_t tbase = tmem_base + b * TILE + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+          for (int h2 = 0; h2 < NP; ++h2) {
+            if (h2 >= nh) break;
+            const int J = I + delta + h2;
+            const uint32_t tbase = tmem_base + b * (NP * TILE) + h2 * TILE + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-          for (int cc = 0; cc < 4; cc += 2) {
-            uint32_t v0[32], v1[32];
-            tmem_ld32(tbase + 32 * cc, v0);
-            tmem_ld32(tbase + 32 * cc + 32, v1);
-            tc_wait_ld();
-            store_chunk(p, v0, q, I, J, 32 * cc, t1, ri, rq, bad, interior);
-            store_chunk(p, v1, q, I, J, 32 * cc + 32, t1, ri, rq, bad, interior);
+            for (int cc = 0; cc < 4; cc += 2) {
+              uint32_t v0[32], v1[32];
+              tmem_ld32(tbase + 32 * cc, v0);
+              tmem_ld32(tbase + 32 * cc + 32, v1);
+              tc_wait_ld();
+              store_chunk(p, v0, q, J, 32 * cc, t1, ri, rq, bad[h2], interior[h2]);
+              store_chunk(p, v1, q, J, 32 * cc + 32, t1, ri, rq, bad[h2], interior[h2]);
+            }
           }
         }
         tc_fence_before();
@@ -308,28 +361,33 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   } else if (p.partials) {
     // ------------------------------------------------------------ diagonal warps (6..13)
     // Warp dw (0..7) covers TMEM lane quarter r = warp mod 4 (tile rows 32 r ..) and
-    // column half h = dw / 4 (blocks b = 2 h, 2 h + 1).  Block b's sums land on tile
-    // diagonals 32 (b - r) + d (rows i < 32 - d) and 32 (b - r - 1) + d (the others), so
-    // the warp keeps three per-lane sums, for e = 2 h - r - 1 + k (k = 0, 1, 2), diagonal
-    // 32 e + lane.
+    // column half h = dw / 4 (blocks b = 2 h, 2 h + 1) of each tile of the accumulator.
+    // Block b's sums land on tile diagonals 32 (b - r) + d (rows i < 32 - d) and
+    // 32 (b - r - 1) + d (the others), so the warp keeps three per-lane sums per tile
+    // diagonal, for e = 2 h - r - 1 + k (k = 0, 1, 2), diagonal 32 e + lane.
     const int dw = warp - 6;
     const int r = warp & 3;
     const int h = dw >> 2;
-    float* Q = diag_smem + dw * SM::priv;
-    float* red = diag_smem + N_DIAG_WARPS * SM::priv;  // [warp][k][lane]
+    float* Q = diag_smem + dw * CF::priv;
+    float* red = diag_smem + N_DIAG_WARPS * CF::priv;  // [half][warp][k][lane]
     const int i_row = r * 32 + lane;
-    for (int x = lane; x < SM::priv; x += 32) Q[x] = 0.f;  // entries never written stay 0
+    for (int x = lane; x < CF::priv; x += 32) Q[x] = 0.f;  // entries never written stay 0
     float* qw = Q + (32 - lane) * Q_LD + lane;                // element (lane, j) at qw[Q_LD * j]
-    uint32_t tile = 0;
+    uint32_t unit = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
       const int4 w = p.items[item];
       const int q = w.x, delta = w.y;
       const float* rq = p.r + (size_t)q * p.T_pad;
-      float acc[3] = {0.f, 0.f, 0.f};
-      for (int I = w.z; I < w.w && ok; ++I, ++tile) {
-        const int J = I + delta;
-        const uint32_t b = tile & 1, tph = (tile >> 1) & 1;
+      // the item's second tile diagonal (pairs) holds tiles
+      const bool has2 = NP == 2 && w.z + delta + 1 < p.nT;
+      float acc[NP][3];
+#pragma unroll
+      for (int h2 = 0; h2 < NP; ++h2) acc[h2][0] = acc[h2][1] = acc[h2][2] = 0.f;
+      const int n_units = units_of(p, w);
+      for (int u = 0; u < n_units && ok; ++u, ++unit) {
+        const int I = unit_range(p, w, u).I_begin;
+        const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
         const float ri = p.raw ? rq[(size_t)I * TILE + i_row] : 1.f;
         if (*abort_flag || !mbar_wait_warp(&tfull[b], tph, p.status)) {  // warp-uniform outcome
           *abort_flag = 1;
@@ -337,75 +395,92 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           break;
         }
         tc_fence_after();
-        const uint32_t tbase = tmem_base + b * TILE + ((uint32_t)(r * 32) << 16) + 64 * h;
-        const float* rj = rq + (size_t)J * TILE + 64 * h;
-        if constexpr (STRIP) {
-          // whole strip: row 32 k + lane holds strip diagonal 32 (k - 1) + lane (acc[k])
-          __syncwarp();  // the previous tile's row sums are read
+        const int nh = (NP == 2 && (p.merge ? has2 : I + delta + 1 < p.nT)) ? 2 : 1;
 #pragma unroll
-          for (int sb = 0; sb < 2; ++sb) {
-            uint32_t v[32];
-            tmem_ld32(tbase + 32 * sb, v);
-            tc_wait_ld();
-            if (sb == 1) {  // TMEM is released once block 1 is in registers
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&tempty[b]);
+        for (int h2 = 0; h2 < NP; ++h2) {
+          if (h2 >= nh) break;
+          const bool last = h2 == nh - 1;  // TMEM is released after the unit's last load
+          const uint32_t tbase =
+              tmem_base + b * (NP * TILE) + h2 * TILE + ((uint32_t)(r * 32) << 16) + 64 * h;
+          const float* rj = rq + (size_t)(I + delta + h2) * TILE + 64 * h;
+          if constexpr (STRIP) {
+            // whole strip: row 32 k + lane holds strip diagonal 32 (k - 1) + lane (acc[k])
+            __syncwarp();  // the previous tile's row sums are read
+#pragma unroll
+            for (int sb = 0; sb < 2; ++sb) {
+              uint32_t v[32];
+              tmem_ld32(tbase + 32 * sb, v);
+              tc_wait_ld();
+              if (last && sb == 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+              }
+              if (p.raw) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                  v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
+              }
+#pragma unroll
+              for (int j = 0; j < 32; ++j) qw[Q_LD * (32 * sb + j)] = __uint_as_float(v[j]);
             }
-            if (p.raw) {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) qw[Q_LD * (32 * sb + j)] = __uint_as_float(v[j]);
-          }
-          __syncwarp();
-          acc[0] += skew_row_sum<Q_LD>(Q, lane, 32 - lane, 32);
-          acc[1] += skew_row_sum<Q_LD>(Q, 32 + lane, 0, 32);
-          acc[2] += skew_row_sum<Q_LD>(Q, 64 + lane, 0, 32 - lane);
-        } else {
-          // one 32-column block at a time: row lane holds block diagonal lane - 32 (acc[sb]),
-          // row 32 + lane block diagonal lane (acc[sb + 1])
-#pragma unroll
-          for (int sb = 0; sb < 2; ++sb) {
-            uint32_t v[32];
-            tmem_ld32(tbase + 32 * sb, v);
-            tc_wait_ld();
-            if (sb == 1) {
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&tempty[b]);
-            }
-            if (p.raw) {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
-            }
-            __syncwarp();  // the previous block's row sums are read
-#pragma unroll
-            for (int j = 0; j < 32; ++j) qw[Q_LD * j] = __uint_as_float(v[j]);
             __syncwarp();
-            acc[sb] += skew_row_sum<Q_LD>(Q, lane, 32 - lane, 32);
-            acc[sb + 1] += skew_row_sum<Q_LD>(Q, 32 + lane, 0, 32 - lane);
+            acc[h2][0] += skew_row_sum<Q_LD>(Q, lane, 32 - lane, 32);
+            acc[h2][1] += skew_row_sum<Q_LD>(Q, 32 + lane, 0, 32);
+            acc[h2][2] += skew_row_sum<Q_LD>(Q, 64 + lane, 0, 32 - lane);
+          } else {
+            // one 32-column block at a time: row lane holds block diagonal lane - 32
+            // (acc[sb]), row 32 + lane block diagonal lane (acc[sb + 1])
+#pragma unroll
+            for (int sb = 0; sb < 2; ++sb) {
+              uint32_t v[32];
+              tmem_ld32(tbase + 32 * sb, v);
+              tc_wait_ld();
+              if (last && sb == 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+              }
+              if (p.raw) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                  v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
+              }
+              __syncwarp();  // the previous block's row sums are read
+#pragma unroll
+              for (int j = 0; j < 32; ++j) qw[Q_LD * j] = __uint_as_float(v[j]);
+              __syncwarp();
+              acc[h2][sb] += skew_row_sum<Q_LD>(Q, lane, 32 - lane, 32);
+              acc[h2][sb + 1] += skew_row_sum<Q_LD>(Q, 32 + lane, 0, 32 - lane);
+            }
           }
         }
       }
       // every diagonal warp reaches these barriers once per item, also after an abort
       // (each of its waits is bounded), so none is left waiting
 #pragma unroll
-      for (int k = 0; k < 3; ++k) red[(dw * 3 + k) * 32 + lane] = acc[k];
+      for (int h2 = 0; h2 < NP; ++h2)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) red[((h2 * N_DIAG_WARPS + dw) * 3 + k) * 32 + lane] = acc[h2][k];
       named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
       if (ok && !*abort_flag) {
-        // warp dw finishes diagonals 32 (dw - 4) + lane, adding the warps in a fixed order
+        // warp dw finishes diagonals 32 (dw - 4) + lane of each tile diagonal, adding the
+        // warps in a fixed order
         const int e = dw - 4;
-        float sum = 0.f;
-#pragma unroll
-        for (int u = 0; u < N_DIAG_WARPS; ++u) {
-          const int k = e - (2 * (u >> 2) - ((u + 6) & 3) - 1);
-          if (k >= 0 && k < 3) sum += red[(u * 3 + k) * 32 + lane];
-        }
         const int chunk = w.z / p.CH;
-        float* slot = p.partials + (((size_t)q * p.nT + delta) * p.maxC + chunk) * DIAG_SLOTS;
-        slot[32 * dw + lane] = sum;
+#pragma unroll
+        for (int h2 = 0; h2 < NP; ++h2) {
+          if (h2 == 1 && !has2) break;
+          const float* rh = red + h2 * N_DIAG_WARPS * 3 * 32;
+          float sum = 0.f;
+#pragma unroll
+          for (int u = 0; u < N_DIAG_WARPS; ++u) {
+            const int k = e - (2 * (u >> 2) - ((u + 6) & 3) - 1);
+            if (k >= 0 && k < 3) sum += rh[(u * 3 + k) * 32 + lane];
+          }
+          float* slot = p.partials + (((size_t)q * p.nT + delta + h2) * p.maxC + chunk) * DIAG_SLOTS;
+          slot[32 * dw + lane] = sum;
+        }
       }
       named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);  // red is free again
       if (!ok || *abort_flag) break;
@@ -416,33 +491,40 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, TMEM_COLS);
+    tmem_dealloc(tmem_base, CF::tmem_cols);
   }
 }
 
 }  // namespace
 
-int gram_smem_bytes() { return GramSmem<true>::bytes > GramSmem<false>::bytes ? GramSmem<true>::bytes : GramSmem<false>::bytes; }
+int gram_smem_bytes() {
+  int m = GramCfg<true, 1>::bytes;
+  m = GramCfg<false, 1>::bytes > m ? GramCfg<false, 1>::bytes : m;
+  return GramCfg<false, 2>::bytes > m ? GramCfg<false, 2>::bytes : m;
+}
 
-template <bool STRIP>
+template <bool STRIP, int NP>
 static cudaError_t launch_gram_t(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
                                  cudaStream_t st) {
-  constexpr int smem = GramSmem<STRIP>::bytes;
+  constexpr int smem = GramCfg<STRIP, NP>::bytes;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<STRIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<STRIP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  gram_tc_kernel<STRIP><<<grid, GRAM_THREADS, smem, st>>>(tmL, tmR, p);
+  gram_tc_kernel<STRIP, NP><<<grid, GRAM_THREADS, smem, st>>>(tmL, tmR, p);
   return cudaGetLastError();
 }
 
-// the diagonal schedule is a parameter (chosen per call: the whole-strip schedule for hi/lo
-// operand pieces and the block schedule otherwise unless an autotuned choice says otherwise)
+// The diagonal schedule and the tile pairing are parameters of the call: tile pairs take
+// the 32-column block schedule (the whole-strip buffers leave too little shared memory for
+// three stages of 48 KB); otherwise the strip schedule for hi/lo operand pieces and the
+// block schedule for single operands unless an autotuned choice says otherwise.
 cudaError_t launch_gram(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
                         cudaStream_t st) {
-  return p.strip ? launch_gram_t<true>(tmL, tmR, p, grid, st) : launch_gram_t<false>(tmL, tmR, p, grid, st);
+  if (p.pairs) return launch_gram_t<false, 2>(tmL, tmR, p, grid, st);
+  return p.strip ? launch_gram_t<true, 1>(tmL, tmR, p, grid, st) : launch_gram_t<false, 1>(tmL, tmR, p, grid, st);
 }
 
 }  // namespace xpcs

@@ -28,7 +28,8 @@ struct xpcs_ctx {
   std::string err;
   std::mutex err_mu;  // error text may be written from a server's scheduler thread
   int num_sms = 0;
-  uint32_t* d_status = nullptr;
+  uint32_t* d_status = nullptr;  // status word; the u64 8 bytes after it is the wait limit
+  uint64_t wait_ns = 0;          // bounded-wait limit of the context's kernels (0: default)
   void* scratch = nullptr;
   size_t scratch_cap = 0;
   cusolverDnHandle_t solver = nullptr;
@@ -36,7 +37,7 @@ struct xpcs_ctx {
   // work items of the two-time kernel, cached for the last (n_q, nT, CH)
   int4* d_items = nullptr;
   size_t items_n = 0, items_bytes = 0;
-  int items_key[3] = {-1, -1, -1};
+  int items_key[4] = {-1, -1, -1, -1};  // (n_q, nT, tiles per item, tile pairs)
   bool prof = false;
   std::vector<xpcs_prof_entry> prof_entries;
   std::vector<cudaEvent_t> event_pool;
@@ -45,13 +46,19 @@ struct xpcs_ctx {
   // basis copies) may move or change
   // two-time configuration per workload shape (key from gram_tune_key), set by the
   // autotuner; `forced` overrides everything while the autotuner times a candidate
-  std::map<uint64_t, std::pair<int, int>> gram_tune;  // key -> (tiles per work item, strip)
+  std::map<uint64_t, std::pair<int, int>> gram_tune;  // key -> (tiles per work item, schedule)
   bool tune_forced = false;
   std::pair<int, int> tune_force{0, 0};
+  std::pair<int, int> user_config{0, 0};  // xpcs_twotime_config: (tiles, schedule); tiles 0 = automatic
   bool capturing = false;
   bool async_before_capture = false;
   uint64_t launches_at_capture = 0;
   int graphs = 0;
+  // xpcs_encode_host: two copy streams and the events of its staging buffers (made on
+  // first use)
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};
+  cudaEvent_t ev_loaded[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_free[3] = {nullptr, nullptr, nullptr};
 };
 
 struct xpcs_rings {
@@ -119,6 +126,10 @@ struct xpcs_stream {
   float* d_a = nullptr;              // max_batch x k
   __nv_bfloat16* d_W2 = nullptr;     // (max_batch n_q) x 2 kpad  r_q(t) a_t G_q, bf16 hi | lo
   double* d_g2 = nullptr;            // n_q x W read-out buffer
+  // XPCS_QMEAN_EXACT_RAW: the stream's own copy of the ring labels (M) and a step's exact
+  // ring sums (64 x n_q), both null otherwise
+  int* d_qmap = nullptr;
+  long long* d_Sx = nullptr;
   int kpad = 0;                      // k rounded up to 64
   CUtensorMap tmA, tmW, tmR;         // tensor maps of d_A2, d_W2 (64 x 128 boxes) and d_Rh
   // tensor maps of d_g2sum and d_cnt (row pitch Wp), one per row-update lag tile RT_LTS[i]
@@ -173,6 +184,19 @@ xpcs_status finish(xpcs_ctx* ctx);
 xpcs_status make_map(xpcs_ctx* ctx, CUtensorMap* map, const void* base, CUtensorMapDataType dt, int elem_bytes,
                      uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw,
                      uint64_t pitch_bytes = 0);
+
+// Default two-time configurations (tiles per work item, schedule: 0 = 32-column diagonal
+// blocks, 1 = whole 64-column strips, 2 = tile pairs with the block schedule), from timings
+// on one GB300.  Raw counts: tile pairs, 4 tiles per item (the long K loop is bound by
+// operand traffic, which pairs cut by a quarter; 512x512, T = 10^4: 28.0 ms against 38.3 ms
+// with single tiles).  Compressed with C stored: strips for hi/lo operand pieces, blocks
+// otherwise (bound by the C stores).  Compressed g2 only (merged items, one diagonal pass
+// per item): tile pairs, 4 tiles per item.
+inline std::pair<int, int> gram_default_raw() { return {4, 2}; }
+inline std::pair<int, int> gram_default_compressed(bool split, bool merge) {
+  if (merge) return {4, 2};
+  return {CHUNK_TILES, split ? 1 : 0};
+}
 
 // Key of a two-time workload shape in the context's tuning table.
 inline uint64_t gram_tune_key(int n_q, int nT, int fmt, int split, int raw, bool C) {

@@ -43,6 +43,10 @@ struct GramParams {
                            //    C = L_hi R_hi + L_lo R_hi + L_hi R_lo
   int raw;                 // 1: C = acc * r(t1) * r(t2); 0: operands already scaled
   int strip;               // diagonal schedule: 1 whole 64-column strips, 0 32-column blocks
+  int pairs;               // 1: tile pairs (I, J), (I, J + 1) per accumulator (N = 256 MMA);
+                           //    items then cover the tile diagonals delta (even) and delta + 1
+  int merge;               // 1: the tiles of an item accumulate into one accumulator (compressed
+                           //    path, g2 only, no C store); the diagonal pass runs once per item
   const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined
   const uint32_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
   float* C;                // nullable [n_q][T][T]
@@ -67,20 +71,18 @@ struct RawIngestParams {
   const int* pos_ring;     // [Mp] ring of position or -1
   int n_q;
   __nv_bfloat16* Xp;       // [T_pad][Mp] (nullable when only sums are wanted)
-  long long* S;            // [n_q][T]
-  long long* S2;           // nullable [n_q][T] per-frame sum of squared counts
-  unsigned long long* sq;  // [n_q] max over frames of sum of squares (atomicMax)
+  long long* S;            // [n_q][T] (accumulated with atomics; the launch zeroes it)
+  long long* S2;           // nullable [n_q][T] per-frame sum of squared counts (likewise)
   uint32_t* status;
 };
 cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st);
 
 // r[q][t] for the chosen normalisation (xpcs_norm) from the raw int64 sums S, the
 // per-frame sums of squares S2 (FROB) or the ring means Sbar (EQ12), and block flags
-// (also flags XPCS_DEV_RANGE when a ring's max sum of squares reaches 2^24)
+// (also flags XPCS_DEV_RANGE when a frame's sum of squares over a ring reaches 2^24)
 cudaError_t launch_raw_scales(const long long* S, const long long* S2, const double* Sbar, int norm,
-                              const long long* Mq, int n_q, long long T, int T_pad, int nT,
-                              const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status,
-                              cudaStream_t st);
+                              const long long* Mq, int n_q, long long T, int T_pad, int nT, float* r,
+                              uint32_t* blk_bad, uint32_t* status, cudaStream_t st);
 // Sbar[q] = mean over T frames of S[q][t]
 cudaError_t launch_ring_mean(const long long* S, int n_q, long long T, double* Sbar, cudaStream_t st);
 // Sbar[q] = (column means of A) . s_q, the compressed ring sum averaged over T frames
@@ -106,6 +108,7 @@ struct PrepParams {
   double* St;              // nullable [n_q][T] compressed ring sums
   int norm;                // xpcs_norm
   const double* Sbar;      // [n_q] mean compressed ring sums (XPCS_NORM_EQ12)
+  const long long* S_exact;  // nullable [n_q][T] exact raw ring sums (XPCS_QMEAN_EXACT_RAW)
   int skip_L;              // 1: ring sums, scales and R rows only (L from the tensor-core kernel)
 };
 
@@ -133,6 +136,15 @@ cudaError_t launch_counts(const float* r, int n_q, long long T, int T_pad, uint3
                           long long* count, cudaStream_t st);
 cudaError_t launch_g2_finalize(const float* partials, const long long* count, int n_q, long long T, int nT,
                                int maxC, int CH, double* g2, cudaStream_t st);
+// Row splits of the g2-over-C kernel: enough CTAs for about 8 per SM, and no CTA walking
+// more than about 1024 rows (its rows are a serial chain of loads), at most 64.
+inline int g2_from_C_splits(long long T, int n_q, int num_sms) {
+  const long long blocks = (T + TILE - 1) / TILE * n_q;
+  const long long by_sms = (8LL * num_sms + blocks - 1) / blocks;
+  const long long by_rows = (T + 1023) / 1024;
+  const long long s = by_sms > by_rows ? by_sms : by_rows;
+  return (int)(s < 1 ? 1 : (s > 64 ? 64 : s));
+}
 cudaError_t launch_g2_from_C(const float* C, int n_q, long long T, double* partial, int row_splits,
                              long long* cnt_partial, cudaStream_t st);
 cudaError_t launch_g2_from_C_reduce(const double* partial, const long long* cnt_partial, int n_q, long long T,
@@ -176,6 +188,8 @@ struct StreamStep {
   const float* G32;        // n_q x k x k
   const double* s64;       // n_q x k
   const long long* Mq;     // n_q
+  const int* qmap;         // nullable M ring labels: with Sx, exact ring sums of the frames
+  long long* Sx;           // nullable b x n_q exact ring sums (zeroed by the step launch)
   float* part;             // b x nblk x k
   float* a;                // b x k
   __nv_bfloat16* W2;       // (max_batch n_q) x 2 kpad: w_q(t) rows, bf16 hi | lo

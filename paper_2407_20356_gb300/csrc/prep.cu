@@ -11,84 +11,110 @@ namespace xpcs {
 
 namespace {
 
-constexpr int MAX_RINGS_SMEM = 1024;
 
 // ---------------------------------------------------------------- raw ingest (ring sums)
-// One CTA per (padded) frame.  Gathers the frame's pixels into ring-sorted order as bf16
-// (exact for counts <= 256) and accumulates S_q(t) = sum of counts and the sum of squares
-// per ring (Eq. 1 denominators and the exactness bound of the f32 Gram).
-// Each warp step covers 64 consecutive sorted positions (2 per lane).  Ring segments
-// start at multiples of 64, so those 64 positions belong to one ring (or its padding),
-// which the first position names: the warp reduces its counts with shuffles and issues
-// one shared atomic per step.  A warp issues the loads of RI_U steps before using any of
-// them, so that enough gathers are in flight to cover the memory latency.
-constexpr int RI_U = 4;
+// Grid (position chunks of RI_CHUNK ring-sorted positions, groups of RI_F frames).  A CTA
+// stages its chunk of the position -> pixel map in shared memory once, then for each of
+// its frames gathers the counts into ring-sorted order as bf16 (exact for counts <= 256),
+// written as coalesced rows of the operand, and accumulates S_q(t) = sum of counts and the
+// sum of squares per ring (Eq. 1 denominators and the exactness bound of the f32 Gram).
+// Ring segments start at multiples of 64 positions, so each 64-position group belongs to
+// one ring (or its padding): the warp that gathers a group reduces it with shuffles, and at
+// the end the CTA adds its groups ring by ring into S and S2 with one 64-bit atomic per
+// (ring, frame) it touched (the launch zeroes S and S2).  A warp issues all its gathers of
+// a frame (16 per thread) before using any of them.
+constexpr int RI_CHUNK = 4096;            // positions per CTA (a multiple of 64)
+constexpr int RI_GROUPS = RI_CHUNK / 64;  // 64-position groups per chunk
+constexpr int RI_F = 8;                   // frames per CTA
+constexpr int RI_J = RI_GROUPS / 8;       // groups per warp (8 warps)
+
 __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p) {
-  __shared__ unsigned long long ssum[MAX_RINGS_SMEM];
-  __shared__ unsigned long long ssq[MAX_RINGS_SMEM];
-  const long long t = blockIdx.x;
+  __shared__ int sperm[RI_CHUNK];
+  __shared__ int sring[RI_GROUPS];
+  __shared__ unsigned long long gsum[RI_F][RI_GROUPS];
+  __shared__ unsigned long long gsq[RI_F][RI_GROUPS];
+  const long long P0 = (long long)blockIdx.x * RI_CHUNK;
+  const long long t0 = (long long)blockIdx.y * RI_F;
+  const int npos = (int)min((long long)RI_CHUNK, p.Mp - P0);  // a multiple of 64
+  const int ngrp = npos / 64;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int q = threadIdx.x; q < p.n_q; q += blockDim.x) {
-    ssum[q] = 0;
-    ssq[q] = 0;
-  }
+  for (int i = threadIdx.x; i < RI_CHUNK; i += blockDim.x) sperm[i] = i < npos ? p.perm[P0 + i] : -1;
+  for (int g = threadIdx.x; g < RI_GROUPS; g += blockDim.x) sring[g] = g < ngrp ? p.pos_ring[P0 + 64 * g] : -1;
   __syncthreads();
-  const bool live = t < p.T;
   bool too_big = false;
-  const uint8_t* x8 = static_cast<const uint8_t*>(p.X) + t * p.M;
-  const uint16_t* x16 = static_cast<const uint16_t*>(p.X) + t * p.M;
-  for (long long base = (long long)warp * 64 * RI_U; base < p.Mp; base += 64 * RI_U * 8) {
-    int2 src[RI_U];
-    int qs[RI_U];
+  for (int f = 0; f < RI_F; ++f) {
+    const long long t = t0 + f;
+    if (t >= p.T_pad) break;  // CTA-uniform
+    const bool live = t < p.T;
+    const uint8_t* x8 = static_cast<const uint8_t*>(p.X) + t * p.M;
+    const uint16_t* x16 = static_cast<const uint16_t*>(p.X) + t * p.M;
+    unsigned a[RI_J], b[RI_J];
 #pragma unroll
-    for (int u = 0; u < RI_U; ++u) {
-      const long long o = base + 64 * u + 2 * lane;
-      const bool in = base + 64 * u < p.Mp;
-      src[u] = in ? *reinterpret_cast<const int2*>(p.perm + o) : make_int2(-1, -1);
-      qs[u] = in ? p.pos_ring[base + 64 * u] : -1;
-    }
-    unsigned x0[RI_U], x1[RI_U];
-#pragma unroll
-    for (int u = 0; u < RI_U; ++u) {
-      x0[u] = 0;
-      x1[u] = 0;
+    for (int j = 0; j < RI_J; ++j) {
+      const int o = 64 * (warp + 8 * j) + 2 * lane;
+      const int sa = sperm[o], sb = sperm[o + 1];  // -1 for padding and past the chunk
+      a[j] = 0;
+      b[j] = 0;
       if (live) {
-        if (src[u].x >= 0) x0[u] = p.dtype == 0 ? (unsigned)x8[src[u].x] : (unsigned)x16[src[u].x];
-        if (src[u].y >= 0) x1[u] = p.dtype == 0 ? (unsigned)x8[src[u].y] : (unsigned)x16[src[u].y];
+        if (sa >= 0) a[j] = p.dtype == 0 ? (unsigned)x8[sa] : (unsigned)x16[sa];
+        if (sb >= 0) b[j] = p.dtype == 0 ? (unsigned)x8[sb] : (unsigned)x16[sb];
       }
     }
 #pragma unroll
-    for (int u = 0; u < RI_U; ++u) {
-      const long long o = base + 64 * u + 2 * lane;
-      if (base + 64 * u >= p.Mp) break;  // warp-uniform
-      const bool big = (x0[u] > 256u) | (x1[u] > 256u);
+    for (int j = 0; j < RI_J; ++j) {
+      const int g = warp + 8 * j;
+      if (g >= ngrp) break;  // warp-uniform
+      const int o = 64 * g + 2 * lane;
+      const bool big = (a[j] > 256u) | (b[j] > 256u);
       too_big |= big;
       if (p.Xp) {
-        __nv_bfloat162 v = __floats2bfloat162_rn((float)x0[u], (float)x1[u]);
-        *reinterpret_cast<__nv_bfloat162*>(p.Xp + t * p.Mp + o) = v;
+        const __nv_bfloat162 v = __floats2bfloat162_rn((float)a[j], (float)b[j]);
+        *reinterpret_cast<__nv_bfloat162*>(p.Xp + t * p.Mp + P0 + o) = v;
       }
-      const int q = qs[u];
-      if (q < 0) continue;
-      if (!__any_sync(0xffffffffu, big)) {
-        const unsigned s = __reduce_add_sync(0xffffffffu, x0[u] + x1[u]);
-        const unsigned s2 = __reduce_add_sync(0xffffffffu, x0[u] * x0[u] + x1[u] * x1[u]);
-        if (lane == 0 && s) {
-          atomicAdd(&ssum[q], (unsigned long long)s);
-          atomicAdd(&ssq[q], (unsigned long long)s2);
+      unsigned long long s1, s2;
+      if (!__any_sync(0xffffffffu, big)) {  // squares < 2^17 per lane: 32-bit sums are exact
+        s1 = __reduce_add_sync(0xffffffffu, a[j] + b[j]);
+        s2 = __reduce_add_sync(0xffffffffu, a[j] * a[j] + b[j] * b[j]);
+      } else {
+        s1 = (unsigned long long)a[j] + b[j];
+        s2 = (unsigned long long)a[j] * a[j] + (unsigned long long)b[j] * b[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, off);
         }
-      } else if (x0[u] | x1[u]) {
-        atomicAdd(&ssum[q], (unsigned long long)x0[u] + x1[u]);
-        atomicAdd(&ssq[q], (unsigned long long)x0[u] * x0[u] + (unsigned long long)x1[u] * x1[u]);
+      }
+      if (lane == 0) {
+        gsum[f][g] = s1;
+        gsq[f][g] = s2;
       }
     }
   }
   if (too_big && p.Xp) set_status(p.status, XPCS_DEV_RANGE);
   __syncthreads();
-  if (live) {
-    for (int q = threadIdx.x; q < p.n_q; q += blockDim.x) {
-      p.S[(size_t)q * p.T + t] = (long long)ssum[q];
-      if (p.S2) p.S2[(size_t)q * p.T + t] = (long long)ssq[q];
-      atomicMax(&p.sq[q], ssq[q]);
+  // groups of one ring are consecutive: one thread per frame walks the chunk's groups and
+  // adds each ring's run into S (and S2)
+  if (threadIdx.x < RI_F) {
+    const int f = threadIdx.x;
+    const long long t = t0 + f;
+    if (t < p.T) {
+      int q = -1;
+      unsigned long long r1 = 0, r2 = 0;
+      for (int g = 0; g <= ngrp; ++g) {
+        const int qg = g < ngrp ? sring[g] : -2;
+        if (qg != q) {
+          if (q >= 0 && (r1 | r2)) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(p.S + (size_t)q * p.T + t), r1);
+            if (p.S2) atomicAdd(reinterpret_cast<unsigned long long*>(p.S2 + (size_t)q * p.T + t), r2);
+          }
+          q = qg;
+          r1 = r2 = 0;
+        }
+        if (g < ngrp && q >= 0) {
+          r1 += gsum[f][g];
+          r2 += gsq[f][g];
+        }
+      }
     }
   }
 }
@@ -99,13 +125,14 @@ __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p
 //   XPCS_NORM_EQ12  r = sqrt(M_q) / mean_t S_q(t)   (Eq. 12), every frame defined
 // Undefined frames get r = 0; blk_bad marks tiles with an undefined frame.
 __global__ void raw_scales_kernel(const long long* S, const long long* S2, const double* Sbar, int norm,
-                                  const long long* Mq, int n_q, long long T, int T_pad, int nT,
-                                  const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status) {
+                                  const long long* Mq, int n_q, long long T, int T_pad, int nT, float* r,
+                                  uint32_t* blk_bad, uint32_t* status) {
   const int q = blockIdx.y, I = blockIdx.x;
-  if (I == 0 && threadIdx.x == 0 && sq && sq[q] >= (1ull << 24)) set_status(status, XPCS_DEV_RANGE);
   const long long t = (long long)I * TILE + threadIdx.x;
   float v = 0.f;
   bool bad = false;
+  // the exactness bound of the f32 Gram: every frame's sum of squares below 2^24
+  if (t < T && S2[(size_t)q * T + t] >= (1ll << 24)) set_status(status, XPCS_DEV_RANGE);
   if (t < T) {
     double den;
     if (norm == XPCS_NORM_FROB)
@@ -222,7 +249,8 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
       const long long t = t0 + f;
       float v = 0.f;
       if (t < p.T) {
-        const double acc = (double)hi + (double)lo;
+        // the ring sum of the denominators: a_t s_q, or the raw frame's exact sum
+        const double acc = p.S_exact ? (double)p.S_exact[(size_t)q * p.T + t] : (double)hi + (double)lo;
         if (p.St) p.St[(size_t)q * p.T + t] = acc;
         // per-frame scale (xpcs_norm); the Frobenius one needs W and is set below
         const double den = p.norm == XPCS_NORM_EQ12 ? p.Sbar[q] : acc;
@@ -458,8 +486,9 @@ __global__ void g2_finalize_kernel(const float* partials, const long long* count
 // ---------------------------------------------------------------- g2 over a stored C
 // C holds the lower triangle: C[s][s - tau] = C(s - tau, s) for tau >= 0.
 // Grid (lag blocks of 128, rings, row splits); 8 warps.  Lane l of every warp owns lags
-// L0 + l + 32 m (m = 0..3); the warp walks rows s, reading C[s][s - L0 - 127 .. s - L0]
-// as 128-byte coalesced segments.  Undefined (NaN) entries are skipped and counted out.
+// L0 + l + 32 m (m = 0..3); the warp walks its rows s four at a time, reading
+// C[s][s - L0 - 127 .. s - L0] as 128-byte coalesced segments (16 loads per thread in
+// flight).  Undefined (NaN) entries are skipped and counted out.
 constexpr int G2C_WARPS = 8;
 __global__ void __launch_bounds__(256) g2_from_C_kernel(const float* __restrict__ C, int n_q, long long T,
                                                         double* partial, long long* cnt_partial, int row_splits) {
@@ -475,20 +504,28 @@ __global__ void __launch_bounds__(256) g2_from_C_kernel(const float* __restrict_
   float s[4] = {0.f, 0.f, 0.f, 0.f};
   int c[4] = {0, 0, 0, 0};
   const float* Cq = C + (size_t)q * T * T;
-  for (long long row = r0 + warp; row < r1; row += G2C_WARPS) {
-    const float* p = Cq + (size_t)row * T + (row - L0);  // element of lag L0
-    const long long lim = row - L0;                      // lags L0 + l with l <= lim
+  // four rows per warp step: their 16 loads per thread are all in flight before any is used
+  for (long long row = r0 + 4 * warp; row < r1; row += 4 * G2C_WARPS) {
+    float v[4][4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int l = lane + 32 * m;
-      if (l <= lim) {
-        const float v = __ldcs(p - l);
-        if (v == v) {
-          s[m] += v;
-          c[m] += 1;
-        }
+    for (int i = 0; i < 4; ++i) {
+      const long long rr = row + i;
+      const long long lim = rr - L0;                       // lags L0 + l with l <= lim
+      const float* p = Cq + (size_t)rr * T + (rr - L0);     // element of lag L0
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int l = lane + 32 * m;
+        v[i][m] = (rr < r1 && l <= lim) ? __ldcs(p - l) : __int_as_float(0x7fc00000);
       }
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        if (v[i][m] == v[i][m]) {  // NaN: undefined pair (or no element)
+          s[m] += v[i][m];
+          c[m] += 1;
+        }
   }
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -530,17 +567,18 @@ __global__ void g2_from_C_reduce_kernel(const double* partial, const long long* 
 }  // namespace
 
 cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st) {
-  if (p.n_q > MAX_RINGS_SMEM) return cudaErrorInvalidValue;
-  raw_ingest_kernel<<<p.T_pad, 256, 0, st>>>(p);
+  cudaError_t e = cudaMemsetAsync(p.S, 0, (size_t)p.n_q * p.T * sizeof(long long), st);
+  if (e == cudaSuccess && p.S2) e = cudaMemsetAsync(p.S2, 0, (size_t)p.n_q * p.T * sizeof(long long), st);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((p.Mp + RI_CHUNK - 1) / RI_CHUNK), (unsigned)((p.T_pad + RI_F - 1) / RI_F));
+  raw_ingest_kernel<<<grid, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_raw_scales(const long long* S, const long long* S2, const double* Sbar, int norm,
-                              const long long* Mq, int n_q, long long T, int T_pad, int nT,
-                              const unsigned long long* sq, float* r, uint32_t* blk_bad, uint32_t* status,
-                              cudaStream_t st) {
-  raw_scales_kernel<<<dim3(nT, n_q), TILE, 0, st>>>(S, S2, Sbar, norm, Mq, n_q, T, T_pad, nT, sq, r, blk_bad,
-                                                     status);
+                              const long long* Mq, int n_q, long long T, int T_pad, int nT, float* r,
+                              uint32_t* blk_bad, uint32_t* status, cudaStream_t st) {
+  raw_scales_kernel<<<dim3(nT, n_q), TILE, 0, st>>>(S, S2, Sbar, norm, Mq, n_q, T, T_pad, nT, r, blk_bad, status);
   return cudaGetLastError();
 }
 

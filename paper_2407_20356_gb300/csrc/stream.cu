@@ -6,7 +6,10 @@
 //   1. sparse encode: a_t = sum over pixels with x_p > 0 of x_p V_K[p, :] (f32).  Only the
 //      nonzero pixels' basis rows are read, a few percent of V_K at low photon rates.
 //      Per-slice partials are summed in a fixed order (deterministic).
-//   2. frame factors: S~_q(t) = a_t s_q, r_q(t) = sqrt(M_q)/S~_q(t) (0 if undefined),
+//      With exact ring sums (XPCS_QMEAN_EXACT_RAW) the same pass adds each nonzero count
+//      into its ring's sum S_q(t).
+//   2. frame factors: S~_q(t) = a_t s_q (or the exact S_q(t)), r_q(t) = sqrt(M_q)/S~_q(t)
+//      (0 if undefined),
 //      w_q(t) = r_q(t) a_t G_q; a_t and r_q(t) go into the ring buffer slot of t.
 //   3. row update: for every lag tau < W, thread tau takes history row s = t - tau and adds
 //      C_q(t, s) = w_q(t) . a_s r_q(s) to g2sum_q[tau] (count_q[tau] += 1) for all rings.
@@ -25,11 +28,13 @@ namespace {
 constexpr int SE_PX = 4096;   // pixels per sparse-encode slice
 
 // --------------------------------------------------------------------------- 1. encode
+constexpr int SE_MAX_RINGS = 1024;
 __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) {
   __shared__ int nz_idx[SE_PX];
   __shared__ float nz_val[SE_PX];
   __shared__ int warp_tot[8];
   __shared__ float red[256];
+  __shared__ unsigned ring_acc[SE_MAX_RINGS];  // exact ring sums of this slice (at most 2^28)
   const int blk = blockIdx.x, fi = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long p0 = (long long)blk * SE_PX + (long long)tid * 16;
@@ -84,6 +89,18 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
       ++off;
     }
   __syncthreads();
+  if (s.Sx) {  // exact ring sums: each nonzero count into its ring, then one atomic per ring
+    for (int q = tid; q < s.n_q; q += 256) ring_acc[q] = 0u;
+    __syncthreads();
+    for (int e = tid; e < total; e += 256) {
+      const int q = s.qmap[nz_idx[e]];
+      if (q >= 0) atomicAdd(&ring_acc[q], (unsigned)nz_val[e]);
+    }
+    __syncthreads();
+    for (int q = tid; q < s.n_q; q += 256)
+      if (ring_acc[q]) atomicAdd(reinterpret_cast<unsigned long long*>(s.Sx + (size_t)fi * s.n_q + q),
+                                 (unsigned long long)ring_acc[q]);
+  }
   // accumulate: ng groups of k threads split the nonzero list
   const int k = s.k;
   for (int j0 = 0; j0 < k; j0 += 256) {
@@ -178,7 +195,7 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
   for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
   if ((tid & 31) == 0) dred[tid >> 5] = d;
   __syncthreads();
-  const double S = dred[0] + dred[1] + dred[2] + dred[3];
+  const double S = s.Sx ? (double)s.Sx[(size_t)fi * s.n_q + q] : dred[0] + dred[1] + dred[2] + dred[3];
   const float r = S > 0.0 ? (float)(sqrt((double)s.Mq[q]) / S) : 0.f;
   const int npad = stream_npad(s.n_q);
   if (tid == 0) {
@@ -260,8 +277,11 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   // the pair-ordered w rows of this step must fit the W2 allocation
   if (s.b < 1 || s.b > 64 || (long long)((s.n_q + 35) / 36) * w2_mtiles(s.b, s.n_q) * 128 > s.w2_rows)
     return cudaErrorInvalidValue;
+  if (s.Sx && s.n_q > SE_MAX_RINGS) return cudaErrorInvalidValue;
+  cudaError_t e = s.Sx ? cudaMemsetAsync(s.Sx, 0, (size_t)s.b * s.n_q * sizeof(long long), st) : cudaSuccess;
+  if (e != cudaSuccess) return e;
   sparse_encode_kernel<<<dim3(s.nblk, s.b), 256, 0, st>>>(s);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   stream_reduce_kernel<<<(s.b * s.k + 31) / 32, 256, 0, st>>>(s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -77,6 +77,8 @@ void stream_free(xpcs_stream* S) {
   dev_free(ctx, S->d_W2, z.W2);
   if (S->h_status) cudaFreeHost(S->h_status);
   dev_free(ctx, S->d_g2, z.g2);
+  dev_free(ctx, S->d_qmap, (size_t)S->M * 4);
+  dev_free(ctx, S->d_Sx, (size_t)64 * S->n_q * 8);
   for (int i = 0; i < 2; ++i) {
     if (S->h_stage[i]) cudaFreeHost(S->h_stage[i]);
     if (S->stage_done[i]) cudaEventDestroy(S->stage_done[i]);
@@ -123,16 +125,23 @@ cudaError_t calibrate_clock(xpcs_stream* S) {
 
 extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int64_t history, int max_batch,
                                         xpcs_dtype dtype, xpcs_stream** out) {
+  return xpcs_stream_open_opts(ctx, B, history, max_batch, dtype, nullptr, out);
+}
+
+extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B, int64_t history, int max_batch,
+                                             xpcs_dtype dtype, const xpcs_options* opt, xpcs_stream** out) {
   if (!ctx || !B || !out || B->ctx != ctx || history < 1 || max_batch < 1 || max_batch > 1024 || B->k > 256 ||
-      (dtype != XPCS_U8 && dtype != XPCS_U16))
+      (dtype != XPCS_U8 && dtype != XPCS_U16) || (opt && (opt->qmean < 0 || opt->qmean > 1)))
     return fail(ctx, XPCS_EINVAL, "bad stream_open args");
+  const bool exact = opt && opt->qmean == XPCS_QMEAN_EXACT_RAW;
   *out = nullptr;
   int lt = 0, wst = 0, epi = 0;  // steps of up to 64 frames: the largest a push is cut into
   if (!row_update_config(B->rings->n_q, kpad_of(B->k), 64, &lt, &wst, &epi))
     return fail(ctx, XPCS_ENOTSUP, "stream: the row-update tile does not fit shared memory at this k");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int eb = dtype == XPCS_U8 ? 1 : 2;
-  const size_t need = stream_footprint(B, history, max_batch, eb);
+  const size_t exact_bytes = exact ? (size_t)B->rings->M * 4 + (size_t)64 * B->rings->n_q * 8 : 0;
+  const size_t need = stream_footprint(B, history, max_batch, eb) + exact_bytes;
   if (ctx->budget && ctx->held + need > ctx->budget)
     return fail(ctx, XPCS_EBUSY,
                 "stream needs " + std::to_string(need) + " device bytes; " +
@@ -175,6 +184,10 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
   XPCS_SALLOC(d_a, z.a, float*)
   XPCS_SALLOC(d_W2, z.W2, __nv_bfloat16*)
   XPCS_SALLOC(d_g2, z.g2, double*)
+  if (exact) {
+    XPCS_SALLOC(d_qmap, (size_t)B->rings->M * 4, int*)
+    XPCS_SALLOC(d_Sx, (size_t)64 * B->rings->n_q * 8, long long*)
+  }
 #undef XPCS_SALLOC
   cudaError_t e = cudaSuccess;
   if (st == XPCS_OK) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
@@ -183,11 +196,15 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->stage_done[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(S->stage_done[i], S->stream);
   }
+  if (st == XPCS_OK && e == cudaSuccess && exact)  // the stream's own copy of the ring labels
+    e = cudaMemcpyAsync(S->d_qmap, B->rings->d_qmap, (size_t)B->rings->M * 4, cudaMemcpyDeviceToDevice, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_A2, 0, z.A2, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_W2, 0, z.W2, S->stream);
-  if (st == XPCS_OK && e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_status, 4, cudaHostAllocMapped);
+  // status word, then (8 bytes on) the bounded-wait limit taken from the context
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_status, 16, cudaHostAllocMapped);
   if (st == XPCS_OK && e == cudaSuccess) {
     *S->h_status = 0;
+    *reinterpret_cast<volatile uint64_t*>(S->h_status + 2) = ctx->wait_ns;
     e = cudaHostGetDevicePointer((void**)&S->d_status, S->h_status, 0);
   }
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_Rh, 0, z.Rh, S->stream);
@@ -299,6 +316,8 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.G32 = B->d_G32;
   s.s64 = B->d_s;
   s.Mq = B->rings->d_Mq;
+  s.qmap = S->d_qmap;
+  s.Sx = S->d_Sx;
   s.part = S->d_part;
   s.a = S->d_a;
   s.W2 = S->d_W2;

@@ -30,6 +30,14 @@ XPCS_PREC_FP16, XPCS_PREC_BF16, XPCS_PREC_BF16X3 = 0, 1, 2
 PRECISIONS = {"fp16": XPCS_PREC_FP16, "bf16": XPCS_PREC_BF16, "bf16x3": XPCS_PREC_BF16X3}
 XPCS_NORM_MEAN, XPCS_NORM_FROB, XPCS_NORM_EQ12 = 0, 1, 2
 NORMS = {"mean": XPCS_NORM_MEAN, "frob": XPCS_NORM_FROB, "eq12": XPCS_NORM_EQ12}
+SCHEDULES = ("blocks", "strips", "tile_pairs")  # two-time kernel schedules (codes 0, 1, 2)
+XPCS_QMEAN_COMPRESSED, XPCS_QMEAN_EXACT_RAW = 0, 1
+QMEANS = {"compressed": XPCS_QMEAN_COMPRESSED, "exact_raw": XPCS_QMEAN_EXACT_RAW}
+
+
+class XpcsOptions(C.Structure):
+    """xpcs_options: precision, normalisation and ring sums of the compressed calls."""
+    _fields_ = [("precision", C.c_int), ("norm", C.c_int), ("qmean", C.c_int)]
 
 vp = C.c_void_p
 i64 = C.c_int64
@@ -62,8 +70,17 @@ _SIGS = {
     "xpcs_encode": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     "xpcs_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp]),
     "xpcs_twotime_norm": (C.c_int, [vp, vp, vp, i64, C.c_int, C.c_int, vp, vp, vp]),
+    "xpcs_twotime_opts": (C.c_int, [vp, vp, vp, i64, C.POINTER(XpcsOptions), vp, vp, vp, vp]),
+    "xpcs_encode_sums": (C.c_int, [vp, vp, vp, C.c_int, i64, vp, vp]),
+    "xpcs_encode_host": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
+    "xpcs_stream_open_opts": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.POINTER(XpcsOptions), C.POINTER(vp)]),
     "xpcs_autotune_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp, C.c_int, C.POINTER(C.c_int),
                                         C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "xpcs_autotune_twotime_raw": (C.c_int, [vp, vp, vp, C.c_int, i64, vp, vp, vp, vp, C.c_int,
+                                            C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "xpcs_set_timeout": (C.c_int, [vp, C.c_int]),
+    "xpcs_twotime_config": (C.c_int, [vp, C.c_int, C.c_int]),
+    "xpcs_get_timeout": (C.c_int, [vp]),
     "xpcs_g2": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_fit_relaxation": (C.c_int, [vp, vp, C.c_int, i64, i64, i64, C.c_double, C.c_double, vp]),
     "xpcs_twotime_stats": (C.c_int, [vp, vp, C.c_int, i64, vp, vp]),
@@ -180,6 +197,20 @@ class Context:
 
     def set_async(self, on: bool):
         self.check(_lib.xpcs_set_async(self.h, 1 if on else 0))
+
+    def set_timeout(self, timeout_ms: int):
+        """Limit (ms) of the bounded device waits of this context's kernels and of the streams
+        opened on it afterwards; 0 restores the default."""
+        self.check(_lib.xpcs_set_timeout(self.h, int(timeout_ms)))
+
+    def timeout(self) -> int:
+        return int(_lib.xpcs_get_timeout(self.h))
+
+    def twotime_config(self, tiles: int = 0, schedule="blocks"):
+        """Fix the two-time kernel's configuration (tiles per work item, schedule name or
+        code); tiles = 0 returns to the autotuned or default choice."""
+        sc = SCHEDULES.index(schedule) if isinstance(schedule, str) else int(schedule)
+        self.check(_lib.xpcs_twotime_config(self.h, int(tiles), sc))
 
     def synchronize(self):
         self.check(_lib.xpcs_synchronize(self.h))
@@ -321,6 +352,29 @@ def xpcs_encode(ctx: Context, basis: Basis, X, T: int, A_out, dtype=None):
     ctx.check(_lib.xpcs_encode(ctx.h, basis.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(A_out)))
 
 
+def xpcs_encode_host(ctx: Context, basis: Basis, X_host, T: int, A_out, dtype=None):
+    """Encode frames in (pinned) host memory, the host-to-device copy overlapped with the encode."""
+    ctx.check(_lib.xpcs_encode_host(ctx.h, basis.h, _ptr(X_host), _dtype_code(dtype or X_host), T, _ptr(A_out)))
+
+
+def xpcs_encode_sums(ctx: Context, basis: Basis, X, T: int, A_out, S_out, dtype=None):
+    """Encode and also capture the exact ring sums of the raw frames (S_out: n_q x T int64)."""
+    ctx.check(_lib.xpcs_encode_sums(ctx.h, basis.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(A_out), _ptr(S_out)))
+
+
+def _options(prec="fp16", norm="mean", qmean="compressed") -> XpcsOptions:
+    return XpcsOptions(PRECISIONS[prec] if isinstance(prec, str) else int(prec), _norm_code(norm),
+                       QMEANS[qmean] if isinstance(qmean, str) else int(qmean))
+
+
+def xpcs_twotime_opts(ctx: Context, basis: Basis, A, T: int, prec="fp16", norm="mean", qmean="compressed",
+                      S_raw=None, C_out=None, g2_out=None, count_out=None):
+    """Compressed two-time with every option; qmean="exact_raw" takes the raw ring sums S_raw."""
+    o = _options(prec, norm, qmean)
+    ctx.check(_lib.xpcs_twotime_opts(ctx.h, basis.h, _ptr(A), T, C.byref(o), _ptr(S_raw), _ptr(C_out), _ptr(g2_out),
+                                     _ptr(count_out)))
+
+
 def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None, g2_out=None, count_out=None,
                  norm="mean"):
     if _norm_code(norm) != XPCS_NORM_MEAN:
@@ -329,14 +383,29 @@ def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None,
     ctx.check(_lib.xpcs_twotime(ctx.h, basis.h, _ptr(A), T, p, _ptr(C_out), _ptr(g2_out), _ptr(count_out)))
 
 
+def _tune_result(tiles, sched, ms) -> dict:
+    return {"tiles_per_item": tiles.value, "schedule": SCHEDULES[sched.value], "strip": sched.value == 1,
+            "pairs": sched.value == 2, "ms": ms.value}
+
+
 def xpcs_autotune_twotime(ctx: Context, basis: Basis, A, T: int, prec="bf16x3", C_out=None, g2_out=None,
                           count_out=None, reps: int = 2) -> dict:
     """Time the two-time kernel's configurations on these arguments, keep the fastest."""
     p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
-    tiles, strip, ms = C.c_int(), C.c_int(), C.c_double()
+    tiles, sched, ms = C.c_int(), C.c_int(), C.c_double()
     ctx.check(_lib.xpcs_autotune_twotime(ctx.h, basis.h, _ptr(A), T, p, _ptr(C_out), _ptr(g2_out), _ptr(count_out),
-                                         reps, C.byref(tiles), C.byref(strip), C.byref(ms)))
-    return {"tiles_per_item": tiles.value, "strip": bool(strip.value), "ms": ms.value}
+                                         reps, C.byref(tiles), C.byref(sched), C.byref(ms)))
+    return _tune_result(tiles, sched, ms)
+
+
+def xpcs_autotune_twotime_raw(ctx: Context, rings: Rings, X, T: int, C_out=None, N_out=None, g2_out=None,
+                              count_out=None, reps: int = 2, dtype=None) -> dict:
+    """The autotuner for the raw two-time call."""
+    tiles, sched, ms = C.c_int(), C.c_int(), C.c_double()
+    ctx.check(_lib.xpcs_autotune_twotime_raw(ctx.h, rings.h, _ptr(X), _dtype_code(dtype or X), T, _ptr(C_out),
+                                             _ptr(N_out), _ptr(g2_out), _ptr(count_out), reps, C.byref(tiles),
+                                             C.byref(sched), C.byref(ms)))
+    return _tune_result(tiles, sched, ms)
 
 
 def xpcs_twotime_norm(ctx: Context, basis: Basis, A, T: int, prec, norm, C_out=None, g2_out=None, count_out=None):
@@ -401,7 +470,8 @@ def xpcs_g2(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
 
 
 def xpcs_selftest_timeout(ctx: Context, limit_ms: int):
-    """Run a bounded device wait that nothing satisfies; raises XpcsError(XPCS_ETIMEOUT)."""
+    """Run a bounded device wait that nothing satisfies; raises XpcsError(XPCS_ETIMEOUT).
+    limit_ms = 0 waits through the library's own bounded wait with the context's limit."""
     ctx.check(_lib.xpcs_selftest_timeout(ctx.h, limit_ms))
 
 
@@ -411,6 +481,7 @@ def clock_ns() -> int:
 
 
 G2_NOALLOC_MAX_CELLS = 1 << 20  # n_q * T limit of xpcs_g2_noalloc (its fixed scratch)
+G2_MAX_RINGS = 65535  # n_q limit of xpcs_g2 and xpcs_g2_noalloc
 
 
 def xpcs_g2_noalloc(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
@@ -421,9 +492,11 @@ def xpcs_g2_noalloc(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None
 class Stream:
     """An xpcs_stream: online encode + two-time row update of every pushed frame."""
 
-    def __init__(self, ctx: Context, basis: Basis, history: int, max_batch: int, dtype="uint16"):
+    def __init__(self, ctx: Context, basis: Basis, history: int, max_batch: int, dtype="uint16", qmean="compressed"):
         h = vp()
-        st = _lib.xpcs_stream_open(ctx.h, basis.h, history, max_batch, _dtype_code(dtype), C.byref(h))
+        o = _options(qmean=qmean)
+        st = _lib.xpcs_stream_open_opts(ctx.h, basis.h, history, max_batch, _dtype_code(dtype), C.byref(o),
+                                        C.byref(h))
         if st != XPCS_OK:
             raise XpcsError(st, _lib.xpcs_last_error(ctx.h).decode())
         self.ctx, self.basis, self.h, self.W = ctx, basis, h, history

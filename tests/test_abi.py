@@ -52,6 +52,8 @@ def test_binding_constants_match_the_header():
     src = open(HEADER).read()
     m = re.search(r"#define\s+XPCS_G2_NOALLOC_MAX_CELLS\s+\(1 << (\d+)\)", src)
     assert m and xpcs.G2_NOALLOC_MAX_CELLS == 1 << int(m.group(1))
+    m = re.search(r"#define\s+XPCS_G2_MAX_RINGS\s+(\d+)", src)
+    assert m and xpcs.G2_MAX_RINGS == int(m.group(1))
     for name, val in re.findall(r"\b(XPCS_NORM_[A-Z0-9]+)\s*=\s*(\d+)", src):
         assert getattr(xpcs, name) == int(val), name
 

@@ -59,8 +59,32 @@ def test_expired_wait_in_async_mode_surfaces_at_synchronize(X):
 
 def test_selftest_rejects_out_of_range_limits(X):
     ctx = X.Context(0)
-    for bad in (0, -5, 1001):
+    for bad in (-5, 1001):  # 0 selects the context's limit
         with pytest.raises(X.XpcsError) as ei:
             X.xpcs_selftest_timeout(ctx, bad)
+        assert ei.value.status == X.XPCS_EINVAL
+    ctx.close()
+
+
+def test_context_wait_limit_reaches_the_device_waits(X):
+    """xpcs_set_timeout changes the limit of the library's own bounded wait (the one every
+    tensor-core kernel uses), read by the kernel from the context's status block."""
+    ctx = X.Context(0)
+    assert ctx.timeout() == 2000  # the default
+    for limit_ms in (60, 400):
+        ctx.set_timeout(limit_ms)
+        assert ctx.timeout() == limit_ms
+        t0 = time.perf_counter()
+        with pytest.raises(X.XpcsError) as ei:
+            X.xpcs_selftest_timeout(ctx, 0)  # a wait nothing satisfies, with the context's limit
+        dt = time.perf_counter() - t0
+        assert ei.value.status == X.XPCS_ETIMEOUT
+        assert limit_ms / 1000 <= dt < limit_ms / 1000 + 1.0, dt
+        _still_usable(X, ctx)  # real work completes well within the shortened limit
+    ctx.set_timeout(0)
+    assert ctx.timeout() == 2000
+    for bad in (-1, 600001):
+        with pytest.raises(X.XpcsError) as ei:
+            ctx.set_timeout(bad)
         assert ei.value.status == X.XPCS_EINVAL
     ctx.close()

@@ -103,7 +103,7 @@ def test_autotuned_configuration_gives_the_same_results(X):
         cnt = torch.empty((n_q, T), dtype=torch.int64, device=dev)
         if tune:
             got = X.xpcs_autotune_twotime(ctx, basis, A, T, "bf16x3", C_out=C, g2_out=g2, count_out=cnt, reps=1)
-            assert got["tiles_per_item"] in (4, 8, 16, 32) and got["ms"] > 0
+            assert got["tiles_per_item"] in (1, 2, 4, 8, 16, 32) and got["ms"] > 0
         else:
             X.xpcs_twotime(ctx, basis, A, T, "bf16x3", C_out=C, g2_out=g2, count_out=cnt)
         ctx.synchronize()

@@ -119,3 +119,94 @@ def test_g2_over_stored_twotime(X, ctx):
         g = g2[q].cpu().numpy()
         ok = ~np.isnan(g_ref)
         np.testing.assert_allclose(g[ok], g_ref[ok], rtol=1e-6)
+
+
+# ---------------------------------------------------------------- the 2^24 bound at its edge
+# The raw path promises a bit-exact integer Gram for any ring whose largest per-frame sum
+# of squared counts is below 2^24: the f32 accumulator then holds every partial sum of
+# N(t1, t2) exactly (all terms are non-negative integers bounded by sqrt(N(t1,t1) N(t2,t2))).
+# These cases fill the f32 significand: a frame with 255 pixels at 256 and 65535 pixels
+# at 1 has sum of squares 2^24 - 1, so N(t, t) needs all 24 bits, reached by large
+# products followed by tens of thousands of unit ones.  A tensor-core adder that kept
+# fewer than 24 bits, or dropped small addends next to a large running sum, would lose
+# them.
+
+_BIG = 255                    # pixels at count 256: 255 * 2^16 = 2^24 - 2^16
+_ONES = (1 << 16) - 1         # pixels at count 1: fills the rest up to 2^24 - 1
+_R0 = _BIG + _ONES            # ring 0: 65790 pixels
+_R1 = 2050                    # ring 1: mixed magnitudes
+_M = _R0 + _R1                # 67840 = 64 x 1060
+
+
+def _edge_frames(T, seed):
+    rng = np.random.default_rng(seed)
+    F = np.zeros((T, _M), dtype=np.uint16)
+    for t in range(T):
+        kind = t % 7
+        r0 = F[t, :_R0]
+        if kind == 0:    # large products first, then the unit ones: sum of squares 2^24 - 1
+            r0[:_BIG] = 256
+            r0[_BIG:] = 1
+        elif kind == 1:  # unit ones first, large ones last in the ring's pixel order
+            r0[:_ONES] = 1
+            r0[_ONES:] = 256
+        elif kind == 2:  # large ones only: 2^24 - 2^16
+            r0[:_BIG] = 256
+        elif kind == 3:  # large ones scattered, small counts 1..3 elsewhere
+            r0[:] = rng.integers(1, 4, size=_R0)
+            big = rng.choice(_R0, size=200, replace=False)
+            r0[big] = 256
+        elif kind == 4:  # large ones in the last 64-wide chunk positions of the ring
+            r0[_R0 - 128:_R0 - 128 + _BIG // 2] = 256
+            r0[:30000] = rng.integers(0, 3, size=30000)
+        elif kind == 5:  # sparse small counts
+            r0[:] = (rng.random(_R0) < 0.3) * rng.integers(1, 4, size=_R0)
+        # kind 6: dark in ring 0 (undefined pairs)
+        r1 = F[t, _R0:]
+        nb = int(rng.integers(0, 251))         # a few pixels at 256, the rest 1..3
+        r1[:] = rng.integers(1, 4, size=_R1)
+        if nb:
+            r1[rng.choice(_R1, size=nb, replace=False)] = 256
+    return F
+
+
+def _edge_qmap():
+    q = np.zeros(_M, dtype=np.int32)
+    q[_R0:] = 1
+    return q
+
+
+def test_raw_exact_at_sum_of_squares_edge(X, ctx):
+    T = 140  # two tile rows, the second ragged
+    frames = _edge_frames(T, 24)
+    S2 = (frames[:, :_R0].astype(np.int64) ** 2).sum(1)
+    assert S2.max() == (1 << 24) - 1  # the largest value the bound admits is reached
+    S2b = (frames[:, _R0:].astype(np.int64) ** 2).sum(1)
+    assert S2b.max() < (1 << 24)
+    out = _check_raw(X, ctx, frames, _edge_qmap(), 2)
+    # the diagonal of the frames at the edge needs all 24 bits of the f32 significand
+    assert out["N"][0, 0, 0] == (1 << 24) - 1 and out["N"][0, 1, 1] == (1 << 24) - 1
+
+
+def test_raw_exact_edge_reversed_pixel_order(X, ctx):
+    # the same frames with the pixel order of each ring reversed: the small terms now come
+    # first in the chunk order and the large ones last
+    T = 140
+    frames = _edge_frames(T, 25)
+    frames = np.concatenate([frames[:, :_R0][:, ::-1], frames[:, _R0:][:, ::-1]], axis=1).copy()
+    _check_raw(X, ctx, frames, _edge_qmap(), 2)
+
+
+def test_raw_rejects_sum_of_squares_at_two_to_24(X, ctx):
+    # one frame of ring 0 with 256 pixels at 256: sum of squares exactly 2^24
+    frames = np.zeros((9, 512), dtype=np.uint16)
+    frames[:, :64] = 1
+    frames[4, 100:356] = 256
+    qmap = np.zeros(512, dtype=np.int32)
+    qmap[400:] = 1
+    with pytest.raises(X.XpcsError) as e:
+        run_raw(X, ctx, frames, qmap, 2)
+    assert e.value.status == X.XPCS_ERANGE
+    # one count less is inside the bound and exact
+    frames[4, 100] = 255
+    _check_raw(X, ctx, frames, qmap, 2)

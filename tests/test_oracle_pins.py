@@ -183,6 +183,46 @@ def test_eq10_homomorphic_equals_decompress_then_correlate():
                                    rtol=1e-10, atol=1e-10)
 
 
+def test_exact_ring_sums_reduce_to_raw_with_a_lossless_basis():
+    # with B = I the coefficients are the counts: the compressed Gram with the exact ring
+    # sums is the raw two-time correlation, and a s_q equals the exact sums
+    X, qmap, n_q = _small_speckle()
+    X[[4, 17]] = 0  # dark frames: undefined pairs
+    Craw, N, S, Mq = O.raw_twotime(X, qmap, n_q)
+    G, s, M2 = O.ring_factors(np.eye(X.shape[1]), qmap, n_q)
+    Ce = O.compressed_twotime_exact_sums(O.encode(X, np.eye(X.shape[1])), G, S, M2)
+    np.testing.assert_array_equal(np.isnan(Ce), np.isnan(Craw))
+    ok = ~np.isnan(Craw)
+    np.testing.assert_allclose(Ce[ok], Craw[ok], rtol=1e-15)
+
+
+def test_exact_ring_sums_with_a_lossy_basis_from_pixel_definitions():
+    # lossy basis: numerator = ring Gram of the decompressed frames (Eq. 8), denominators =
+    # the raw frames' ring sums, each summed pixel by pixel for a few pairs
+    X, qmap, n_q = _small_speckle(T=30)
+    X[5] = 0
+    B, _ = O.fit_basis(X[:20], 5)
+    A = O.encode(X, B)
+    Xt = O.decompress(A, B)
+    G, s, Mq = O.ring_factors(B, qmap, n_q)
+    S = O.ring_sums(X, qmap, n_q)
+    Ce = O.compressed_twotime_exact_sums(A, G, S, Mq)
+    rng = np.random.default_rng(9)
+    for q in range(n_q):
+        idx = [p for p in range(X.shape[1]) if qmap[p] == q]
+        for t1, t2 in list(rng.integers(0, 30, size=(12, 2))) + [(5, 3), (7, 7)]:
+            num = sum(Xt[t1, p] * Xt[t2, p] for p in idx)
+            s1 = sum(int(X[t1, p]) for p in idx)
+            s2 = sum(int(X[t2, p]) for p in idx)
+            if s1 > 0 and s2 > 0:
+                assert Ce[q, t1, t2] == pytest.approx(len(idx) * num / (s1 * s2), rel=1e-10, abs=1e-12)
+            else:
+                assert np.isnan(Ce[q, t1, t2])
+    # lossy: the exact sums differ from a s_q, so the two forms differ
+    Cc, St = O.compressed_twotime(A, G, s, Mq)
+    assert not np.allclose(St, S)
+
+
 def test_basis_orthonormal_eckart_young_and_svd():
     X, _, _ = _small_speckle(T=50)
     k = 7

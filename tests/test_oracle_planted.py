@@ -138,3 +138,34 @@ def test_compressed_pair_values_with_swapped_frames_in_one_sum_are_caught(monkey
 
     _patch(monkeypatch, "compressed_pair_values", bad)
     assert _fails(*PAIR_PINS)
+
+
+EXACT_SUM_PINS = (
+    P.test_exact_ring_sums_reduce_to_raw_with_a_lossless_basis,
+    P.test_exact_ring_sums_with_a_lossy_basis_from_pixel_definitions,
+)
+
+
+def test_exact_sums_of_the_wrong_ring_are_caught(monkeypatch):
+    orig = OX.compressed_twotime_exact_sums
+    _patch(monkeypatch, "compressed_twotime_exact_sums",
+           lambda A, G, S, Mq: orig(A, G, np.roll(np.asarray(S), 1, axis=0), Mq))
+    assert _fails(*EXACT_SUM_PINS)
+
+
+def test_exact_sums_as_pixel_means_are_caught(monkeypatch):
+    orig = OX.compressed_twotime_exact_sums
+    _patch(monkeypatch, "compressed_twotime_exact_sums",
+           lambda A, G, S, Mq: orig(A, G, np.asarray(S, float) / np.asarray(Mq, float)[:, None], Mq))
+    assert _fails(*EXACT_SUM_PINS)
+
+
+def test_exact_sums_without_the_ring_factor_are_caught(monkeypatch):
+    orig = OX.compressed_twotime_exact_sums
+
+    def bad(A, G, S, Mq):
+        eye = np.broadcast_to(np.eye(np.asarray(A).shape[1]), np.asarray(G).shape)
+        return orig(A, eye, S, Mq)  # N~ = a a^T: the ring factor G_q dropped
+
+    _patch(monkeypatch, "compressed_twotime_exact_sums", bad)
+    assert _fails(*EXACT_SUM_PINS)

@@ -98,7 +98,23 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(X):
     assert ei.value.status == X.XPCS_ERANGE
     assert "exceeds its fixed scratch" in str(ei.value)
     assert ctx.launch_count() == launches
-    # at the limit it runs
+    # more rings than a launch grid takes, though n_q * T is inside the cell limit
+    with pytest.raises(X.XpcsError) as ei:
+        X.xpcs_g2_noalloc(ctx, C, X.G2_MAX_RINGS + 1, 8, g)
+    assert ei.value.status == X.XPCS_ERANGE
+    assert ctx.launch_count() == launches
+    # at the limit it runs and fills the whole array (partials and the count block at its
+    # far end): values in [0.5, 1.5) with scattered NaN (undefined pairs), against xpcs_g2
     n_q = X.G2_NOALLOC_MAX_CELLS // 128
-    X.xpcs_g2_noalloc(ctx, C[:n_q], n_q, T, g[:n_q])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20356)
+    Cl = C[:n_q]
+    Cl.copy_(torch.rand((n_q, T, T), generator=gen, device=dev) + 0.5)
+    Cl[torch.rand((n_q, T, T), generator=gen, device=dev) < 0.05] = float("nan")
+    Cl[5] = float("nan")  # one ring with no defined pair: g2 NaN, counts 0
+    c = torch.full((n_q, T), -1, dtype=torch.int64, device=dev)
+    X.xpcs_g2_noalloc(ctx, Cl, n_q, T, g[:n_q], c)
+    g_ref, c_ref = _g2_pair(X, ctx, Cl, n_q, T)
+    _check(g[:n_q].cpu().numpy(), c.cpu().numpy(), g_ref, c_ref)
+    assert np.all(c_ref[5] == 0)
     ctx.close()
