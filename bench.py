@@ -443,6 +443,8 @@ def run_ours(args, wl):
 
     e2e_ms, _, _ = timed(e2e_step, max(1, min(args.steps, 5)), 1)
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    # the bound of the end-to-end step: one plain copy of the frames from pinned host memory
+    copy_ms, _, _ = timed(lambda: Xd.copy_(Xh, non_blocking=True), 3, 1)
     del Xh
 
     # ---- parity at full size on sampled outputs, and the CPU oracle baseline (rank 0)
@@ -553,6 +555,7 @@ def run_ours(args, wl):
         "e2e": {"value": world * T / (e2e_ms * 1e-3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "h2d_gbs_over_step": h2d / (e2e_ms * 1e-3) / 1e9,
+                "h2d_copy_only_ms": copy_ms, "h2d_copy_only_gbs": h2d / (copy_ms * 1e-3) / 1e9,
                 "path": "xpcs_encode_host (copies of 256 MB blocks on two copy streams overlapped with the "
                         "encode) + xpcs_twotime + g2/count read back"},
         "gpu_launches": launches,
@@ -975,15 +978,60 @@ def run_stream_leg(X, ctx, dev, args, sw=STREAM):
                                 "frame scan + basis rows of nonzero pixels per frame"},
         "sustained_gbs": (bytes_batch_fixed / sw["max_batch"] + bytes_frame) * fps_sustained / 1e9,
         "raw_equivalent_frames_per_s_model": pk["hbm_gbs"] * 1e9 / raw_frame_bytes,
-        "raw_equivalent_note": "raw path row update reads the uint16 history (history x M) once per frame at the "
-                               "measured HBM bandwidth",
+        "raw_equivalent_note": "cross-check only: a raw row update that reads the uint16 history (history x M) "
+                               "once per frame at the measured HBM bandwidth",
         "pool_frames": P, "nnz_per_frame": nnz_per_frame,
     }
     st.close()
+    out["raw_equivalent"] = run_raw_stream_equivalent(X, ctx, basis, rings, pool, sw)
     basis.close()
     rings.close()
     del pool
     torch.cuda.empty_cache()
+    return out
+
+
+def run_raw_stream_equivalent(X, ctx, basis, rings, pool, sw, histories=(10000, 20000)):
+    """The raw-path equivalent of the online stream, measured: xpcs_raw_stream (every pushed
+    frame's exact raw two-time row against the window, integer Gram on the tensor cores)
+    on the same 1 Mpx frames, at histories that fit HBM as bf16 rows, in 64-frame steps and
+    one frame at a time; the compressed stream is timed at the same history beside it.
+    Both cost in proportion to the history, which the two histories show."""
+    P = pool.shape[0]
+
+    def feed(push, wait, n, batch, pushed):
+        t0 = time.perf_counter()
+        last = None
+        while n > 0:
+            i = pushed % P
+            m = min(n, P - i, batch)
+            last = push(pool[i:i + m])
+            pushed += m
+            n -= m
+        wait(last)
+        return time.perf_counter() - t0, pushed
+
+    out = {"note": "exact raw row update (bf16 counts, f32 integer Gram on the tensor cores, FP64 g2 sums) "
+                   "against the compressed stream (bf16x3) on the same frames and history"}
+    for Wr in histories:
+        rs = X.RawStream(ctx, rings, Wr, dtype=sw["dtype"])
+        rwait = lambda _t: ctx.synchronize()  # the raw stream runs on the context's stream
+        _, pushed = feed(rs.push, rwait, Wr, 64, 0)  # fill the history
+        t64, pushed = feed(rs.push, rwait, 1280, 64, pushed)
+        t1, pushed = feed(rs.push, rwait, 64, 1, pushed)
+        rs.close()
+        st = X.Stream(ctx, basis, Wr, sw["max_batch"], dtype=sw["dtype"])
+        swait = lambda t: st.poll(t, 600000)  # the stream runs on its own CUDA stream
+        _, pc = feed(st.push, swait, Wr, 64, 0)
+        c64, pc = feed(st.push, swait, 4096, 64, pc)
+        c1, pc = feed(st.push, swait, 1024, 1, pc)
+        st.close()
+        out[f"history_{Wr}"] = {
+            "raw_frames_per_s_batch64": 1280 / t64, "raw_frames_per_s_batch1": 64 / t1,
+            "compressed_frames_per_s_batch64": 4096 / c64, "compressed_frames_per_s_batch1": 1024 / c1,
+            "speedup_batch64": (4096 / c64) / (1280 / t64), "speedup_batch1": (1024 / c1) / (64 / t1),
+            "raw_history_gb": (128 * ((Wr + 126) // 128 + 2)) * rings_padded(rings) * 2 / 1e9,
+        }
     return out
 
 

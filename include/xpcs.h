@@ -421,6 +421,30 @@ xpcs_status xpcs_stream_latency(xpcs_stream* s, int reset, double* p50_us, doubl
                                 int64_t* n_frames);
 xpcs_status xpcs_stream_close(xpcs_stream* s);
 
+/* ------------------------------------------------------------------ online stream on raw frames
+ * The raw-path counterpart of the online stream (Sec. 2.2 online mode, against which Sec.
+ * 3.2 times the compressed path): every pushed frame's exact two-time row against the last
+ * `history` frames, C_q(t, s) = M_q N_q(t, s) / (S_q(t) S_q(s)) with the integer Gram of
+ * Eq. 2 on the tensor cores (bf16 counts, exact below the raw path's bounds: counts <= 256
+ * and every frame's sum of squared counts per ring below 2^24, else XPCS_ERANGE), folded
+ * into running FP64 sums per lag.  The frames are kept in ring-sorted bf16 rows (128 x
+ * ceil(history / 128) + 256 rows of the ring plan's padded length), so every push reads the
+ * whole window once.  Work runs on the context's stream; the ring plan must stay alive
+ * while frames are pushed. */
+typedef struct xpcs_raw_stream xpcs_raw_stream;
+xpcs_status xpcs_raw_stream_open(xpcs_ctx* ctx, const xpcs_rings* rings, int64_t history, xpcs_dtype dtype,
+                                 xpcs_raw_stream** out);
+/* Push n frames already in device memory (n x M counts of the stream's dtype), processed in
+ * steps of at most 64 frames that do not cross a 128-frame block.  Returns once they are
+ * folded in (unless the context is asynchronous). */
+xpcs_status xpcs_raw_stream_push_device(xpcs_raw_stream* rs, const void* frames, int64_t n);
+/* g2_host (nullable): n_q x history f64, NaN without pairs; count_host (nullable): n_q x
+ * history int64.  Waits for the context's stream. */
+xpcs_status xpcs_raw_stream_read_g2(xpcs_raw_stream* rs, double* g2_host, int64_t* count_host);
+/* Frames pushed so far (-1 for a null handle). */
+int64_t xpcs_raw_stream_frames(const xpcs_raw_stream* rs);
+xpcs_status xpcs_raw_stream_close(xpcs_raw_stream* rs);
+
 /* ------------------------------------------------------------------ serving several streams
  * A server owns a scheduler thread for streams opened through it.  xpcs_server_submit
  * copies frames into the stream's host queue and returns at once; the scheduler takes,

@@ -141,16 +141,29 @@ namespace {
 
 // Work items of the two-time kernel: (q, delta, I0, I1), the tiles (I, I+delta) of one
 // tile diagonal (with tile pairs also (I, I+delta+1); delta then runs over even values),
-// CH tiles per item.  Order, ring by ring: items of full length first, then the shorter
+// CH tiles per item.  Calls that store C take them ring by ring, chunk by chunk, delta
+// ascending, so that the CTAs running together write neighbouring row blocks of C.  The
+// others (raw counts with their long K loop, g2-only calls), bound by operand traffic,
+// take this grouped order, ring by ring: items of full length first, then the shorter
 // ones at the triangle's edge, so that items launched together also finish together;
 // within each group items come in blocks of consecutive e = I0 + delta (the R row block of
 // the item's first tile), all chunks c = I0 / CH of a block together.  Items with the same
 // c read the same L row blocks at every step and items with the same e the same R row
 // blocks, so the items that a persistent grid of `grid` CTAs runs at one time share their
 // operand panels in L2.
-std::vector<int4> make_items(int n_q, int nT, int CH, int pairs, int grid) {
+std::vector<int4> make_items(int n_q, int nT, int CH, int pairs, int grid, bool grouped) {
   const int step = pairs ? 2 : 1;
   const int nC = (nT + CH - 1) / CH;
+  if (!grouped) {  // ring by ring, chunk by chunk, delta ascending (consecutive C row blocks)
+    std::vector<int4> items;
+    for (int q = 0; q < n_q; ++q)
+      for (int c = 0; c < nC; ++c)
+        for (int d = 0; d < nT; d += step) {
+          const int I0 = c * CH, I1 = std::min(c * CH + CH, nT - d);
+          if (I0 < I1) items.push_back(make_int4(q, d, I0, I1));
+        }
+    return items;
+  }
   // e-block width: about `grid` items per block over all chunks
   const int eb = std::max(step, (grid * step + nC - 1) / nC);
   std::vector<int4> items;
@@ -173,14 +186,16 @@ std::vector<int4> make_items(int n_q, int nT, int CH, int pairs, int grid) {
 }
 
 // Device copy of the work items for (n_q, nT, CH), rebuilt only when they change.
-xpcs_status cached_items(xpcs_ctx* ctx, int n_q, int nT, int CH, int pairs, int4** d_items, int* n_items) {
+xpcs_status cached_items(xpcs_ctx* ctx, int n_q, int nT, int CH, int pairs, bool grouped, int4** d_items,
+                         int* n_items) {
+  const int key3 = pairs | (grouped ? 2 : 0);
   if (ctx->items_key[0] != n_q || ctx->items_key[1] != nT || ctx->items_key[2] != CH ||
-      ctx->items_key[3] != pairs) {
+      ctx->items_key[3] != key3) {
     if (ctx->capturing || ctx->graphs > 0)
       return fail(ctx, XPCS_EBUSY,
                   "two-time work items of another shape cannot be built during a capture or while captured "
                   "graphs exist: run the call once before capturing");
-    const std::vector<int4> items = make_items(n_q, nT, CH, pairs, ctx->num_sms);
+    const std::vector<int4> items = make_items(n_q, nT, CH, pairs, ctx->num_sms, grouped);
     const size_t bytes = items.size() * sizeof(int4);
     if (bytes > ctx->items_bytes) {
       XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -199,7 +214,7 @@ xpcs_status cached_items(xpcs_ctx* ctx, int n_q, int nT, int CH, int pairs, int4
     ctx->items_key[0] = n_q;
     ctx->items_key[1] = nT;
     ctx->items_key[2] = CH;
-    ctx->items_key[3] = pairs;
+    ctx->items_key[3] = key3;
   }
   *d_items = ctx->d_items;
   *n_items = (int)ctx->items_n;
@@ -523,7 +538,8 @@ xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap
                         double* g2_out) {
   int4* d_items = nullptr;
   int n_items = 0;
-  XPCS_TRY(cached_items(ctx, n_q, nT, gp.CH, gp.pairs, &d_items, &n_items));
+  const bool grouped = gp.raw || gp.merge || !gp.C;
+  XPCS_TRY(cached_items(ctx, n_q, nT, gp.CH, gp.pairs, grouped, &d_items, &n_items));
   gp.items = d_items;
   gp.n_items = n_items;
   const int grid = std::min<int>(gp.n_items, ctx->num_sms);

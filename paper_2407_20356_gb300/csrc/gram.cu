@@ -143,6 +143,19 @@ __device__ __forceinline__ UnitRange unit_range(const GramParams& p, const int4&
 }
 __device__ __forceinline__ int units_of(const GramParams& p, const int4& w) { return p.merge ? 1 : w.w - w.z; }
 
+// Work item i: from the list, or computed for a stream's raw row update (a ring of blocks)
+__device__ __forceinline__ int4 item_at(const GramParams& p, int i) {
+  if (p.items) return p.items[i];
+  const int q = i / p.ring_nd, d = i - q * p.ring_nd;
+  const int I = ((p.ring_J - d) % p.ring_nb + p.ring_nb) % p.ring_nb;
+  return make_int4(q, d, I, I + 1);
+}
+// Column block of tile (I, I + delta): wraps around the ring of a stream's history
+__device__ __forceinline__ int col_block(const GramParams& p, int I, int delta) {
+  const int J = I + delta;
+  return p.ring_nb ? J % p.ring_nb : J;
+}
+
 template <bool STRIP, int NP>
 __global__ void __launch_bounds__(GRAM_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR,
@@ -195,14 +208,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       uint32_t it = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
-        const int4 w = p.items[item];
+        const int4 w = item_at(p, item);
         const int q = w.x, delta = w.y;
         const int nk = p.k_chunks[q];
         const int nc = p.split ? 2 * nk : nk;  // chunks per tile
         const int koff = p.k_off[q];
         const int rowbase = q * p.ring_rows;
         for (int I = w.z; I < w.w && ok; ++I) {
-          const int J = I + delta;
+          const int J = col_block(p, I, delta);
           for (int c = 0; c < nc; ++c, ++it) {
             const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
             if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, p.status)) {
@@ -233,7 +246,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       uint32_t it = 0, unit = 0;
       bool ok = true, issued = false;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
-        const int4 w = p.items[item];
+        const int4 w = item_at(p, item);
         const int nk = p.k_chunks[w.x];
         const int nc = p.split ? 2 * nk : nk;
         const int n_units = units_of(p, w);
@@ -312,7 +325,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     uint32_t unit = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
-      const int4 w = p.items[item];
+      const int4 w = item_at(p, item);
       const int q = w.x, delta = w.y;
       const float* rq = p.r + (size_t)q * p.T_pad;
       const int n_units = units_of(p, w);
@@ -327,7 +340,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
 #pragma unroll
         for (int h2 = 0; h2 < NP; ++h2) {
           const int J = I + delta + h2;
-          bad[h2] = h2 < nh && (p.blk_bad[(size_t)q * p.nT + I] | p.blk_bad[(size_t)q * p.nT + J]);
+          bad[h2] = work && h2 < nh && (p.blk_bad[(size_t)q * p.nT + I] | p.blk_bad[(size_t)q * p.nT + J]);
           interior[h2] = !bad[h2] && (long long)(I + 1) * TILE <= T && (long long)(J + 1) * TILE <= T;
         }
         if (!mbar_wait_warp(&tfull[b], tph, p.status)) {  // warp-uniform outcome
@@ -376,7 +389,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
     uint32_t unit = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
-      const int4 w = p.items[item];
+      const int4 w = item_at(p, item);
       const int q = w.x, delta = w.y;
       const float* rq = p.r + (size_t)q * p.T_pad;
       // the item's second tile diagonal (pairs) holds tiles
@@ -402,7 +415,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           const bool last = h2 == nh - 1;  // TMEM is released after the unit's last load
           const uint32_t tbase =
               tmem_base + b * (NP * TILE) + h2 * TILE + ((uint32_t)(r * 32) << 16) + 64 * h;
-          const float* rj = rq + (size_t)(I + delta + h2) * TILE + 64 * h;
+          const float* rj = (p.rc ? p.rc + (size_t)q * p.T_pad : rq) + (size_t)col_block(p, I, delta + h2) * TILE + 64 * h;
           if constexpr (STRIP) {
             // whole strip: row 32 k + lane holds strip diagonal 32 (k - 1) + lane (acc[k])
             __syncwarp();  // the previous tile's row sums are read

@@ -37,7 +37,7 @@ struct xpcs_ctx {
   // work items of the two-time kernel, cached for the last (n_q, nT, CH)
   int4* d_items = nullptr;
   size_t items_n = 0, items_bytes = 0;
-  int items_key[4] = {-1, -1, -1, -1};  // (n_q, nT, tiles per item, tile pairs)
+  int items_key[4] = {-1, -1, -1, -1};  // (n_q, nT, tiles per item, tile pairs | 2 grouped order)
   bool prof = false;
   std::vector<xpcs_prof_entry> prof_entries;
   std::vector<cudaEvent_t> event_pool;

@@ -47,6 +47,11 @@ struct GramParams {
                            //    items then cover the tile diagonals delta (even) and delta + 1
   int merge;               // 1: the tiles of an item accumulate into one accumulator (compressed
                            //    path, g2 only, no C store); the diagonal pass runs once per item
+  // raw row update of a stream (items == nullptr): row blocks live in a ring of ring_nb
+  // blocks, column block J = (I + delta) mod ring_nb, and item i is (q, delta, I, I + 1)
+  // with q = i / ring_nd, delta = i mod ring_nd, I = (ring_J - delta) mod ring_nb
+  int ring_nb, ring_nd, ring_J;
+  const float* rc;         // nullable [n_q][T_pad] column scales (default: r)
   const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined
   const uint32_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
   float* C;                // nullable [n_q][T][T]
@@ -71,6 +76,7 @@ struct RawIngestParams {
   const int* pos_ring;     // [Mp] ring of position or -1
   int n_q;
   __nv_bfloat16* Xp;       // [T_pad][Mp] (nullable when only sums are wanted)
+  long long xp_row0;       // row of Xp that frame 0 goes to (a stream's ring slot; else 0)
   long long* S;            // [n_q][T] (accumulated with atomics; the launch zeroes it)
   long long* S2;           // nullable [n_q][T] per-frame sum of squared counts (likewise)
   uint32_t* status;

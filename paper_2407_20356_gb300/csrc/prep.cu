@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p
       too_big |= big;
       if (p.Xp) {
         const __nv_bfloat162 v = __floats2bfloat162_rn((float)a[j], (float)b[j]);
-        *reinterpret_cast<__nv_bfloat162*>(p.Xp + t * p.Mp + P0 + o) = v;
+        *reinterpret_cast<__nv_bfloat162*>(p.Xp + (p.xp_row0 + t) * p.Mp + P0 + o) = v;
       }
       unsigned long long s1, s2;
       if (!__any_sync(0xffffffffu, big)) {  // squares < 2^17 per lane: 32-bit sums are exact

@@ -73,6 +73,11 @@ _SIGS = {
     "xpcs_twotime_opts": (C.c_int, [vp, vp, vp, i64, C.POINTER(XpcsOptions), vp, vp, vp, vp]),
     "xpcs_encode_sums": (C.c_int, [vp, vp, vp, C.c_int, i64, vp, vp]),
     "xpcs_encode_host": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
+    "xpcs_raw_stream_open": (C.c_int, [vp, vp, i64, C.c_int, C.POINTER(vp)]),
+    "xpcs_raw_stream_push_device": (C.c_int, [vp, vp, i64]),
+    "xpcs_raw_stream_read_g2": (C.c_int, [vp, vp, vp]),
+    "xpcs_raw_stream_frames": (i64, [vp]),
+    "xpcs_raw_stream_close": (C.c_int, [vp]),
     "xpcs_stream_open_opts": (C.c_int, [vp, vp, i64, C.c_int, C.c_int, C.POINTER(XpcsOptions), C.POINTER(vp)]),
     "xpcs_autotune_twotime": (C.c_int, [vp, vp, vp, i64, C.c_int, vp, vp, vp, C.c_int, C.POINTER(C.c_int),
                                         C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -178,7 +183,7 @@ class Context:
         if st != XPCS_OK:
             raise XpcsError(st, _lib.xpcs_last_error(self.h).decode())
 
-    _CLOSE_ORDER = {"Server": 0, "Graph": 1, "Stream": 2, "Basis": 3, "Rings": 4}
+    _CLOSE_ORDER = {"Server": 0, "Graph": 1, "Stream": 2, "RawStream": 2, "Basis": 3, "Rings": 4}
 
     def close(self):
         """Destroy the context after every handle created on it, each handle before the
@@ -487,6 +492,37 @@ G2_MAX_RINGS = 65535  # n_q limit of xpcs_g2 and xpcs_g2_noalloc
 def xpcs_g2_noalloc(ctx: Context, C_in, n_q: int, T: int, g2_out, count_out=None):
     """xpcs_g2 with its scratch in a fixed per-device array: allocates no device memory."""
     ctx.check(_lib.xpcs_g2_noalloc(ctx.h, _ptr(C_in), n_q, T, _ptr(g2_out), _ptr(count_out)))
+
+
+class RawStream:
+    """An xpcs_raw_stream: every pushed frame's exact raw two-time row folded into g2."""
+
+    def __init__(self, ctx: Context, rings: Rings, history: int, dtype="uint16"):
+        h = vp()
+        st = _lib.xpcs_raw_stream_open(ctx.h, rings.h, history, _dtype_code(dtype), C.byref(h))
+        if st != XPCS_OK:
+            raise XpcsError(st, _lib.xpcs_last_error(ctx.h).decode())
+        self.ctx, self.rings, self.h, self.W = ctx, rings, h, history
+        self.n_q = rings.n_q
+        ctx._adopt(self)
+
+    def push(self, frames_dev):
+        """Push device frames (n x M tensor); returns once they are folded in."""
+        self.ctx.check(_lib.xpcs_raw_stream_push_device(self.h, _ptr(frames_dev), int(frames_dev.shape[0])))
+
+    def read_g2(self):
+        g2 = np.empty((self.n_q, self.W), dtype=np.float64)
+        cnt = np.empty((self.n_q, self.W), dtype=np.int64)
+        self.ctx.check(_lib.xpcs_raw_stream_read_g2(self.h, g2.ctypes.data, cnt.ctypes.data))
+        return g2, cnt
+
+    def frames(self) -> int:
+        return int(_lib.xpcs_raw_stream_frames(self.h))
+
+    def close(self):
+        if self.h:
+            _lib.xpcs_raw_stream_close(self.h)
+            self.h = None
 
 
 class Stream:
