@@ -1041,7 +1041,8 @@ def stream_capture(mode, path):
     make: fit the basis of the online-stream workload, fill a stream with history + 64
     frames, and save the basis and a checkpoint under `path`.  run: import that basis,
     restore the checkpoint into a fresh stream and push three single frames, each waited
-    for, so a profiler sees about twenty launches before them.  Prints no bench line."""
+    for, then one 64-frame step, so a profiler sees about twenty launches before them.
+    Prints no bench line."""
     import torch
     from paper_2407_20356_gb300 import xpcs as X
     from synth import ring_qmap
@@ -1069,6 +1070,7 @@ def stream_capture(mode, path):
         st.restore(np.fromfile(f_ckpt, dtype=np.uint8))
         for j in range(3):
             assert st.poll(st.push(pool[j:j + 1]), 60000)
+        assert st.poll(st.push(pool[:64]), 60000)  # then one 64-frame step
     print(f"stream capture {mode}: {st.frames()} frames", file=sys.stderr)
     st.close()
     ctx.close()
@@ -1078,8 +1080,9 @@ def profile_leg(args):
     """Profiling aid, no bench line: run one leg alone so that a profiler sees few launches.
 
     raw: the exact raw path (ingest, integer Gram with C, g2 and counts) on the chosen
-    workload, `--steps` calls after `--warmup`; grouped: the grouped masks' encode and
-    g2-only two-time (bf16x3) on the small grouped case.  Prints a short JSON line of
+    workload, `--steps` calls after `--warmup`; compressed: the compressed two-time of the
+    chosen workload with C stored, g2 and counts (default configuration); grouped: the
+    grouped masks' g2-only two-time on the small grouped case.  Prints a short JSON line of
     event-timed milliseconds per call."""
     import torch
     from paper_2407_20356_gb300 import xpcs as X
@@ -1108,6 +1111,27 @@ def profile_leg(args):
             X.xpcs_twotime_raw(ctx, rings, Xd, T, C_out=C, g2_out=g2, count_out=cnt)
 
         flops = 2.0 * H * W * T * (T + 1) / 2
+    elif args.leg == "compressed":
+        wl = dict(WORKLOAD if args.workload == "c2" else SMALL)
+        H, W, T, n_q, k = wl["H"], wl["W"], wl["T"], wl["n_q"], wl["k"]
+        gen = TorchSpeckle(H, W, wl["mean"], wl["D"], wl["seed"], dtype=wl["dtype"], device=str(dev))
+        Xd = torch.empty((T, H * W), dtype=torch.uint16, device=dev)
+        for i in range(0, T, 1000):
+            Xd[i:i + 1000].copy_(gen.next(min(1000, T - i)))
+        del gen
+        ctx = X.Context(0, 0, stream.cuda_stream)
+        rings = X.Rings(ctx, torch.from_numpy(ring_qmap(H, W, n_q)).to(dev), H * W, n_q)
+        basis = X.xpcs_fit_basis(ctx, rings, Xd, wl["n_fit"], k)
+        A = torch.empty((T, k), dtype=torch.float32, device=dev)
+        X.xpcs_encode(ctx, basis, Xd, T, A)
+        C = torch.empty((n_q, T, T), dtype=torch.float32, device=dev)
+        g2 = torch.empty((n_q, T), dtype=torch.float64, device=dev)
+        cnt = torch.empty((n_q, T), dtype=torch.int64, device=dev)
+
+        def call():
+            X.xpcs_twotime(ctx, basis, A, T, args.prec, C_out=C, g2_out=g2, count_out=cnt)
+
+        flops = 2.0 * n_q * k * T * (T + 1) / 2
     else:
         gw = dict(GROUPED_SMALL)
         from synth import sector_qmap
@@ -1188,13 +1212,14 @@ def main():
     ap.add_argument("--stream-seconds", type=float, default=10.0, help="paced part of the stream leg")
     ap.add_argument("--stream-capture", choices=["make", "run"],
                     help="profiling aid, no bench line: make = fill the online stream and checkpoint it; "
-                         "run = restore it and push three single frames")
+                         "run = restore it and push three single frames and one 64-frame step")
     ap.add_argument("--capture-dir", default="/tmp", help="where --stream-capture keeps its basis and checkpoint")
     ap.add_argument("--sweep", action="store_true",
                     help="with --leg: also time the two-time kernel in every configuration")
-    ap.add_argument("--leg", choices=["raw", "grouped"],
-                    help="profiling aid, no bench line: run only the raw path (on --workload) or the grouped "
-                         "g2-only two-time (small grouped case) and print its event-timed call time")
+    ap.add_argument("--leg", choices=["raw", "compressed", "grouped"],
+                    help="profiling aid, no bench line: run only the raw path or the compressed two-time with C "
+                         "stored (on --workload), or the grouped g2-only two-time (small grouped case), and print "
+                         "its event-timed call time")
     args = ap.parse_args()
     if args.stream_capture:
         stream_capture(args.stream_capture, args.capture_dir)

@@ -74,10 +74,11 @@ XPCS_DEV uint64_t wait_limit_ns(const uint32_t* status) {
 }
 
 // Wait until the phase with the given parity has completed, within the kernel's limit.
-// Every limit is at least 1 ms, so the limit word (device or host-mapped memory) is read
-// only once a wait has already lasted that long: short waits never touch it.
-XPCS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
-  if (mbar_try_wait(bar, parity)) return true;
+// The first poll is inline; the rest of the wait is one out-of-line function, which keeps
+// the code at each of the many wait sites of a kernel small (inlined everywhere, the waits
+// made the two-time kernel 8 % slower).  Every limit is at least 1 ms, so the limit word
+// (device or host-mapped memory) is read only once a wait has already lasted that long.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, uint32_t* status) {
   const uint64_t t0 = globaltimer();
   uint64_t limit = 1000000ull;  // 1 ms, until the real limit is read
   bool have_limit = false;
@@ -94,6 +95,11 @@ XPCS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
       return false;
     }
   }
+}
+
+XPCS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity, status);
 }
 
 // Warp-wide bounded wait: lane 0 polls, the warp then agrees on the outcome.  The
