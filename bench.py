@@ -49,10 +49,10 @@ SERVING = dict(streams=[dict(H=1536, W=2048, rate_hz=2000.0, k=256, D=1e-4),
                         dict(H=1024, W=1024, rate_hz=10000.0, k=128, D=4.64e-4),
                         dict(H=512, W=512, rate_hz=50000.0, k=128, D=2.15e-3),
                         dict(H=256, W=256, rate_hz=100000.0, k=64, D=1e-2)],
-               n_q=100, history=200000, max_batch=64, mean=0.02, n_fit=1000, pool=64, seed=20356005)
+               n_q=100, history=200000, max_batch=128, mean=0.02, n_fit=1000, pool=128, seed=20356005)
 # online stream: one 1 Mpx detector at 10 kHz, history of 1e5 frames
 STREAM = dict(H=1024, W=1024, dtype="uint16", mean=0.02, D=5e-4, n_q=36, k=128, n_fit=1000, history=100000,
-              rate_hz=10000.0, pool=2048, max_batch=64, seed=20356003)
+              rate_hz=10000.0, pool=2048, max_batch=128, seed=20356003)
 STREAM_NAME = ("1024x1024 uint16 stream, Poisson AR(1) speckle mean 0.02 D=5e-4, 36 q-rings, k=128 basis fit on "
                "a 1000-frame calibration run, history 100000 frames, frames arriving at 10 kHz in device memory")
 
@@ -1016,20 +1016,21 @@ def run_raw_stream_equivalent(X, ctx, basis, rings, pool, sw, histories=(10000, 
     for Wr in histories:
         rs = X.RawStream(ctx, rings, Wr, dtype=sw["dtype"])
         rwait = lambda _t: ctx.synchronize()  # the raw stream runs on the context's stream
-        _, pushed = feed(rs.push, rwait, Wr, 64, 0)  # fill the history
-        t64, pushed = feed(rs.push, rwait, 1280, 64, pushed)
+        _, pushed = feed(rs.push, rwait, Wr, sw["max_batch"], 0)  # fill the history
+        t64, pushed = feed(rs.push, rwait, 1280, sw["max_batch"], pushed)
         t1, pushed = feed(rs.push, rwait, 64, 1, pushed)
         rs.close()
         st = X.Stream(ctx, basis, Wr, sw["max_batch"], dtype=sw["dtype"])
         swait = lambda t: st.poll(t, 600000)  # the stream runs on its own CUDA stream
-        _, pc = feed(st.push, swait, Wr, 64, 0)
-        c64, pc = feed(st.push, swait, 4096, 64, pc)
+        _, pc = feed(st.push, swait, Wr, sw["max_batch"], 0)
+        c64, pc = feed(st.push, swait, 4096, sw["max_batch"], pc)
         c1, pc = feed(st.push, swait, 1024, 1, pc)
         st.close()
         out[f"history_{Wr}"] = {
-            "raw_frames_per_s_batch64": 1280 / t64, "raw_frames_per_s_batch1": 64 / t1,
-            "compressed_frames_per_s_batch64": 4096 / c64, "compressed_frames_per_s_batch1": 1024 / c1,
-            "speedup_batch64": (4096 / c64) / (1280 / t64), "speedup_batch1": (1024 / c1) / (64 / t1),
+            "batch": sw["max_batch"],
+            "raw_frames_per_s_batch": 1280 / t64, "raw_frames_per_s_batch1": 64 / t1,
+            "compressed_frames_per_s_batch": 4096 / c64, "compressed_frames_per_s_batch1": 1024 / c1,
+            "speedup_batch": (4096 / c64) / (1280 / t64), "speedup_batch1": (1024 / c1) / (64 / t1),
             "raw_history_gb": (128 * ((Wr + 126) // 128 + 2)) * rings_padded(rings) * 2 / 1e9,
         }
     return out
@@ -1041,7 +1042,8 @@ def stream_capture(mode, path):
     make: fit the basis of the online-stream workload, fill a stream with history + 64
     frames, and save the basis and a checkpoint under `path`.  run: import that basis,
     restore the checkpoint into a fresh stream and push three single frames, each waited
-    for, then one 64-frame step, so a profiler sees about twenty launches before them.
+    for, then a 64-frame and a 128-frame step, so a profiler sees about twenty launches
+    before them.
     Prints no bench line."""
     import torch
     from paper_2407_20356_gb300 import xpcs as X
@@ -1070,7 +1072,8 @@ def stream_capture(mode, path):
         st.restore(np.fromfile(f_ckpt, dtype=np.uint8))
         for j in range(3):
             assert st.poll(st.push(pool[j:j + 1]), 60000)
-        assert st.poll(st.push(pool[:64]), 60000)  # then one 64-frame step
+        assert st.poll(st.push(pool[:64]), 60000)  # then a 64-frame step (to the block's end)
+        assert st.poll(st.push(pool[:128]), 60000)  # and a whole 128-frame block
     print(f"stream capture {mode}: {st.frames()} frames", file=sys.stderr)
     st.close()
     ctx.close()
@@ -1212,7 +1215,7 @@ def main():
     ap.add_argument("--stream-seconds", type=float, default=10.0, help="paced part of the stream leg")
     ap.add_argument("--stream-capture", choices=["make", "run"],
                     help="profiling aid, no bench line: make = fill the online stream and checkpoint it; "
-                         "run = restore it and push three single frames and one 64-frame step")
+                         "run = restore it and push three single frames, a 64-frame and a 128-frame step")
     ap.add_argument("--capture-dir", default="/tmp", help="where --stream-capture keeps its basis and checkpoint")
     ap.add_argument("--sweep", action="store_true",
                     help="with --leg: also time the two-time kernel in every configuration")

@@ -371,12 +371,15 @@ xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t his
 xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t history, int max_batch,
                                   xpcs_dtype dtype, const xpcs_options* opt, xpcs_stream** out);
 /* The row-update configuration a stream step of b frames takes for n_q rings and a k-term
- * basis (host-side, no context or device needed): *lags = the lag tile (the longest of
- * 128, 120, 96, 64, 32 with lags + b - 1 <= 128 whose layout fits shared memory),
- * *w_stages = pair-operand stages (1 or 2), *epilogue = 0 rotated blocks, 1 skewed
- * buffers, 2 the small-step form (exactly when b <= 8), *smem_bytes = dynamic shared
- * memory of the launch.  Outputs are nullable.  XPCS_EINVAL unless 1 <= n_q <= 1024,
- * 1 <= k <= 256 and 1 <= b <= 64; XPCS_ENOTSUP if nothing fits. */
+ * basis (host-side, no context or device needed).  Steps of 32 frames or more (cut so that
+ * they stay within one 128-frame block) run on the two-time kernel: *epilogue = 3, *lags =
+ * 128 (one tile diagonal per work item), *w_stages = 0, *smem_bytes = that kernel's.
+ * Smaller steps take the row update kernel: *lags = the lag tile (the longest of 128, 120,
+ * 96, 64, 32 with lags + b - 1 <= 128 whose layout fits shared memory), *w_stages =
+ * pair-operand stages (1 or 2), *epilogue = 0 rotated blocks, 1 skewed buffers, 2 the
+ * small-step form (exactly when b <= 8), *smem_bytes = dynamic shared memory of the
+ * launch.  Outputs are nullable.  XPCS_EINVAL unless 1 <= n_q <= 1024, 1 <= k <= 256 and
+ * 1 <= b <= 64; XPCS_ENOTSUP if nothing fits. */
 xpcs_status xpcs_stream_row_tile(int n_q, int k, int b, int* lags, int* w_stages, int* epilogue, int* smem_bytes);
 /* Push n frames (n x M counts in host memory).  The frames are copied before the call
  * returns, so the caller may reuse its buffer.  *ticket (nullable) = frames pushed so far;
@@ -435,7 +438,7 @@ typedef struct xpcs_raw_stream xpcs_raw_stream;
 xpcs_status xpcs_raw_stream_open(xpcs_ctx* ctx, const xpcs_rings* rings, int64_t history, xpcs_dtype dtype,
                                  xpcs_raw_stream** out);
 /* Push n frames already in device memory (n x M counts of the stream's dtype), processed in
- * steps of at most 64 frames that do not cross a 128-frame block.  Returns once they are
+ * steps that do not cross a 128-frame block.  Returns once they are
  * folded in (unless the context is asynchronous). */
 xpcs_status xpcs_raw_stream_push_device(xpcs_raw_stream* rs, const void* frames, int64_t n);
 /* g2_host (nullable): n_q x history f64, NaN without pairs; count_host (nullable): n_q x

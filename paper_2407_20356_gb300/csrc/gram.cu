@@ -210,12 +210,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const int4 w = item_at(p, item);
         const int q = w.x, delta = w.y;
-        const int nk = p.k_chunks[q];
+        const int nk = p.sm ? p.sm_nk : p.k_chunks[q];
         const int nc = p.split ? 2 * nk : nk;  // chunks per tile
-        const int koff = p.k_off[q];
-        const int rowbase = q * p.ring_rows;
+        const int koff = p.sm ? 0 : p.k_off[q];
+        const int rowbase = p.sm ? 0 : q * p.ring_rows;
         for (int I = w.z; I < w.w && ok; ++I) {
           const int J = col_block(p, I, delta);
+          const int rrow = p.sm ? q * TILE : rowbase + J * TILE;  // first row of the R box
           for (int c = 0; c < nc; ++c, ++it) {
             const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
             if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, p.status)) {
@@ -229,7 +230,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
             mbar_arrive_expect_tx(&full[s], CF::stage_bytes);
             tma_load_2d(st, &tmL, &full[s], x, rowbase + I * TILE);
             // NP x 128 rows of R (rows past the matrix are filled with zeros)
-            tma_load_2d(st + CF::chunk_l, &tmR, &full[s], x, rowbase + J * TILE);
+            tma_load_2d(st + CF::chunk_l, &tmR, &full[s], x, rrow);
           }
         }
       }
@@ -247,7 +248,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       bool ok = true, issued = false;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const int4 w = item_at(p, item);
-        const int nk = p.k_chunks[w.x];
+        const int nk = p.sm ? p.sm_nk : p.k_chunks[w.x];
         const int nc = p.split ? 2 * nk : nk;
         const int n_units = units_of(p, w);
         for (int u = 0; u < n_units && ok; ++u, ++unit) {
@@ -334,7 +335,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
         const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
         // per-tile metadata first, so its load latency overlaps the wait for the MMA
         const long long t1 = (long long)I * TILE + i_row;
-        const float ri = rq[t1];
+        const float ri = work ? rq[t1] : 0.f;
         const int nh = (NP == 2 && I + delta + 1 < p.nT) ? 2 : 1;
         bool bad[NP], interior[NP];
 #pragma unroll
@@ -401,7 +402,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       for (int u = 0; u < n_units && ok; ++u, ++unit) {
         const int I = unit_range(p, w, u).I_begin;
         const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
-        const float ri = p.raw ? rq[(size_t)I * TILE + i_row] : 1.f;
+        const float ri = !p.raw ? 1.f
+                         : p.sm ? p.r[((size_t)I * TILE + i_row) * p.r_ld + q]
+                                : rq[(size_t)I * TILE + i_row];
         if (*abort_flag || !mbar_wait_warp(&tfull[b], tph, p.status)) {  // warp-uniform outcome
           *abort_flag = 1;
           ok = false;
@@ -415,7 +418,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           const bool last = h2 == nh - 1;  // TMEM is released after the unit's last load
           const uint32_t tbase =
               tmem_base + b * (NP * TILE) + h2 * TILE + ((uint32_t)(r * 32) << 16) + 64 * h;
-          const float* rj = (p.rc ? p.rc + (size_t)q * p.T_pad : rq) + (size_t)col_block(p, I, delta + h2) * TILE + 64 * h;
+          const float* rj = p.sm ? nullptr
+                                 : (p.rc ? p.rc + (size_t)q * p.T_pad : rq) +
+                                       (size_t)col_block(p, I, delta + h2) * TILE + 64 * h;
           if constexpr (STRIP) {
             // whole strip: row 32 k + lane holds strip diagonal 32 (k - 1) + lane (acc[k])
             __syncwarp();  // the previous tile's row sums are read
@@ -429,7 +434,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[b]);
               }
-              if (p.raw) {
+              if (p.sm) {  // stream step: the w columns carry their own scale
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * ri);
+              } else if (p.raw) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
                   v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
@@ -454,7 +462,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[b]);
               }
-              if (p.raw) {
+              if (p.sm) {  // stream step: the w columns carry their own scale
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * ri);
+              } else if (p.raw) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
                   v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));

@@ -130,6 +130,10 @@ struct xpcs_stream {
   // ring sums (64 x n_q), both null otherwise
   int* d_qmap = nullptr;
   long long* d_Sx = nullptr;
+  // steps on the two-time kernel: the block's w rows per ring (zero outside a step), partials
+  __nv_bfloat16* d_Wg = nullptr;     // n_q x 128 x 2 kpad
+  float* d_gpart = nullptr;          // n_q x nd x 256
+  CUtensorMap tmWg;
   int kpad = 0;                      // k rounded up to 64
   CUtensorMap tmA, tmW, tmR;         // tensor maps of d_A2, d_W2 (64 x 128 boxes) and d_Rh
   // tensor maps of d_g2sum and d_cnt (row pitch Wp), one per row-update lag tile RT_LTS[i]

@@ -52,6 +52,11 @@ struct GramParams {
   // with q = i / ring_nd, delta = i mod ring_nd, I = (ring_J - delta) mod ring_nb
   int ring_nb, ring_nd, ring_J;
   const float* rc;         // nullable [n_q][T_pad] column scales (default: r)
+  // compressed stream step (sm = 1, with the ring fields above): L = the coefficient history
+  // shared by all rings (rows I*128 ..), R = the step's block of 128 w rows of ring q (rows
+  // q*128 .., zero except the step's frames, which carry their scale r_q(t)), sm_nk
+  // 64-wide chunks per piece, row scale r[slot * r_ld + q], no column scale
+  int sm, sm_nk, r_ld;
   const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined
   const uint32_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
   float* C;                // nullable [n_q][T][T]
@@ -216,7 +221,19 @@ struct StreamStep {
   const CUtensorMap* tmR;
   const CUtensorMap* tmG;  // [RT_N_LT]: one per lag tile of RT_LTS
   const CUtensorMap* tmC;  // [RT_N_LT]
+  // steps of at least STREAM_GRAM_MIN frames (all in one 128-frame block) run on the
+  // two-time kernel: w rows of the block per ring, diagonal partials
+  __nv_bfloat16* Wg;       // n_q x 128 x 2 kpad: w_q(t) of the step's frames, row t mod 128,
+                           // zero rows elsewhere (the fold clears the step's rows)
+  float* gpart;            // n_q x nd x 256 diagonal partial sums
+  int nd;                  // tile diagonals that can hold a lag < W
+  const CUtensorMap* tmWg;
 };
+// Smallest step (frames) that runs on the two-time kernel; smaller steps take the row
+// update kernel.  Steps never cross a 128-frame block when they may take the former.
+constexpr int STREAM_GRAM_MIN = 32;
+// tile diagonals of the history that can hold a lag < W
+inline int stream_nd(long long W) { return (int)((W + 126) / 128 + 1); }
 cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st);
 
 // Row update of a step of at most 64 frames on the tensor cores (see stream_tc.cu).

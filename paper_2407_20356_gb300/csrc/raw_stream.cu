@@ -41,8 +41,8 @@ struct xpcs_raw_stream {
   __nv_bfloat16* d_Xp = nullptr;  // (128 nb) x Mp ring-sorted bf16 counts
   float* d_r = nullptr;           // n_q x (128 nb) row scales sqrt(M_q)/S_q(t)
   float* d_rc = nullptr;          // n_q x (128 nb) column scales: nonzero only during a step
-  long long* d_S = nullptr;       // n_q x 64 ring sums of a step's frames
-  long long* d_S2 = nullptr;      // n_q x 64 sums of squares
+  long long* d_S = nullptr;       // n_q x 128 ring sums of a step's frames
+  long long* d_S2 = nullptr;      // n_q x 128 sums of squares
   float* d_part = nullptr;        // n_q x nd x nb x 256 diagonal partial sums
   double* d_g2sum = nullptr;      // n_q x W
   long long* d_cnt = nullptr;     // n_q x W
@@ -52,7 +52,7 @@ struct xpcs_raw_stream {
 
 namespace {
 
-constexpr int RS_STEP = 64;  // frames per step at most
+constexpr int RS_STEP = 128;  // frames per step at most (one 128-frame block)
 
 __global__ void raw_stream_factors_kernel(const long long* S, const long long* S2, const long long* Mq, int n_q,
                                           int b, long long slot0, long long rows, float* r, float* rc,
@@ -251,7 +251,7 @@ extern "C" xpcs_status xpcs_raw_stream_push_device(xpcs_raw_stream* R, const voi
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const size_t fb = (size_t)R->M * (R->dtype == XPCS_U8 ? 1 : 2);
   for (int64_t f0 = 0; f0 < n;) {
-    // steps of at most 64 frames that do not cross a 128-frame block
+    // steps that do not cross a 128-frame block
     const int64_t room = 128 - (R->frames & 127);
     const int b = (int)std::min<int64_t>({RS_STEP, room, n - f0});
     XPCS_TRY(raw_stream_step(R, static_cast<const char*>(frames) + f0 * fb, b));

@@ -212,7 +212,11 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
         atomicAnd(vb + (sl >> 6), ~bit);
     }
   }
-  __nv_bfloat16* wrow = s.W2 + (size_t)w2_pair_row(fi, q, s.b, s.n_q) * 2 * kp;
+  // the w row: pair order for the row update kernel, or row t mod 128 of the ring's block
+  // for the two-time kernel (its other rows are zero, so only the step's frames count)
+  const bool gram = s.b >= STREAM_GRAM_MIN;
+  __nv_bfloat16* wrow = gram ? s.Wg + ((size_t)q * 128 + (t & 127)) * 2 * kp
+                             : s.W2 + (size_t)w2_pair_row(fi, q, s.b, s.n_q) * 2 * kp;
   const float* Gq = s.G32 + (size_t)q * k * k;
   for (int j = tid; j < kp; j += blockDim.x) {
     float v = 0.f;
@@ -256,6 +260,51 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
   }
 }
 
+// Bits [slot, slot + n) (n <= 64) of one ring's validity words (slots past the ring's end
+// are its mirror, so no wrap is needed for slot < cap).
+XPCS_DEV unsigned long long vbits_window(const unsigned long long* vb, long long slot, int n) {
+  const int sh = (int)(slot & 63);
+  const unsigned long long lo = vb[slot >> 6] >> sh;
+  const unsigned long long hi = sh ? vb[(slot >> 6) + 1] << (64 - sh) : 0ull;
+  const unsigned long long v = lo | hi;
+  return n >= 64 ? v : v & ((1ull << n) - 1ull);
+}
+
+// After a step on the two-time kernel: lag tau = 128 d + e gets slot 128 + e of tile
+// diagonal d and slot e of tile diagonal d + 1 (TwoSum into the f32-pair sums), its pair
+// count from the validity bits of the step's frames and of the frames tau earlier, and the
+// step's w rows are cleared (the next step of the block must not see them).
+__global__ void stream_fold_kernel(const StreamStep s, int nd_step) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long span = s.W > s.b ? s.W : s.b;
+  if (i >= (long long)s.n_q * span) return;
+  const int q = (int)(i / span);
+  const long long tau = i - (long long)q * span;
+  if (tau < s.W) {
+    const int d = (int)(tau >> 7), e = (int)(tau & 127);
+    float sum = 0.f;
+    if (d < nd_step) sum += s.gpart[((size_t)q * s.nd + d) * DIAG_SLOTS + TILE + e];
+    if (d + 1 < nd_step) sum += s.gpart[((size_t)q * s.nd + d + 1) * DIAG_SLOTS + e];
+    // pairs (t0 + f, t0 + f - tau), f < b, both frames defined and t0 + f - tau >= 0
+    const unsigned long long* vb = s.vbits + (size_t)q * s.vwords;
+    const long long f0 = tau > s.t0 ? tau - s.t0 : 0;  // first frame with a partner
+    long long n = 0;
+    for (long long f = f0; f < s.b; f += 64) {  // up to 128 frames: two 64-bit windows
+      const int nf = (int)min(64LL, s.b - f);
+      const unsigned long long a = vbits_window(vb, (s.t0 + f) % s.cap, nf);
+      const unsigned long long h = vbits_window(vb, (s.t0 + f - tau) % s.cap, nf);
+      n += __popcll(a & h);
+    }
+    const size_t j = (size_t)q * s.Wp + tau;
+    if (sum != 0.f) s.g2sum[j] = f32pair_add(s.g2sum[j], sum);
+    s.cnt[j] += n;
+  }
+  if (tau < s.b) {  // clear w row (q, t0 + tau) of the block: 2 kpad bf16, 16 bytes at a time
+    uint4* row = reinterpret_cast<uint4*>(s.Wg + ((size_t)q * 128 + ((s.t0 + tau) & 127)) * 2 * s.kpad);
+    for (int c = 0; c < s.kpad / 4; ++c) row[c] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
 // g2 = (hi + lo) / count of each lag bin (f32 pair sums, added in FP64); NaN without pairs
 __global__ void stream_g2_kernel(const float2* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
                                  double* g2) {
@@ -275,7 +324,8 @@ __global__ void basis_f32_kernel(const double* B, long long n, float* B32) {
 
 cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   // the pair-ordered w rows of this step must fit the W2 allocation
-  if (s.b < 1 || s.b > 64 || (long long)((s.n_q + 35) / 36) * w2_mtiles(s.b, s.n_q) * 128 > s.w2_rows)
+  if (s.b < 1 || s.b > 128 ||
+      (s.b < STREAM_GRAM_MIN && (long long)((s.n_q + 35) / 36) * w2_mtiles(s.b, s.n_q) * 128 > s.w2_rows))
     return cudaErrorInvalidValue;
   if (s.Sx && s.n_q > SE_MAX_RINGS) return cudaErrorInvalidValue;
   cudaError_t e = s.Sx ? cudaMemsetAsync(s.Sx, 0, (size_t)s.b * s.n_q * sizeof(long long), st) : cudaSuccess;
@@ -287,6 +337,40 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   frame_factors_kernel<<<dim3(s.b, s.n_q), 128, 0, st>>>(s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (s.b >= STREAM_GRAM_MIN) {
+    // the two-time kernel on (history block J - delta, the step's block J) tiles of every
+    // ring: L = the coefficient history (shared by the rings), R = the block's w rows of
+    // ring q (scaled by r_q(t); zero for frames outside the step), row scale r_q(s); the
+    // diagonal sums then go into the running lag sums
+    if (s.cap % 128 || ((s.t0 & 127) + s.b) > 128) return cudaErrorInvalidValue;
+    const int nb = (int)(s.cap / 128);
+    const int nd_step = (int)std::min<long long>(s.nd, (s.t0 >> 7) + 1);
+    GramParams gp{};
+    gp.T = (int)s.cap;
+    gp.nT = s.nd;  // partials [n_q][nd][1][256]
+    gp.T_pad = 0;
+    gp.maxC = 1;
+    gp.CH = nb + 1;  // chunk index I / CH = 0
+    gp.n_items = s.n_q * nd_step;
+    gp.items = nullptr;
+    gp.ring_nb = nb;
+    gp.ring_nd = nd_step;
+    gp.ring_J = (int)((s.t0 >> 7) % nb);
+    gp.sm = 1;
+    gp.sm_nk = s.kpad / 64;
+    gp.r_ld = stream_npad(s.n_q);
+    gp.fmt = 1;
+    gp.split = 1;
+    gp.raw = 1;  // epilogue scales: r_q(s) for the history rows, the mask for the columns
+    gp.r = s.Rh;
+    gp.partials = s.gpart;
+    gp.status = s.status;
+    e = launch_gram(*s.tmA, *s.tmWg, gp, std::min(gp.n_items, s.num_sms), st);
+    if (e != cudaSuccess) return e;
+    const long long span = std::max<long long>(s.W, s.b);
+    stream_fold_kernel<<<(unsigned)((s.n_q * span + 255) / 256), 256, 0, st>>>(s, nd_step);
+    return cudaGetLastError();
+  }
   // row update of the step (at most 64 frames: every pair of a lag tile then lies in
   // one 128-row history operand)
   RowTcParams p{};
@@ -347,6 +431,13 @@ extern "C" xpcs_status xpcs_stream_row_tile(int n_q, int k, int b, int* lags, in
                                             int* smem_bytes) {
   if (n_q < 1 || n_q > 1024 || k < 1 || k > 256 || b < 1 || b > 64) return XPCS_EINVAL;
   const int kpad = (k + 63) / 64 * 64;
+  if (b >= xpcs::STREAM_GRAM_MIN) {  // the two-time kernel on 128-frame blocks
+    if (lags) *lags = 128;
+    if (w_stages) *w_stages = 0;
+    if (epilogue) *epilogue = 3;
+    if (smem_bytes) *smem_bytes = xpcs::gram_smem_bytes();
+    return XPCS_OK;
+  }
   int lt = 0, wst = 0, epi = 0;
   if (!xpcs::row_update_config(n_q, kpad, b, &lt, &wst, &epi)) return XPCS_ENOTSUP;
   if (lags) *lags = lt;

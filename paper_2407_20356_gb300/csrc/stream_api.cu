@@ -26,10 +26,16 @@ namespace {
 
 int kpad_of(int k) { return (k + 63) / 64 * 64; }
 // ring slots: the window plus a batch, and at least 256 so that a 128-row history
-// operand starting anywhere in the ring ends before the 128 mirrored rows do
-int64_t ring_cap(int64_t W, int max_batch) { return std::max<int64_t>(W + max_batch, 256); }
+// operand starting anywhere in the ring ends before the 128 mirrored rows do; whole
+// 128-frame blocks, at least one more than the tile diagonals a lag < W can reach (the
+// two-time kernel reads the history by blocks, the step's block among them)
+int64_t ring_cap(int64_t W, int max_batch) {
+  const int64_t c = std::max<int64_t>({W + max_batch, 256, 128LL * (stream_nd(W) + 1)});
+  return (c + 127) / 128 * 128;
+}
 // frames per stream step (one launch of each stream kernel)
-constexpr int STEP_MAX = 64;
+constexpr int STEP_MAX = 64;        // frames per step on the row update kernel (at most)
+constexpr int STEP_MAX_GRAM = 128;  // frames per step on the two-time kernel (one block)
 // W2 rows: the pair-ordered M-tiles of every ring group for any step size, plus one
 // spare 128-row box
 int64_t w2_rows(int max_batch, int n_q) {
@@ -42,7 +48,7 @@ int nblk_of(int64_t M) { return (int)((M + 4095) / 4096); }
 int64_t wpitch(int64_t W) { return (W + 63) / 64 * 64; }
 
 struct Sizes {
-  size_t frames, A2, Rh, vbits, g2sum, cnt, part, a, W2, g2, stage;
+  size_t frames, A2, Rh, vbits, g2sum, cnt, part, a, W2, g2, stage, Wg, gpart;
 };
 
 Sizes stream_sizes(int64_t M, int n_q, int k, int64_t W, int max_batch, int eb) {
@@ -59,6 +65,8 @@ Sizes stream_sizes(int64_t M, int n_q, int k, int64_t W, int max_batch, int eb) 
   z.W2 = (size_t)w2_rows(max_batch, n_q) * 2 * kpad_of(k) * 2;
   z.g2 = (size_t)n_q * W * 8;
   z.stage = (size_t)max_batch * M * eb;
+  z.Wg = (size_t)n_q * 128 * 2 * kpad_of(k) * 2;
+  z.gpart = (size_t)n_q * stream_nd(W) * DIAG_SLOTS * 4;
   return z;
 }
 
@@ -75,10 +83,12 @@ void stream_free(xpcs_stream* S) {
   dev_free(ctx, S->d_part, z.part);
   dev_free(ctx, S->d_a, z.a);
   dev_free(ctx, S->d_W2, z.W2);
+  dev_free(ctx, S->d_Wg, z.Wg);
+  dev_free(ctx, S->d_gpart, z.gpart);
   if (S->h_status) cudaFreeHost(S->h_status);
   dev_free(ctx, S->d_g2, z.g2);
   dev_free(ctx, S->d_qmap, (size_t)S->M * 4);
-  dev_free(ctx, S->d_Sx, (size_t)64 * S->n_q * 8);
+  dev_free(ctx, S->d_Sx, (size_t)STEP_MAX_GRAM * S->n_q * 8);
   for (int i = 0; i < 2; ++i) {
     if (S->h_stage[i]) cudaFreeHost(S->h_stage[i]);
     if (S->stage_done[i]) cudaEventDestroy(S->stage_done[i]);
@@ -100,7 +110,7 @@ namespace xpcs {
 
 size_t stream_footprint(const xpcs_basis* B, int64_t W, int max_batch, int elem_bytes) {
   const Sizes z = stream_sizes(B->M, B->n_q, B->k, W, max_batch, elem_bytes);
-  size_t b = z.frames + z.A2 + z.Rh + z.vbits + z.g2sum + z.cnt + z.part + z.a + z.W2 + z.g2;
+  size_t b = z.frames + z.A2 + z.Rh + z.vbits + z.g2sum + z.cnt + z.part + z.a + z.W2 + z.g2 + z.Wg + z.gpart;
   if (!B->d_B32) b += (size_t)B->rings->M * B->k * 4;  // f32 basis copy made on first use
   return b;
 }
@@ -135,12 +145,12 @@ extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B,
     return fail(ctx, XPCS_EINVAL, "bad stream_open args");
   const bool exact = opt && opt->qmean == XPCS_QMEAN_EXACT_RAW;
   *out = nullptr;
-  int lt = 0, wst = 0, epi = 0;  // steps of up to 64 frames: the largest a push is cut into
-  if (!row_update_config(B->rings->n_q, kpad_of(B->k), 64, &lt, &wst, &epi))
+  int lt = 0, wst = 0, epi = 0;  // the largest step the row update kernel takes
+  if (!row_update_config(B->rings->n_q, kpad_of(B->k), STREAM_GRAM_MIN - 1, &lt, &wst, &epi))
     return fail(ctx, XPCS_ENOTSUP, "stream: the row-update tile does not fit shared memory at this k");
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int eb = dtype == XPCS_U8 ? 1 : 2;
-  const size_t exact_bytes = exact ? (size_t)B->rings->M * 4 + (size_t)64 * B->rings->n_q * 8 : 0;
+  const size_t exact_bytes = exact ? (size_t)B->rings->M * 4 + (size_t)STEP_MAX_GRAM * B->rings->n_q * 8 : 0;
   const size_t need = stream_footprint(B, history, max_batch, eb) + exact_bytes;
   if (ctx->budget && ctx->held + need > ctx->budget)
     return fail(ctx, XPCS_EBUSY,
@@ -184,9 +194,11 @@ extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B,
   XPCS_SALLOC(d_a, z.a, float*)
   XPCS_SALLOC(d_W2, z.W2, __nv_bfloat16*)
   XPCS_SALLOC(d_g2, z.g2, double*)
+  XPCS_SALLOC(d_Wg, z.Wg, __nv_bfloat16*)
+  XPCS_SALLOC(d_gpart, z.gpart, float*)
   if (exact) {
     XPCS_SALLOC(d_qmap, (size_t)B->rings->M * 4, int*)
-    XPCS_SALLOC(d_Sx, (size_t)64 * B->rings->n_q * 8, long long*)
+    XPCS_SALLOC(d_Sx, (size_t)STEP_MAX_GRAM * B->rings->n_q * 8, long long*)
   }
 #undef XPCS_SALLOC
   cudaError_t e = cudaSuccess;
@@ -200,6 +212,7 @@ extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B,
     e = cudaMemcpyAsync(S->d_qmap, B->rings->d_qmap, (size_t)B->rings->M * 4, cudaMemcpyDeviceToDevice, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_A2, 0, z.A2, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_W2, 0, z.W2, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_Wg, 0, z.Wg, S->stream);
   // status word, then (8 bytes on) the bounded-wait limit taken from the context
   if (st == XPCS_OK && e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_status, 16, cudaHostAllocMapped);
   if (st == XPCS_OK && e == cudaSuccess) {
@@ -222,6 +235,9 @@ extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B,
   if (st == XPCS_OK)
     st = make_map(ctx, &S->tmW, S->d_W2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * S->kpad,
                   w2_rows(max_batch, B->rings->n_q), 64, 128, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (st == XPCS_OK)
+    st = make_map(ctx, &S->tmWg, S->d_Wg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * S->kpad,
+                  (uint64_t)128 * B->rings->n_q, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B);
   if (st == XPCS_OK) {
     const int npad = stream_npad(B->rings->n_q);
     st = make_map(ctx, &S->tmR, S->d_Rh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, npad, S->cap + 128,
@@ -336,16 +352,25 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.tmC = S->tmC;
   s.g2sum = S->d_g2sum;
   s.cnt = S->d_cnt;
-  // steps of at most STEP_MAX frames; the batch completes with its last step
+  s.Wg = S->d_Wg;
+  s.gpart = S->d_gpart;
+  s.nd = stream_nd(S->W);
+  s.tmWg = &S->tmWg;
+  // steps of at most STEP_MAX_GRAM frames; the batch completes with its last step
   const size_t fb = (size_t)B->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
   cudaError_t e = cudaSuccess;
-  for (int64_t f0 = 0; f0 < n && e == cudaSuccess; f0 += STEP_MAX) {
+  for (int64_t f0 = 0; f0 < n && e == cudaSuccess; f0 += s.b) {
     s.X = static_cast<const char*>(X) + f0 * fb;
     s.vec16 = (reinterpret_cast<uintptr_t>(s.X) % 16 == 0) && fb % 16 == 0;
-    s.b = (int)std::min<int64_t>(STEP_MAX, n - f0);
     s.t0 = S->frames + f0;
+    // a step large enough for the two-time kernel takes up to the rest of its 128-frame
+    // block; smaller ones go to the row update kernel
+    const int room = 128 - (int)(s.t0 & 127);
+    s.b = (int)std::min<int64_t>(STEP_MAX_GRAM, n - f0);
+    if (s.b >= STREAM_GRAM_MIN) s.b = std::min(s.b, room);
+    if (s.b < STREAM_GRAM_MIN) s.b = std::min(s.b, STEP_MAX);
     e = launch_stream_step(s, S->stream);
-    if (e == cudaSuccess) ctx->launches += 4;
+    if (e == cudaSuccess) ctx->launches += s.b >= STREAM_GRAM_MIN ? 5 : 4;
   }
   if (e != cudaSuccess) {
     delete stamp;

@@ -270,3 +270,32 @@ def test_stream_checkpoint_and_resume(X, ctx):
     with pytest.raises(X.XpcsError) as e:
         other.restore(ck)
     assert e.value.status == X.XPCS_EINVAL
+
+
+@pytest.mark.parametrize("dtype,k,n_q,Wl,T,sizes,mb", [(np.uint16, 20, 4, 300, 900, (64, 40, 33, 100, 1, 64), 64),
+                                                       (np.uint8, 64, 40, 60, 500, (64, 32, 7), 64),
+                                                       (np.uint16, 150, 5, 200, 700, (64,), 64),
+                                                       (np.uint16, 24, 6, 400, 1000, (128, 100, 130, 5), 128)])
+def test_stream_large_steps_on_the_twotime_kernel(X, ctx, dtype, k, n_q, Wl, T, sizes, mb):
+    # steps of 32 frames or more run on the two-time kernel (history blocks x the step's
+    # 128-frame block); pushes are cut at block boundaries, the history ring wraps, and
+    # small steps on the row update kernel are mixed in
+    H, W = 24, 40
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 250, dtype, 700 + k)
+    st = X.Stream(ctx, basis, Wl, mb, dtype=np.dtype(dtype).name)
+    i, j = 0, 0
+    ticket = 0
+    while i < T:
+        n = min(sizes[j % len(sizes)], T - i)
+        ticket = st.push(np.ascontiguousarray(Xs[i:i + n]))
+        i += n
+        j += 1
+    assert st.poll(ticket, 10000)
+    assert st.frames() == T
+    g2, cnt = st.read_g2()
+    g_ref, c_ref = _oracle_window_g2(Xs, B, qmap, n_q, Wl)
+    np.testing.assert_array_equal(cnt, c_ref)
+    for q in range(n_q):
+        rm, _ = rel_errors(g2[q], g_ref[q])
+        assert rm < 1e-4, (q, rm)
+    st.close()
