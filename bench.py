@@ -415,6 +415,21 @@ def run_ours(args, wl):
     if not (args.no_serving or args.no_host) and args.workload == "c2":
         serving_res = run_serving_leg(X, dev, args)
 
+    # ---- ceiling of the serving workload: two-time tiles it needs per second at full
+    # history against the tile rate the online stream sustains on this GPU (steps of 128
+    # frames: every ring x every tile diagonal of the history per step)
+    if serving_res and stream_res:
+        sv, sw = SERVING, STREAM
+        nd = lambda W: (W + 126) // 128 + 1
+        need = sum(st["rate_hz"] for st in sv["streams"]) * sv["n_q"] * nd(sv["history"]) / 128
+        have = stream_res["sustained_frames_per_s"] * sw["n_q"] * nd(sw["history"]) / 128
+        serving_res["ceiling_model"] = {
+            "tiles_per_s_needed_at_full_history": need, "tiles_per_s_sustained_by_stream_leg": have,
+            "ratio": need / have,
+            "note": "a 128-frame step of a stream with n_q rings and history W runs n_q x (ceil(W/128)+1) "
+                    "two-time tiles; at the 2e5-frame cap the four streams' arrival rates need the ratio "
+                    "times the tile rate the online stream sustains, so they cannot all keep up on one GPU"}
+
     # ---- the small raw workload, timed in full beside the oracle
     c1_res = None
     if not args.no_host and rank == 0:
