@@ -146,9 +146,15 @@ __device__ __forceinline__ int units_of(const GramParams& p, const int4& w) { re
 // Work item i: from the list, or computed for a stream's raw row update (a ring of blocks)
 __device__ __forceinline__ int4 item_at(const GramParams& p, int i) {
   if (p.items) return p.items[i];
-  const int q = i / p.ring_nd, d = i - q * p.ring_nd;
+  const int qi = i / p.ring_nd, d = i - qi * p.ring_nd;
+  const int q = (p.sm && p.pairs) ? 2 * qi : qi;  // ring pairs of a stream step
   const int I = ((p.ring_J - d) % p.ring_nb + p.ring_nb) % p.ring_nb;
   return make_int4(q, d, I, I + 1);
+}
+// Whether the second half of a tile pair exists: tile (I, I + delta + 1) offline, ring q + 1
+// in a stream step
+__device__ __forceinline__ bool second_half(const GramParams& p, int q, int I, int delta) {
+  return p.sm ? q + 1 < p.sm_nq : I + delta + 1 < p.nT;
 }
 // Column block of tile (I, I + delta): wraps around the ring of a stream's history
 __device__ __forceinline__ int col_block(const GramParams& p, int I, int delta) {
@@ -264,7 +270,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           bool first = true;  // the unit's first MMA overwrites the accumulator
           for (int I = ur.I_begin; I < ur.I_end && ok; ++I) {
             // tile pair when the second tile exists, else N = 128 (first half only)
-            const uint32_t idesc = (NP == 2 && I + w.y + 1 < p.nT) ? idesc2 : idesc1;
+            const uint32_t idesc = (NP == 2 && second_half(p, w.x, I, w.y)) ? idesc2 : idesc1;
             for (int c = 0; c < nc; ++c, ++it) {
               const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
               if (*abort_flag || !mbar_wait(&full[s], ph, p.status)) {
@@ -393,8 +399,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       const int4 w = item_at(p, item);
       const int q = w.x, delta = w.y;
       const float* rq = p.r + (size_t)q * p.T_pad;
-      // the item's second tile diagonal (pairs) holds tiles
-      const bool has2 = NP == 2 && w.z + delta + 1 < p.nT;
+      // the item's second tile diagonal (pairs; in a stream step the second ring) holds tiles
+      const bool has2 = NP == 2 && second_half(p, q, w.z, delta);
       float acc[NP][3];
 #pragma unroll
       for (int h2 = 0; h2 < NP; ++h2) acc[h2][0] = acc[h2][1] = acc[h2][2] = 0.f;
@@ -405,13 +411,15 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
         const float ri = !p.raw ? 1.f
                          : p.sm ? p.r[((size_t)I * TILE + i_row) * p.r_ld + q]
                                 : rq[(size_t)I * TILE + i_row];
+        // a stream step's second half is ring q + 1, with its own row scale
+        const float ri2 = (NP == 2 && p.sm && has2) ? p.r[((size_t)I * TILE + i_row) * p.r_ld + q + 1] : ri;
         if (*abort_flag || !mbar_wait_warp(&tfull[b], tph, p.status)) {  // warp-uniform outcome
           *abort_flag = 1;
           ok = false;
           break;
         }
         tc_fence_after();
-        const int nh = (NP == 2 && (p.merge ? has2 : I + delta + 1 < p.nT)) ? 2 : 1;
+        const int nh = (NP == 2 && (p.merge || p.sm ? has2 : I + delta + 1 < p.nT)) ? 2 : 1;
 #pragma unroll
         for (int h2 = 0; h2 < NP; ++h2) {
           if (h2 >= nh) break;
@@ -436,7 +444,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
               }
               if (p.sm) {  // stream step: the w columns carry their own scale
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * ri);
+                for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * (h2 ? ri2 : ri));
               } else if (p.raw) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
@@ -464,7 +472,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
               }
               if (p.sm) {  // stream step: the w columns carry their own scale
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * ri);
+                for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * (h2 ? ri2 : ri));
               } else if (p.raw) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
@@ -502,7 +510,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
             const int k = e - (2 * (u >> 2) - ((u + 6) & 3) - 1);
             if (k >= 0 && k < 3) sum += rh[(u * 3 + k) * 32 + lane];
           }
-          float* slot = p.partials + (((size_t)q * p.nT + delta + h2) * p.maxC + chunk) * DIAG_SLOTS;
+          // offline: tile diagonal delta + h2 of ring q; stream step: ring q + h2, diagonal delta
+          const int sq = p.sm ? q + h2 : q, sd = p.sm ? delta : delta + h2;
+          float* slot = p.partials + (((size_t)sq * p.nT + sd) * p.maxC + chunk) * DIAG_SLOTS;
           slot[32 * dw + lane] = sum;
         }
       }

@@ -133,7 +133,7 @@ struct xpcs_stream {
   // steps on the two-time kernel: the block's w rows per ring (zero outside a step), partials
   __nv_bfloat16* d_Wg = nullptr;     // n_q x 128 x 2 kpad
   float* d_gpart = nullptr;          // n_q x nd x 256
-  CUtensorMap tmWg;
+  CUtensorMap tmWg, tmWg2;           // boxes of 128 and 256 rows
   int kpad = 0;                      // k rounded up to 64
   CUtensorMap tmA, tmW, tmR;         // tensor maps of d_A2, d_W2 (64 x 128 boxes) and d_Rh
   // tensor maps of d_g2sum and d_cnt (row pitch Wp), one per row-update lag tile RT_LTS[i]

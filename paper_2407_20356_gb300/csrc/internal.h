@@ -57,6 +57,8 @@ struct GramParams {
   // q*128 .., zero except the step's frames, which carry their scale r_q(t)), sm_nk
   // 64-wide chunks per piece, row scale r[slot * r_ld + q], no column scale
   int sm, sm_nk, r_ld;
+  int sm_nq;               // stream step: rings; with pairs, the two halves of an accumulator are
+                           // rings q and q + 1 (item q = 2 (i / ring_nd)) of one tile diagonal
   const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined
   const uint32_t* blk_bad;  // [n_q][nT] block holds an undefined frame (< T)
   float* C;                // nullable [n_q][T][T]
@@ -227,7 +229,8 @@ struct StreamStep {
                            // zero rows elsewhere (the fold clears the step's rows)
   float* gpart;            // n_q x nd x 256 diagonal partial sums
   int nd;                  // tile diagonals that can hold a lag < W
-  const CUtensorMap* tmWg;
+  const CUtensorMap* tmWg;  // boxes of 128 w rows (one ring)
+  const CUtensorMap* tmWg2; // boxes of 256 w rows (two rings)
 };
 // Smallest step (frames) that runs on the two-time kernel; smaller steps take the row
 // update kernel.  Steps never cross a 128-frame block when they may take the former.

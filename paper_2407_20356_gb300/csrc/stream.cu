@@ -351,7 +351,12 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     gp.T_pad = 0;
     gp.maxC = 1;
     gp.CH = nb + 1;  // chunk index I / CH = 0
-    gp.n_items = s.n_q * nd_step;
+    // ring pairs: one N = 256 MMA per K step covers rings q and q + 1 against one history
+    // chunk (the w blocks of neighbouring rings are consecutive rows)
+    const int pairs = s.n_q >= 2 ? 1 : 0;
+    gp.pairs = pairs;
+    gp.sm_nq = s.n_q;
+    gp.n_items = (pairs ? (s.n_q + 1) / 2 : s.n_q) * nd_step;
     gp.items = nullptr;
     gp.ring_nb = nb;
     gp.ring_nd = nd_step;
@@ -365,7 +370,7 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     gp.r = s.Rh;
     gp.partials = s.gpart;
     gp.status = s.status;
-    e = launch_gram(*s.tmA, *s.tmWg, gp, std::min(gp.n_items, s.num_sms), st);
+    e = launch_gram(*s.tmA, pairs ? *s.tmWg2 : *s.tmWg, gp, std::min(gp.n_items, s.num_sms), st);
     if (e != cudaSuccess) return e;
     const long long span = std::max<long long>(s.W, s.b);
     stream_fold_kernel<<<(unsigned)((s.n_q * span + 255) / 256), 256, 0, st>>>(s, nd_step);
