@@ -153,8 +153,9 @@ __device__ __forceinline__ int4 item_at(const GramParams& p, int i) {
 }
 // Whether the second half of a tile pair exists: tile (I, I + delta + 1) offline, ring q + 1
 // in a stream step
+template <int NP>
 __device__ __forceinline__ bool second_half(const GramParams& p, int q, int I, int delta) {
-  return p.sm ? q + 1 < p.sm_nq : I + delta + 1 < p.nT;
+  return (NP == 2 && p.sm) ? q + 1 < p.sm_nq : I + delta + 1 < p.nT;
 }
 // Column block of tile (I, I + delta): wraps around the ring of a stream's history
 __device__ __forceinline__ int col_block(const GramParams& p, int I, int delta) {
@@ -205,6 +206,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const bool sm = NP == 2 && p.sm;  // stream steps always run as ring pairs
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -216,13 +218,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const int4 w = item_at(p, item);
         const int q = w.x, delta = w.y;
-        const int nk = p.sm ? p.sm_nk : p.k_chunks[q];
+        const int nk = sm ? p.sm_nk : p.k_chunks[q];
         const int nc = p.split ? 2 * nk : nk;  // chunks per tile
-        const int koff = p.sm ? 0 : p.k_off[q];
-        const int rowbase = p.sm ? 0 : q * p.ring_rows;
+        const int koff = sm ? 0 : p.k_off[q];
+        const int rowbase = sm ? 0 : q * p.ring_rows;
         for (int I = w.z; I < w.w && ok; ++I) {
           const int J = col_block(p, I, delta);
-          const int rrow = p.sm ? q * TILE : rowbase + J * TILE;  // first row of the R box
+          const int rrow = sm ? q * TILE : rowbase + J * TILE;  // first row of the R box
           for (int c = 0; c < nc; ++c, ++it) {
             const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
             if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, p.status)) {
@@ -254,7 +256,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       bool ok = true, issued = false;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const int4 w = item_at(p, item);
-        const int nk = p.sm ? p.sm_nk : p.k_chunks[w.x];
+        const int nk = sm ? p.sm_nk : p.k_chunks[w.x];
         const int nc = p.split ? 2 * nk : nk;
         const int n_units = units_of(p, w);
         for (int u = 0; u < n_units && ok; ++u, ++unit) {
@@ -270,7 +272,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           bool first = true;  // the unit's first MMA overwrites the accumulator
           for (int I = ur.I_begin; I < ur.I_end && ok; ++I) {
             // tile pair when the second tile exists, else N = 128 (first half only)
-            const uint32_t idesc = (NP == 2 && second_half(p, w.x, I, w.y)) ? idesc2 : idesc1;
+            const uint32_t idesc = (NP == 2 && second_half<NP>(p, w.x, I, w.y)) ? idesc2 : idesc1;
             for (int c = 0; c < nc; ++c, ++it) {
               const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
               if (*abort_flag || !mbar_wait(&full[s], ph, p.status)) {
@@ -400,7 +402,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       const int q = w.x, delta = w.y;
       const float* rq = p.r + (size_t)q * p.T_pad;
       // the item's second tile diagonal (pairs; in a stream step the second ring) holds tiles
-      const bool has2 = NP == 2 && second_half(p, q, w.z, delta);
+      const bool has2 = NP == 2 && second_half<NP>(p, q, w.z, delta);
       float acc[NP][3];
 #pragma unroll
       for (int h2 = 0; h2 < NP; ++h2) acc[h2][0] = acc[h2][1] = acc[h2][2] = 0.f;
@@ -409,24 +411,24 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
         const int I = unit_range(p, w, u).I_begin;
         const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
         const float ri = !p.raw ? 1.f
-                         : p.sm ? p.r[((size_t)I * TILE + i_row) * p.r_ld + q]
+                         : sm ? p.r[((size_t)I * TILE + i_row) * p.r_ld + q]
                                 : rq[(size_t)I * TILE + i_row];
         // a stream step's second half is ring q + 1, with its own row scale
-        const float ri2 = (NP == 2 && p.sm && has2) ? p.r[((size_t)I * TILE + i_row) * p.r_ld + q + 1] : ri;
+        const float ri2 = (NP == 2 && sm && has2) ? p.r[((size_t)I * TILE + i_row) * p.r_ld + q + 1] : ri;
         if (*abort_flag || !mbar_wait_warp(&tfull[b], tph, p.status)) {  // warp-uniform outcome
           *abort_flag = 1;
           ok = false;
           break;
         }
         tc_fence_after();
-        const int nh = (NP == 2 && (p.merge || p.sm ? has2 : I + delta + 1 < p.nT)) ? 2 : 1;
+        const int nh = (NP == 2 && (p.merge || sm ? has2 : I + delta + 1 < p.nT)) ? 2 : 1;
 #pragma unroll
         for (int h2 = 0; h2 < NP; ++h2) {
           if (h2 >= nh) break;
           const bool last = h2 == nh - 1;  // TMEM is released after the unit's last load
           const uint32_t tbase =
               tmem_base + b * (NP * TILE) + h2 * TILE + ((uint32_t)(r * 32) << 16) + 64 * h;
-          const float* rj = p.sm ? nullptr
+          const float* rj = sm ? nullptr
                                  : (p.rc ? p.rc + (size_t)q * p.T_pad : rq) +
                                        (size_t)col_block(p, I, delta + h2) * TILE + 64 * h;
           if constexpr (STRIP) {
@@ -442,7 +444,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[b]);
               }
-              if (p.sm) {  // stream step: the w columns carry their own scale
+              if (sm) {  // stream step: the w columns carry their own scale
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * (h2 ? ri2 : ri));
               } else if (p.raw) {
@@ -470,7 +472,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[b]);
               }
-              if (p.sm) {  // stream step: the w columns carry their own scale
+              if (sm) {  // stream step: the w columns carry their own scale
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * (h2 ? ri2 : ri));
               } else if (p.raw) {
@@ -511,7 +513,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
             if (k >= 0 && k < 3) sum += rh[(u * 3 + k) * 32 + lane];
           }
           // offline: tile diagonal delta + h2 of ring q; stream step: ring q + h2, diagonal delta
-          const int sq = p.sm ? q + h2 : q, sd = p.sm ? delta : delta + h2;
+          const int sq = sm ? q + h2 : q, sd = sm ? delta : delta + h2;
           float* slot = p.partials + (((size_t)sq * p.nT + sd) * p.maxC + chunk) * DIAG_SLOTS;
           slot[32 * dw + lane] = sum;
         }

@@ -352,11 +352,12 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     gp.maxC = 1;
     gp.CH = nb + 1;  // chunk index I / CH = 0
     // ring pairs: one N = 256 MMA per K step covers rings q and q + 1 against one history
-    // chunk (the w blocks of neighbouring rings are consecutive rows)
-    const int pairs = s.n_q >= 2 ? 1 : 0;
+    // chunk (the w blocks of neighbouring rings are consecutive rows; a last odd ring runs
+    // alone, N = 128)
+    const int pairs = 1;
     gp.pairs = pairs;
     gp.sm_nq = s.n_q;
-    gp.n_items = (pairs ? (s.n_q + 1) / 2 : s.n_q) * nd_step;
+    gp.n_items = (s.n_q + 1) / 2 * nd_step;
     gp.items = nullptr;
     gp.ring_nb = nb;
     gp.ring_nd = nd_step;
@@ -370,7 +371,7 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     gp.r = s.Rh;
     gp.partials = s.gpart;
     gp.status = s.status;
-    e = launch_gram(*s.tmA, pairs ? *s.tmWg2 : *s.tmWg, gp, std::min(gp.n_items, s.num_sms), st);
+    e = launch_gram(*s.tmA, *s.tmWg2, gp, std::min(gp.n_items, s.num_sms), st);
     if (e != cudaSuccess) return e;
     const long long span = std::max<long long>(s.W, s.b);
     stream_fold_kernel<<<(unsigned)((s.n_q * span + 255) / 256), 256, 0, st>>>(s, nd_step);
