@@ -232,10 +232,9 @@ xpcs_status xpcs_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const float* A,
  * arguments, `reps` timed calls each after one untimed call, keeps the fastest in the
  * context for later calls of that shape, and runs it once more so the outputs are its
  * own.  Candidates: tiles per work item (1, 2, 4, 8, 16 or 32 along a tile diagonal) x schedule
- * (0: diagonal sums by 32-column blocks, 1: by whole 64-column strips, 2: tile pairs, one
- * N = 256 MMA for tiles (I, J) and (I, J + 1), block schedule).  The default stays unless
- * another candidate is at least 3 % faster: 8 tiles with strips for hi/lo operands (bf16x3)
- * and blocks otherwise when C is stored; 4 tiles with tile pairs for g2 only (C not
+ * (0: single tiles, one N = 128 MMA per tile; 1: tile pairs, one N = 256 MMA for tiles
+ * (I, J) and (I, J + 1)).  The default stays unless another candidate is at least 3 %
+ * faster: 8 single tiles when C is stored; 4 tiles with tile pairs for g2 only (C not
  * stored, where all tiles of a work item accumulate into one accumulator).
  * tiles_out, sched_out, ms_out (host, nullable): the choice and its time per call.  Not
  * during a capture. */
@@ -243,13 +242,14 @@ xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* basis, const 
                                   xpcs_precision prec, float* C_out, double* g2_out, int64_t* count_out, int reps,
                                   int* tiles_out, int* sched_out, double* ms_out);
 /* Fix the two-time configuration of this context's calls (xpcs_twotime*, xpcs_twotime_raw*)
- * instead of the tuned or default one: `tiles` per work item (1..64) and `schedule` (0, 1
- * or 2 as for the autotuner).  tiles = 0 returns to the automatic choice.  The results of
+ * instead of the tuned or default one: `tiles` per work item (1..64) and `schedule` (0 or 1
+ * as for the autotuner).  tiles = 0 returns to the automatic choice.  The results of
  * every configuration agree up to the f32 rounding order of the g2 partial sums (the raw
  * integer Gram and C are bit-identical).  XPCS_EINVAL for values out of range. */
 xpcs_status xpcs_twotime_config(xpcs_ctx* ctx, int tiles, int schedule);
 /* The same autotuner for xpcs_twotime_raw (arguments as that call's); the raw default is
- * 4 tiles per work item with tile pairs. */
+ * tile pairs, one per work item, or the fewest tiles per item (a power of two) that keep
+ * the g2 partial slots (1 KB per ring, tile diagonal and item chunk) within 512 MB. */
 xpcs_status xpcs_autotune_twotime_raw(xpcs_ctx* ctx, const xpcs_rings* rings, const void* X, xpcs_dtype dtype,
                                       int64_t T, float* C_out, int64_t* N_out, double* g2_out, int64_t* count_out,
                                       int reps, int* tiles_out, int* sched_out, double* ms_out);

@@ -521,8 +521,8 @@ extern "C" xpcs_status xpcs_ring_sums(xpcs_ctx* ctx, const xpcs_rings* R, const 
 namespace {
 
 // Two-time configuration for a workload shape, (tiles per work item, schedule) with
-// schedule 0 = 32-column diagonal blocks, 1 = whole 64-column strips, 2 = tile pairs (N =
-// 256 MMAs, block schedule): the autotuner's choice if there is one, else the given default.
+// schedule 0 = single tiles (N = 128 MMAs), 1 = tile pairs (N = 256 MMAs): the autotuner's
+// choice if there is one, else the given default.
 std::pair<int, int> gram_tune_for(xpcs_ctx* ctx, uint64_t key, std::pair<int, int> dflt) {
   if (ctx->tune_forced) return ctx->tune_force;
   if (ctx->user_config.first > 0) return ctx->user_config;
@@ -556,8 +556,8 @@ xpcs_status run_twotime(xpcs_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap
 
 extern "C" xpcs_status xpcs_twotime_config(xpcs_ctx* ctx, int tiles, int schedule) {
   if (!ctx) return XPCS_EINVAL;
-  if (tiles < 0 || tiles > 64 || schedule < 0 || schedule > 2)
-    return fail(ctx, XPCS_EINVAL, "twotime_config: tiles must be 0..64 and schedule 0..2");
+  if (tiles < 0 || tiles > 64 || schedule < 0 || schedule > 1)
+    return fail(ctx, XPCS_EINVAL, "twotime_config: tiles must be 0..64 and schedule 0..1");
   ctx->user_config = {tiles, schedule};
   return XPCS_OK;
 }
@@ -579,7 +579,7 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   const int nT = (int)((T + TILE - 1) / TILE);
   const int T_pad = nT * TILE;
   const std::pair<int, int> tune =
-      gram_tune_for(ctx, gram_tune_key(n_q, nT, 1, 0, 1, C_out || N_out), gram_default_raw());
+      gram_tune_for(ctx, gram_tune_key(n_q, nT, 1, 0, 1, C_out || N_out), gram_default_raw(n_q, nT));
   const int CH = tune.first;
   const int maxC = (nT + CH - 1) / CH;
   const bool want_g2 = g2_out != nullptr;
@@ -608,7 +608,7 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   XPCS_LAUNCH(ctx, "raw_scales", 1,
               launch_raw_scales(b.S, b.S2, b.Sbar, (int)norm, R->d_Mq, n_q, T, T_pad, nT, b.r, b.blk_bad,
                                 ctx->d_status, ctx->stream));
-  const int pairs = tune.second == 2;
+  const int pairs = tune.second == 1;
   CUtensorMap tm, tmR;
   XPCS_TRY(make_map(ctx, &tm, b.Xp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, R->Mp, T_pad, KCH, TILE,
                     CU_TENSOR_MAP_SWIZZLE_128B));
@@ -626,7 +626,6 @@ extern "C" xpcs_status xpcs_twotime_raw_norm(xpcs_ctx* ctx, const xpcs_rings* R,
   gp.fmt = 1;
   gp.split = 0;
   gp.raw = 1;
-  gp.strip = tune.second == 1;
   gp.pairs = pairs;
   gp.merge = 0;
   gp.r = b.r;
@@ -925,7 +924,7 @@ extern "C" xpcs_status xpcs_twotime_opts(xpcs_ctx* ctx, const xpcs_basis* B, con
   const bool merge = C_out == nullptr && g2_out != nullptr;  // g2 only: one diagonal pass per item
   const std::pair<int, int> tune =
       gram_tune_for(ctx, gram_tune_key(n_q, nT, prec == XPCS_PREC_FP16 ? 0 : 1, split ? 1 : 0, 0, C_out != nullptr),
-                    gram_default_compressed(split, merge));
+                    gram_default_compressed(merge));
   const int CH = tune.first;
   const int maxC = (nT + CH - 1) / CH;
   const int nkp = (k + KCH - 1) / KCH;           // 64-wide chunks per operand piece
@@ -1022,7 +1021,7 @@ extern "C" xpcs_status xpcs_twotime_opts(xpcs_ctx* ctx, const xpcs_basis* B, con
   }
   const CUtensorMapDataType dt =
       prec == XPCS_PREC_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const int pairs = tune.second == 2;
+  const int pairs = tune.second == 1;
   CUtensorMap tmL, tmR;
   XPCS_TRY(make_map(ctx, &tmL, b.L, dt, 2, Kc, (uint64_t)n_q * T_pad, KCH, TILE, CU_TENSOR_MAP_SWIZZLE_128B));
   XPCS_TRY(make_map(ctx, &tmR, b.R, dt, 2, Kc, (uint64_t)n_q * T_pad, KCH, pairs ? 2 * TILE : TILE,
@@ -1039,7 +1038,6 @@ extern "C" xpcs_status xpcs_twotime_opts(xpcs_ctx* ctx, const xpcs_basis* B, con
   gp.fmt = prec == XPCS_PREC_FP16 ? 0 : 1;
   gp.split = split ? 1 : 0;
   gp.raw = 0;
-  gp.strip = tune.second == 1;
   gp.pairs = pairs;
   gp.merge = merge ? 1 : 0;
   gp.r = b.r;

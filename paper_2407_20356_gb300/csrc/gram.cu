@@ -16,9 +16,10 @@
 //
 // Structure (one CTA per SM, persistent over work items):
 //   warp 0      TMA producer: 64-wide K chunks of the L and R row blocks, NSTAGE ring
-//   warp 1      TMEM allocator and MMA issuer: f32 accumulators, 2 TMEM buffers
+//   warp 1      TMEM allocator and MMA issuer: f32 accumulators in all 512 TMEM columns
+//               (4 single-tile accumulators, or 2 for tile pairs)
 //   warps 2..5  drain: TMEM -> registers -> C store
-//   warps 6..13 TMEM -> registers -> per-warp skewed 32x32 blocks -> diagonal sums
+//   warps 6..13 TMEM -> registers -> warp shuffles -> diagonal sums
 // Any warp may read the TMEM lanes of its quarter (warp id mod 4), so both groups read
 // the accumulator independently; they meet only at the TMEM full/empty barriers, and the
 // C stores of one tile overlap the diagonal pass of another.
@@ -43,18 +44,13 @@
 // C store: C is symmetric, so tile (I, J >= I) is written transposed into the lower
 // triangle, straight from registers and fully coalesced.
 //
-// Diagonal sums: a diagonal warp holds 32 tile rows (its lane quarter) x 64 columns of the
-// accumulator.  Lane i stores element (i, j) at row j - i + 32, column i of the warp's own
-// skewed buffer Q (96 rows of 36 floats): every diagonal j - i lands on one row, the
-// per-lane base address is fixed and the stores use constant offsets, hitting 32 distinct
-// banks (bank 4 j - 3 i mod 32).  Entries no lane ever writes stay zero from the kernel
-// start.  Lane d then adds up its rows with 16-byte loads and packed f32x2 adds, skipping
-// the 16-byte groups that hold no entry (those lanes issue no shared-memory traffic).  Two
-// schedules, chosen by operand format (each measured faster for its own): with hi/lo
-// operand pieces the whole 64-column strip is stored and rows d, d + 32, d + 64 are read
-// once; with single operands each 32-column block is stored and read (rows d, d + 32) in
-// turn.  The warps need no barrier per tile; the eight warps' per-lane sums meet once per
-// work item, added in a fixed order.
+// Diagonal sums: a diagonal warp holds 32 tile rows (its lane quarter) x 64 columns (a
+// strip) of the accumulator, lane i = row i.  For strip column c, lane l takes the element
+// of row (c + l) mod 32 with one shuffle (source lane (c + l) mod 32, the same register
+// c in every lane), so every element a lane receives lies on strip diagonal c - i = -l,
+// 32 - l or 64 - l, whichever the wrap of (c + l) says: three per-lane sums per tile
+// diagonal, no shared memory.  The eight warps' per-lane sums meet once per work item in
+// shared memory and are added in a fixed order.
 
 #include "common.cuh"
 #include "internal.h"
@@ -64,33 +60,33 @@ namespace xpcs {
 namespace {
 
 constexpr int N_DIAG_WARPS = 8;
-constexpr int Q_LD = 36;                               // skewed buffer row: 32 floats + 4 pad
 constexpr int GRAM_THREADS = 64 + 4 * 32 + N_DIAG_WARPS * 32;  // producer, MMA, 4 drain, 8 diagonal warps
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_MAX = 227 * 1024;
-constexpr int DIAG_BAR = 1;                        // named barrier of the eight diagonal warps
+constexpr int DIAG_BAR = 1;
+constexpr int MAX_STAGE = 4;  // deeper rings measured slower for the C-storing calls                        // named barrier of the eight diagonal warps
 
-// Shared-memory layout and pipeline depth of one configuration: STRIP = whole 64-column
-// strips (96 skewed rows per diagonal warp) or one 32-column block at a time (64 rows);
-// NP = tiles per accumulator (1, or 2 for tile pairs).  As many operand stages as fit,
-// at most four.
-template <bool STRIP, int NP>
+// Shared-memory layout, pipeline depth and accumulators of one configuration: NP = tiles
+// per accumulator (1, or 2 for tile pairs).  As many operand stages as fit, at most
+// MAX_STAGE; as many TMEM accumulators as the 512 columns hold (4 single, 2 pairs), so
+// that the drain warps can run ahead of the diagonal warps.
+template <int NP>
 struct GramCfg {
-  static constexpr int q_rows = STRIP ? 96 : 64;
-  static constexpr int priv = q_rows * Q_LD;  // floats of one warp's skewed buffer
   static constexpr int red_floats = NP * N_DIAG_WARPS * 3 * 32;  // per-warp sums of a work item
-  static constexpr int diag_bytes = (N_DIAG_WARPS * priv + red_floats) * 4;
+  static constexpr int diag_bytes = red_floats * 4;
   static constexpr int chunk_l = TILE * KCH * 2;       // L chunk: 128 rows x 128 B
   static constexpr int chunk_r = NP * TILE * KCH * 2;  // R chunk: 128 NP rows x 128 B
   static constexpr int stage_bytes = chunk_l + chunk_r;
   static constexpr int fixed = 1024 + diag_bytes + BAR_BYTES;
   static constexpr int fit = (SMEM_MAX - fixed) / stage_bytes;
-  static constexpr int nstage = fit > 4 ? 4 : fit;
+  static constexpr int nstage = fit > MAX_STAGE ? MAX_STAGE : fit;
   static constexpr int bytes = fixed + nstage * stage_bytes;
-  static constexpr uint32_t tmem_cols = 2 * NP * TILE;  // two accumulators
+  static constexpr int nacc = 4 / NP;
+  static constexpr uint32_t tmem_cols = nacc * NP * TILE;
   static_assert(nstage >= 3, "at least three operand stages");
   static_assert(bytes <= SMEM_MAX, "shared memory of one CTA");
   static_assert(tmem_cols == 256 || tmem_cols == 512, "TMEM allocation is a power of two");
+  static_assert(2 * MAX_STAGE + 2 * 4 + 1 <= BAR_BYTES / 8 - 1, "barriers and the TMEM slot fit");
 };
 
 // Stores one 32-column chunk of a tile row: element (i, j) of tile (I, J) is C(t1, t2)
@@ -163,11 +159,11 @@ __device__ __forceinline__ int col_block(const GramParams& p, int I, int delta) 
   return p.ring_nb ? J % p.ring_nb : J;
 }
 
-template <bool STRIP, int NP>
+template <int NP>
 __global__ void __launch_bounds__(GRAM_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR,
                const GramParams p) {
-  using CF = GramCfg<STRIP, NP>;
+  using CF = GramCfg<NP>;
   constexpr int NSTAGE = CF::nstage;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -176,10 +172,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * CF::stage_bytes + CF::diag_bytes);
   uint64_t* full = bars;                    // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;          // [NSTAGE]
-  uint64_t* tfull = bars + 2 * NSTAGE;      // [2]
-  uint64_t* tempty = bars + 2 * NSTAGE + 2; // [2]
-  uint64_t* mma_done = bars + 2 * NSTAGE + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSTAGE + 5);
+  uint64_t* tfull = bars + 2 * NSTAGE;                // [nacc]
+  uint64_t* tempty = bars + 2 * NSTAGE + CF::nacc;    // [nacc]
+  uint64_t* mma_done = bars + 2 * NSTAGE + 2 * CF::nacc;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -190,7 +186,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < CF::nacc; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], p.partials ? 4 + N_DIAG_WARPS : 4);  // drain (+ diagonal) warps
     }
@@ -260,7 +256,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
         const int nc = p.split ? 2 * nk : nk;
         const int n_units = units_of(p, w);
         for (int u = 0; u < n_units && ok; ++u, ++unit) {
-          const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
+          const uint32_t b = unit % CF::nacc, tph = (unit / CF::nacc) & 1;
           if (*abort_flag || !mbar_wait(&tempty[b], tph ^ 1, p.status)) {
             *abort_flag = 1;
             ok = false;
@@ -340,7 +336,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       const int n_units = units_of(p, w);
       for (int u = 0; u < n_units; ++u, ++unit) {
         const int I = unit_range(p, w, u).I_begin;
-        const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
+        const uint32_t b = unit % CF::nacc, tph = (unit / CF::nacc) & 1;
         // per-tile metadata first, so its load latency overlaps the wait for the MMA
         const long long t1 = (long long)I * TILE + i_row;
         const float ri = work ? rq[t1] : 0.f;
@@ -383,18 +379,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   } else if (p.partials) {
     // ------------------------------------------------------------ diagonal warps (6..13)
     // Warp dw (0..7) covers TMEM lane quarter r = warp mod 4 (tile rows 32 r ..) and
-    // column half h = dw / 4 (blocks b = 2 h, 2 h + 1) of each tile of the accumulator.
-    // Block b's sums land on tile diagonals 32 (b - r) + d (rows i < 32 - d) and
-    // 32 (b - r - 1) + d (the others), so the warp keeps three per-lane sums per tile
-    // diagonal, for e = 2 h - r - 1 + k (k = 0, 1, 2), diagonal 32 e + lane.
+    // column half h = dw / 4 (strip columns 64 h .. 64 h + 63) of each tile of the
+    // accumulator.  Lane l gathers, for every strip column c, the element of row
+    // (c + l) mod 32 (a shuffle per column), which lies on strip diagonal c - i = 32 m - l
+    // for m = 0, 1 or 2; it keeps one sum per m and tile diagonal of the item.  Strip
+    // diagonal 32 m - l is diagonal 32 (e - 1) + (32 - l) of the slot layout below.
     const int dw = warp - 6;
     const int r = warp & 3;
     const int h = dw >> 2;
-    float* Q = diag_smem + dw * CF::priv;
-    float* red = diag_smem + N_DIAG_WARPS * CF::priv;  // [half][warp][k][lane]
+    float* red = diag_smem;  // [half][warp][k][lane]: strip diagonal 32 (k - 1) + lane
     const int i_row = r * 32 + lane;
-    for (int x = lane; x < CF::priv; x += 32) Q[x] = 0.f;  // entries never written stay 0
-    float* qw = Q + (32 - lane) * Q_LD + lane;                // element (lane, j) at qw[Q_LD * j]
     uint32_t unit = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
@@ -409,7 +403,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
       const int n_units = units_of(p, w);
       for (int u = 0; u < n_units && ok; ++u, ++unit) {
         const int I = unit_range(p, w, u).I_begin;
-        const uint32_t b = unit & 1, tph = (unit >> 1) & 1;
+        const uint32_t b = unit % CF::nacc, tph = (unit / CF::nacc) & 1;
         const float ri = !p.raw ? 1.f
                          : sm ? p.r[((size_t)I * TILE + i_row) * p.r_ld + q]
                                 : rq[(size_t)I * TILE + i_row];
@@ -431,71 +425,55 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           const float* rj = sm ? nullptr
                                  : (p.rc ? p.rc + (size_t)q * p.T_pad : rq) +
                                        (size_t)col_block(p, I, delta + h2) * TILE + 64 * h;
-          if constexpr (STRIP) {
-            // whole strip: row 32 k + lane holds strip diagonal 32 (k - 1) + lane (acc[k])
-            __syncwarp();  // the previous tile's row sums are read
-#pragma unroll
-            for (int sb = 0; sb < 2; ++sb) {
-              uint32_t v[32];
-              tmem_ld32(tbase + 32 * sb, v);
-              tc_wait_ld();
-              if (last && sb == 1) {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[b]);
-              }
-              if (sm) {  // stream step: the w columns carry their own scale
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * (h2 ? ri2 : ri));
-              } else if (p.raw) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                  v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
-              }
-#pragma unroll
-              for (int j = 0; j < 32; ++j) qw[Q_LD * (32 * sb + j)] = __uint_as_float(v[j]);
-            }
+          uint32_t v0[32], v1[32];
+          tmem_ld32(tbase, v0);
+          tmem_ld32(tbase + 32, v1);
+          tc_wait_ld();
+          if (last) {
+            tc_fence_before();
             __syncwarp();
-            acc[h2][0] += skew_row_sum<Q_LD>(Q, lane, 32 - lane, 32);
-            acc[h2][1] += skew_row_sum<Q_LD>(Q, 32 + lane, 0, 32);
-            acc[h2][2] += skew_row_sum<Q_LD>(Q, 64 + lane, 0, 32 - lane);
-          } else {
-            // one 32-column block at a time: row lane holds block diagonal lane - 32
-            // (acc[sb]), row 32 + lane block diagonal lane (acc[sb + 1])
+            if (lane == 0) mbar_arrive(&tempty[b]);
+          }
+          if (sm) {  // stream step: the w columns carry their own scale
+            const float s = h2 ? ri2 : ri;
 #pragma unroll
-            for (int sb = 0; sb < 2; ++sb) {
-              uint32_t v[32];
-              tmem_ld32(tbase + 32 * sb, v);
-              tc_wait_ld();
-              if (last && sb == 1) {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[b]);
-              }
-              if (sm) {  // stream step: the w columns carry their own scale
+            for (int j = 0; j < 32; ++j) {
+              v0[j] = __float_as_uint(__uint_as_float(v0[j]) * s);
+              v1[j] = __float_as_uint(__uint_as_float(v1[j]) * s);
+            }
+          } else if (p.raw) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * (h2 ? ri2 : ri));
-              } else if (p.raw) {
+            for (int j = 0; j < 32; ++j) {
+              v0[j] = __float_as_uint((__uint_as_float(v0[j]) * ri) * __ldg(rj + j));
+              v1[j] = __float_as_uint((__uint_as_float(v1[j]) * ri) * __ldg(rj + 32 + j));
+            }
+          }
+          // column c of the strip from row (c + lane) mod 32: strip diagonal 32 m - lane
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                  v[j] = __float_as_uint((__uint_as_float(v[j]) * ri) * __ldg(rj + 32 * sb + j));
-              }
-              __syncwarp();  // the previous block's row sums are read
-#pragma unroll
-              for (int j = 0; j < 32; ++j) qw[Q_LD * j] = __uint_as_float(v[j]);
-              __syncwarp();
-              acc[h2][sb] += skew_row_sum<Q_LD>(Q, lane, 32 - lane, 32);
-              acc[h2][sb + 1] += skew_row_sum<Q_LD>(Q, 32 + lane, 0, 32 - lane);
+          for (int j = 0; j < 32; ++j) {
+            const int src = (lane + j) & 31;
+            const float x0 = __shfl_sync(0xffffffffu, __uint_as_float(v0[j]), src);
+            const float x1 = __shfl_sync(0xffffffffu, __uint_as_float(v1[j]), src);
+            if (lane + j >= 32) {
+              acc[h2][1] += x0;
+              acc[h2][2] += x1;
+            } else {
+              acc[h2][0] += x0;
+              acc[h2][1] += x1;
             }
           }
         }
       }
       // every diagonal warp reaches these barriers once per item, also after an abort
       // (each of its waits is bounded), so none is left waiting
+      // lane l > 0 holds strip diagonals 32 (k - 1) + (32 - l); lane 0 holds 0 and 32 (k = 1,
+      // 2), and strip diagonal -32 (k = 0, lane 0) has no element
+      const int lp = (32 - lane) & 31;
 #pragma unroll
       for (int h2 = 0; h2 < NP; ++h2)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) red[((h2 * N_DIAG_WARPS + dw) * 3 + k) * 32 + lane] = acc[h2][k];
+        for (int k = 0; k < 3; ++k)
+          red[((h2 * N_DIAG_WARPS + dw) * 3 + k) * 32 + lp] = lane ? acc[h2][k] : (k ? acc[h2][k - 1] : 0.f);
       named_bar_sync(DIAG_BAR, N_DIAG_WARPS * 32);
       if (ok && !*abort_flag) {
         // warp dw finishes diagonals 32 (dw - 4) + lane of each tile diagonal, adding the
@@ -533,34 +511,26 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
 
 }  // namespace
 
-int gram_smem_bytes() {
-  int m = GramCfg<true, 1>::bytes;
-  m = GramCfg<false, 1>::bytes > m ? GramCfg<false, 1>::bytes : m;
-  return GramCfg<false, 2>::bytes > m ? GramCfg<false, 2>::bytes : m;
-}
+int gram_smem_bytes() { return GramCfg<1>::bytes > GramCfg<2>::bytes ? GramCfg<1>::bytes : GramCfg<2>::bytes; }
 
-template <bool STRIP, int NP>
+template <int NP>
 static cudaError_t launch_gram_t(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
                                  cudaStream_t st) {
-  constexpr int smem = GramCfg<STRIP, NP>::bytes;
+  constexpr int smem = GramCfg<NP>::bytes;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<STRIP, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  gram_tc_kernel<STRIP, NP><<<grid, GRAM_THREADS, smem, st>>>(tmL, tmR, p);
+  gram_tc_kernel<NP><<<grid, GRAM_THREADS, smem, st>>>(tmL, tmR, p);
   return cudaGetLastError();
 }
 
-// The diagonal schedule and the tile pairing are parameters of the call: tile pairs take
-// the 32-column block schedule (the whole-strip buffers leave too little shared memory for
-// three stages of 48 KB); otherwise the strip schedule for hi/lo operand pieces and the
-// block schedule for single operands unless an autotuned choice says otherwise.
+// The tile pairing is a parameter of the call (autotuned per workload shape).
 cudaError_t launch_gram(const CUtensorMap& tmL, const CUtensorMap& tmR, const GramParams& p, int grid,
                         cudaStream_t st) {
-  if (p.pairs) return launch_gram_t<false, 2>(tmL, tmR, p, grid, st);
-  return p.strip ? launch_gram_t<true, 1>(tmL, tmR, p, grid, st) : launch_gram_t<false, 1>(tmL, tmR, p, grid, st);
+  return p.pairs ? launch_gram_t<2>(tmL, tmR, p, grid, st) : launch_gram_t<1>(tmL, tmR, p, grid, st);
 }
 
 }  // namespace xpcs

@@ -189,17 +189,21 @@ xpcs_status make_map(xpcs_ctx* ctx, CUtensorMap* map, const void* base, CUtensor
                      uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw,
                      uint64_t pitch_bytes = 0);
 
-// Default two-time configurations (tiles per work item, schedule: 0 = 32-column diagonal
-// blocks, 1 = whole 64-column strips, 2 = tile pairs with the block schedule), from timings
-// on one GB300.  Raw counts: tile pairs, 4 tiles per item (the long K loop is bound by
-// operand traffic, which pairs cut by a quarter; 512x512, T = 10^4: 28.0 ms against 38.3 ms
-// with single tiles).  Compressed with C stored: strips for hi/lo operand pieces, blocks
-// otherwise (bound by the C stores).  Compressed g2 only (merged items, one diagonal pass
-// per item): tile pairs, 4 tiles per item.
-inline std::pair<int, int> gram_default_raw() { return {4, 2}; }
-inline std::pair<int, int> gram_default_compressed(bool split, bool merge) {
-  if (merge) return {4, 2};
-  return {CHUNK_TILES, split ? 1 : 0};
+// Default two-time configurations (tiles per work item, schedule: 0 = single tiles, 1 =
+// tile pairs), from timings on one GB300.  Raw counts: tile pairs (the long K loop is
+// bound by operand traffic, which pairs cut by a quarter), one tile pair per work item
+// (512x512, T = 10^4: 17.5 ms against 24.4 ms with 4), more only where the g2 partial
+// slots (1 KB per ring, tile diagonal and work-item chunk) would pass 512 MB.  Compressed
+// with C stored: single tiles, 8 per item (bound by the C stores).  Compressed g2 only
+// (merged items, one diagonal pass per item): tile pairs, 4 tiles per item.
+inline std::pair<int, int> gram_default_raw(int n_q, int nT) {
+  int ch = 1;
+  while (ch < 64 && (double)n_q * nT * ((nT + ch - 1) / ch) * DIAG_SLOTS * 4 > 512.0 * (1 << 20)) ch *= 2;
+  return {ch, 1};
+}
+inline std::pair<int, int> gram_default_compressed(bool merge) {
+  if (merge) return {4, 1};
+  return {CHUNK_TILES, 0};
 }
 
 // Key of a two-time workload shape in the context's tuning table.

@@ -42,7 +42,6 @@ struct GramParams {
   int split;               // 1: operand rows are [hi | lo] pieces of k_chunks chunks each;
                            //    C = L_hi R_hi + L_lo R_hi + L_hi R_lo
   int raw;                 // 1: C = acc * r(t1) * r(t2); 0: operands already scaled
-  int strip;               // diagonal schedule: 1 whole 64-column strips, 0 32-column blocks
   int pairs;               // 1: tile pairs (I, J), (I, J + 1) per accumulator (N = 256 MMA);
                            //    items then cover the tile diagonals delta (even) and delta + 1
   int merge;               // 1: the tiles of an item accumulate into one accumulator (compressed

@@ -3,9 +3,8 @@
 // The two-time kernel has two run-time choices for a workload shape: the length of a work
 // item (tiles along one tile diagonal whose diagonal sums meet once: 1, 2, 4, 8, 16 or 32; it
 // trades load balance across the SMs against the number of partial-sum slots and per-item
-// overheads) and its schedule: the diagonal sums by whole 64-column strips or by 32-column
-// blocks, or tile pairs (one N = 256 MMA for tiles (I, J) and (I, J + 1), block
-// schedule).  The autotuner times every candidate on the caller's own inputs and outputs
+// overheads) and its schedule: single tiles, or tile pairs (one N = 256 MMA for tiles
+// (I, J) and (I, J + 1)).  The autotuner times every candidate on the caller's own inputs and outputs
 // (CUDA events on the context's stream, after one untimed run per candidate that builds
 // its work items), keeps the fastest in the context's table for the shape (rings, tiles,
 // operand format, raw or compressed, whether C is stored), and finally runs it, so the
@@ -37,7 +36,7 @@ xpcs_status tune_shape(xpcs_ctx* ctx, uint64_t key, std::pair<int, int> dflt, in
   double best_ms = 1e300, dflt_ms = 1e300;
   xpcs_status st = XPCS_OK;
   const int tiles[6] = {1, 2, 4, 8, 16, 32};
-  for (int sched = 0; sched < 3 && st == XPCS_OK; ++sched) {
+  for (int sched = 0; sched < 2 && st == XPCS_OK; ++sched) {
     for (int ti = 0; ti < 6 && st == XPCS_OK; ++ti) {
       ctx->tune_forced = true;
       ctx->tune_force = {tiles[ti], sched};
@@ -95,7 +94,7 @@ extern "C" xpcs_status xpcs_autotune_twotime(xpcs_ctx* ctx, const xpcs_basis* B,
   const bool split = prec == XPCS_PREC_BF16X3;
   const uint64_t key = gram_tune_key(n_q, nT, prec == XPCS_PREC_FP16 ? 0 : 1, split ? 1 : 0, 0, C_out != nullptr);
   const bool merge = C_out == nullptr && g2_out != nullptr;
-  return tune_shape(ctx, key, gram_default_compressed(split, merge), reps,
+  return tune_shape(ctx, key, gram_default_compressed(merge), reps,
                     [&] { return xpcs_twotime(ctx, B, A, T, prec, C_out, g2_out, count_out); }, tiles_out,
                     sched_out, ms_out);
 }
@@ -110,7 +109,7 @@ extern "C" xpcs_status xpcs_autotune_twotime_raw(xpcs_ctx* ctx, const xpcs_rings
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int nT = (int)((T + TILE - 1) / TILE);
   const uint64_t key = gram_tune_key(R->n_q, nT, 1, 0, 1, C_out || N_out);
-  return tune_shape(ctx, key, gram_default_raw(), reps,
+  return tune_shape(ctx, key, gram_default_raw(R->n_q, nT), reps,
                     [&] { return xpcs_twotime_raw(ctx, R, X, dtype, T, C_out, N_out, g2_out, count_out); },
                     tiles_out, sched_out, ms_out);
 }

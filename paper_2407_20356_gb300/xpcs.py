@@ -30,7 +30,7 @@ XPCS_PREC_FP16, XPCS_PREC_BF16, XPCS_PREC_BF16X3 = 0, 1, 2
 PRECISIONS = {"fp16": XPCS_PREC_FP16, "bf16": XPCS_PREC_BF16, "bf16x3": XPCS_PREC_BF16X3}
 XPCS_NORM_MEAN, XPCS_NORM_FROB, XPCS_NORM_EQ12 = 0, 1, 2
 NORMS = {"mean": XPCS_NORM_MEAN, "frob": XPCS_NORM_FROB, "eq12": XPCS_NORM_EQ12}
-SCHEDULES = ("blocks", "strips", "tile_pairs")  # two-time kernel schedules (codes 0, 1, 2)
+SCHEDULES = ("tiles", "tile_pairs")  # two-time kernel schedules (codes 0, 1)
 XPCS_QMEAN_COMPRESSED, XPCS_QMEAN_EXACT_RAW = 0, 1
 QMEANS = {"compressed": XPCS_QMEAN_COMPRESSED, "exact_raw": XPCS_QMEAN_EXACT_RAW}
 
@@ -211,7 +211,7 @@ class Context:
     def timeout(self) -> int:
         return int(_lib.xpcs_get_timeout(self.h))
 
-    def twotime_config(self, tiles: int = 0, schedule="blocks"):
+    def twotime_config(self, tiles: int = 0, schedule="tiles"):
         """Fix the two-time kernel's configuration (tiles per work item, schedule name or
         code); tiles = 0 returns to the autotuned or default choice."""
         sc = SCHEDULES.index(schedule) if isinstance(schedule, str) else int(schedule)
@@ -389,8 +389,8 @@ def xpcs_twotime(ctx: Context, basis: Basis, A, T: int, prec="fp16", C_out=None,
 
 
 def _tune_result(tiles, sched, ms) -> dict:
-    return {"tiles_per_item": tiles.value, "schedule": SCHEDULES[sched.value], "strip": sched.value == 1,
-            "pairs": sched.value == 2, "ms": ms.value}
+    return {"tiles_per_item": tiles.value, "schedule": SCHEDULES[sched.value], "pairs": sched.value == 1,
+            "ms": ms.value}
 
 
 def xpcs_autotune_twotime(ctx: Context, basis: Basis, A, T: int, prec="bf16x3", C_out=None, g2_out=None,

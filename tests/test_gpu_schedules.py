@@ -1,7 +1,7 @@
 """Parity of every two-time kernel configuration against the oracle.
 
-The two-time kernel runs in one of three schedules (diagonal sums by 32-column blocks, by
-whole 64-column strips, or tile pairs: one N = 256 MMA for tiles (I, J) and (I, J + 1)),
+The two-time kernel runs in one of two schedules (single tiles, one N = 128 MMA per tile,
+or tile pairs: one N = 256 MMA for tiles (I, J) and (I, J + 1)),
 with a caller-chosen number of tiles per work item, and, for compressed g2-only calls,
 with all tiles of a work item accumulated into one accumulator.  Each configuration is
 forced with xpcs_twotime_config and checked against the oracle: the raw integer Gram
@@ -18,8 +18,8 @@ from tests.gpu_util import lower, rel_errors, run_raw, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = [(8, "blocks"), (8, "strips"), (8, "tile_pairs"), (1, "tile_pairs"), (3, "tile_pairs"),
-           (16, "tile_pairs"), (4, "blocks"), (2, "strips")]
+CONFIGS = [(8, "tiles"), (1, "tiles"), (8, "tile_pairs"), (1, "tile_pairs"), (3, "tile_pairs"),
+           (16, "tile_pairs"), (4, "tiles"), (5, "tiles")]
 TOL = {"fp16": 1e-3, "bf16x3": 1e-4}
 
 
