@@ -1040,6 +1040,7 @@ extern "C" xpcs_status xpcs_twotime_opts(xpcs_ctx* ctx, const xpcs_basis* B, con
   gp.raw = 0;
   gp.pairs = pairs;
   gp.merge = merge ? 1 : 0;
+  gp.rmerge = (C_out && want_g2 && !merge && !pairs) ? 1 : 0;
   gp.r = b.r;
   gp.blk_bad = b.blk_bad;
   gp.C = C_out;

@@ -269,15 +269,48 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   }
 }
 
+// A = scale * (sum of the split partials), added in split order.  Element g of A (row t,
+// column j, g = t k + j) is element g of every split's slab of T_pad x k floats, so the
+// sum runs over flat indices: four consecutive ones per thread (16-byte loads when A and
+// the slabs allow it) and four splits' loads in flight before any is added.
 __global__ void encode_reduce_kernel(const float* partials, int n_split, long long T, int T_pad, int k, float scale,
-                                     float* A) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= T * k) return;
-  const long long t = gid / k;
-  const int j = (int)(gid % k);
-  float a = 0.f;
-  for (int s = 0; s < n_split; ++s) a += partials[((size_t)s * T_pad + t) * k + j];
-  A[gid] = a * scale;
+                                     float* A, int vec) {
+  const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  const long long n = T * k;
+  if (g0 >= n) return;
+  const size_t slab = (size_t)T_pad * k;
+  float a[4] = {0.f, 0.f, 0.f, 0.f};
+  if (vec && g0 + 4 <= n) {
+    const float4* p4 = reinterpret_cast<const float4*>(partials + g0);
+    const size_t s4 = slab / 4;
+    int s = 0;
+    for (; s + 4 <= n_split; s += 4) {
+      float4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = __ldcs(p4 + (size_t)(s + u) * s4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[0] += x[u].x;
+        a[1] += x[u].y;
+        a[2] += x[u].z;
+        a[3] += x[u].w;
+      }
+    }
+    for (; s < n_split; ++s) {
+      const float4 x = __ldcs(p4 + (size_t)s * s4);
+      a[0] += x.x;
+      a[1] += x.y;
+      a[2] += x.z;
+      a[3] += x.w;
+    }
+    *reinterpret_cast<float4*>(A + g0) = make_float4(a[0] * scale, a[1] * scale, a[2] * scale, a[3] * scale);
+    return;
+  }
+  for (long long g = g0; g < g0 + 4 && g < n; ++g) {
+    float x = 0.f;
+    for (int s = 0; s < n_split; ++s) x += partials[(size_t)s * slab + g];
+    A[g] = x * scale;
+  }
 }
 
 }  // namespace
@@ -301,8 +334,9 @@ cudaError_t launch_encode(const CUtensorMap& tmX, const CUtensorMap& tmB, const 
 
 cudaError_t launch_encode_reduce(const float* partials, int n_split, long long T, int T_pad, int k, float scale,
                                  float* A, cudaStream_t st) {
-  const long long n = T * k;
-  encode_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, n_split, T, T_pad, k, scale, A);
+  const long long n4 = (T * k + 3) / 4;  // four elements per thread
+  const int vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && reinterpret_cast<uintptr_t>(partials) % 16 == 0) ? 1 : 0;
+  encode_reduce_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(partials, n_split, T, T_pad, k, scale, A, vec);
   return cudaGetLastError();
 }
 

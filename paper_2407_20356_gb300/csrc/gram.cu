@@ -16,8 +16,8 @@
 //
 // Structure (one CTA per SM, persistent over work items):
 //   warp 0      TMA producer: 64-wide K chunks of the L and R row blocks, NSTAGE ring
-//   warp 1      TMEM allocator and MMA issuer: f32 accumulators in all 512 TMEM columns
-//               (4 single-tile accumulators, or 2 for tile pairs)
+//   warp 1      TMEM allocator and MMA issuer: two f32 tile accumulators in TMEM (128
+//               columns each, 256 for tile pairs; single tiles add a merge accumulator)
 //   warps 2..5  drain: TMEM -> registers -> C store
 //   warps 6..13 TMEM -> registers -> warp shuffles -> diagonal sums
 // Any warp may read the TMEM lanes of its quarter (warp id mod 4), so both groups read
@@ -35,11 +35,14 @@
 // for I in [I0, I1).  The diagonal sums of each tile diagonal of an item go to one partial
 // slot; no atomics, deterministic.
 //
-// Merged items (compressed path, g2 only, C not stored): every tile of an item lies on one
-// tile diagonal, and element (i, j) of each of them belongs to lag 128 delta + j - i, so
-// the diagonal sums of the item are the diagonal sums of the SUM of its tiles.  The MMAs
-// of all its tiles then accumulate into one TMEM accumulator and the diagonal pass runs
-// once per item instead of once per tile.
+// Merged items (compressed path): every tile of an item lies on one tile diagonal, and
+// element (i, j) of each of them belongs to lag 128 delta + j - i, so the diagonal sums of
+// the item are the diagonal sums of the SUM of its tiles (the compressed operand rows
+// carry both scales, so each accumulator is C itself).  For g2 only (C not stored) the
+// MMAs of all its tiles accumulate into one TMEM accumulator.  When C is stored (single
+// tiles), the diagonal warps add each tile, as they read it, into a running sum in a
+// merge accumulator (TMEM load, f32 add, TMEM store) and shuffle-reduce only the item's
+// last sum: one diagonal pass per item instead of one per tile.
 //
 // C store: C is symmetric, so tile (I, J >= I) is written transposed into the lower
 // triangle, straight from registers and fully coalesced.
@@ -68,8 +71,8 @@ constexpr int MAX_STAGE = 4;  // deeper rings measured slower for the C-storing 
 
 // Shared-memory layout, pipeline depth and accumulators of one configuration: NP = tiles
 // per accumulator (1, or 2 for tile pairs).  As many operand stages as fit, at most
-// MAX_STAGE; as many TMEM accumulators as the 512 columns hold (4 single, 2 pairs), so
-// that the drain warps can run ahead of the diagonal warps.
+// MAX_STAGE; two TMEM tile accumulators, and for single tiles a merge accumulator of 128
+// columns beside them.
 template <int NP>
 struct GramCfg {
   static constexpr int red_floats = NP * N_DIAG_WARPS * 3 * 32;  // per-warp sums of a work item
@@ -81,11 +84,12 @@ struct GramCfg {
   static constexpr int fit = (SMEM_MAX - fixed) / stage_bytes;
   static constexpr int nstage = fit > MAX_STAGE ? MAX_STAGE : fit;
   static constexpr int bytes = fixed + nstage * stage_bytes;
-  static constexpr int nacc = 4 / NP;
-  static constexpr uint32_t tmem_cols = nacc * NP * TILE;
+  static constexpr int nacc = 2;                        // tile accumulators of NP x 128 columns
+  static constexpr uint32_t macc_col = nacc * NP * TILE;  // merge accumulator (single tiles)
+  static constexpr uint32_t tmem_cols = 512;
   static_assert(nstage >= 3, "at least three operand stages");
   static_assert(bytes <= SMEM_MAX, "shared memory of one CTA");
-  static_assert(tmem_cols == 256 || tmem_cols == 512, "TMEM allocation is a power of two");
+  static_assert(NP == 2 || macc_col + TILE <= tmem_cols, "the merge accumulator fits the TMEM");
   static_assert(2 * MAX_STAGE + 2 * 4 + 1 <= BAR_BYTES / 8 - 1, "barriers and the TMEM slot fit");
 };
 
@@ -202,7 +206,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const bool sm = NP == 2 && p.sm;  // stream steps always run as ring pairs
+  const bool sm = NP == 2 && p.sm;        // stream steps always run as ring pairs
+  const bool rm = NP == 1 && p.rmerge;    // per-item running sum of the tiles in TMEM
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -434,7 +439,29 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
           }
-          if (sm) {  // stream step: the w columns carry their own scale
+          if (rm) {
+            // compressed tiles with C stored: add the strip to the item's running sum in the
+            // merge accumulator (the operand rows carry both scales, so each tile is C
+            // itself); the item's last tile reduces the sum along its diagonals
+            const uint32_t mbase = tmem_base + CF::macc_col + ((uint32_t)(r * 32) << 16) + 64 * h;
+            if (u > 0) {
+              uint32_t m[32];
+              tmem_ld32(mbase, m);
+              tc_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v0[j] = __float_as_uint(__uint_as_float(m[j]) + __uint_as_float(v0[j]));
+              tmem_ld32(mbase + 32, m);
+              tc_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v1[j] = __float_as_uint(__uint_as_float(m[j]) + __uint_as_float(v1[j]));
+            }
+            if (u < n_units - 1) {
+              tmem_st32(mbase, v0);
+              tmem_st32(mbase + 32, v1);
+              tc_wait_st();  // written before the next tile reads it (and before v0, v1 are reused)
+              continue;
+            }
+          } else if (sm) {  // stream step: the w columns carry their own scale
             const float s = h2 ? ri2 : ri;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
@@ -464,8 +491,6 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
           }
         }
       }
-      // every diagonal warp reaches these barriers once per item, also after an abort
-      // (each of its waits is bounded), so none is left waiting
       // lane l > 0 holds strip diagonals 32 (k - 1) + (32 - l); lane 0 holds 0 and 32 (k = 1,
       // 2), and strip diagonal -32 (k = 0, lane 0) has no element
       const int lp = (32 - lane) & 31;

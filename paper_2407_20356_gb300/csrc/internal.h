@@ -46,6 +46,8 @@ struct GramParams {
                            //    items then cover the tile diagonals delta (even) and delta + 1
   int merge;               // 1: the tiles of an item accumulate into one accumulator (compressed
                            //    path, g2 only, no C store); the diagonal pass runs once per item
+  int rmerge;              // 1 (single tiles, compressed, C and g2): C stored per tile, the tiles of
+                           //    an item summed in a TMEM accumulator for one diagonal pass per item
   // raw row update of a stream (items == nullptr): row blocks live in a ring of ring_nb
   // blocks, column block J = (I + delta) mod ring_nb, and item i is (q, delta, I, I + 1)
   // with q = i / ring_nd, delta = i mod ring_nd, I = (ring_J - delta) mod ring_nb

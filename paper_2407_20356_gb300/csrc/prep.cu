@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   const int lda = k + 1;
   float* As = sm;                          // [64][k+1]  a
   float* rs = As + PREP_FRAMES * lda;      // [64] r of this block's frames
-  float* Ws = rs + PREP_FRAMES;            // [64][k+1]  a G_q  (not allocated with skip_L)
-  float* Gs = Ws + PREP_FRAMES * lda;      // [k][64]           (not allocated with skip_L)
+  float* Ws = rs + PREP_FRAMES;            // [64][k+1]  a G_q
+  float* Gs = Ws + PREP_FRAMES * lda;      // [k][64]
   const int q = blockIdx.y;
   const long long t0 = (long long)blockIdx.x * PREP_FRAMES;
   const int tid = threadIdx.x;
@@ -249,14 +249,16 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
       const long long t = t0 + f;
       float v = 0.f;
       if (t < p.T) {
-        // the ring sum of the denominators: a_t s_q, or the raw frame's exact sum
-        const double acc = p.S_exact ? (double)p.S_exact[(size_t)q * p.T + t] : (double)hi + (double)lo;
-        if (p.St) p.St[(size_t)q * p.T + t] = acc;
-        // per-frame scale (xpcs_norm); the Frobenius one needs W and is set below
-        const double den = p.norm == XPCS_NORM_EQ12 ? p.Sbar[q] : acc;
+        // the ring sum of the denominators: a_t s_q (hi + lo; hi alone decides the sign),
+        // or the raw frame's exact sum
+        const long long* se = p.S_exact ? p.S_exact + (size_t)q * p.T + t : nullptr;
+        if (p.St) p.St[(size_t)q * p.T + t] = se ? (double)*se : (double)hi + (double)lo;
+        // per-frame scale (xpcs_norm) in f32, the FP64 units being slow on this part (the
+        // scale is a float either way); the Frobenius one needs W and is set below
+        const float den = p.norm == XPCS_NORM_EQ12 ? (float)p.Sbar[q] : se ? (float)*se : hi + lo;
         if (p.norm != XPCS_NORM_FROB) {
-          if (den > 0.0)
-            v = (float)(sqrt((double)p.Mq[q]) / den);
+          if (den > 0.f)
+            v = sqrtf((float)p.Mq[q]) / den;
           else
             atomicOr(&p.blk_bad[(size_t)q * p.nT + (t >> 7)], 1u);
         }
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
   // columns 8 cg .. 8 cg + 7 of the chunk (16 outputs, 4 shared loads per 16 FMAs)
   const int fl = tid & 31, cg = tid >> 5;
   const float* Gq = p.G32 + (size_t)q * k * k;
-  for (int j0 = 0; j0 < (p.skip_L ? 0 : k); j0 += 64) {
+  for (int j0 = 0; j0 < k; j0 += 64) {
     const int nc = min(64, k - j0);
     __syncthreads();
     for (int c = tid >> 6; c < k; c += 4) {
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
       if (jb + 8 <= k) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const float wv = p.skip_L ? 0.f : rf * wrow[jb + e], av = rf * arow[jb + e];
+          const float wv = rf * wrow[jb + e], av = rf * arow[jb + e];
           if (!lo) {
             lv[e] = to16<T16>(wv);
             rv[e] = to16<T16>(av);
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int j = jb + e;
-          const float wv = (j < k && !p.skip_L) ? rf * wrow[j] : 0.f, av = j < k ? rf * arow[j] : 0.f;
+          const float wv = j < k ? rf * wrow[j] : 0.f, av = j < k ? rf * arow[j] : 0.f;
           if (!lo) {
             lv[e] = to16<T16>(wv);
             rv[e] = to16<T16>(av);
@@ -383,13 +385,122 @@ __global__ void __launch_bounds__(256) comp_operands_kernel(const PrepParams p) 
           }
         }
       }
-      if (!p.skip_L) L[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(lv);
+      L[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(lv);
       R[(size_t)ff * nvec + vv] = *reinterpret_cast<const uint4*>(rv);
     }
   }
 }
 
 // ---------------------------------------------------------------- tensor-core operand pieces
+// Ring sums, scales and R rows of the tensor-core path (L comes from ring_w_tc_kernel;
+// not the Frobenius normalisation): a block takes 128 frames and SR_QG rings.  The frames'
+// coefficient rows are loaded into shared memory once for all its rings (row pitch = k
+// rounded up to 32, plus 2, so the two threads of a frame read distinct banks).  Two
+// threads per frame form the compensated ring sum a_t s_q (as in comp_operands_kernel,
+// each over every other coefficient, the halves combined in a fixed order so both hold
+// the same value), the scale r in f32 (the FP64 units are slow on this part), and write
+// the frame's R row (16-byte vectors, the two threads alternating).
+constexpr int SR_FRAMES = 128, SR_QG = 4;
+template <typename T16, bool SPLIT>
+__global__ void __launch_bounds__(256) scales_rows_kernel(const PrepParams p, int lda, int vec) {
+  extern __shared__ float sm[];
+  const int k = p.k;
+  float* As = sm;                                                   // [128][lda]
+  float2* Ss = reinterpret_cast<float2*>(As + SR_FRAMES * lda);     // [SR_QG][k]
+  const long long t0 = (long long)blockIdx.x * SR_FRAMES;
+  const int q0 = blockIdx.y * SR_QG;
+  const int qn = min(SR_QG, p.n_q - q0);
+  const int tid = threadIdx.x;
+  // the tile's rows are 128 k consecutive floats of A (zeros past frame T): 16-byte loads,
+  // eight per thread in flight before any is stored, when k is a multiple of 4
+  const long long have = (p.T - t0) * k;  // floats of the tile that exist
+  if (vec) {
+    const float4* A4 = reinterpret_cast<const float4*>(p.A + t0 * k);
+    const int n4 = SR_FRAMES * k / 4;
+    for (int e0 = tid; e0 < n4; e0 += 8 * 256) {
+      float4 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e4 = e0 + u * 256;
+        x[u] = (e4 < n4 && 4ll * e4 < have) ? __ldg(A4 + e4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e4 = e0 + u * 256;
+        if (e4 < n4) {
+          const int f = 4 * e4 / k, c = 4 * e4 - f * k;
+          float* d = As + f * lda + c;
+          d[0] = x[u].x;
+          d[1] = x[u].y;
+          d[2] = x[u].z;
+          d[3] = x[u].w;
+        }
+      }
+    }
+  } else {
+    for (int f = tid >> 6; f < SR_FRAMES; f += 4) {
+      const long long t = t0 + f;
+      for (int c = tid & 63; c < k; c += 64) As[f * lda + c] = (t < p.T) ? p.A[t * k + c] : 0.f;
+    }
+  }
+  for (int e = tid; e < qn * k; e += 256) Ss[e] = p.s32[(size_t)q0 * k + e];
+  __syncthreads();
+  const int f = tid >> 1, part = tid & 1;
+  const long long t = t0 + f;
+  const float* arow = As + f * lda;
+  const int nvec = p.Kc / 8;                  // 16-byte vectors per row
+  const int piece = SPLIT ? p.Kc / 2 : p.Kc;  // split rows are [hi | lo], each `piece` wide
+  for (int qi = 0; qi < qn; ++qi) {
+    const int q = q0 + qi;
+    const float2* sq = Ss + qi * k;
+    float hi = 0.f, lo = 0.f;
+    for (int c = part; c < k; c += 2) {  // TwoProduct by fma, TwoSum (Ogita, Rump and Oishi)
+      const float2 sv = sq[c];
+      const float x = arow[c];
+      const float prod = x * sv.x;
+      const float perr = fmaf(x, sv.x, -prod) + x * sv.y;
+      const float sum = hi + prod;
+      const float z = sum - hi;
+      lo += ((hi - (sum - z)) + (prod - z)) + perr;
+      hi = sum;
+    }
+    {  // both threads combine (half 0, half 1) in the same order
+      const float ohi = __shfl_xor_sync(0xffffffffu, hi, 1), olo = __shfl_xor_sync(0xffffffffu, lo, 1);
+      const float a = part ? ohi : hi, b = part ? hi : ohi;
+      const float la = part ? olo : lo, lb = part ? lo : olo;
+      const float sum = a + b;
+      const float z = sum - a;
+      lo = ((la + ((a - (sum - z)) + (b - z))) + lb);
+      hi = sum;
+    }
+    float v = 0.f;
+    if (t < p.T) {
+      const long long* se = p.S_exact ? p.S_exact + (size_t)q * p.T + t : nullptr;
+      if (p.St && part == 0) p.St[(size_t)q * p.T + t] = se ? (double)*se : (double)hi + (double)lo;
+      const float den = p.norm == XPCS_NORM_EQ12 ? (float)p.Sbar[q] : se ? (float)*se : hi + lo;
+      if (den > 0.f)
+        v = sqrtf((float)p.Mq[q]) / den;
+      else if (part == 0)
+        atomicOr(&p.blk_bad[(size_t)q * p.nT + (t >> 7)], 1u);
+    }
+    if (part == 0) p.r[(size_t)q * p.T_pad + t] = v;
+    uint4* R = reinterpret_cast<uint4*>(static_cast<T16*>(p.R) + ((size_t)q * p.T_pad + t) * p.Kc);
+    for (int vv = part; vv < nvec; vv += 2) {
+      // a vector never straddles the hi | lo boundary (piece is a multiple of 64)
+      const bool lov = SPLIT && vv * 8 >= piece;
+      const int jb = vv * 8 - (lov ? piece : 0);
+      alignas(16) T16 rv[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int j = jb + e;
+        const float av = j < k ? v * arow[j] : 0.f;
+        rv[e] = lov ? to16<T16>(av - (float)to16<T16>(av)) : to16<T16>(av);
+      }
+      R[vv] = *reinterpret_cast<const uint4*>(rv);
+    }
+  }
+}
+
 __global__ void coef_pieces_kernel(const float* A, long long T, int k, int kq, long long n, __nv_bfloat16* out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long t = i / kq;
@@ -466,19 +577,23 @@ __global__ void g2_finalize_kernel(const float* partials, const long long* count
   const int q = (int)(gid / T);
   const long long tau = gid % T;
   const int d1 = (int)(tau / TILE), e1 = (int)(tau % TILE);
-  double s1 = 0.0, s2 = 0.0;  // two independent chains, added in a fixed order
+  // two independent chains of compensated f32 sums (hi + lo pairs by TwoSum: about twice
+  // the f32 precision, no FP64 arithmetic, which is slow on this part), added in a fixed
+  // order; one FP64 division per lag
+  float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
   {
     const int nC = (nT - d1 + CH - 1) / CH;
     const float* base = partials + ((size_t)q * nT + d1) * maxC * DIAG_SLOTS;
-    for (int c = 0; c < nC; ++c) s1 += (double)base[(size_t)c * DIAG_SLOTS + TILE + e1];
+    for (int c = 0; c < nC; ++c) s1 = f32pair_add(s1, base[(size_t)c * DIAG_SLOTS + TILE + e1]);
   }
   const int d2 = d1 + 1;
   if (d2 < nT) {
     const int nC = (nT - d2 + CH - 1) / CH;
     const float* base = partials + ((size_t)q * nT + d2) * maxC * DIAG_SLOTS;
-    for (int c = 0; c < nC; ++c) s2 += (double)base[(size_t)c * DIAG_SLOTS + e1];
+    for (int c = 0; c < nC; ++c) s2 = f32pair_add(s2, base[(size_t)c * DIAG_SLOTS + e1]);
   }
-  const double sum = s1 + s2;
+  s1 = f32pair_add(f32pair_add(s1, s2.x), s2.y);
+  const double sum = (double)s1.x + (double)s1.y;
   const long long n = count[gid];
   g2[gid] = n > 0 ? sum / (double)n : __longlong_as_double(0x7ff8000000000000ll);
 }
@@ -596,8 +711,33 @@ cudaError_t launch_coef_mean(const float* A, long long T, int k, const double* s
 cudaError_t launch_prep_compressed(const PrepParams& p, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(p.blk_bad, 0, (size_t)p.n_q * p.nT * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  const int smem = (p.skip_L ? PREP_FRAMES * (p.k + 1) + PREP_FRAMES
-                              : 2 * PREP_FRAMES * (p.k + 1) + p.k * 64 + PREP_FRAMES) * (int)sizeof(float);
+  if (p.skip_L) {  // the tensor-core path: ring sums, scales and R rows only
+    if (p.norm == XPCS_NORM_FROB) return cudaErrorInvalidValue;
+    const int lda = (p.k + 31) / 32 * 32 + 2;
+    const int vec = (p.k % 4 == 0 && reinterpret_cast<uintptr_t>(p.A) % 16 == 0) ? 1 : 0;
+    const int smem_sr = (SR_FRAMES * lda + SR_QG * p.k * 2) * (int)sizeof(float);
+    const dim3 grid_sr(p.T_pad / SR_FRAMES, (p.n_q + SR_QG - 1) / SR_QG);
+#define XPCS_SR_LAUNCH(T16, SPLIT)                                                                    \
+  do {                                                                                                \
+    static int attr_bytes = 0; /* the attribute only ever grows */                                   \
+    if (smem_sr > attr_bytes) {                                                                       \
+      e = cudaFuncSetAttribute(scales_rows_kernel<T16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                               smem_sr);                                                              \
+      if (e != cudaSuccess) return e;                                                                 \
+      attr_bytes = smem_sr;                                                                           \
+    }                                                                                                 \
+    scales_rows_kernel<T16, SPLIT><<<grid_sr, 256, smem_sr, st>>>(p, lda, vec);                       \
+  } while (0)
+    if (p.prec == XPCS_PREC_FP16)
+      XPCS_SR_LAUNCH(__half, false);
+    else if (p.prec == XPCS_PREC_BF16)
+      XPCS_SR_LAUNCH(__nv_bfloat16, false);
+    else
+      XPCS_SR_LAUNCH(__nv_bfloat16, true);
+#undef XPCS_SR_LAUNCH
+    return cudaGetLastError();
+  }
+  const int smem = (2 * PREP_FRAMES * (p.k + 1) + p.k * 64 + PREP_FRAMES) * (int)sizeof(float);
   const dim3 grid(p.T_pad / PREP_FRAMES, p.n_q);
 #define XPCS_PREP_LAUNCH(T16, SPLIT)                                                                  \
   do {                                                                                                \
