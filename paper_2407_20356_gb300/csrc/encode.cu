@@ -176,6 +176,7 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     // converters + epilogue: 128 threads
     const int ct = threadIdx.x - 64;
     const int quarter = warp & 3;
+    const bool vec_out = p.k % 4 == 0 && reinterpret_cast<uintptr_t>(p.partials) % 16 == 0;
     uint32_t it = 0, item_i = 0;
     uint32_t over = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++item_i) {
@@ -249,9 +250,19 @@ encode_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tmem_ld32(lane_base + lay.kp + j0, lo);
           tc_wait_ld();
           const int nj = min(32, p.k - j0);
+          if (nj == 32 && vec_out) {  // the row's 32 coefficients as eight 16-byte stores
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j < nj) dst[j0 + j] = __uint_as_float(hi[j]) + __uint_as_float(lo[j]);
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(dst + j0 + j) =
+                  make_float4(__uint_as_float(hi[j]) + __uint_as_float(lo[j]),
+                              __uint_as_float(hi[j + 1]) + __uint_as_float(lo[j + 1]),
+                              __uint_as_float(hi[j + 2]) + __uint_as_float(lo[j + 2]),
+                              __uint_as_float(hi[j + 3]) + __uint_as_float(lo[j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nj) dst[j0 + j] = __uint_as_float(hi[j]) + __uint_as_float(lo[j]);
+          }
         }
       }
       tc_fence_before();
