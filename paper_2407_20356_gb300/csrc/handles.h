@@ -134,6 +134,7 @@ struct xpcs_stream {
   __nv_bfloat16* d_Wg = nullptr;     // n_q x 128 x 2 kpad
   float* d_gpart = nullptr;          // n_q x nd x 256
   CUtensorMap tmWg, tmWg2;           // boxes of 128 and 256 rows
+  CUtensorMap tmW48;                 // d_W2 in boxes of 64 x 48 (single-frame steps)
   int kpad = 0;                      // k rounded up to 64
   CUtensorMap tmA, tmW, tmR;         // tensor maps of d_A2, d_W2 (64 x 128 boxes) and d_Rh
   // tensor maps of d_g2sum and d_cnt (row pitch Wp), one per row-update lag tile RT_LTS[i]

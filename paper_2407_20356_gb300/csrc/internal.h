@@ -232,6 +232,7 @@ struct StreamStep {
   int nd;                  // tile diagonals that can hold a lag < W
   const CUtensorMap* tmWg;  // boxes of 128 w rows (one ring)
   const CUtensorMap* tmWg2; // boxes of 256 w rows (two rings)
+  const CUtensorMap* tmW48; // W2 in boxes of 48 rows (single-frame steps)
 };
 // Smallest step (frames) that runs on the two-time kernel; smaller steps take the row
 // update kernel.  Steps never cross a 128-frame block when they may take the former.
@@ -266,6 +267,20 @@ struct RowTcParams {
   uint32_t* status;
 };
 int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2, int epi);
+// Single-frame steps (b = 1, n_q <= 36) on the tensor cores (stream_tc.cu): frame t
+struct Row1Params {
+  long long t, W, cap;
+  int n_q, kpad, n_kc, npad, qb, n_tiles;  // qb = npad (r values per history row)
+  long long Wp;            // row pitch of g2sum / cnt
+  const float* Rh;         // (cap + 128) x npad
+  float2* g2sum;           // n_q x Wp
+  long long* cnt;          // n_q x Wp
+  uint32_t* status;
+};
+int row1_tc_smem(int n_kc, int qb);
+// tensor maps: A2 history (64 x 128 boxes), W2 (64 x 48 boxes), Rh (qb x 128 boxes)
+cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR, const Row1Params& p,
+                           int grid, cudaStream_t st);
 // tensor maps: A2 history, W2 pairs, Rh r values, g2sum and cnt (lt x qg2 boxes)
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
                                  const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,

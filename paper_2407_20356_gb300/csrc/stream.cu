@@ -377,6 +377,26 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     stream_fold_kernel<<<(unsigned)((s.n_q * span + 255) / 256), 256, 0, st>>>(s, nd_step);
     return cudaGetLastError();
   }
+  if (s.b == 1 && s.n_q <= 36 && s.tmW48) {
+    // one frame: the persistent single-frame kernel (lag tiles of 128, direct fold)
+    Row1Params p1{};
+    p1.t = s.t0;
+    p1.W = s.W;
+    p1.cap = s.cap;
+    p1.n_q = s.n_q;
+    p1.kpad = s.kpad;
+    p1.n_kc = s.kpad / 64;
+    p1.npad = stream_npad(s.n_q);
+    p1.qb = p1.npad;
+    p1.n_tiles = (int)((std::min<long long>(s.W, s.t0 + 1) + 127) / 128);
+    p1.Wp = s.Wp;
+    p1.Rh = s.Rh;
+    p1.g2sum = s.g2sum;
+    p1.cnt = s.cnt;
+    p1.status = s.status;
+    if (p1.n_kc <= 2 && row1_tc_smem(p1.n_kc, p1.qb) <= 227 * 1024)
+      return launch_row1_tc(*s.tmA, *s.tmW48, *s.tmR, p1, std::min(p1.n_tiles, s.num_sms), st);
+  }
   // row update of the step (at most 64 frames: every pair of a lag tile then lies in
   // one 128-row history operand)
   RowTcParams p{};

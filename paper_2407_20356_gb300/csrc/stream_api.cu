@@ -236,6 +236,9 @@ extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B,
     st = make_map(ctx, &S->tmW, S->d_W2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * S->kpad,
                   w2_rows(max_batch, B->rings->n_q), 64, 128, CU_TENSOR_MAP_SWIZZLE_128B);
   if (st == XPCS_OK)
+    st = make_map(ctx, &S->tmW48, S->d_W2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * S->kpad,
+                  w2_rows(max_batch, B->rings->n_q), 64, 48, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (st == XPCS_OK)
     st = make_map(ctx, &S->tmWg, S->d_Wg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2 * S->kpad,
                   (uint64_t)128 * B->rings->n_q, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B);
   if (st == XPCS_OK)  // ring pairs (rows past the last ring read as zeros)
@@ -360,6 +363,7 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.nd = stream_nd(S->W);
   s.tmWg = &S->tmWg;
   s.tmWg2 = &S->tmWg2;
+  s.tmW48 = &S->tmW48;
   // steps of at most STEP_MAX_GRAM frames; the batch completes with its last step
   const size_t fb = (size_t)B->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
   cudaError_t e = cudaSuccess;

@@ -568,4 +568,244 @@ cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW,
   }
 }
 
+// ====================================================================== single frames
+// Steps of one frame t (at most 36 rings): for every lag tau < min(W, t + 1), ring q,
+//     g2sum_q[tau] += (w_q(t) . a_s) r_q(s),  cnt_q[tau] += 1,  s = t - tau,
+// when r_q(t) > 0 and r_q(s) > 0 (both frames defined).  Work item = a tile of 128 lags
+// tau0 .. tau0 + 127, history rows s = t - tau0 - 127 + c (c = 0..127): D[c][q] = a_s . w_q
+// on the tensor cores (M = the 128 history rows, N = 48 >= 36 ring columns, bf16 hi | lo
+// pieces as in the row update kernel, the same products in the same order).  The CTA is
+// persistent over its tiles and double-buffers the history rows and their r values, so a
+// tile's loads overlap the previous tile's epilogue; the frame's w rows are loaded once.
+// Eight epilogue warps (TMEM lane quarter = warp mod 4, rings 18 h .. 18 h + 17 for
+// h = (warp - 2) / 4): the thread of lane c adds its lag's product to the running sum (f32
+// pair, TwoSum) and count of each ring in global memory, 32 consecutive lags per warp
+// access.  Each (ring, lag) has one owner: no atomics, the additions of every step in
+// stream order.  Every mbarrier wait is bounded.
+namespace {
+
+constexpr int R1_EPI_WARPS = 8;
+constexpr int R1_THREADS = 64 + 32 * R1_EPI_WARPS;
+constexpr int R1_N = 48;                      // MMA N: the 36 ring columns, rounded up to 16
+constexpr int R1_WCHUNK = R1_N * RT_CH * 2;   // 6 KB: 48 w rows x 128 B
+
+struct R1Layout {
+  int n_kc, qb;
+  __host__ __device__ int hist_bytes() const { return 2 * n_kc * RT_CHUNK; }
+  __host__ __device__ int w_bytes() const { return 2 * n_kc * R1_WCHUNK; }
+  __host__ __device__ int rs_bytes() const { return (RT_ROWS * qb * 4 + 1023) / 1024 * 1024; }
+  __host__ __device__ int smem() const { return 1024 + 2 * hist_bytes() + w_bytes() + 2 * rs_bytes() + 256; }
+};
+
+__global__ void __launch_bounds__(R1_THREADS, 1)
+    row1_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
+                   const __grid_constant__ CUtensorMap tmR, const Row1Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const R1Layout L{p.n_kc, p.qb};
+  uint8_t* hist = smem;                                 // [2][hi kc..., lo kc...]
+  uint8_t* wbuf = smem + 2 * L.hist_bytes();            // [hi kc..., lo kc...] 48-row chunks
+  uint8_t* rsb = wbuf + L.w_bytes();                    // [2][128][qb] r of the rows
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rsb + 2 * L.rs_bytes());
+  uint64_t* h_full = bars;       // [2] history rows + their r values landed
+  uint64_t* h_empty = bars + 2;  // [2] MMAs and epilogue done with them
+  uint64_t* w_full = bars + 4;   // the frame's w rows landed
+  uint64_t* tfull = bars + 5;    // [2] accumulator ready
+  uint64_t* tempty = bars + 7;   // [2] accumulator read
+  uint64_t* mma_done = bars + 9;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long t = p.t;
+
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&h_full[b], 1);
+      mbar_init(&h_empty[b], 1 + R1_EPI_WARPS);
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], R1_EPI_WARPS);
+    }
+    mbar_init(w_full, 1);
+    mbar_init(mma_done, 1);
+    mbar_fence_init();
+    *abort_flag = 0;
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmW);
+      tma_prefetch_desc(&tmR);
+      mbar_arrive_expect_tx(w_full, (uint32_t)L.w_bytes());
+      for (int kc = 0; kc < p.n_kc; ++kc) {
+        tma_load_2d(wbuf + kc * R1_WCHUNK, &tmW, w_full, kc * RT_CH, 0);
+        tma_load_2d(wbuf + (p.n_kc + kc) * R1_WCHUNK, &tmW, w_full, p.kpad + kc * RT_CH, 0);
+      }
+      uint32_t i = 0;
+      for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++i) {
+        const uint32_t bi = i & 1;
+        if (*abort_flag || !mbar_wait(&h_empty[bi], ((i >> 1) & 1) ^ 1, p.status)) {
+          *abort_flag = 1;
+          break;
+        }
+        const long long s_start = t - (long long)tile * RT_ROWS - (RT_ROWS - 1);
+        // before the ring buffer wraps, rows before frame 0 are read as zeros (negative
+        // coordinates); afterwards the window is contiguous thanks to the mirrored rows
+        const int y = (s_start < 0 && t + 1 <= p.cap) ? (int)s_start : (int)(((s_start % p.cap) + p.cap) % p.cap);
+        uint8_t* hb = hist + bi * L.hist_bytes();
+        mbar_arrive_expect_tx(&h_full[bi], (uint32_t)(L.hist_bytes() + RT_ROWS * p.qb * 4));
+        for (int kc = 0; kc < p.n_kc; ++kc) {
+          tma_load_2d(hb + kc * RT_CHUNK, &tmA, &h_full[bi], kc * RT_CH, y);
+          tma_load_2d(hb + (p.n_kc + kc) * RT_CHUNK, &tmA, &h_full[bi], p.kpad + kc * RT_CH, y);
+        }
+        tma_load_2d(rsb + bi * L.rs_bytes(), &tmR, &h_full[bi], 0, y);
+      }
+      // never leave the CTA with bulk copies in flight
+      mbar_wait(w_full, 0, p.status);
+      for (uint32_t j = (i > 2 ? i - 2 : 0); j < i; ++j) mbar_wait(&h_full[j & 1], (j >> 1) & 1, p.status);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(1, RT_ROWS, R1_N);
+      bool issued = false;
+      if (!*abort_flag && mbar_wait(w_full, 0, p.status)) {
+        uint32_t i = 0;
+        for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++i) {
+          const uint32_t bi = i & 1, ph = (i >> 1) & 1;
+          if (*abort_flag || !mbar_wait(&tempty[bi], ph ^ 1, p.status) || !mbar_wait(&h_full[bi], ph, p.status)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem_base + bi * 64;
+          const uint8_t* hb = hist + bi * L.hist_bytes();
+          for (int kc = 0; kc < p.n_kc; ++kc) {
+            const uint64_t hhi = smem_desc_sw128(hb + kc * RT_CHUNK);
+            const uint64_t hlo = smem_desc_sw128(hb + (p.n_kc + kc) * RT_CHUNK);
+            const uint64_t whi = smem_desc_sw128(wbuf + kc * R1_WCHUNK);
+            const uint64_t wlo = smem_desc_sw128(wbuf + (p.n_kc + kc) * R1_WCHUNK);
+#pragma unroll
+            for (int kk = 0; kk < RT_CH / 16; ++kk) {  // D[history row][ring]
+              tc_mma_f16(d, hhi + 2 * kk, whi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+              tc_mma_f16(d, hhi + 2 * kk, wlo + 2 * kk, idesc, 1u);
+              tc_mma_f16(d, hlo + 2 * kk, whi + 2 * kk, idesc, 1u);
+            }
+          }
+          tc_commit(&h_empty[bi]);  // the history rows are free once these MMAs complete
+          tc_commit(&tfull[bi]);
+          issued = true;
+        }
+      } else {
+        *abort_flag = 1;
+      }
+      if (issued) {  // all issued MMAs complete before TMEM is released
+        tc_commit(mma_done);
+        mbar_wait(mma_done, 0, p.status);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2..9)
+    const int quarter = warp & 3, h = (warp - 2) >> 2;
+    const int c = quarter * 32 + lane;  // history row = TMEM lane
+    const int q0 = 18 * h, qn = max(0, min(18, p.n_q - q0));
+    // r of the new frame for this warp's rings
+    const long long slot_t = t % p.cap;
+    float rt[18];
+#pragma unroll
+    for (int u = 0; u < 18; ++u) rt[u] = u < qn ? p.Rh[slot_t * p.npad + q0 + u] : 0.f;
+    uint32_t i = 0;
+    for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++i) {
+      const uint32_t bi = i & 1, ph = (i >> 1) & 1;
+      const bool good = !__any_sync(0xffffffffu, *abort_flag != 0) && mbar_wait_warp(&tfull[bi], ph, p.status) &&
+                        mbar_wait_warp(&h_full[bi], ph, p.status);  // warp-uniform outcome
+      if (!good) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      uint32_t v[32];  // columns q0 - 16 h .. : ring q0 + u is v[u + 2 h]
+      tmem_ld32(tmem_base + bi * 64 + 16 * h + ((uint32_t)(quarter * 32) << 16), v);
+      const float* rrow = reinterpret_cast<const float*>(rsb + bi * L.rs_bytes()) + (size_t)c * p.qb + q0;
+      float rs[18];
+#pragma unroll
+      for (int u = 0; u < 18; ++u) rs[u] = u < qn ? rrow[u] : 0.f;
+      tc_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&tempty[bi]);
+        mbar_arrive(&h_empty[bi]);
+      }
+      const long long tau = (long long)tile * RT_ROWS + (RT_ROWS - 1 - c);
+      if (tau >= p.W || tau > t || qn == 0) continue;
+      float2* gs = p.g2sum + (size_t)q0 * p.Wp + tau;
+      long long* cn = p.cnt + (size_t)q0 * p.Wp + tau;
+      // two batches of nine rings: loads of a batch in flight together, then the adds
+#pragma unroll
+      for (int u0 = 0; u0 < 18; u0 += 9) {
+        bool pr[9];
+        float2 acc[9];
+        long long cv[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+          const int u = u0 + e;
+          pr[e] = u < qn && rt[u] > 0.f && rs[u] > 0.f;
+          if (pr[e]) {
+            acc[e] = gs[(size_t)u * p.Wp];
+            cv[e] = cn[(size_t)u * p.Wp];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+          const int u = u0 + e;
+          if (pr[e]) {
+            const float d = __uint_as_float(h ? v[u + 2] : v[u]);  // compile-time register indices
+            gs[(size_t)u * p.Wp] = f32pair_add(acc[e], d * rs[u]);
+            cn[(size_t)u * p.Wp] = cv[e] + 1;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 128);
+  }
+}
+
+}  // namespace
+
+int row1_tc_smem(int n_kc, int qb) { return R1Layout{n_kc, qb}.smem(); }
+
+cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR, const Row1Params& p,
+                           int grid, cudaStream_t st) {
+  if (p.n_q < 1 || p.n_q > 36 || p.qb < p.n_q || p.n_kc < 1 || p.n_kc > 2) return cudaErrorInvalidValue;
+  const int smem = row1_tc_smem(p.n_kc, p.qb);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  static int attr_bytes = 0;  // the attribute only ever grows
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(row1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  row1_tc_kernel<<<grid, R1_THREADS, smem, st>>>(tmA, tmW, tmR, p);
+  return cudaGetLastError();
+}
+
 }  // namespace xpcs
