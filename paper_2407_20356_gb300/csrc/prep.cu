@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -28,8 +29,9 @@ constexpr int RI_GROUPS = RI_CHUNK / 64;  // 64-position groups per chunk
 constexpr int RI_F = 8;                   // frames per CTA
 constexpr int RI_J = RI_GROUPS / 8;       // groups per warp (8 warps)
 
+template <int DT>
 __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p) {
-  __shared__ int sperm[RI_CHUNK];
+  __shared__ __align__(16) int sperm[RI_CHUNK];
   __shared__ int sring[RI_GROUPS];
   __shared__ unsigned long long gsum[RI_F][RI_GROUPS];
   __shared__ unsigned long long gsq[RI_F][RI_GROUPS];
@@ -46,19 +48,17 @@ __global__ void __launch_bounds__(256) raw_ingest_kernel(const RawIngestParams p
     const long long t = t0 + f;
     if (t >= p.T_pad) break;  // CTA-uniform
     const bool live = t < p.T;
-    const uint8_t* x8 = static_cast<const uint8_t*>(p.X) + t * p.M;
-    const uint16_t* x16 = static_cast<const uint16_t*>(p.X) + t * p.M;
+    using Tx = typename std::conditional<DT == 0, uint8_t, uint16_t>::type;
+    const Tx* xr = static_cast<const Tx*>(p.X) + t * p.M;
     unsigned a[RI_J], b[RI_J];
 #pragma unroll
     for (int j = 0; j < RI_J; ++j) {
       const int o = 64 * (warp + 8 * j) + 2 * lane;
-      const int sa = sperm[o], sb = sperm[o + 1];  // -1 for padding and past the chunk
-      a[j] = 0;
-      b[j] = 0;
-      if (live) {
-        if (sa >= 0) a[j] = p.dtype == 0 ? (unsigned)x8[sa] : (unsigned)x16[sa];
-        if (sb >= 0) b[j] = p.dtype == 0 ? (unsigned)x8[sb] : (unsigned)x16[sb];
-      }
+      // the pair of map entries in one 8-byte load (no bank conflicts); -1 for padding and
+      // past the chunk
+      const int2 sp = *reinterpret_cast<const int2*>(sperm + o);
+      a[j] = (live && sp.x >= 0) ? (unsigned)xr[sp.x] : 0u;
+      b[j] = (live && sp.y >= 0) ? (unsigned)xr[sp.y] : 0u;
     }
 #pragma unroll
     for (int j = 0; j < RI_J; ++j) {
@@ -686,7 +686,10 @@ cudaError_t launch_raw_ingest(const RawIngestParams& p, cudaStream_t st) {
   if (e == cudaSuccess && p.S2) e = cudaMemsetAsync(p.S2, 0, (size_t)p.n_q * p.T * sizeof(long long), st);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((p.Mp + RI_CHUNK - 1) / RI_CHUNK), (unsigned)((p.T_pad + RI_F - 1) / RI_F));
-  raw_ingest_kernel<<<grid, 256, 0, st>>>(p);
+  if (p.dtype == 0)
+    raw_ingest_kernel<0><<<grid, 256, 0, st>>>(p);
+  else
+    raw_ingest_kernel<1><<<grid, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
