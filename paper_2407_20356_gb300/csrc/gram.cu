@@ -425,6 +425,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ 
         for (int h2 = 0; h2 < NP; ++h2) {
           if (h2 >= nh) break;
           const bool last = h2 == nh - 1;  // TMEM is released after the unit's last load
+          // a stream step's w block is zero outside the step's frames: a strip without any
+          // of them adds nothing
+          if (sm && !(p.sm_c0 < 64 * h + 64 && p.sm_c1 > 64 * h)) {
+            if (last) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&tempty[b]);
+            }
+            continue;
+          }
           const uint32_t tbase =
               tmem_base + b * (NP * TILE) + h2 * TILE + ((uint32_t)(r * 32) << 16) + 64 * h;
           const float* rj = sm ? nullptr

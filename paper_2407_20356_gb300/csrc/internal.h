@@ -58,6 +58,7 @@ struct GramParams {
   // q*128 .., zero except the step's frames, which carry their scale r_q(t)), sm_nk
   // 64-wide chunks per piece, row scale r[slot * r_ld + q], no column scale
   int sm, sm_nk, r_ld;
+  int sm_c0, sm_c1;        // stream step: the step's frames are rows [sm_c0, sm_c1) of each w block
   int sm_nq;               // stream step: rings; with pairs, the two halves of an accumulator are
                            // rings q and q + 1 (item q = 2 (i / ring_nd)) of one tile diagonal
   const float* r;          // [n_q][T_pad] sqrt(M_q)/S_q(t); 0 where undefined

@@ -364,6 +364,8 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     gp.ring_J = (int)((s.t0 >> 7) % nb);
     gp.sm = 1;
     gp.sm_nk = s.kpad / 64;
+    gp.sm_c0 = (int)(s.t0 & 127);
+    gp.sm_c1 = gp.sm_c0 + s.b;
     gp.r_ld = stream_npad(s.n_q);
     gp.fmt = 1;
     gp.split = 1;
