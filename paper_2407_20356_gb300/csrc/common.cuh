@@ -112,6 +112,15 @@ XPCS_DEV bool mbar_wait_warp(uint64_t* bar, uint32_t parity, uint32_t* status) {
   return ok;
 }
 
+// ------------------------------------------------------------------ dependent launches
+// A kernel launched with programmatic stream serialization may start before the kernel
+// ahead of it in the stream has finished: pdl_wait blocks the calling thread until that
+// kernel has completed and its memory operations are visible (at once when the launch was
+// an ordinary one), and pdl_trigger lets the kernel behind this one start launching.
+// Every kernel of such a chain waits before it ends, so completion stays transitive.
+XPCS_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+XPCS_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------ TMA (no multicast)
 
 XPCS_DEV void tma_prefetch_desc(const void* map) {

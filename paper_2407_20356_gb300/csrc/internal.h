@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units (not part of the ABI).
 #pragma once
+#include <utility>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -26,6 +27,24 @@ constexpr int DIAG_SLOTS = 256;  // local diagonal slots per (ring, tile-diagona
 constexpr int CHUNK_TILES = 8;   // default tiles per work item along a tile diagonal
 
 // ------------------------------------------------------------------ Gram kernel
+
+// Launch of a kernel with programmatic stream serialization (its threads call pdl_wait
+// before they read what the kernel ahead of it wrote).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 struct GramParams {
   int T;                   // frames

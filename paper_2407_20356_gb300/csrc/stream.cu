@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
   __shared__ int warp_tot[8];
   __shared__ float red[256];
   __shared__ unsigned ring_acc[SE_MAX_RINGS];  // exact ring sums of this slice (at most 2^28)
+  pdl_trigger();
   const int blk = blockIdx.x, fi = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long p0 = (long long)blk * SE_PX + (long long)tid * 16;
@@ -129,6 +130,9 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
     }
     __syncthreads();
   }
+  // reads nothing the kernels ahead wrote, so it only waits before it ends (the frame
+  // factors behind it rewrite rows that the previous step's kernels read)
+  pdl_wait();
 }
 
 // a_t[j] = sum of the nblk slice partials of frame t.  Block = 32 (frame, column) pairs x
@@ -138,6 +142,8 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
 constexpr int RD_GROUPS = 8;
 __global__ void __launch_bounds__(256) stream_reduce_kernel(const StreamStep s) {
   __shared__ float red[RD_GROUPS][32];
+  pdl_trigger();
+  pdl_wait();  // the slice partials
   const int jj = threadIdx.x & 31, g = threadIdx.x >> 5;
   const long long col = (long long)blockIdx.x * 32 + jj;  // (frame, column) = (col / k, col mod k)
   const bool live = col < (long long)s.b * s.k;
@@ -182,6 +188,8 @@ XPCS_DEV void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
 __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) {
   __shared__ float as[256];
   __shared__ double dred[4];
+  pdl_trigger();
+  pdl_wait();  // the coefficients
   const int fi = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
   const int k = s.k, kp = s.kpad;
   const long long t = s.t0 + fi;
@@ -330,13 +338,11 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   if (s.Sx && s.n_q > SE_MAX_RINGS) return cudaErrorInvalidValue;
   cudaError_t e = s.Sx ? cudaMemsetAsync(s.Sx, 0, (size_t)s.b * s.n_q * sizeof(long long), st) : cudaSuccess;
   if (e != cudaSuccess) return e;
-  sparse_encode_kernel<<<dim3(s.nblk, s.b), 256, 0, st>>>(s);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  stream_reduce_kernel<<<(s.b * s.k + 31) / 32, 256, 0, st>>>(s);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  frame_factors_kernel<<<dim3(s.b, s.n_q), 128, 0, st>>>(s);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // dependent launches: each kernel may start while the one ahead of it finishes
+  if ((e = launch_pdl(sparse_encode_kernel, dim3(s.nblk, s.b), dim3(256), 0, st, s)) != cudaSuccess) return e;
+  if ((e = launch_pdl(stream_reduce_kernel, dim3((s.b * s.k + 31) / 32), dim3(256), 0, st, s)) != cudaSuccess)
+    return e;
+  if ((e = launch_pdl(frame_factors_kernel, dim3(s.b, s.n_q), dim3(128), 0, st, s)) != cudaSuccess) return e;
   if (s.b >= STREAM_GRAM_MIN) {
     // the two-time kernel on (history block J - delta, the step's block J) tiles of every
     // ring: L = the coefficient history (shared by the rings), R = the block's w rows of

@@ -635,10 +635,12 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
     tmem_alloc(tmem_slot, 128);
     tmem_relinquish();
   }
+  pdl_trigger();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();  // the frame's w, history and r rows
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -804,8 +806,7 @@ cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  row1_tc_kernel<<<grid, R1_THREADS, smem, st>>>(tmA, tmW, tmR, p);
-  return cudaGetLastError();
+  return launch_pdl(row1_tc_kernel, dim3(grid), dim3(R1_THREADS), (size_t)smem, st, tmA, tmW, tmR, p);
 }
 
 }  // namespace xpcs
