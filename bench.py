@@ -571,7 +571,7 @@ def run_ours(args, wl):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "h2d_gbs_over_step": h2d / (e2e_ms * 1e-3) / 1e9,
                 "h2d_copy_only_ms": copy_ms, "h2d_copy_only_gbs": h2d / (copy_ms * 1e-3) / 1e9,
-                "path": "xpcs_encode_host (copies of 256 MB blocks on two copy streams overlapped with the "
+                "path": "xpcs_encode_host (copies of 256 MB blocks, on one or two copy streams as the context calibrates on its first call, overlapped with the "
                         "encode) + xpcs_twotime + g2/count read back"},
         "gpu_launches": launches,
         "clocks": sampler.summary() if sampler else None,

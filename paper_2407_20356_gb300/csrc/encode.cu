@@ -475,6 +475,41 @@ extern "C" xpcs_status xpcs_encode_host(xpcs_ctx* ctx, const xpcs_basis* B, cons
       XPCS_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_free[i], cudaEventDisableTiming));
     }
   }
+  // Copy scheme: whether two block copies in flight at once (two copy engines) move the
+  // frames faster than one after the other depends on the host link of the machine, so the
+  // first call times both on two 128 MB pieces of the caller's frames and keeps the faster
+  // (two only when at least 5 % faster)
+  if (ctx->copy_streams == 0) {
+    XPCS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the staging buffers are free
+    const size_t piece = std::min<size_t>((size_t)blk * fb, (size_t)128 << 20);
+    const size_t avail = (size_t)T * fb;
+    if (avail < 2 * piece) {
+      ctx->copy_streams = 1;
+    } else {
+      cudaEvent_t e[4];
+      for (int i = 0; i < 4; ++i) XPCS_CUDA(ctx, cudaEventCreate(&e[i]));
+      const char* hs = static_cast<const char*>(X_host);
+      cudaError_t ce = cudaEventRecord(e[0], ctx->copy_stream[0]);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(stage[0], hs, piece, cudaMemcpyHostToDevice, ctx->copy_stream[0]);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(stage[1], hs + piece, piece, cudaMemcpyHostToDevice, ctx->copy_stream[0]);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e[1], ctx->copy_stream[0]);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e[1]);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e[2], ctx->copy_stream[0]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ctx->copy_stream[1], e[2], 0);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(stage[0], hs, piece, cudaMemcpyHostToDevice, ctx->copy_stream[0]);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(stage[1], hs + piece, piece, cudaMemcpyHostToDevice, ctx->copy_stream[1]);
+      float one = 0.f, two = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventRecord(ctx->ev_loaded[0], ctx->copy_stream[1]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ctx->copy_stream[0], ctx->ev_loaded[0], 0);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e[3], ctx->copy_stream[0]);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e[3]);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&one, e[0], e[1]);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&two, e[2], e[3]);
+      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+      if (ce != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("copy calibration: ") + cudaGetErrorString(ce));
+      ctx->copy_streams = two < 0.95f * one ? 2 : 1;
+    }
+  }
   // the staging buffers are scratch: earlier work on the context's stream may still use it
   XPCS_CUDA(ctx, cudaEventRecord(ctx->ev_free[0], ctx->stream));
   for (int i = 1; i < ENC_HOST_BUFS; ++i) XPCS_CUDA(ctx, cudaEventRecord(ctx->ev_free[i], ctx->stream));
@@ -482,7 +517,7 @@ extern "C" xpcs_status xpcs_encode_host(xpcs_ctx* ctx, const xpcs_basis* B, cons
   for (int64_t t0 = 0, i = 0; t0 < T; t0 += blk, ++i) {
     const int64_t n = std::min(blk, T - t0);
     const int buf = (int)(i % ENC_HOST_BUFS);
-    cudaStream_t cs = ctx->copy_stream[i % 2];
+    cudaStream_t cs = ctx->copy_stream[ctx->copy_streams == 2 ? i % 2 : 0];
     XPCS_CUDA(ctx, cudaStreamWaitEvent(cs, ctx->ev_free[buf], 0));
     XPCS_CUDA(ctx, cudaMemcpyAsync(stage[buf], src + (size_t)t0 * fb, (size_t)n * fb, cudaMemcpyHostToDevice, cs));
     XPCS_CUDA(ctx, cudaEventRecord(ctx->ev_loaded[buf], cs));

@@ -57,6 +57,7 @@ struct xpcs_ctx {
   // xpcs_encode_host: two copy streams and the events of its staging buffers (made on
   // first use)
   cudaStream_t copy_stream[2] = {nullptr, nullptr};
+  int copy_streams = 0;  // host-frame copies on 1 or 2 streams (0: not yet calibrated)
   cudaEvent_t ev_loaded[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t ev_free[3] = {nullptr, nullptr, nullptr};
 };
