@@ -348,7 +348,10 @@ xpcs_status xpcs_graph_destroy(xpcs_graph* graph);
 
 /* ------------------------------------------------------------------ online stream (Sec. 2.2, Fig. 1c)
  * Online compression with a basis fit before acquisition: every pushed frame is encoded
- * (a_t = x_t V_K, sparse: only nonzero pixels read their basis row, f32), appended to a
+ * (a_t = x_t V_K: in steps of fewer than 32 frames sparse, only nonzero pixels reading
+ * their f32 basis row; steps of 32 or more, on 16-byte aligned frame rows and without
+ * exact ring sums, take the tensor-core encode of xpcs_encode, whose counts must stay
+ * below 1024 — larger ones are flagged XPCS_ERANGE as there), appended to a
  * device ring buffer of the last `history` coefficient rows, and its two-time row
  * C_q(t, s) for s in (t - history, t] is folded into running sums over lags
  * tau = 0 .. history-1 (C itself is not stored).  xpcs_stream_read_g2 returns

@@ -378,7 +378,7 @@ static int pick_splits(int n_m, long long M_pad, int num_sms) {
 }
 
 // Partial-sum floats an encode of T frames needs (its pixel splits x padded frames x k).
-static size_t encode_partials(const xpcs_basis* B, int64_t T, int num_sms) {
+size_t xpcs::encode_partials(const xpcs_basis* B, int64_t T, int num_sms) {
   const int nT = (int)((T + TILE - 1) / TILE);
   const int n_mp = (nT + encode_frame_blocks(B->k) - 1) / encode_frame_blocks(B->k);
   return (size_t)pick_splits(n_mp, B->M_pad, num_sms) * nT * TILE * B->k;
@@ -417,6 +417,44 @@ static xpcs_status enqueue_encode(xpcs_ctx* ctx, const xpcs_basis* B, const void
   XPCS_LAUNCH(ctx, "encode", 1, launch_encode(tmX, tmB, p, std::min(n_items, ctx->num_sms), ctx->stream));
   XPCS_LAUNCH(ctx, "encode_reduce", 1,
               launch_encode_reduce(partials, n_split, T, T_pad, k, std::ldexp(1.0f, -B->enc_log2), A_out, ctx->stream));
+  return XPCS_OK;
+}
+
+// The encode of T frames X (device, 16-byte aligned rows) on stream `st` into A_out, with
+// `partials` (encode_partials floats) as its split-K scratch and device status `status`:
+// the stream's large steps, on the stream's own CUDA stream.
+xpcs_status xpcs::encode_on_stream(xpcs_ctx* ctx, const xpcs_basis* B, const void* X, xpcs_dtype dtype,
+                                   int64_t T, float* A_out, float* partials, uint32_t* status, cudaStream_t st) {
+  const int64_t M = B->rings->M;
+  const int eb = dtype == XPCS_U8 ? 1 : 2;
+  const int k = B->k;
+  const int nT = (int)((T + TILE - 1) / TILE);
+  const int T_pad = nT * TILE;
+  const int mb = encode_frame_blocks(k);
+  const int n_mp = (nT + mb - 1) / mb;
+  const int n_split = pick_splits(n_mp, B->M_pad, ctx->num_sms);
+  const long long per = ((B->M_pad + n_split - 1) / n_split + KCH - 1) / KCH * KCH;
+  CUtensorMap tmX, tmB;
+  XPCS_TRY(make_map(ctx, &tmX, X, dtype == XPCS_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                    eb, M, T, KCH, TILE, dtype == XPCS_U8 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B));
+  const int N = 2 * B->kp;
+  XPCS_TRY(make_map(ctx, &tmB, B->d_Bcat, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, B->M_pad, N, KCH,
+                    N / ((N + 255) / 256), CU_TENSOR_MAP_SWIZZLE_128B));
+  EncodeParams p{};
+  p.T = T;
+  p.M = M;
+  p.k = k;
+  p.dtype = dtype;
+  p.n_split = n_split;
+  p.px_per_split = per;
+  p.partials = partials;
+  p.T_pad = T_pad;
+  p.status = status;
+  const int n_items = n_mp * n_split;
+  cudaError_t e = launch_encode(tmX, tmB, p, std::min(n_items, ctx->num_sms), st);
+  if (e == cudaSuccess)
+    e = launch_encode_reduce(partials, n_split, T, T_pad, k, std::ldexp(1.0f, -B->enc_log2), A_out, st);
+  if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream encode: ") + cudaGetErrorString(e));
   return XPCS_OK;
 }
 

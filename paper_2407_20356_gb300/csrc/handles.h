@@ -214,6 +214,12 @@ inline uint64_t gram_tune_key(int n_q, int nT, int fmt, int split, int raw, bool
          ((uint64_t)raw << 2) | (C ? 2u : 0u);
 }
 
+// Split-K partial floats of the encode of T frames, and the encode of device frames on a
+// given CUDA stream (encode.cu)
+size_t encode_partials(const xpcs_basis* B, int64_t T, int num_sms);
+xpcs_status encode_on_stream(xpcs_ctx* ctx, const xpcs_basis* B, const void* X, xpcs_dtype dtype, int64_t T,
+                             float* A_out, float* partials, uint32_t* status, cudaStream_t st);
+
 // Scratch: one growing device buffer per context, carved per call.
 struct Carve {
   size_t off = 0;

@@ -253,6 +253,7 @@ struct StreamStep {
   const CUtensorMap* tmWg;  // boxes of 128 w rows (one ring)
   const CUtensorMap* tmWg2; // boxes of 256 w rows (two rings)
   const CUtensorMap* tmW48; // W2 in boxes of 48 rows (single-frame steps)
+  int pre_encoded;         // 1: a already holds the step's coefficients (tensor-core encode)
 };
 // Smallest step (frames) that runs on the two-time kernel; smaller steps take the row
 // update kernel.  Steps never cross a 128-frame block when they may take the former.

@@ -339,9 +339,11 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   cudaError_t e = s.Sx ? cudaMemsetAsync(s.Sx, 0, (size_t)s.b * s.n_q * sizeof(long long), st) : cudaSuccess;
   if (e != cudaSuccess) return e;
   // dependent launches: each kernel may start while the one ahead of it finishes
-  if ((e = launch_pdl(sparse_encode_kernel, dim3(s.nblk, s.b), dim3(256), 0, st, s)) != cudaSuccess) return e;
-  if ((e = launch_pdl(stream_reduce_kernel, dim3((s.b * s.k + 31) / 32), dim3(256), 0, st, s)) != cudaSuccess)
-    return e;
+  if (!s.pre_encoded) {
+    if ((e = launch_pdl(sparse_encode_kernel, dim3(s.nblk, s.b), dim3(256), 0, st, s)) != cudaSuccess) return e;
+    if ((e = launch_pdl(stream_reduce_kernel, dim3((s.b * s.k + 31) / 32), dim3(256), 0, st, s)) != cudaSuccess)
+      return e;
+  }
   if ((e = launch_pdl(frame_factors_kernel, dim3(s.b, s.n_q), dim3(128), 0, st, s)) != cudaSuccess) return e;
   if (s.b >= STREAM_GRAM_MIN) {
     // the two-time kernel on (history block J - delta, the step's block J) tiles of every

@@ -60,7 +60,9 @@ Sizes stream_sizes(int64_t M, int n_q, int k, int64_t W, int max_batch, int eb) 
   z.vbits = (size_t)n_q * stream_vwords(cap) * 8;
   z.g2sum = (size_t)n_q * wpitch(W) * 8;
   z.cnt = (size_t)n_q * wpitch(W) * 8;
-  z.part = (size_t)max_batch * nblk_of(M) * k * 4;
+  // the sparse encode's slice partials, or the tensor-core encode's split-K partials of
+  // one 128-frame step (at most 256 pixel splits)
+  z.part = std::max((size_t)max_batch * nblk_of(M) * k * 4, (size_t)256 * 128 * k * 4);
   z.a = (size_t)max_batch * k * 4;
   z.W2 = (size_t)w2_rows(max_batch, n_q) * 2 * kpad_of(k) * 2;
   z.g2 = (size_t)n_q * W * 8;
@@ -366,6 +368,8 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.tmW48 = &S->tmW48;
   // steps of at most STEP_MAX_GRAM frames; the batch completes with its last step
   const size_t fb = (size_t)B->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
+  const size_t part_bytes =
+      stream_sizes(S->M, S->n_q, S->k, S->W, S->max_batch, S->dtype == XPCS_U8 ? 1 : 2).part;
   cudaError_t e = cudaSuccess;
   for (int64_t f0 = 0; f0 < n && e == cudaSuccess; f0 += s.b) {
     s.X = static_cast<const char*>(X) + f0 * fb;
@@ -377,6 +381,20 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
     s.b = (int)std::min<int64_t>(STEP_MAX_GRAM, n - f0);
     if (s.b >= STREAM_GRAM_MIN) s.b = std::min(s.b, room);
     if (s.b < STREAM_GRAM_MIN) s.b = std::min(s.b, STEP_MAX);
+    // steps on the two-time kernel take the tensor-core encode (frames once, the basis
+    // pieces once per step) instead of gathering the nonzero pixels' f32 basis rows, unless
+    // the exact ring sums of the frames are wanted (the sparse encode forms them)
+    s.pre_encoded = 0;
+    if (s.b >= STREAM_GRAM_MIN && !S->d_Sx && s.vec16 &&
+        encode_partials(B, s.b, ctx->num_sms) * 4 <= part_bytes) {
+      const xpcs_status es =
+          encode_on_stream(ctx, B, s.X, (xpcs_dtype)S->dtype, s.b, s.a, s.part, S->d_status, S->stream);
+      if (es != XPCS_OK) {
+        delete stamp;
+        return es;
+      }
+      s.pre_encoded = 1;
+    }
     e = launch_stream_step(s, S->stream);
     if (e == cudaSuccess) ctx->launches += s.b >= STREAM_GRAM_MIN ? 5 : 4;
   }
