@@ -934,63 +934,72 @@ def run_stream_leg(X, ctx, dev, args, sw=STREAM):
     del gen
     nnz_per_frame = float((pool[:64].view(torch.int16) != 0).sum().item()) / 64
     torch.cuda.synchronize()
-    st = X.Stream(ctx, basis, Wl, sw["max_batch"], dtype=sw["dtype"])
-    pushed = 0
+    def measure(prec, seconds):
+        """Fill, sustained, one-frame and paced phases of one stream of precision `prec`."""
+        st = X.Stream(ctx, basis, Wl, sw["max_batch"], dtype=sw["dtype"], prec=prec)
+        pushed = 0
 
-    def push(n, batch):
-        nonlocal pushed
-        t = 0
-        while n > 0:
+        def push(n, batch):
+            nonlocal pushed
+            t = 0
+            while n > 0:
+                i = pushed % P
+                m = min(n, P - i, batch)
+                t = st.push(pool[i:i + m])
+                pushed += m
+                n -= m
+            return t
+
+        def run_unpaced(n, batch):
+            t0 = time.perf_counter()
+            ticket = push(n, batch)
+            assert st.poll(ticket, 600000)
+            return n / (time.perf_counter() - t0)
+
+        run_unpaced(Wl, sw["max_batch"])  # fill the history
+        fps_sustained = run_unpaced(20000, sw["max_batch"])
+        fps_b1 = run_unpaced(4000, 1)
+        st.latency(reset=True)
+
+        # paced: frame j arrives at t0 + j / rate.  Continuous batching: whenever fewer than
+        # two batches are in flight, every frame that has arrived (up to max_batch) goes out
+        # as one batch, so the batch grows with the load instead of a queue.
+        n_paced = int(sw["rate_hz"] * seconds)
+        period = 1e9 / sw["rate_hz"]
+        t0 = X.clock_ns() + 1_000_000
+        arrive = (t0 + np.arange(n_paced) * period).astype(np.int64)
+        j = 0
+        batches = 0
+        inflight = []
+        ticket = 0
+        while j < n_paced:
+            while inflight and st.poll(inflight[0], 0):
+                inflight.pop(0)
+            if len(inflight) >= 2:
+                continue
+            now = X.clock_ns()
+            due = min(n_paced, int((now - t0) // period) + 1) if now >= t0 else 0
+            if due <= j:
+                continue
+            n = min(due - j, sw["max_batch"])
             i = pushed % P
-            m = min(n, P - i, batch)
-            t = st.push(pool[i:i + m])
-            pushed += m
-            n -= m
-        return t
-
-    def run_unpaced(n, batch):
-        t0 = time.perf_counter()
-        ticket = push(n, batch)
+            n = min(n, P - i)
+            ticket = st.push_at(pool[i:i + n], arrive[j:j + n])
+            inflight.append(ticket)
+            pushed += n
+            j += n
+            batches += 1
         assert st.poll(ticket, 600000)
-        return n / (time.perf_counter() - t0)
+        t_end = X.clock_ns()
+        lat = st.latency(reset=True)
+        st.close()
+        return {"sustained": fps_sustained, "b1": fps_b1, "lat": lat, "n_paced": n_paced, "batches": batches,
+                "paced_fps": n_paced / ((t_end - t0) * 1e-9)}
 
-    run_unpaced(Wl, sw["max_batch"])  # fill the history
-    fps_sustained = run_unpaced(20000, sw["max_batch"])
-    fps_b1 = run_unpaced(4000, 1)
-    st.latency(reset=True)
-
-    # paced: frame j arrives at t0 + j / rate.  Continuous batching: whenever fewer than
-    # two batches are in flight, every frame that has arrived (up to max_batch) goes out
-    # as one batch, so the batch grows with the load instead of a queue.
-    n_paced = int(sw["rate_hz"] * args.stream_seconds)
-    period = 1e9 / sw["rate_hz"]
-    t0 = X.clock_ns() + 1_000_000
-    arrive = (t0 + np.arange(n_paced) * period).astype(np.int64)
-    j = 0
-    batches = 0
-    inflight = []
-    ticket = 0
-    while j < n_paced:
-        while inflight and st.poll(inflight[0], 0):
-            inflight.pop(0)
-        if len(inflight) >= 2:
-            continue
-        now = X.clock_ns()
-        due = min(n_paced, int((now - t0) // period) + 1) if now >= t0 else 0
-        if due <= j:
-            continue
-        n = min(due - j, sw["max_batch"])
-        i = pushed % P
-        n = min(n, P - i)
-        ticket = st.push_at(pool[i:i + n], arrive[j:j + n])
-        inflight.append(ticket)
-        pushed += n
-        j += n
-        batches += 1
-    assert st.poll(ticket, 600000)
-    t_end = X.clock_ns()
-    lat = st.latency(reset=True)
-    nb = st.W  # history length
+    m3 = measure("bf16x3", args.stream_seconds)
+    m16 = measure("fp16", min(args.stream_seconds, 3.0))
+    fps_sustained, fps_b1, lat, n_paced, batches = m3["sustained"], m3["b1"], m3["lat"], m3["n_paced"], m3["batches"]
+    nb = Wl  # history length
     ka = (k + 31) // 32 * 32
     bytes_batch_fixed = nb * ka * 4 + nb * n_q * 4 + 2 * n_q * nb * 16
     bytes_frame = M * 2 + nnz_per_frame * k * 4
@@ -1000,7 +1009,7 @@ def run_stream_leg(X, ctx, dev, args, sw=STREAM):
         "workload": STREAM_NAME, "frames_paced": n_paced, "rate_hz": sw["rate_hz"],
         "p50_us": lat["p50_us"], "p99_us": lat["p99_us"], "max_us": lat["max_us"],
         "frames_measured": lat["batches"], "batches_paced": batches, "mean_batch": n_paced / max(1, batches),
-        "paced_frames_per_s": n_paced / ((t_end - t0) * 1e-9),
+        "paced_frames_per_s": m3["paced_fps"],
         "sustained_frames_per_s": fps_sustained, "sustained_batch": sw["max_batch"],
         "batch1_frames_per_s": fps_b1,
         "bytes_model": {"per_batch_fixed": bytes_batch_fixed, "per_frame": bytes_frame,
@@ -1011,8 +1020,12 @@ def run_stream_leg(X, ctx, dev, args, sw=STREAM):
         "raw_equivalent_note": "cross-check only: a raw row update that reads the uint16 history (history x M) "
                                "once per frame at the measured HBM bandwidth",
         "pool_frames": P, "nnz_per_frame": nnz_per_frame,
+        "precision": "bf16x3",
+        "fp16": {"note": "the same stream in f16 (one product, half the history bytes; 1e-3 of max|g2|)",
+                 "sustained_frames_per_s": m16["sustained"], "batch1_frames_per_s": m16["b1"],
+                 "p50_us": m16["lat"]["p50_us"], "p99_us": m16["lat"]["p99_us"],
+                 "frames_paced": m16["n_paced"], "mean_batch": m16["n_paced"] / max(1, m16["batches"])},
     }
-    st.close()
     out["raw_equivalent"] = run_raw_stream_equivalent(X, ctx, basis, rings, pool, sw)
     basis.close()
     rings.close()
@@ -1066,14 +1079,15 @@ def run_raw_stream_equivalent(X, ctx, basis, rings, pool, sw, histories=(10000, 
     return out
 
 
-def stream_capture(mode, path):
+def stream_capture(mode, path, prec="bf16x3"):
     """A short stream run for profiling one single-frame step at the full history.
 
     make: fit the basis of the online-stream workload, fill a stream with history + 64
     frames, and save the basis and a checkpoint under `path`.  run: import that basis,
     restore the checkpoint into a fresh stream and push three single frames, each waited
     for, then a 64-frame and a 128-frame step, so a profiler sees about twenty launches
-    before them.
+    before them.  prec: the stream's precision (the checkpoint records it, so make and run
+    take the same).
     Prints no bench line."""
     import torch
     from paper_2407_20356_gb300 import xpcs as X
@@ -1085,13 +1099,13 @@ def stream_capture(mode, path):
     H, W, n_q, k, Wl = sw["H"], sw["W"], sw["n_q"], sw["k"], sw["history"]
     ctx = X.Context(0)
     rings = X.Rings(ctx, torch.from_numpy(ring_qmap(H, W, n_q)).to(dev), H * W, n_q)
-    f_basis, f_ckpt = os.path.join(path, "stream_basis.npy"), os.path.join(path, "stream_ckpt.bin")
+    f_basis, f_ckpt = os.path.join(path, "stream_basis.npy"), os.path.join(path, f"stream_ckpt_{prec}.bin")
     if mode == "make":
         gen = TorchSpeckle(H, W, sw["mean"], sw["D"], sw["seed"] + 100, dtype=sw["dtype"], device=str(dev))
         np.save(f_basis, X.xpcs_fit_basis(ctx, rings, gen.next(sw["n_fit"]), sw["n_fit"], k).export()[0])
     basis = X.xpcs_basis_import(ctx, rings, np.load(f_basis))
     pool = TorchSpeckle(H, W, sw["mean"], sw["D"], sw["seed"], dtype=sw["dtype"], device=str(dev)).next(64)
-    st = X.Stream(ctx, basis, Wl, 64, dtype=sw["dtype"])
+    st = X.Stream(ctx, basis, Wl, 64, dtype=sw["dtype"], prec=prec)
     if mode == "make":
         t = 0
         for _ in range(0, Wl + 64, 64):
@@ -1247,6 +1261,8 @@ def main():
                     help="profiling aid, no bench line: make = fill the online stream and checkpoint it; "
                          "run = restore it and push three single frames, a 64-frame and a 128-frame step")
     ap.add_argument("--capture-dir", default="/tmp", help="where --stream-capture keeps its basis and checkpoint")
+    ap.add_argument("--stream-prec", default="bf16x3", choices=["fp16", "bf16x3"],
+                    help="precision of the --stream-capture stream")
     ap.add_argument("--sweep", action="store_true",
                     help="with --leg: also time the two-time kernel in every configuration")
     ap.add_argument("--leg", choices=["raw", "compressed", "grouped"],
@@ -1255,7 +1271,7 @@ def main():
                          "its event-timed call time")
     args = ap.parse_args()
     if args.stream_capture:
-        stream_capture(args.stream_capture, args.capture_dir)
+        stream_capture(args.stream_capture, args.capture_dir, args.stream_prec)
         return
     if args.leg:
         profile_leg(args)

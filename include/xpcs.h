@@ -367,10 +367,15 @@ xpcs_status xpcs_graph_destroy(xpcs_graph* graph);
  * stay alive while frames are pushed; closing the stream does not read it. */
 xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t history, int max_batch,
                              xpcs_dtype dtype, xpcs_stream** out);
-/* xpcs_stream_open with options: of opt (host, NULL = defaults) only qmean is used (a
- * stream always computes Eq. 1 in bf16x3).  With XPCS_QMEAN_EXACT_RAW every pushed frame's
- * exact ring sums, added up from its nonzero pixels during the sparse encode, replace
- * a_t s_q in the denominators. */
+/* xpcs_stream_open with options: of opt (host, NULL = xpcs_stream_open's defaults) qmean
+ * and precision are used.  precision XPCS_PREC_BF16X3 (xpcs_stream_open's) keeps the
+ * coefficient history and the w_q(t) rows of Eq. 1 as bf16 hi | lo pieces (three
+ * products, about 2^-16 relative); XPCS_PREC_FP16 (a zero-initialised opt) keeps them as
+ * one f16 piece (one product, half the history bytes, about 2^-11 relative: the same
+ * error as the offline f16 path), each history row scaled by a power of two that its
+ * ring factors take out again; XPCS_PREC_BF16 is refused (XPCS_EINVAL).  With
+ * XPCS_QMEAN_EXACT_RAW every pushed frame's exact ring sums, added up from its nonzero
+ * pixels during the sparse encode, replace a_t s_q in the denominators. */
 xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* basis, int64_t history, int max_batch,
                                   xpcs_dtype dtype, const xpcs_options* opt, xpcs_stream** out);
 /* The row-update configuration a stream step of b frames takes for n_q rings and a k-term

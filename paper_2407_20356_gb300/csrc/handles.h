@@ -116,10 +116,14 @@ struct xpcs_stream {
   int n_q = 0, k = 0;                // stream never reads the basis (which may be gone)
   int64_t frames = 0;                // frames enqueued so far
   int nblk = 0;                      // pixel slices of the sparse encode
+  int sp = 0;                        // 1: f16 coefficient rows, one product (XPCS_PREC_FP16);
+                                     // 0: bf16 hi | lo rows, three products (XPCS_PREC_BF16X3)
   // device
   void* d_frames = nullptr;          // max_batch x M counts (u16 or u8)
   __nv_bfloat16* d_A2 = nullptr;     // (cap + 128) x 2 kpad coefficient history, bf16 hi | lo
+                                     // (f16 streams: 2^e_s a_s in the first kpad, as f16)
   float* d_Rh = nullptr;             // (cap + 128) x npad  r_q(s) = sqrt(M_q)/S~_q(s), 0 if undefined
+                                     // (f16 streams: 2^-e_s r_q(s))
   unsigned long long* d_vbits = nullptr;  // n_q x vwords  validity bits r_q(s) > 0 per slot
   float2* d_g2sum = nullptr;         // n_q x Wp (W rounded up to 64): sums as f32 pairs (hi, lo)
   long long* d_cnt = nullptr;        // n_q x Wp

@@ -254,6 +254,8 @@ struct StreamStep {
   const CUtensorMap* tmWg2; // boxes of 256 w rows (two rings)
   const CUtensorMap* tmW48; // W2 in boxes of 48 rows (single-frame steps)
   int pre_encoded;         // 1: a already holds the step's coefficients (tensor-core encode)
+  int sp;                  // 1: coefficient rows in f16, one product (the hi halves of the rows
+                           //    only); 0: bf16 hi | lo pieces, three products
 };
 // Smallest step (frames) that runs on the two-time kernel; smaller steps take the row
 // update kernel.  Steps never cross a 128-frame block when they may take the former.
@@ -285,6 +287,7 @@ struct RowTcParams {
   long long vwords;
   long long Wp;  // row pitch (elements) of g2sum and cnt: W rounded up to 64
   int qg2;       // ring rows per g2sum / cnt box: min(36, n_q)
+  int sp;        // 1: f16 rows, one product (hi halves only)
   uint32_t* status;
 };
 int row_update_tc_smem(int n_kc, int lt, int qb, int wst, int qg2, int epi);
@@ -293,12 +296,13 @@ struct Row1Params {
   long long t, W, cap;
   int n_q, kpad, n_kc, npad, qb, n_tiles;  // qb = npad (r values per history row)
   long long Wp;            // row pitch of g2sum / cnt
+  int sp;                  // 1: f16 rows, one product (hi halves only)
   const float* Rh;         // (cap + 128) x npad
   float2* g2sum;           // n_q x Wp
   long long* cnt;          // n_q x Wp
   uint32_t* status;
 };
-int row1_tc_smem(int n_kc, int qb);
+int row1_tc_smem(int n_kc, int qb, int sp);
 // tensor maps: A2 history (64 x 128 boxes), W2 (64 x 48 boxes), Rh (qb x 128 boxes)
 cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR, const Row1Params& p,
                            int grid, cudaStream_t st);

@@ -179,7 +179,11 @@ __global__ void __launch_bounds__(256) stream_reduce_kernel(const StreamStep s) 
 // Block (frame i, ring q), 128 threads: S~_q(t) = a_t . s_q (FP64), r_q(t) = sqrt(M_q)/S~
 // (0 if undefined) into Rh (and its mirror row), w_q(t) = r_q(t) a_t G_q as a bf16 hi | lo
 // row of W2 in pair order; the q = 0 block also writes a_t as a bf16 hi | lo history row
-// of A2 (and its mirror row).
+// of A2 (and its mirror row).  A stream in f16 writes the rows as one f16 piece (the first
+// kpad elements): w_q(t) as it is (its elements are r_q(t)-normalised, like the operand
+// rows of the offline f16 path), the history row as 2^e a_t with e chosen so that the
+// largest |a_t| lies in [2^13, 2^14) (no overflow, small elements stay normal), and
+// 2^-e r_q(t) in Rh, so that the products r_q(s) (w_q(t) . a_s) are unchanged.
 XPCS_DEV void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(x);
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
@@ -188,6 +192,7 @@ XPCS_DEV void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
 __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) {
   __shared__ float as[256];
   __shared__ double dred[4];
+  __shared__ unsigned mred[4];
   pdl_trigger();
   pdl_wait();  // the coefficients
   const int fi = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
@@ -196,19 +201,38 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
   const long long slot = t % s.cap;
   for (int c = tid; c < k; c += blockDim.x) as[c] = s.a[(size_t)fi * k + c];
   __syncthreads();
-  // S~_q(t) in FP64 (k terms)
+  // S~_q(t) in FP64 (k terms), and max |a_t| (the bits of non-negative floats order as
+  // the values)
   double d = 0.0;
-  for (int c = tid; c < k; c += blockDim.x) d = fma((double)as[c], s.s64[(size_t)q * k + c], d);
+  unsigned amax = 0u;
+  for (int c = tid; c < k; c += blockDim.x) {
+    d = fma((double)as[c], s.s64[(size_t)q * k + c], d);
+    amax = max(amax, __float_as_uint(fabsf(as[c])));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-  if ((tid & 31) == 0) dred[tid >> 5] = d;
+  amax = __reduce_max_sync(0xffffffffu, amax);
+  if ((tid & 31) == 0) {
+    dred[tid >> 5] = d;
+    mred[tid >> 5] = amax;
+  }
   __syncthreads();
+  int e2 = 0;  // f16 history rows: 2^e2 a_t
+  if (s.sp) {
+    const float am = __uint_as_float(max(max(mred[0], mred[1]), max(mred[2], mred[3])));
+    if (am > 0.f && isfinite(am)) {
+      int ex;
+      frexpf(am, &ex);  // am in [2^(ex-1), 2^ex)
+      e2 = min(64, max(-64, 14 - ex));
+    }
+  }
   const double S = s.Sx ? (double)s.Sx[(size_t)fi * s.n_q + q] : dred[0] + dred[1] + dred[2] + dred[3];
   const float r = S > 0.0 ? (float)(sqrt((double)s.Mq[q]) / S) : 0.f;
   const int npad = stream_npad(s.n_q);
   if (tid == 0) {
-    s.Rh[slot * npad + q] = r;
-    if (slot < 128) s.Rh[(s.cap + slot) * npad + q] = r;
+    const float rs = s.sp ? ldexpf(r, -e2) : r;
+    s.Rh[slot * npad + q] = rs;
+    if (slot < 128) s.Rh[(s.cap + slot) * npad + q] = rs;
     // validity bit of (q, slot), and of its mirror slot; other frames of the step may
     // touch the same words
     unsigned long long* vb = s.vbits + (size_t)q * s.vwords;
@@ -247,12 +271,24 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
       for (; c < k; ++c) v4[0] = fmaf(as[c], Gq[(size_t)c * k + j], v4[0]);
       v = ((v4[0] + v4[1]) + (v4[2] + v4[3])) * r;
     }
-    __nv_bfloat16 hi, lo;
-    split_bf16(v, hi, lo);
-    wrow[j] = hi;
-    wrow[kp + j] = lo;
+    if (s.sp) {
+      reinterpret_cast<__half*>(wrow)[j] = __float2half_rn(v);
+    } else {
+      __nv_bfloat16 hi, lo;
+      split_bf16(v, hi, lo);
+      wrow[j] = hi;
+      wrow[kp + j] = lo;
+    }
   }
-  if (q == 0) {
+  if (q == 0 && s.sp) {
+    __half* arow = reinterpret_cast<__half*>(s.A2 + (size_t)slot * 2 * kp);
+    __half* mrow = slot < 128 ? reinterpret_cast<__half*>(s.A2 + (size_t)(s.cap + slot) * 2 * kp) : nullptr;
+    for (int c = tid; c < kp; c += blockDim.x) {
+      const __half x = __float2half_rn(c < k ? ldexpf(as[c], e2) : 0.f);
+      arow[c] = x;
+      if (mrow) mrow[c] = x;
+    }
+  } else if (q == 0) {
     __nv_bfloat16* arow = s.A2 + (size_t)slot * 2 * kp;
     __nv_bfloat16* mrow = slot < 128 ? s.A2 + (size_t)(s.cap + slot) * 2 * kp : nullptr;
     for (int c = tid; c < kp; c += blockDim.x) {
@@ -375,8 +411,8 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     gp.sm_c0 = (int)(s.t0 & 127);
     gp.sm_c1 = gp.sm_c0 + s.b;
     gp.r_ld = stream_npad(s.n_q);
-    gp.fmt = 1;
-    gp.split = 1;
+    gp.fmt = s.sp ? 0 : 1;  // f16 rows (one product) or bf16 hi | lo pieces (three)
+    gp.split = s.sp ? 0 : 1;
     gp.raw = 1;  // epilogue scales: r_q(s) for the history rows, the mask for the columns
     gp.r = s.Rh;
     gp.partials = s.gpart;
@@ -400,11 +436,12 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     p1.qb = p1.npad;
     p1.n_tiles = (int)((std::min<long long>(s.W, s.t0 + 1) + 127) / 128);
     p1.Wp = s.Wp;
+    p1.sp = s.sp;
     p1.Rh = s.Rh;
     p1.g2sum = s.g2sum;
     p1.cnt = s.cnt;
     p1.status = s.status;
-    if (p1.n_kc <= 2 && row1_tc_smem(p1.n_kc, p1.qb) <= 227 * 1024)
+    if (p1.n_kc <= (s.sp ? 4 : 2) && row1_tc_smem(p1.n_kc, p1.qb, s.sp) <= 227 * 1024)
       return launch_row1_tc(*s.tmA, *s.tmW48, *s.tmR, p1, std::min(p1.n_tiles, s.num_sms), st);
   }
   // row update of the step (at most 64 frames: every pair of a lag tile then lies in
@@ -432,6 +469,7 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   p.vwords = s.vwords;
   p.Wp = s.Wp;
   p.qg2 = std::min(36, s.n_q);
+  p.sp = s.sp;
   p.status = s.status;
   const int grid = std::min(p.n_tiles * p.n_rg, s.num_sms);
   return launch_row_update_tc(*s.tmA, *s.tmW, *s.tmR, s.tmG[li], s.tmC[li], p, grid, st);

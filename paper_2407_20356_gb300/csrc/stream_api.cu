@@ -143,9 +143,11 @@ extern "C" xpcs_status xpcs_stream_open(xpcs_ctx* ctx, const xpcs_basis* B, int6
 extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B, int64_t history, int max_batch,
                                              xpcs_dtype dtype, const xpcs_options* opt, xpcs_stream** out) {
   if (!ctx || !B || !out || B->ctx != ctx || history < 1 || max_batch < 1 || max_batch > 1024 || B->k > 256 ||
-      (dtype != XPCS_U8 && dtype != XPCS_U16) || (opt && (opt->qmean < 0 || opt->qmean > 1)))
+      (dtype != XPCS_U8 && dtype != XPCS_U16) || (opt && (opt->qmean < 0 || opt->qmean > 1)) ||
+      (opt && opt->precision != XPCS_PREC_FP16 && opt->precision != XPCS_PREC_BF16X3))
     return fail(ctx, XPCS_EINVAL, "bad stream_open args");
   const bool exact = opt && opt->qmean == XPCS_QMEAN_EXACT_RAW;
+  const int sp = (opt && opt->precision == XPCS_PREC_FP16) ? 1 : 0;
   *out = nullptr;
   int lt = 0, wst = 0, epi = 0;  // the largest step the row update kernel takes
   if (!row_update_config(B->rings->n_q, kpad_of(B->k), STREAM_GRAM_MIN - 1, &lt, &wst, &epi))
@@ -178,6 +180,7 @@ extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B,
   S->n_q = B->n_q;
   S->k = B->k;
   S->nblk = nblk_of(B->M);
+  S->sp = sp;
   const Sizes z = stream_sizes(S->M, S->n_q, S->k, history, max_batch, eb);
   xpcs_status st = XPCS_OK;
   void* p = nullptr;
@@ -366,6 +369,7 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.tmWg = &S->tmWg;
   s.tmWg2 = &S->tmWg2;
   s.tmW48 = &S->tmW48;
+  s.sp = S->sp;
   // steps of at most STEP_MAX_GRAM frames; the batch completes with its last step
   const size_t fb = (size_t)B->rings->M * (S->dtype == XPCS_U8 ? 1 : 2);
   const size_t part_bytes =
@@ -593,14 +597,14 @@ namespace {
 struct CkptHeader {
   char magic[8];
   uint32_t version;
-  int32_t k, n_q, dtype;
+  int32_t k, n_q, dtype, precision;  // precision: 1 f16 rows, 0 bf16 hi | lo
   int64_t M, W, cap, frames;
   uint64_t basis_hash;
   uint64_t bytes[5];  // A2, Rh, vbits, g2sum, cnt
 };
 
 constexpr char CKPT_MAGIC[8] = {'X', 'P', 'C', 'S', 'C', 'K', 'P', 'T'};
-constexpr uint32_t CKPT_VERSION = 2;  // 2: g2 sums stored as f32 pairs (1: FP64)
+constexpr uint32_t CKPT_VERSION = 3;  // 3: the row precision recorded; 2: g2 sums as f32 pairs (1: FP64)
 
 xpcs_status basis_hash(xpcs_stream* S, uint64_t* h) {
   const xpcs_basis* B = S->basis;
@@ -655,6 +659,7 @@ extern "C" xpcs_status xpcs_stream_checkpoint(xpcs_stream* S, void* host_buf, si
   h.k = S->basis->k;
   h.n_q = S->basis->rings->n_q;
   h.dtype = S->dtype;
+  h.precision = S->sp;
   h.M = S->basis->rings->M;
   h.W = S->W;
   h.cap = S->cap;
@@ -680,8 +685,9 @@ extern "C" xpcs_status xpcs_stream_restore(xpcs_stream* S, const void* host_buf,
   if (memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != CKPT_VERSION) return fail(ctx, XPCS_EINVAL, "not a stream checkpoint");
   if (S->frames != 0) return fail(ctx, XPCS_EINVAL, "restore needs a freshly opened stream");
   if (h.k != S->basis->k || h.n_q != S->basis->rings->n_q || h.dtype != S->dtype || h.M != S->basis->rings->M ||
-      h.W != S->W || h.cap != S->cap)
-    return fail(ctx, XPCS_EINVAL, "checkpoint of a stream with another shape (k, rings, pixels, history, batch)");
+      h.W != S->W || h.cap != S->cap || h.precision != S->sp)
+    return fail(ctx, XPCS_EINVAL,
+                "checkpoint of a stream with another shape (k, rings, pixels, history, batch, precision)");
   void* ptr[5];
   uint64_t b[5];
   ckpt_parts(S, ptr, b);

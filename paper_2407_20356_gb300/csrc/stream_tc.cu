@@ -158,10 +158,11 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         // coordinates); afterwards the window is contiguous thanks to the mirrored rows
         const int y = (s_start < 0 && p.t0 + p.b <= p.cap) ? (int)s_start
                                                             : (int)(((s_start % p.cap) + p.cap) % p.cap);
-        mbar_arrive_expect_tx(h_full, (uint32_t)(L.hist_bytes() + L.rs_bytes()));
+        // single-product rows: the hi pieces only
+        mbar_arrive_expect_tx(h_full, (uint32_t)((p.sp ? p.n_kc * RT_CHUNK : L.hist_bytes()) + L.rs_bytes()));
         for (int kc = 0; kc < p.n_kc; ++kc) {
           tma_load_2d(hist + kc * RT_CHUNK, &tmA, h_full, kc * RT_CH, y);
-          tma_load_2d(hist + (p.n_kc + kc) * RT_CHUNK, &tmA, h_full, p.kpad + kc * RT_CH, y);
+          if (!p.sp) tma_load_2d(hist + (p.n_kc + kc) * RT_CHUNK, &tmA, h_full, p.kpad + kc * RT_CH, y);
         }
         tma_load_2d(rs, &tmR, h_full, rg * RT_QG, y);
         for (int mt = 0; mt < p.n_mt && ok; ++mt) {
@@ -174,9 +175,9 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             }
             uint8_t* dst = w_st + s * 2 * RT_CHUNK;
             const int wy = (rg * p.n_mt + mt) * RT_ROWS;
-            mbar_arrive_expect_tx(&w_full[s], 2 * RT_CHUNK);
+            mbar_arrive_expect_tx(&w_full[s], (p.sp ? 1 : 2) * RT_CHUNK);
             tma_load_2d(dst, &tmW, &w_full[s], kc * RT_CH, wy);
-            tma_load_2d(dst + RT_CHUNK, &tmW, &w_full[s], p.kpad + kc * RT_CH, wy);
+            if (!p.sp) tma_load_2d(dst + RT_CHUNK, &tmW, &w_full[s], p.kpad + kc * RT_CH, wy);
           }
         }
         // the item's g2 sums and counts, once the previous item's store has read them
@@ -203,8 +204,10 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     if (lane == 0) {
       // large steps: M = pairs, N = the lt + b - 1 history rows used (a multiple of 16);
       // small steps: M = the 128 history rows, N = the 36 ring pairs of a frame (48)
-      const uint32_t idesc = EPI == RT_SMALL ? idesc_f16(1, RT_ROWS, RT_SMALL_N)
-                                             : idesc_f16(1, RT_ROWS, min(RT_ROWS, (lt + p.b - 1 + 15) / 16 * 16));
+      // f16 operands (one product) or bf16 pieces (three)
+      const int fmt = p.sp ? 0 : 1;
+      const uint32_t idesc = EPI == RT_SMALL ? idesc_f16(fmt, RT_ROWS, RT_SMALL_N)
+                                             : idesc_f16(fmt, RT_ROWS, min(RT_ROWS, (lt + p.b - 1 + 15) / 16 * 16));
       uint32_t item_i = 0, it = 0, acc_i = 0;
       bool ok = true, issued = false;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++item_i) {
@@ -234,16 +237,26 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             const uint64_t wlo = smem_desc_sw128(w_st + s * 2 * RT_CHUNK + RT_CHUNK);
             const uint64_t hhi = smem_desc_sw128(hist + kc * RT_CHUNK);
             const uint64_t hlo = smem_desc_sw128(hist + (p.n_kc + kc) * RT_CHUNK);
+            if (p.sp) {
 #pragma unroll
-            for (int kk = 0; kk < RT_CH / 16; ++kk) {  // 16 elements = 32 B per MMA
-              if constexpr (EPI == RT_SMALL) {  // D[history row][pair]
-                tc_mma_f16(d, hhi + 2 * kk, whi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                tc_mma_f16(d, hhi + 2 * kk, wlo + 2 * kk, idesc, 1u);
-                tc_mma_f16(d, hlo + 2 * kk, whi + 2 * kk, idesc, 1u);
-              } else {  // D[pair][history row]
-                tc_mma_f16(d, whi + 2 * kk, hhi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                tc_mma_f16(d, wlo + 2 * kk, hhi + 2 * kk, idesc, 1u);
-                tc_mma_f16(d, whi + 2 * kk, hlo + 2 * kk, idesc, 1u);
+              for (int kk = 0; kk < RT_CH / 16; ++kk) {
+                if constexpr (EPI == RT_SMALL)
+                  tc_mma_f16(d, hhi + 2 * kk, whi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                else
+                  tc_mma_f16(d, whi + 2 * kk, hhi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+              }
+            } else {
+#pragma unroll
+              for (int kk = 0; kk < RT_CH / 16; ++kk) {  // 16 elements = 32 B per MMA
+                if constexpr (EPI == RT_SMALL) {  // D[history row][pair]
+                  tc_mma_f16(d, hhi + 2 * kk, whi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                  tc_mma_f16(d, hhi + 2 * kk, wlo + 2 * kk, idesc, 1u);
+                  tc_mma_f16(d, hlo + 2 * kk, whi + 2 * kk, idesc, 1u);
+                } else {  // D[pair][history row]
+                  tc_mma_f16(d, whi + 2 * kk, hhi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                  tc_mma_f16(d, wlo + 2 * kk, hhi + 2 * kk, idesc, 1u);
+                  tc_mma_f16(d, whi + 2 * kk, hlo + 2 * kk, idesc, 1u);
+                }
               }
             }
             tc_commit(&w_empty[s]);
@@ -574,7 +587,8 @@ cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW,
 // when r_q(t) > 0 and r_q(s) > 0 (both frames defined).  Work item = a tile of 128 lags
 // tau0 .. tau0 + 127, history rows s = t - tau0 - 127 + c (c = 0..127): D[c][q] = a_s . w_q
 // on the tensor cores (M = the 128 history rows, N = 48 >= 36 ring columns, bf16 hi | lo
-// pieces as in the row update kernel, the same products in the same order).  The CTA is
+// pieces as in the row update kernel, the same products in the same order; or one f16
+// product of the hi pieces when the stream computes in f16).  The CTA is
 // persistent over its tiles and double-buffers the history rows and their r values, so a
 // tile's loads overlap the previous tile's epilogue; the frame's w rows are loaded once.
 // Eight epilogue warps (TMEM lane quarter = warp mod 4, rings 18 h .. 18 h + 17 for
@@ -590,9 +604,9 @@ constexpr int R1_N = 48;                      // MMA N: the 36 ring columns, rou
 constexpr int R1_WCHUNK = R1_N * RT_CH * 2;   // 6 KB: 48 w rows x 128 B
 
 struct R1Layout {
-  int n_kc, qb;
-  __host__ __device__ int hist_bytes() const { return 2 * n_kc * RT_CHUNK; }
-  __host__ __device__ int w_bytes() const { return 2 * n_kc * R1_WCHUNK; }
+  int n_kc, qb, np;  // np: pieces per row (2: bf16 hi | lo, 1: f16)
+  __host__ __device__ int hist_bytes() const { return np * n_kc * RT_CHUNK; }
+  __host__ __device__ int w_bytes() const { return np * n_kc * R1_WCHUNK; }
   __host__ __device__ int rs_bytes() const { return (RT_ROWS * qb * 4 + 1023) / 1024 * 1024; }
   __host__ __device__ int smem() const { return 1024 + 2 * hist_bytes() + w_bytes() + 2 * rs_bytes() + 256; }
 };
@@ -602,7 +616,7 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
                    const __grid_constant__ CUtensorMap tmR, const Row1Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const R1Layout L{p.n_kc, p.qb};
+  const R1Layout L{p.n_kc, p.qb, p.sp ? 1 : 2};
   uint8_t* hist = smem;                                 // [2][hi kc..., lo kc...]
   uint8_t* wbuf = smem + 2 * L.hist_bytes();            // [hi kc..., lo kc...] 48-row chunks
   uint8_t* rsb = wbuf + L.w_bytes();                    // [2][128][qb] r of the rows
@@ -651,7 +665,7 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
       mbar_arrive_expect_tx(w_full, (uint32_t)L.w_bytes());
       for (int kc = 0; kc < p.n_kc; ++kc) {
         tma_load_2d(wbuf + kc * R1_WCHUNK, &tmW, w_full, kc * RT_CH, 0);
-        tma_load_2d(wbuf + (p.n_kc + kc) * R1_WCHUNK, &tmW, w_full, p.kpad + kc * RT_CH, 0);
+        if (!p.sp) tma_load_2d(wbuf + (p.n_kc + kc) * R1_WCHUNK, &tmW, w_full, p.kpad + kc * RT_CH, 0);
       }
       uint32_t i = 0;
       for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++i) {
@@ -668,7 +682,7 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
         mbar_arrive_expect_tx(&h_full[bi], (uint32_t)(L.hist_bytes() + RT_ROWS * p.qb * 4));
         for (int kc = 0; kc < p.n_kc; ++kc) {
           tma_load_2d(hb + kc * RT_CHUNK, &tmA, &h_full[bi], kc * RT_CH, y);
-          tma_load_2d(hb + (p.n_kc + kc) * RT_CHUNK, &tmA, &h_full[bi], p.kpad + kc * RT_CH, y);
+          if (!p.sp) tma_load_2d(hb + (p.n_kc + kc) * RT_CHUNK, &tmA, &h_full[bi], p.kpad + kc * RT_CH, y);
         }
         tma_load_2d(rsb + bi * L.rs_bytes(), &tmR, &h_full[bi], 0, y);
       }
@@ -680,7 +694,7 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_f16(1, RT_ROWS, R1_N);
+      const uint32_t idesc = idesc_f16(p.sp ? 0 : 1, RT_ROWS, R1_N);
       bool issued = false;
       if (!*abort_flag && mbar_wait(w_full, 0, p.status)) {
         uint32_t i = 0;
@@ -698,11 +712,17 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
             const uint64_t hlo = smem_desc_sw128(hb + (p.n_kc + kc) * RT_CHUNK);
             const uint64_t whi = smem_desc_sw128(wbuf + kc * R1_WCHUNK);
             const uint64_t wlo = smem_desc_sw128(wbuf + (p.n_kc + kc) * R1_WCHUNK);
+            if (p.sp) {
 #pragma unroll
-            for (int kk = 0; kk < RT_CH / 16; ++kk) {  // D[history row][ring]
-              tc_mma_f16(d, hhi + 2 * kk, whi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-              tc_mma_f16(d, hhi + 2 * kk, wlo + 2 * kk, idesc, 1u);
-              tc_mma_f16(d, hlo + 2 * kk, whi + 2 * kk, idesc, 1u);
+              for (int kk = 0; kk < RT_CH / 16; ++kk)
+                tc_mma_f16(d, hhi + 2 * kk, whi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+            } else {
+#pragma unroll
+              for (int kk = 0; kk < RT_CH / 16; ++kk) {  // D[history row][ring]
+                tc_mma_f16(d, hhi + 2 * kk, whi + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc_mma_f16(d, hhi + 2 * kk, wlo + 2 * kk, idesc, 1u);
+                tc_mma_f16(d, hlo + 2 * kk, whi + 2 * kk, idesc, 1u);
+              }
             }
           }
           tc_commit(&h_empty[bi]);  // the history rows are free once these MMAs complete
@@ -793,12 +813,14 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
 
 }  // namespace
 
-int row1_tc_smem(int n_kc, int qb) { return R1Layout{n_kc, qb}.smem(); }
+int row1_tc_smem(int n_kc, int qb, int sp) { return R1Layout{n_kc, qb, sp ? 1 : 2}.smem(); }
 
 cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR, const Row1Params& p,
                            int grid, cudaStream_t st) {
-  if (p.n_q < 1 || p.n_q > 36 || p.qb < p.n_q || p.n_kc < 1 || p.n_kc > 2) return cudaErrorInvalidValue;
-  const int smem = row1_tc_smem(p.n_kc, p.qb);
+  // at most 256 elements of the history rows' pieces (two 64-wide chunks of hi | lo, or four
+  // of f16)
+  if (p.n_q < 1 || p.n_q > 36 || p.qb < p.n_q || p.n_kc < 1 || p.n_kc > (p.sp ? 4 : 2)) return cudaErrorInvalidValue;
+  const int smem = row1_tc_smem(p.n_kc, p.qb, p.sp);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   static int attr_bytes = 0;  // the attribute only ever grows
   if (smem > attr_bytes) {

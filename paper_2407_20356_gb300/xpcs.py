@@ -526,11 +526,15 @@ class RawStream:
 
 
 class Stream:
-    """An xpcs_stream: online encode + two-time row update of every pushed frame."""
+    """An xpcs_stream: online encode + two-time row update of every pushed frame.
 
-    def __init__(self, ctx: Context, basis: Basis, history: int, max_batch: int, dtype="uint16", qmean="compressed"):
+    prec: "bf16x3" (coefficient rows as bf16 hi | lo pieces, three products) or "fp16"
+    (one f16 product, half the history bytes; about 2^-11 relative per row)."""
+
+    def __init__(self, ctx: Context, basis: Basis, history: int, max_batch: int, dtype="uint16", qmean="compressed",
+                 prec="bf16x3"):
         h = vp()
-        o = _options(qmean=qmean)
+        o = _options(prec=prec, qmean=qmean)
         st = _lib.xpcs_stream_open_opts(ctx.h, basis.h, history, max_batch, _dtype_code(dtype), C.byref(o),
                                         C.byref(h))
         if st != XPCS_OK:

@@ -299,3 +299,70 @@ def test_stream_large_steps_on_the_twotime_kernel(X, ctx, dtype, k, n_q, Wl, T, 
         rm, _ = rel_errors(g2[q], g_ref[q])
         assert rm < 1e-4, (q, rm)
     st.close()
+
+
+# f16 streams: the coefficient history and the w_q(t) rows as one f16 piece (one product,
+# unit roundoff 2^-11), so g2 agrees to 1e-3 of max|g2| (as the offline f16 path); pair
+# counts stay exact.  Single frames (the single-frame kernel, up to k = 256 in f16), small
+# steps (the row update kernel), large steps (the two-time kernel) and the ring buffer's
+# wrap are all covered.
+@pytest.mark.parametrize("dtype,k,n_q,Wl,T,sizes,mb,mean", [(np.uint16, 20, 4, 50, 200, (1, 3, 8, 13, 1, 5), 16, 0.3),
+                                                            (np.uint16, 200, 5, 130, 300, (1, 1, 7, 1, 64), 64, 0.3),
+                                                            (np.uint8, 64, 40, 60, 400, (64, 32, 7, 1), 64, 0.3),
+                                                            (np.uint16, 24, 6, 400, 1000, (128, 100, 130, 5), 128, 0.3),
+                                                            (np.uint16, 48, 3, 90, 300, (1, 9, 20, 3), 32, 5000.0)])
+def test_stream_fp16_matches_oracle(X, ctx, dtype, k, n_q, Wl, T, sizes, mb, mean):
+    # the last case has about 5000 photons per pixel (steps below 32 frames: the sparse
+    # encode takes counts of any size): leading coefficients near 1.5e5, above the f16
+    # range unless each history row carries its scale
+    H, W = 24, 40
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 250, dtype, 900 + k, mean=mean)
+    st = X.Stream(ctx, basis, Wl, mb, dtype=np.dtype(dtype).name, prec="fp16")
+    i, j = 0, 0
+    ticket = 0
+    while i < T:
+        n = min(sizes[j % len(sizes)], T - i)
+        ticket = st.push(np.ascontiguousarray(Xs[i:i + n]))
+        i += n
+        j += 1
+    assert st.poll(ticket, 10000)
+    g2, cnt = st.read_g2()
+    g_ref, c_ref = _oracle_window_g2(Xs, B, qmap, n_q, Wl)
+    np.testing.assert_array_equal(cnt, c_ref)
+    for q in range(n_q):
+        rm, _ = rel_errors(g2[q], g_ref[q])
+        assert rm < 1e-3, (q, rm)
+    st.close()
+
+
+def test_stream_precision_options_and_checkpoints(X, ctx):
+    # bf16 is not a stream precision; a checkpoint goes only into a stream of its own
+    # precision, and an f16 stream resumes from its checkpoint bit for bit
+    H, W, n_q, k, T, Wl = 16, 32, 3, 24, 160, 40
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 120, np.uint16, 91)
+    with pytest.raises(X.XpcsError) as e:
+        X.Stream(ctx, basis, Wl, 8, prec="bf16")
+    assert e.value.status == X.XPCS_EINVAL
+    full = X.Stream(ctx, basis, Wl, 8, prec="fp16")
+    first = X.Stream(ctx, basis, Wl, 8, prec="fp16")
+    for i in range(0, T, 8):
+        full.push(Xs[i:i + 8])
+        if i < 80:
+            first.push(Xs[i:i + 8])
+    ck = first.checkpoint()
+    first.close()
+    wrong = X.Stream(ctx, basis, Wl, 8)  # bf16x3
+    with pytest.raises(X.XpcsError) as e:
+        wrong.restore(ck)
+    assert e.value.status == X.XPCS_EINVAL
+    wrong.close()
+    resumed = X.Stream(ctx, basis, Wl, 8, prec="fp16")
+    resumed.restore(ck)
+    for i in range(80, T, 8):
+        resumed.push(Xs[i:i + 8])
+    gf, cf = full.read_g2()
+    gr, cr = resumed.read_g2()
+    np.testing.assert_array_equal(cr, cf)
+    assert np.array_equal(np.isnan(gr), np.isnan(gf)) and np.array_equal(gr[~np.isnan(gr)], gf[~np.isnan(gf)])
+    full.close()
+    resumed.close()
