@@ -298,4 +298,29 @@ XPCS_DEV float skew_row_sum(const float* Q, int row, int lo, int hi) {
   return (a.x + a.y) + (b.x + b.y);
 }
 
+// ------------------------------------------------------------------ stream pair counts
+// Bits [slot, slot + n) (n <= 64) of one ring's validity words (slots past the ring's end
+// are its mirror, so no wrap is needed for slot < cap).
+XPCS_DEV unsigned long long vbits_window(const unsigned long long* vb, long long slot, int n) {
+  const int sh = (int)(slot & 63);
+  const unsigned long long lo = vb[slot >> 6] >> sh;
+  const unsigned long long hi = sh ? vb[(slot >> 6) + 1] << (64 - sh) : 0ull;
+  const unsigned long long v = lo | hi;
+  return n >= 64 ? v : v & ((1ull << n) - 1ull);
+}
+
+// Defined pairs (t0 + f, t0 + f - tau) of one ring over the frames f of `mask` (bit f:
+// frame t0 + f, f < 64) whose partner exists (t0 + f - tau >= 0): both validity bits set.
+XPCS_DEV long long masked_pair_count(const unsigned long long* vb, long long cap, long long t0,
+                                     unsigned long long mask, long long tau) {
+  const long long f0 = tau > t0 ? tau - t0 : 0;  // first frame with a partner
+  if (f0 >= 64) return 0;
+  const unsigned long long m = mask >> f0;
+  if (!m) return 0;
+  const int n = 64 - (int)f0;
+  const unsigned long long a = vbits_window(vb, (t0 + f0) % cap, n) & m;
+  const unsigned long long h = vbits_window(vb, (t0 + f0 - tau) % cap, n);
+  return __popcll(a & h);
+}
+
 }  // namespace xpcs

@@ -118,6 +118,12 @@ struct xpcs_stream {
   int nblk = 0;                      // pixel slices of the sparse encode
   int sp = 0;                        // 1: f16 coefficient rows, one product (XPCS_PREC_FP16);
                                      // 0: bf16 hi | lo rows, three products (XPCS_PREC_BF16X3)
+  // pair counts deferred by single-frame steps (count blocks of 64 frames): cf_blk = the
+  // block of the latest step (-1: none), cf_cur / cf_prev = deferred frames (bit f: frame
+  // 64 block + f) of that block and of the one before, cf_done = the parts (of 64) of the
+  // lag range already added for cf_prev
+  int64_t cf_blk = -1;
+  uint64_t cf_cur = 0, cf_prev = 0, cf_done = 0;
   // device
   void* d_frames = nullptr;          // max_batch x M counts (u16 or u8)
   __nv_bfloat16* d_A2 = nullptr;     // (cap + 128) x 2 kpad coefficient history, bf16 hi | lo

@@ -256,7 +256,20 @@ struct StreamStep {
   int pre_encoded;         // 1: a already holds the step's coefficients (tensor-core encode)
   int sp;                  // 1: coefficient rows in f16, one product (the hi halves of the rows
                            //    only); 0: bf16 hi | lo pieces, three products
+  // single-frame steps: the deferred pair counts this step adds (frames cf_t0 + f of
+  // cf_mask, lags cf_tau0 .. cf_tau1 - 1; none when cf_mask is 0)
+  long long cf_t0;
+  unsigned long long cf_mask;
+  int cf_tau0, cf_tau1;
 };
+// Single-frame steps leave their pair counts to count blocks of 64 frames (block of frame
+// t: t / 64).  The deferred counts of a block are added in 64 parts of the lag range, part
+// j by the single-frame step at position j of the next block, or by launch_count_flush.
+__host__ __device__ inline long long cf_part_len(long long W) { return (W + 63) / 64; }
+bool stream_step_row1(const StreamStep& s);
+cudaError_t launch_count_flush(const unsigned long long* vbits, long long vwords, long long cap, int n_q,
+                               long long W, long long Wp, long long* cnt, long long t0, unsigned long long mask,
+                               unsigned long long done, cudaStream_t st);
 // Smallest step (frames) that runs on the two-time kernel; smaller steps take the row
 // update kernel.  Steps never cross a 128-frame block when they may take the former.
 constexpr int STREAM_GRAM_MIN = 32;
@@ -299,7 +312,12 @@ struct Row1Params {
   int sp;                  // 1: f16 rows, one product (hi halves only)
   const float* Rh;         // (cap + 128) x npad
   float2* g2sum;           // n_q x Wp
-  long long* cnt;          // n_q x Wp
+  long long* cnt;          // n_q x Wp (only the deferred counts below)
+  const unsigned long long* vbits;
+  long long vwords;
+  long long cf_t0;         // deferred counts to add: frames cf_t0 + f of cf_mask, lags
+  unsigned long long cf_mask;  // cf_tau0 .. cf_tau1 - 1
+  int cf_tau0, cf_tau1;
   uint32_t* status;
 };
 int row1_tc_smem(int n_kc, int qb, int sp);

@@ -304,16 +304,6 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
   }
 }
 
-// Bits [slot, slot + n) (n <= 64) of one ring's validity words (slots past the ring's end
-// are its mirror, so no wrap is needed for slot < cap).
-XPCS_DEV unsigned long long vbits_window(const unsigned long long* vb, long long slot, int n) {
-  const int sh = (int)(slot & 63);
-  const unsigned long long lo = vb[slot >> 6] >> sh;
-  const unsigned long long hi = sh ? vb[(slot >> 6) + 1] << (64 - sh) : 0ull;
-  const unsigned long long v = lo | hi;
-  return n >= 64 ? v : v & ((1ull << n) - 1ull);
-}
-
 // After a step on the two-time kernel: lag tau = 128 d + e gets slot 128 + e of tile
 // diagonal d and slot e of tile diagonal d + 1 (TwoSum into the f32-pair sums), its pair
 // count from the validity bits of the step's frames and of the frames tau earlier, and the
@@ -349,6 +339,21 @@ __global__ void stream_fold_kernel(const StreamStep s, int nd_step) {
   }
 }
 
+// Deferred pair counts of count block [t0, t0 + 64) (the frames of `mask`) for the lags of
+// the parts not in `done` (part j: lags j L .. j L + L - 1, L = ceil(W / 64)): thread =
+// (ring, lag).
+__global__ void count_flush_kernel(const unsigned long long* vbits, long long vwords, long long cap, int n_q,
+                                   long long W, long long Wp, long long* cnt, long long t0, unsigned long long mask,
+                                   unsigned long long done) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)n_q * W) return;
+  const int q = (int)(i / W);
+  const long long tau = i - (long long)q * W;
+  if ((done >> (tau / cf_part_len(W))) & 1ull) return;
+  const long long n = masked_pair_count(vbits + (size_t)q * vwords, cap, t0, mask, tau);
+  if (n) cnt[(size_t)q * Wp + tau] += n;
+}
+
 // g2 = (hi + lo) / count of each lag bin (f32 pair sums, added in FP64); NaN without pairs
 __global__ void stream_g2_kernel(const float2* g2sum, const long long* cnt, int n_q, long long W, long long Wp,
                                  double* g2) {
@@ -365,6 +370,22 @@ __global__ void basis_f32_kernel(const double* B, long long n, float* B32) {
 }
 
 }  // namespace
+
+bool stream_step_row1(const StreamStep& s) {
+  const int n_kc = s.kpad / 64;
+  return s.b == 1 && s.n_q <= 36 && s.tmW48 && n_kc <= (s.sp ? 4 : 2) &&
+         row1_tc_smem(n_kc, stream_npad(s.n_q), s.sp) <= 227 * 1024;
+}
+
+cudaError_t launch_count_flush(const unsigned long long* vbits, long long vwords, long long cap, int n_q,
+                               long long W, long long Wp, long long* cnt, long long t0, unsigned long long mask,
+                               unsigned long long done, cudaStream_t st) {
+  if (!mask || done == ~0ull) return cudaSuccess;
+  const long long n = (long long)n_q * W;
+  count_flush_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vbits, vwords, cap, n_q, W, Wp, cnt, t0, mask,
+                                                                  done);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   // the pair-ordered w rows of this step must fit the W2 allocation
@@ -423,8 +444,10 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     stream_fold_kernel<<<(unsigned)((s.n_q * span + 255) / 256), 256, 0, st>>>(s, nd_step);
     return cudaGetLastError();
   }
-  if (s.b == 1 && s.n_q <= 36 && s.tmW48) {
-    // one frame: the persistent single-frame kernel (lag tiles of 128, direct fold)
+  if (stream_step_row1(s)) {
+    // one frame: the persistent single-frame kernel (lag tiles of 128, direct fold; its
+    // pair count is deferred to its count block, and it adds one part of the deferred
+    // counts of the block before)
     Row1Params p1{};
     p1.t = s.t0;
     p1.W = s.W;
@@ -440,9 +463,14 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     p1.Rh = s.Rh;
     p1.g2sum = s.g2sum;
     p1.cnt = s.cnt;
+    p1.vbits = s.vbits;
+    p1.vwords = s.vwords;
+    p1.cf_t0 = s.cf_t0;
+    p1.cf_mask = s.cf_mask;
+    p1.cf_tau0 = s.cf_tau0;
+    p1.cf_tau1 = s.cf_tau1;
     p1.status = s.status;
-    if (p1.n_kc <= (s.sp ? 4 : 2) && row1_tc_smem(p1.n_kc, p1.qb, s.sp) <= 227 * 1024)
-      return launch_row1_tc(*s.tmA, *s.tmW48, *s.tmR, p1, std::min(p1.n_tiles, s.num_sms), st);
+    return launch_row1_tc(*s.tmA, *s.tmW48, *s.tmR, p1, std::min(p1.n_tiles, s.num_sms), st);
   }
   // row update of the step (at most 64 frames: every pair of a lag tile then lies in
   // one 128-row history operand)

@@ -321,6 +321,39 @@ xpcs_status retire(xpcs_stream* S) {
   return XPCS_OK;
 }
 
+// Add the deferred pair counts still missing: the parts of the block before that are not
+// done, and (all) also the latest block's.  Enqueued on the stream's CUDA stream.
+cudaError_t flush_counts(xpcs_stream* S, bool all) {
+  const long long vw = stream_vwords(S->cap), Wp = wpitch(S->W);
+  cudaError_t e = cudaSuccess;
+  if (S->cf_prev)
+    e = launch_count_flush(S->d_vbits, vw, S->cap, S->n_q, S->W, Wp, S->d_cnt, (S->cf_blk - 1) * 64, S->cf_prev,
+                           S->cf_done, S->stream);
+  S->cf_prev = 0;
+  S->cf_done = 0;
+  if (all && e == cudaSuccess) {
+    if (S->cf_cur)
+      e = launch_count_flush(S->d_vbits, vw, S->cap, S->n_q, S->W, Wp, S->d_cnt, S->cf_blk * 64, S->cf_cur, 0ull,
+                             S->stream);
+    S->cf_cur = 0;
+  }
+  return e;
+}
+
+// Before a step that starts in count block blk: the block before the previous one gets
+// its missing parts; a step in the next block makes the latest block the one whose parts
+// its single-frame steps add, and a larger jump flushes both.
+cudaError_t roll_counts(xpcs_stream* S, int64_t blk) {
+  if (blk == S->cf_blk) return cudaSuccess;
+  const bool next = blk == S->cf_blk + 1;
+  const cudaError_t e = flush_counts(S, !next);
+  if (next) S->cf_prev = S->cf_cur;
+  S->cf_cur = 0;
+  S->cf_done = 0;
+  S->cf_blk = blk;
+  return e;
+}
+
 // Enqueue one batch whose counts are already on the device.
 xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream::Stamp* stamp) {
   xpcs_ctx* ctx = S->ctx;
@@ -398,6 +431,22 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
         return es;
       }
       s.pre_encoded = 1;
+    }
+    // pair counts: a single-frame step defers its own to its count block and adds part
+    // (t mod 64) of the block before's; other steps count their frames themselves
+    s.cf_mask = 0;
+    if ((e = roll_counts(S, s.t0 >> 6)) != cudaSuccess) break;
+    if (stream_step_row1(s)) {
+      const int j = (int)(s.t0 & 63);
+      S->cf_cur |= 1ull << j;
+      const long long L = cf_part_len(S->W);
+      if (S->cf_prev && !((S->cf_done >> j) & 1ull) && j * L < S->W) {
+        s.cf_t0 = (S->cf_blk - 1) * 64;
+        s.cf_mask = S->cf_prev;
+        s.cf_tau0 = (int)(j * L);
+        s.cf_tau1 = (int)std::min<long long>(S->W, (j + 1) * L);
+      }
+      S->cf_done |= 1ull << j;
     }
     e = launch_stream_step(s, S->stream);
     if (e == cudaSuccess) ctx->launches += s.b >= STREAM_GRAM_MIN ? 5 : 4;
@@ -536,6 +585,10 @@ extern "C" xpcs_status xpcs_stream_read_g2(xpcs_stream* S, double* g2_host, int6
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
   const int n_q = S->basis->rings->n_q;
   const long long n = (long long)n_q * S->W;
+  {  // the pair counts deferred by single-frame steps
+    const cudaError_t e = flush_counts(S, true);
+    if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream counts: ") + cudaGetErrorString(e));
+  }
   if (g2_host) {
     cudaError_t e = launch_stream_g2(S->d_g2sum, S->d_cnt, n_q, S->W, wpitch(S->W), S->d_g2, S->stream);
     if (e != cudaSuccess) return fail(ctx, XPCS_ECUDA, std::string("stream g2: ") + cudaGetErrorString(e));
@@ -651,6 +704,7 @@ extern "C" xpcs_status xpcs_stream_checkpoint(xpcs_stream* S, void* host_buf, si
   xpcs_stream_checkpoint_size(S, &need);
   if (bytes < need) return fail(ctx, XPCS_EINVAL, "checkpoint buffer too small: need " + std::to_string(need));
   XPCS_CUDA(ctx, cudaSetDevice(ctx->device));
+  XPCS_CUDA(ctx, flush_counts(S, true));  // the pair counts deferred by single-frame steps
   XPCS_CUDA(ctx, cudaStreamSynchronize(S->stream));  // every queued batch folded in
   XPCS_TRY(retire(S));
   CkptHeader h{};
@@ -709,5 +763,7 @@ extern "C" xpcs_status xpcs_stream_restore(xpcs_stream* S, const void* host_buf,
     off += b[i];
   }
   S->frames = h.frames;
+  S->cf_blk = -1;  // a checkpoint holds every pair count
+  S->cf_cur = S->cf_prev = S->cf_done = 0;
   return XPCS_OK;
 }

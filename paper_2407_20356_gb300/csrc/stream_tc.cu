@@ -583,8 +583,11 @@ cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW,
 
 // ====================================================================== single frames
 // Steps of one frame t (at most 36 rings): for every lag tau < min(W, t + 1), ring q,
-//     g2sum_q[tau] += (w_q(t) . a_s) r_q(s),  cnt_q[tau] += 1,  s = t - tau,
-// when r_q(t) > 0 and r_q(s) > 0 (both frames defined).  Work item = a tile of 128 lags
+//     g2sum_q[tau] += (w_q(t) . a_s) r_q(s),  s = t - tau,
+// when r_q(t) > 0 and r_q(s) > 0 (both frames defined).  The pair counts are deferred to
+// the frame's count block of 64 frames (a pass over all lags per frame would cost as many
+// bytes as the sums); the kernel adds instead one 64th of the lag range of the deferred
+// counts of the block before, from the validity bits.  Work item = a tile of 128 lags
 // tau0 .. tau0 + 127, history rows s = t - tau0 - 127 + c (c = 0..127): D[c][q] = a_s . w_q
 // on the tensor cores (M = the 128 history rows, N = 48 >= 36 ring columns, bf16 hi | lo
 // pieces as in the row update kernel, the same products in the same order; or one f16
@@ -593,8 +596,7 @@ cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW,
 // tile's loads overlap the previous tile's epilogue; the frame's w rows are loaded once.
 // Eight epilogue warps (TMEM lane quarter = warp mod 4, rings 18 h .. 18 h + 17 for
 // h = (warp - 2) / 4): the thread of lane c adds its lag's product to the running sum (f32
-// pair, TwoSum) and count of each ring in global memory, 32 consecutive lags per warp
-// access.  Each (ring, lag) has one owner: no atomics, the additions of every step in
+// pair, TwoSum) of each ring in global memory, 32 consecutive lags per warp access.  Each (ring, lag) has one owner: no atomics, the additions of every step in
 // stream order.  Every mbarrier wait is bounded.
 namespace {
 
@@ -748,6 +750,19 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
     float rt[18];
 #pragma unroll
     for (int u = 0; u < 18; ++u) rt[u] = u < qn ? p.Rh[slot_t * p.npad + q0 + u] : 0.f;
+    // deferred pair counts (ring, lag) of the block before, spread over the epilogue threads
+    // of all CTAs while the first tiles load
+    if (p.cf_mask) {
+      const long long nl = p.cf_tau1 - p.cf_tau0;
+      const long long n = (long long)p.n_q * nl;
+      const int nth = R1_EPI_WARPS * 32;
+      for (long long e = (long long)blockIdx.x * nth + (threadIdx.x - 64); e < n; e += (long long)gridDim.x * nth) {
+        const int q = (int)(e / nl);
+        const long long tau = p.cf_tau0 + (e - (long long)q * nl);
+        const long long m = masked_pair_count(p.vbits + (size_t)q * p.vwords, p.cap, p.cf_t0, p.cf_mask, tau);
+        if (m) p.cnt[(size_t)q * p.Wp + tau] += m;
+      }
+    }
     uint32_t i = 0;
     for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++i) {
       const uint32_t bi = i & 1, ph = (i >> 1) & 1;
@@ -774,21 +789,16 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
       const long long tau = (long long)tile * RT_ROWS + (RT_ROWS - 1 - c);
       if (tau >= p.W || tau > t || qn == 0) continue;
       float2* gs = p.g2sum + (size_t)q0 * p.Wp + tau;
-      long long* cn = p.cnt + (size_t)q0 * p.Wp + tau;
       // two batches of nine rings: loads of a batch in flight together, then the adds
 #pragma unroll
       for (int u0 = 0; u0 < 18; u0 += 9) {
         bool pr[9];
         float2 acc[9];
-        long long cv[9];
 #pragma unroll
         for (int e = 0; e < 9; ++e) {
           const int u = u0 + e;
           pr[e] = u < qn && rt[u] > 0.f && rs[u] > 0.f;
-          if (pr[e]) {
-            acc[e] = gs[(size_t)u * p.Wp];
-            cv[e] = cn[(size_t)u * p.Wp];
-          }
+          if (pr[e]) acc[e] = gs[(size_t)u * p.Wp];
         }
 #pragma unroll
         for (int e = 0; e < 9; ++e) {
@@ -796,7 +806,6 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
           if (pr[e]) {
             const float d = __uint_as_float(h ? v[u + 2] : v[u]);  // compile-time register indices
             gs[(size_t)u * p.Wp] = f32pair_add(acc[e], d * rs[u]);
-            cn[(size_t)u * p.Wp] = cv[e] + 1;
           }
         }
       }

@@ -366,3 +366,55 @@ def test_stream_precision_options_and_checkpoints(X, ctx):
     assert np.array_equal(np.isnan(gr), np.isnan(gf)) and np.array_equal(gr[~np.isnan(gr)], gf[~np.isnan(gf)])
     full.close()
     resumed.close()
+
+
+def test_stream_deferred_pair_counts(X, ctx):
+    # single-frame steps defer their pair counts to blocks of 64 frames, added one 64th of
+    # the lag range per later single-frame step (or at a read, a checkpoint, or a larger
+    # step): exact counts at reads in mid-block, around larger steps and across a
+    # checkpoint, with about a third of the frames undefined in a ring (exact ring sums of
+    # sparse frames: a ring without photons has S = 0)
+    H, W, n_q, k, T, Wl = 24, 40, 4, 20, 560, 150
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 250, np.uint16, 4242, mean=0.004)
+    G, s, Mq = O.ring_factors(B, qmap, n_q)
+    A = O.encode(Xs, B)
+    S = O.ring_sums(Xs, qmap, n_q)
+    assert (S == 0).mean() > 0.1
+
+    def check(st, Tr, tol):
+        g2, cnt = st.read_g2()
+        C = O.compressed_twotime_exact_sums(A[:Tr], G, S[:, :Tr], Mq)
+        m = min(Tr, Wl)  # lags beyond the frames so far have no pairs
+        for q in range(n_q):
+            g_ref, c_ref = O.windowed_g2(C[q], Wl)
+            np.testing.assert_array_equal(cnt[q][:m], c_ref[:m])
+            assert not cnt[q][m:].any() and np.isnan(g2[q][m:]).all()
+            rm, _ = rel_errors(g2[q][:m], g_ref[:m])
+            assert rm < tol, (Tr, q, rm)
+
+    # one frame at a time, a 5-frame step at frame 100, a 40-frame step at 180, reads at
+    # 131 (mid-block) and 300, a checkpoint at 400 (mid-block) resumed in a fresh stream
+    plan = [1] * 100 + [5] + [1] * 75 + [40] + [1] * 180 + [1] * 160
+    st = X.Stream(ctx, basis, Wl, 64, qmean="exact_raw")
+    i = 0
+    for n in plan:
+        st.push(np.ascontiguousarray(Xs[i:i + n]))
+        i += n
+        if i in (131, 300):
+            check(st, i, 1e-4)
+        if i == 400:
+            ck = st.checkpoint()
+            st.close()
+            st = X.Stream(ctx, basis, Wl, 64, qmean="exact_raw")
+            st.restore(ck)
+    assert i == T
+    check(st, T, 1e-4)
+    st.close()
+    # the same in f16
+    st = X.Stream(ctx, basis, Wl, 64, qmean="exact_raw", prec="fp16")
+    i = 0
+    for n in plan:
+        st.push(np.ascontiguousarray(Xs[i:i + n]))
+        i += n
+    check(st, T, 1e-3)
+    st.close()
