@@ -135,6 +135,7 @@ struct xpcs_stream {
   long long* d_cnt = nullptr;        // n_q x Wp
   float* d_part = nullptr;           // max_batch x nblk x k sparse-encode partials
   float* d_a = nullptr;              // max_batch x k
+  unsigned* d_se_done = nullptr;     // 128 per-frame counters of the sparse encode's slice blocks
   __nv_bfloat16* d_W2 = nullptr;     // (max_batch n_q) x 2 kpad  r_q(t) a_t G_q, bf16 hi | lo
   double* d_g2 = nullptr;            // n_q x W read-out buffer
   // XPCS_QMEAN_EXACT_RAW: the stream's own copy of the ring labels (M) and a step's exact

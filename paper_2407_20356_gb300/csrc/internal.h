@@ -226,6 +226,7 @@ struct StreamStep {
   long long* Sx;           // nullable b x n_q exact ring sums (zeroed by the step launch)
   float* part;             // b x nblk x k
   float* a;                // b x k
+  unsigned* se_done;       // b slice blocks finished per frame (the last adds the partials)
   __nv_bfloat16* W2;       // (max_batch n_q) x 2 kpad: w_q(t) rows, bf16 hi | lo
   __nv_bfloat16* A2;       // (cap + 128) x 2 kpad: coefficient history, bf16 hi | lo;
                            // rows cap .. cap + 127 mirror rows 0 .. 127

@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
   __shared__ float nz_val[SE_PX];
   __shared__ int warp_tot[8];
   __shared__ float red[256];
+  __shared__ float4 red4[256];
+  __shared__ int se_last;
   __shared__ unsigned ring_acc[SE_MAX_RINGS];  // exact ring sums of this slice (at most 2^28)
   pdl_trigger();
   const int blk = blockIdx.x, fi = blockIdx.y;
@@ -104,6 +106,127 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
   }
   // accumulate: ng groups of k threads split the nonzero list
   const int k = s.k;
+  if ((k & 3) == 0) {
+    // 16-byte loads: a group of k / 4 threads reads a basis row (a warp reads 512 bytes at
+    // once for k = 128), 256 / (k / 4) groups split the nonzero list and each thread keeps
+    // eight rows' loads in flight; the groups' sums are added in a fixed order
+    const int k4 = k >> 2, ng = 256 / k4;
+    const int g = tid / k4, j4 = tid - g * k4;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g < ng) {
+      const float4* B4 = reinterpret_cast<const float4*>(s.B32) + j4;
+      float4 a8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a8[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      int e = g;
+      for (; e + 7 * ng < total; e += 8 * ng) {
+        float4 b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) b[u] = __ldg(B4 + (size_t)nz_idx[e + u * ng] * k4);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float x = nz_val[e + u * ng];
+          a8[u].x = fmaf(x, b[u].x, a8[u].x);
+          a8[u].y = fmaf(x, b[u].y, a8[u].y);
+          a8[u].z = fmaf(x, b[u].z, a8[u].z);
+          a8[u].w = fmaf(x, b[u].w, a8[u].w);
+        }
+      }
+      for (; e < total; e += ng) {
+        const float4 b = __ldg(B4 + (size_t)nz_idx[e] * k4);
+        const float x = nz_val[e];
+        a8[0].x = fmaf(x, b.x, a8[0].x);
+        a8[0].y = fmaf(x, b.y, a8[0].y);
+        a8[0].z = fmaf(x, b.z, a8[0].z);
+        a8[0].w = fmaf(x, b.w, a8[0].w);
+      }
+#pragma unroll
+      for (int u = 1; u < 8; ++u) {
+        a8[0].x += a8[u].x;
+        a8[0].y += a8[u].y;
+        a8[0].z += a8[u].z;
+        a8[0].w += a8[u].w;
+      }
+      a = a8[0];
+    }
+    red4[tid] = a;
+    // the slice partials are rewritten only once the kernels ahead (the previous step's,
+    // which read them) have completed
+    pdl_wait();
+    __syncthreads();
+    float4* part4 = reinterpret_cast<float4*>(s.part);
+    if (tid < k4) {
+      float4 t = red4[tid];
+      for (int gg = 1; gg < ng; ++gg) {
+        const float4 v = red4[gg * k4 + tid];
+        t.x += v.x;
+        t.y += v.y;
+        t.z += v.z;
+        t.w += v.w;
+      }
+      part4[((size_t)fi * s.nblk + blk) * k4 + tid] = t;
+    }
+    // the frame's last slice block adds the nblk partials: a_t[j], 8 slice groups x 32
+    // column quads (group g: slices g, g + 8, ... in order, then the groups in order)
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) se_last = atomicAdd(s.se_done + fi, 1u) == (unsigned)(s.nblk - 1);
+    __syncthreads();
+    if (!se_last) return;
+    __threadfence();
+    const int cg = tid >> 5;
+    for (int c0 = 0; c0 < k4; c0 += 32) {
+      const int c4 = c0 + lane;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c4 < k4) {
+        const float4* src = part4 + (size_t)fi * s.nblk * k4 + c4;
+        float4 a4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        int b0 = cg;
+        for (; b0 + 3 * 8 < s.nblk; b0 += 4 * 8) {
+          float4 x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[u] = __ldcg(src + (size_t)(b0 + 8 * u) * k4);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            a4[u].x += x[u].x;
+            a4[u].y += x[u].y;
+            a4[u].z += x[u].z;
+            a4[u].w += x[u].w;
+          }
+        }
+        for (; b0 < s.nblk; b0 += 8) {
+          const float4 x = __ldcg(src + (size_t)b0 * k4);
+          a4[0].x += x.x;
+          a4[0].y += x.y;
+          a4[0].z += x.z;
+          a4[0].w += x.w;
+        }
+        acc.x = (a4[0].x + a4[1].x) + (a4[2].x + a4[3].x);
+        acc.y = (a4[0].y + a4[1].y) + (a4[2].y + a4[3].y);
+        acc.z = (a4[0].z + a4[1].z) + (a4[2].z + a4[3].z);
+        acc.w = (a4[0].w + a4[1].w) + (a4[2].w + a4[3].w);
+      }
+      red4[tid] = acc;
+      __syncthreads();
+      if (cg == 0 && c4 < k4) {
+        float4 t = red4[lane];
+#pragma unroll
+        for (int gg = 1; gg < 8; ++gg) {
+          const float4 v = red4[gg * 32 + lane];
+          t.x += v.x;
+          t.y += v.y;
+          t.z += v.z;
+          t.w += v.w;
+        }
+        reinterpret_cast<float4*>(s.a + (size_t)fi * k)[c4] = t;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) s.se_done[fi] = 0u;  // ready for the next step
+    return;
+  }
   for (int j0 = 0; j0 < k; j0 += 256) {
     const int kk = min(256, k - j0);
     const int ng = max(1, 256 / kk);
@@ -122,6 +245,7 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
       acc = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
     }
     red[tid] = acc;
+    if (j0 == 0) pdl_wait();  // the previous step's kernels read the partials
     __syncthreads();
     if (tid < kk) {
       float a = 0.f;
@@ -130,9 +254,9 @@ __global__ void __launch_bounds__(256) sparse_encode_kernel(const StreamStep s) 
     }
     __syncthreads();
   }
-  // reads nothing the kernels ahead wrote, so it only waits before it ends (the frame
-  // factors behind it rewrite rows that the previous step's kernels read)
-  pdl_wait();
+  // (it waited before its first partial store: the kernels ahead, the previous step's,
+  // read the partials, and the frame factors behind it rewrite rows they read; waiting
+  // also keeps completion transitive along the chain)
 }
 
 // a_t[j] = sum of the nblk slice partials of frame t.  Block = 32 (frame, column) pairs x
@@ -189,10 +313,15 @@ XPCS_DEV void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-__global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) {
+// SPLIT (1 or 4) threads per w column split the k terms of w_q(t) (one-frame steps: the
+// G_q loads of a column in one round instead of four), their sums added in split order.
+template <int SPLIT>
+XPCS_DEV void frame_factors(const StreamStep& s) {
+  constexpr int NW = 4 * SPLIT;  // warps
   __shared__ float as[256];
-  __shared__ double dred[4];
-  __shared__ unsigned mred[4];
+  __shared__ double dred[NW];
+  __shared__ unsigned mred[NW];
+  __shared__ float vpart[SPLIT][256];
   pdl_trigger();
   pdl_wait();  // the coefficients
   const int fi = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
@@ -219,14 +348,20 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
   __syncthreads();
   int e2 = 0;  // f16 history rows: 2^e2 a_t
   if (s.sp) {
-    const float am = __uint_as_float(max(max(mred[0], mred[1]), max(mred[2], mred[3])));
+    unsigned mb = mred[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) mb = max(mb, mred[w]);
+    const float am = __uint_as_float(mb);
     if (am > 0.f && isfinite(am)) {
       int ex;
       frexpf(am, &ex);  // am in [2^(ex-1), 2^ex)
       e2 = min(64, max(-64, 14 - ex));
     }
   }
-  const double S = s.Sx ? (double)s.Sx[(size_t)fi * s.n_q + q] : dred[0] + dred[1] + dred[2] + dred[3];
+  double Sd = dred[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) Sd += dred[w];  // warps past the k terms add zeros
+  const double S = s.Sx ? (double)s.Sx[(size_t)fi * s.n_q + q] : Sd;
   const float r = S > 0.0 ? (float)(sqrt((double)s.Mq[q]) / S) : 0.f;
   const int npad = stream_npad(s.n_q);
   if (tid == 0) {
@@ -250,27 +385,34 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
   __nv_bfloat16* wrow = gram ? s.Wg + ((size_t)q * 128 + (t & 127)) * 2 * kp
                              : s.W2 + (size_t)w2_pair_row(fi, q, s.b, s.n_q) * 2 * kp;
   const float* Gq = s.G32 + (size_t)q * k * k;
-  for (int j = tid; j < kp; j += blockDim.x) {
+  const int jt = SPLIT == 1 ? tid : tid & 127, ks = SPLIT == 1 ? 0 : tid >> 7;  // column thread, k split
+  const int c_lo = SPLIT == 1 ? 0 : ks * k / SPLIT, c_hi = SPLIT == 1 ? k : (ks + 1) * k / SPLIT;
+  for (int j = jt; j < kp; j += 128) {
     float v = 0.f;
     if (j < k && r > 0.f) {
       float v4[4] = {0.f, 0.f, 0.f, 0.f};
-      int c = 0;
+      int c = c_lo;
       // 32 loads of G_q in flight at a time (a one-frame step has only n_q blocks); chain
-      // u takes rows u, u + 4, u + 8, ... in order
-      for (; c + 32 <= k; c += 32) {
+      // u takes rows u, u + 4, u + 8, ... of the split in order
+      for (; c + 32 <= c_hi; c += 32) {
         float g[32];
 #pragma unroll
         for (int u = 0; u < 32; ++u) g[u] = Gq[(size_t)(c + u) * k + j];
 #pragma unroll
         for (int u = 0; u < 32; ++u) v4[u & 3] = fmaf(as[c + u], g[u], v4[u & 3]);
       }
-      for (; c + 4 <= k; c += 4) {
+      for (; c + 4 <= c_hi; c += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) v4[u] = fmaf(as[c + u], Gq[(size_t)(c + u) * k + j], v4[u]);
       }
-      for (; c < k; ++c) v4[0] = fmaf(as[c], Gq[(size_t)c * k + j], v4[0]);
-      v = ((v4[0] + v4[1]) + (v4[2] + v4[3])) * r;
+      for (; c < c_hi; ++c) v4[0] = fmaf(as[c], Gq[(size_t)c * k + j], v4[0]);
+      v = (v4[0] + v4[1]) + (v4[2] + v4[3]);
     }
+    if (SPLIT > 1) {
+      vpart[ks][j] = v;
+      continue;
+    }
+    v *= r;
     if (s.sp) {
       reinterpret_cast<__half*>(wrow)[j] = __float2half_rn(v);
     } else {
@@ -278,6 +420,26 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
       split_bf16(v, hi, lo);
       wrow[j] = hi;
       wrow[kp + j] = lo;
+    }
+  }
+  if (SPLIT > 1) {
+    __syncthreads();
+    for (int j = tid; j < kp; j += blockDim.x) {
+      float v = 0.f;
+      if (j < k && r > 0.f) {
+        v = vpart[0][j];
+#pragma unroll
+        for (int u = 1; u < SPLIT; ++u) v += vpart[u][j];
+        v *= r;
+      }
+      if (s.sp) {
+        reinterpret_cast<__half*>(wrow)[j] = __float2half_rn(v);
+      } else {
+        __nv_bfloat16 hi, lo;
+        split_bf16(v, hi, lo);
+        wrow[j] = hi;
+        wrow[kp + j] = lo;
+      }
     }
   }
   if (q == 0 && s.sp) {
@@ -303,6 +465,9 @@ __global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) 
     }
   }
 }
+
+__global__ void __launch_bounds__(128) frame_factors_kernel(const StreamStep s) { frame_factors<1>(s); }
+__global__ void __launch_bounds__(512, 1) frame_factors_split_kernel(const StreamStep s) { frame_factors<4>(s); }
 
 // After a step on the two-time kernel: lag tau = 128 d + e gets slot 128 + e of tile
 // diagonal d and slot e of tile diagonal d + 1 (TwoSum into the f32-pair sums), its pair
@@ -398,10 +563,15 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
   // dependent launches: each kernel may start while the one ahead of it finishes
   if (!s.pre_encoded) {
     if ((e = launch_pdl(sparse_encode_kernel, dim3(s.nblk, s.b), dim3(256), 0, st, s)) != cudaSuccess) return e;
-    if ((e = launch_pdl(stream_reduce_kernel, dim3((s.b * s.k + 31) / 32), dim3(256), 0, st, s)) != cudaSuccess)
+    // with k a multiple of 4 the sparse encode's last slice block of a frame adds the
+    // partials itself
+    if ((s.k & 3) &&
+        (e = launch_pdl(stream_reduce_kernel, dim3((s.b * s.k + 31) / 32), dim3(256), 0, st, s)) != cudaSuccess)
       return e;
   }
-  if ((e = launch_pdl(frame_factors_kernel, dim3(s.b, s.n_q), dim3(128), 0, st, s)) != cudaSuccess) return e;
+  if ((e = s.b == 1 ? launch_pdl(frame_factors_split_kernel, dim3(s.b, s.n_q), dim3(512), 0, st, s)
+                     : launch_pdl(frame_factors_kernel, dim3(s.b, s.n_q), dim3(128), 0, st, s)) != cudaSuccess)
+    return e;
   if (s.b >= STREAM_GRAM_MIN) {
     // the two-time kernel on (history block J - delta, the step's block J) tiles of every
     // ring: L = the coefficient history (shared by the rings), R = the block's w rows of

@@ -48,7 +48,7 @@ int nblk_of(int64_t M) { return (int)((M + 4095) / 4096); }
 int64_t wpitch(int64_t W) { return (W + 63) / 64 * 64; }
 
 struct Sizes {
-  size_t frames, A2, Rh, vbits, g2sum, cnt, part, a, W2, g2, stage, Wg, gpart;
+  size_t frames, A2, Rh, vbits, g2sum, cnt, part, a, W2, g2, stage, Wg, gpart, se;
 };
 
 Sizes stream_sizes(int64_t M, int n_q, int k, int64_t W, int max_batch, int eb) {
@@ -69,6 +69,7 @@ Sizes stream_sizes(int64_t M, int n_q, int k, int64_t W, int max_batch, int eb) 
   z.stage = (size_t)max_batch * M * eb;
   z.Wg = (size_t)n_q * 128 * 2 * kpad_of(k) * 2;
   z.gpart = (size_t)n_q * stream_nd(W) * DIAG_SLOTS * 4;
+  z.se = (size_t)STEP_MAX_GRAM * 4;  // per-frame counters of the sparse encode's slice blocks
   return z;
 }
 
@@ -87,6 +88,7 @@ void stream_free(xpcs_stream* S) {
   dev_free(ctx, S->d_W2, z.W2);
   dev_free(ctx, S->d_Wg, z.Wg);
   dev_free(ctx, S->d_gpart, z.gpart);
+  dev_free(ctx, S->d_se_done, z.se);
   if (S->h_status) cudaFreeHost(S->h_status);
   dev_free(ctx, S->d_g2, z.g2);
   dev_free(ctx, S->d_qmap, (size_t)S->M * 4);
@@ -112,7 +114,7 @@ namespace xpcs {
 
 size_t stream_footprint(const xpcs_basis* B, int64_t W, int max_batch, int elem_bytes) {
   const Sizes z = stream_sizes(B->M, B->n_q, B->k, W, max_batch, elem_bytes);
-  size_t b = z.frames + z.A2 + z.Rh + z.vbits + z.g2sum + z.cnt + z.part + z.a + z.W2 + z.g2 + z.Wg + z.gpart;
+  size_t b = z.frames + z.A2 + z.Rh + z.vbits + z.g2sum + z.cnt + z.part + z.a + z.W2 + z.g2 + z.Wg + z.gpart + z.se;
   if (!B->d_B32) b += (size_t)B->rings->M * B->k * 4;  // f32 basis copy made on first use
   return b;
 }
@@ -201,6 +203,7 @@ extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B,
   XPCS_SALLOC(d_g2, z.g2, double*)
   XPCS_SALLOC(d_Wg, z.Wg, __nv_bfloat16*)
   XPCS_SALLOC(d_gpart, z.gpart, float*)
+  XPCS_SALLOC(d_se_done, z.se, unsigned*)
   if (exact) {
     XPCS_SALLOC(d_qmap, (size_t)B->rings->M * 4, int*)
     XPCS_SALLOC(d_Sx, (size_t)STEP_MAX_GRAM * B->rings->n_q * 8, long long*)
@@ -229,6 +232,7 @@ extern "C" xpcs_status xpcs_stream_open_opts(xpcs_ctx* ctx, const xpcs_basis* B,
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_vbits, 0, z.vbits, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_g2sum, 0, z.g2sum, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_cnt, 0, z.cnt, S->stream);
+  if (st == XPCS_OK && e == cudaSuccess) e = cudaMemsetAsync(S->d_se_done, 0, z.se, S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
   if (st == XPCS_OK && e == cudaSuccess) e = cudaEventCreate(&S->base_ev);
   if (st == XPCS_OK && e == cudaSuccess) e = calibrate_clock(S);
@@ -379,6 +383,7 @@ xpcs_status enqueue_batch(xpcs_stream* S, const void* X, int64_t n, xpcs_stream:
   s.qmap = S->d_qmap;
   s.Sx = S->d_Sx;
   s.part = S->d_part;
+  s.se_done = S->d_se_done;
   s.a = S->d_a;
   s.W2 = S->d_W2;
   s.A2 = S->d_A2;
