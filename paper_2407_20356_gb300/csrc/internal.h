@@ -311,6 +311,8 @@ struct Row1Params {
   int n_q, kpad, n_kc, npad, qb, n_tiles;  // qb = npad (r values per history row)
   long long Wp;            // row pitch of g2sum / cnt
   int sp;                  // 1: f16 rows, one product (hi halves only)
+  int sb, qg2;             // sb = 2: each tile's g2 sums (qg2 = min(36, n_q) rings x 128 lags)
+                           // staged in shared memory by TMA ahead of the epilogue; 0: read in place
   const float* Rh;         // (cap + 128) x npad
   float2* g2sum;           // n_q x Wp
   long long* cnt;          // n_q x Wp (only the deferred counts below)
@@ -321,10 +323,11 @@ struct Row1Params {
   int cf_tau0, cf_tau1;
   uint32_t* status;
 };
-int row1_tc_smem(int n_kc, int qb, int sp);
-// tensor maps: A2 history (64 x 128 boxes), W2 (64 x 48 boxes), Rh (qb x 128 boxes)
-cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR, const Row1Params& p,
-                           int grid, cudaStream_t st);
+int row1_tc_smem(int n_kc, int qb, int sp, int sb, int qg2);
+// tensor maps: A2 history (64 x 128 boxes), W2 (64 x 48 boxes), Rh (qb x 128 boxes),
+// g2sum (128 x qg2 boxes)
+cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
+                           const CUtensorMap& tmG, const Row1Params& p, int grid, cudaStream_t st);
 // tensor maps: A2 history, W2 pairs, Rh r values, g2sum and cnt (lt x qg2 boxes)
 cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
                                  const CUtensorMap& tmG, const CUtensorMap& tmC, const RowTcParams& p, int grid,

@@ -539,7 +539,7 @@ __global__ void basis_f32_kernel(const double* B, long long n, float* B32) {
 bool stream_step_row1(const StreamStep& s) {
   const int n_kc = s.kpad / 64;
   return s.b == 1 && s.n_q <= 36 && s.tmW48 && n_kc <= (s.sp ? 4 : 2) &&
-         row1_tc_smem(n_kc, stream_npad(s.n_q), s.sp) <= 227 * 1024;
+         row1_tc_smem(n_kc, stream_npad(s.n_q), s.sp, 0, std::min(36, s.n_q)) <= 227 * 1024;
 }
 
 cudaError_t launch_count_flush(const unsigned long long* vbits, long long vwords, long long cap, int n_q,
@@ -630,6 +630,9 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     p1.n_tiles = (int)((std::min<long long>(s.W, s.t0 + 1) + 127) / 128);
     p1.Wp = s.Wp;
     p1.sp = s.sp;
+    p1.qg2 = std::min(36, s.n_q);
+    // the tiles' g2 sums staged in shared memory when two slices fit beside the rest
+    p1.sb = row1_tc_smem(p1.n_kc, p1.qb, s.sp, 2, p1.qg2) <= 227 * 1024 ? 2 : 0;
     p1.Rh = s.Rh;
     p1.g2sum = s.g2sum;
     p1.cnt = s.cnt;
@@ -640,7 +643,8 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     p1.cf_tau0 = s.cf_tau0;
     p1.cf_tau1 = s.cf_tau1;
     p1.status = s.status;
-    return launch_row1_tc(*s.tmA, *s.tmW48, *s.tmR, p1, std::min(p1.n_tiles, s.num_sms), st);
+    return launch_row1_tc(*s.tmA, *s.tmW48, *s.tmR, s.tmG[rt_lt_index(128)], p1, std::min(p1.n_tiles, s.num_sms),
+                          st);
   }
   // row update of the step (at most 64 frames: every pair of a lag tile then lies in
   // one 128-row history operand)

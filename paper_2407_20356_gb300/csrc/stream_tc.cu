@@ -607,29 +607,37 @@ constexpr int R1_WCHUNK = R1_N * RT_CH * 2;   // 6 KB: 48 w rows x 128 B
 
 struct R1Layout {
   int n_kc, qb, np;  // np: pieces per row (2: bf16 hi | lo, 1: f16)
+  int sb, qg2;       // sb: staged g2-sum slices (0 or 2) of qg2 rings x 128 lags
   __host__ __device__ int hist_bytes() const { return np * n_kc * RT_CHUNK; }
   __host__ __device__ int w_bytes() const { return np * n_kc * R1_WCHUNK; }
   __host__ __device__ int rs_bytes() const { return (RT_ROWS * qb * 4 + 1023) / 1024 * 1024; }
-  __host__ __device__ int smem() const { return 1024 + 2 * hist_bytes() + w_bytes() + 2 * rs_bytes() + 256; }
+  __host__ __device__ int sums_bytes() const { return (qg2 * RT_ROWS * 8 + 1023) / 1024 * 1024; }
+  __host__ __device__ int smem() const {
+    return 1024 + 2 * hist_bytes() + w_bytes() + 2 * rs_bytes() + sb * sums_bytes() + 256;
+  }
 };
 
 __global__ void __launch_bounds__(R1_THREADS, 1)
     row1_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
-                   const __grid_constant__ CUtensorMap tmR, const Row1Params p) {
+                   const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmG,
+                   const Row1Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const R1Layout L{p.n_kc, p.qb, p.sp ? 1 : 2};
+  const R1Layout L{p.n_kc, p.qb, p.sp ? 1 : 2, p.sb, p.qg2};
   uint8_t* hist = smem;                                 // [2][hi kc..., lo kc...]
   uint8_t* wbuf = smem + 2 * L.hist_bytes();            // [hi kc..., lo kc...] 48-row chunks
   uint8_t* rsb = wbuf + L.w_bytes();                    // [2][128][qb] r of the rows
-  uint64_t* bars = reinterpret_cast<uint64_t*>(rsb + 2 * L.rs_bytes());
+  uint8_t* sums = rsb + 2 * L.rs_bytes();               // [sb][qg2][128] staged g2 sums (f32 pairs)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sums + L.sb * L.sums_bytes());
   uint64_t* h_full = bars;       // [2] history rows + their r values landed
   uint64_t* h_empty = bars + 2;  // [2] MMAs and epilogue done with them
   uint64_t* w_full = bars + 4;   // the frame's w rows landed
   uint64_t* tfull = bars + 5;    // [2] accumulator ready
   uint64_t* tempty = bars + 7;   // [2] accumulator read
   uint64_t* mma_done = bars + 9;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  uint64_t* s_full = bars + 10;   // [2] staged sums landed
+  uint64_t* s_empty = bars + 12;  // [2] staged sums read
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -641,6 +649,8 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
       mbar_init(&h_empty[b], 1 + R1_EPI_WARPS);
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], R1_EPI_WARPS);
+      mbar_init(&s_full[b], 1);
+      mbar_init(&s_empty[b], R1_EPI_WARPS);
     }
     mbar_init(w_full, 1);
     mbar_init(mma_done, 1);
@@ -664,6 +674,7 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
       tma_prefetch_desc(&tmA);
       tma_prefetch_desc(&tmW);
       tma_prefetch_desc(&tmR);
+      if (p.sb) tma_prefetch_desc(&tmG);
       mbar_arrive_expect_tx(w_full, (uint32_t)L.w_bytes());
       for (int kc = 0; kc < p.n_kc; ++kc) {
         tma_load_2d(wbuf + kc * R1_WCHUNK, &tmW, w_full, kc * RT_CH, 0);
@@ -672,7 +683,8 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
       uint32_t i = 0;
       for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++i) {
         const uint32_t bi = i & 1;
-        if (*abort_flag || !mbar_wait(&h_empty[bi], ((i >> 1) & 1) ^ 1, p.status)) {
+        if (*abort_flag || !mbar_wait(&h_empty[bi], ((i >> 1) & 1) ^ 1, p.status) ||
+            (p.sb && !mbar_wait(&s_empty[bi], ((i >> 1) & 1) ^ 1, p.status))) {
           *abort_flag = 1;
           break;
         }
@@ -687,10 +699,19 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
           if (!p.sp) tma_load_2d(hb + (p.n_kc + kc) * RT_CHUNK, &tmA, &h_full[bi], p.kpad + kc * RT_CH, y);
         }
         tma_load_2d(rsb + bi * L.rs_bytes(), &tmR, &h_full[bi], 0, y);
+        if (p.sb) {
+          // the tile's running sums (lags tile * 128 .. + 127 of the qg2 rings; lags past
+          // the window read as zeros and are not written back)
+          mbar_arrive_expect_tx(&s_full[bi], (uint32_t)(p.qg2 * RT_ROWS * 8));
+          tma_load_2d(sums + bi * L.sums_bytes(), &tmG, &s_full[bi], tile * RT_ROWS, 0);
+        }
       }
       // never leave the CTA with bulk copies in flight
       mbar_wait(w_full, 0, p.status);
-      for (uint32_t j = (i > 2 ? i - 2 : 0); j < i; ++j) mbar_wait(&h_full[j & 1], (j >> 1) & 1, p.status);
+      for (uint32_t j = (i > 2 ? i - 2 : 0); j < i; ++j) {
+        mbar_wait(&h_full[j & 1], (j >> 1) & 1, p.status);
+        if (p.sb) mbar_wait(&s_full[j & 1], (j >> 1) & 1, p.status);
+      }
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -787,8 +808,31 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
         mbar_arrive(&h_empty[bi]);
       }
       const long long tau = (long long)tile * RT_ROWS + (RT_ROWS - 1 - c);
-      if (tau >= p.W || tau > t || qn == 0) continue;
+      const bool live = !(tau >= p.W || tau > t || qn == 0);
       float2* gs = p.g2sum + (size_t)q0 * p.Wp + tau;
+      if (p.sb) {
+        // the running sums come from the staged slice (ring q0 + u, lag 127 - c of the
+        // tile): no load latency in the loop, only the stores of the new sums
+        if (!mbar_wait_warp(&s_full[bi], ph, p.status)) {
+          *abort_flag = 1;
+          break;
+        }
+        const float2* ss = reinterpret_cast<const float2*>(sums + bi * L.sums_bytes()) + (size_t)q0 * RT_ROWS +
+                           (RT_ROWS - 1 - c);
+        if (live) {
+#pragma unroll
+          for (int u = 0; u < 18; ++u) {
+            if (u < qn && rt[u] > 0.f && rs[u] > 0.f) {
+              const float d = __uint_as_float(h ? v[u + 2] : v[u]);  // compile-time register indices
+              gs[(size_t)u * p.Wp] = f32pair_add(ss[(size_t)u * RT_ROWS], d * rs[u]);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[bi]);
+        continue;
+      }
+      if (!live) continue;
       // two batches of nine rings: loads of a batch in flight together, then the adds
 #pragma unroll
       for (int u0 = 0; u0 < 18; u0 += 9) {
@@ -822,14 +866,16 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
 
 }  // namespace
 
-int row1_tc_smem(int n_kc, int qb, int sp) { return R1Layout{n_kc, qb, sp ? 1 : 2}.smem(); }
+int row1_tc_smem(int n_kc, int qb, int sp, int sb, int qg2) { return R1Layout{n_kc, qb, sp ? 1 : 2, sb, qg2}.smem(); }
 
-cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR, const Row1Params& p,
-                           int grid, cudaStream_t st) {
+cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const CUtensorMap& tmR,
+                           const CUtensorMap& tmG, const Row1Params& p, int grid, cudaStream_t st) {
   // at most 256 elements of the history rows' pieces (two 64-wide chunks of hi | lo, or four
   // of f16)
-  if (p.n_q < 1 || p.n_q > 36 || p.qb < p.n_q || p.n_kc < 1 || p.n_kc > (p.sp ? 4 : 2)) return cudaErrorInvalidValue;
-  const int smem = row1_tc_smem(p.n_kc, p.qb, p.sp);
+  if (p.n_q < 1 || p.n_q > 36 || p.qb < p.n_q || p.n_kc < 1 || p.n_kc > (p.sp ? 4 : 2) ||
+      (p.sb != 0 && p.sb != 2) || p.qg2 != std::min(36, p.n_q))
+    return cudaErrorInvalidValue;
+  const int smem = row1_tc_smem(p.n_kc, p.qb, p.sp, p.sb, p.qg2);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   static int attr_bytes = 0;  // the attribute only ever grows
   if (smem > attr_bytes) {
@@ -837,7 +883,7 @@ cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  return launch_pdl(row1_tc_kernel, dim3(grid), dim3(R1_THREADS), (size_t)smem, st, tmA, tmW, tmR, p);
+  return launch_pdl(row1_tc_kernel, dim3(grid), dim3(R1_THREADS), (size_t)smem, st, tmA, tmW, tmR, tmG, p);
 }
 
 }  // namespace xpcs
