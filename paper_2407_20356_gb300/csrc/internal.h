@@ -311,8 +311,9 @@ struct Row1Params {
   int n_q, kpad, n_kc, npad, qb, n_tiles;  // qb = npad (r values per history row)
   long long Wp;            // row pitch of g2sum / cnt
   int sp;                  // 1: f16 rows, one product (hi halves only)
-  int sb, qg2;             // sb = 2: each tile's g2 sums (qg2 = min(36, n_q) rings x 128 lags)
-                           // staged in shared memory by TMA ahead of the epilogue; 0: read in place
+  int sb, qg2;             // sb = 2 (1): each tile's g2 sums (qg2 = min(36, n_q) rings x 128
+                           // lags) staged in shared memory by TMA in two slices, one tile ahead
+                           // (in one slice); 0: read in place
   const float* Rh;         // (cap + 128) x npad
   float2* g2sum;           // n_q x Wp
   long long* cnt;          // n_q x Wp (only the deferred counts below)

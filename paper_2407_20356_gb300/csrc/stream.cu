@@ -631,8 +631,10 @@ cudaError_t launch_stream_step(const StreamStep& s, cudaStream_t st) {
     p1.Wp = s.Wp;
     p1.sp = s.sp;
     p1.qg2 = std::min(36, s.n_q);
-    // the tiles' g2 sums staged in shared memory when two slices fit beside the rest
-    p1.sb = row1_tc_smem(p1.n_kc, p1.qb, s.sp, 2, p1.qg2) <= 227 * 1024 ? 2 : 0;
+    // the tiles' g2 sums staged in shared memory in as many slices (two, one) as fit
+    p1.sb = row1_tc_smem(p1.n_kc, p1.qb, s.sp, 2, p1.qg2) <= 227 * 1024   ? 2
+            : row1_tc_smem(p1.n_kc, p1.qb, s.sp, 1, p1.qg2) <= 227 * 1024 ? 1
+                                                                            : 0;
     p1.Rh = s.Rh;
     p1.g2sum = s.g2sum;
     p1.cnt = s.cnt;

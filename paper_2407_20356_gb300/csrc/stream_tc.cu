@@ -607,7 +607,7 @@ constexpr int R1_WCHUNK = R1_N * RT_CH * 2;   // 6 KB: 48 w rows x 128 B
 
 struct R1Layout {
   int n_kc, qb, np;  // np: pieces per row (2: bf16 hi | lo, 1: f16)
-  int sb, qg2;       // sb: staged g2-sum slices (0 or 2) of qg2 rings x 128 lags
+  int sb, qg2;       // sb: staged g2-sum slices (0, 1 or 2) of qg2 rings x 128 lags
   __host__ __device__ int hist_bytes() const { return np * n_kc * RT_CHUNK; }
   __host__ __device__ int w_bytes() const { return np * n_kc * R1_WCHUNK; }
   __host__ __device__ int rs_bytes() const { return (RT_ROWS * qb * 4 + 1023) / 1024 * 1024; }
@@ -680,11 +680,10 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
         tma_load_2d(wbuf + kc * R1_WCHUNK, &tmW, w_full, kc * RT_CH, 0);
         if (!p.sp) tma_load_2d(wbuf + (p.n_kc + kc) * R1_WCHUNK, &tmW, w_full, p.kpad + kc * RT_CH, 0);
       }
-      uint32_t i = 0;
-      for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++i) {
+      uint32_t i = 0, ns = 0;  // tiles whose history rows, and whose sums, were loaded
+      for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
         const uint32_t bi = i & 1;
-        if (*abort_flag || !mbar_wait(&h_empty[bi], ((i >> 1) & 1) ^ 1, p.status) ||
-            (p.sb && !mbar_wait(&s_empty[bi], ((i >> 1) & 1) ^ 1, p.status))) {
+        if (*abort_flag || !mbar_wait(&h_empty[bi], ((i >> 1) & 1) ^ 1, p.status)) {
           *abort_flag = 1;
           break;
         }
@@ -699,19 +698,26 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
           if (!p.sp) tma_load_2d(hb + (p.n_kc + kc) * RT_CHUNK, &tmA, &h_full[bi], p.kpad + kc * RT_CH, y);
         }
         tma_load_2d(rsb + bi * L.rs_bytes(), &tmR, &h_full[bi], 0, y);
+        ++i;
         if (p.sb) {
           // the tile's running sums (lags tile * 128 .. + 127 of the qg2 rings; lags past
-          // the window read as zeros and are not written back)
-          mbar_arrive_expect_tx(&s_full[bi], (uint32_t)(p.qg2 * RT_ROWS * 8));
-          tma_load_2d(sums + bi * L.sums_bytes(), &tmG, &s_full[bi], tile * RT_ROWS, 0);
+          // the window read as zeros and are not written back), into its slice once the
+          // epilogue has read the slice's tile before (two slices: two tiles before)
+          const uint32_t sbi = p.sb == 2 ? (ns & 1) : 0u, sph = p.sb == 2 ? ((ns >> 1) & 1) : (ns & 1);
+          if (*abort_flag || !mbar_wait(&s_empty[sbi], sph ^ 1, p.status)) {
+            *abort_flag = 1;
+            break;
+          }
+          mbar_arrive_expect_tx(&s_full[sbi], (uint32_t)(p.qg2 * RT_ROWS * 8));
+          tma_load_2d(sums + sbi * L.sums_bytes(), &tmG, &s_full[sbi], tile * RT_ROWS, 0);
+          ++ns;
         }
       }
       // never leave the CTA with bulk copies in flight
       mbar_wait(w_full, 0, p.status);
-      for (uint32_t j = (i > 2 ? i - 2 : 0); j < i; ++j) {
-        mbar_wait(&h_full[j & 1], (j >> 1) & 1, p.status);
-        if (p.sb) mbar_wait(&s_full[j & 1], (j >> 1) & 1, p.status);
-      }
+      for (uint32_t j = (i > 2 ? i - 2 : 0); j < i; ++j) mbar_wait(&h_full[j & 1], (j >> 1) & 1, p.status);
+      for (uint32_t j = (ns > (uint32_t)p.sb ? ns - p.sb : 0); j < ns; ++j)
+        mbar_wait(&s_full[p.sb == 2 ? (j & 1) : 0u], p.sb == 2 ? ((j >> 1) & 1) : (j & 1), p.status);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -813,11 +819,12 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
       if (p.sb) {
         // the running sums come from the staged slice (ring q0 + u, lag 127 - c of the
         // tile): no load latency in the loop, only the stores of the new sums
-        if (!mbar_wait_warp(&s_full[bi], ph, p.status)) {
+        const uint32_t sbi = p.sb == 2 ? bi : 0u, sph = p.sb == 2 ? ph : (i & 1);
+        if (!mbar_wait_warp(&s_full[sbi], sph, p.status)) {
           *abort_flag = 1;
           break;
         }
-        const float2* ss = reinterpret_cast<const float2*>(sums + bi * L.sums_bytes()) + (size_t)q0 * RT_ROWS +
+        const float2* ss = reinterpret_cast<const float2*>(sums + sbi * L.sums_bytes()) + (size_t)q0 * RT_ROWS +
                            (RT_ROWS - 1 - c);
         if (live) {
 #pragma unroll
@@ -829,7 +836,7 @@ __global__ void __launch_bounds__(R1_THREADS, 1)
           }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[bi]);
+        if (lane == 0) mbar_arrive(&s_empty[sbi]);
         continue;
       }
       if (!live) continue;
@@ -873,7 +880,7 @@ cudaError_t launch_row1_tc(const CUtensorMap& tmA, const CUtensorMap& tmW, const
   // at most 256 elements of the history rows' pieces (two 64-wide chunks of hi | lo, or four
   // of f16)
   if (p.n_q < 1 || p.n_q > 36 || p.qb < p.n_q || p.n_kc < 1 || p.n_kc > (p.sp ? 4 : 2) ||
-      (p.sb != 0 && p.sb != 2) || p.qg2 != std::min(36, p.n_q))
+      p.sb < 0 || p.sb > 2 || p.qg2 != std::min(36, p.n_q))
     return cudaErrorInvalidValue;
   const int smem = row1_tc_smem(p.n_kc, p.qb, p.sp, p.sb, p.qg2);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
