@@ -418,3 +418,33 @@ def test_stream_deferred_pair_counts(X, ctx):
         i += n
     check(st, T, 1e-3)
     st.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16"])
+def test_stream_single_frames_at_long_history(X, ctx, prec):
+    # 36 rings and k = 128: one frame at a time takes the single-frame kernel with each
+    # tile's running sums staged in shared memory (one slice for bf16x3 rows, two for f16),
+    # and with 157 lag tiles over at most 152 CTAs some fold two tiles, so the slices'
+    # phases turn over.  The same frames in steps of two (the row update kernel, which
+    # counts its pairs itself) give the same counts and g2 up to the products' summation
+    # order.
+    H, W, n_q, k, T, Wl = 48, 48, 36, 128, 20200, 20000
+    Xs, B, qmap, rings, basis = _setup(X, ctx, H, W, n_q, k, T, 400, np.uint16, 1571, mean=0.3)
+    a = X.Stream(ctx, basis, Wl, 2, prec=prec)
+    b = X.Stream(ctx, basis, Wl, 2, prec=prec)
+    t = 0
+    for i in range(T):
+        t = a.push(Xs[i:i + 1])
+    assert a.poll(t, 60000)
+    for i in range(0, T, 2):
+        t = b.push(Xs[i:i + 2])
+    assert b.poll(t, 60000)
+    ga, ca = a.read_g2()
+    gb, cb = b.read_g2()
+    np.testing.assert_array_equal(ca, cb)
+    assert ca[:, 0].min() > 0 and ca[:, Wl - 1].min() > 0
+    ok = ~np.isnan(ga)
+    assert np.array_equal(ok, ~np.isnan(gb))
+    np.testing.assert_allclose(ga[ok], gb[ok], rtol=1e-5)
+    a.close()
+    b.close()
