@@ -11,9 +11,12 @@
 //   2. frame factors: S~_q(t) = a_t s_q (or the exact S_q(t)), r_q(t) = sqrt(M_q)/S~_q(t)
 //      (0 if undefined),
 //      w_q(t) = r_q(t) a_t G_q; a_t and r_q(t) go into the ring buffer slot of t.
-//   3. row update: for every lag tau < W, thread tau takes history row s = t - tau and adds
-//      C_q(t, s) = w_q(t) . a_s r_q(s) to g2sum_q[tau] (count_q[tau] += 1) for all rings.
-//      Each thread owns its lag bins: no atomics, deterministic for a given batching.
+//   3. row update: for every lag tau < W and ring q, C_q(t, s) = w_q(t) . a_s r_q(s) with
+//      s = t - tau is added to g2sum_q[tau] and the pair to count_q[tau] (on the tensor
+//      cores: the single-frame kernel, the row update kernel, or the two-time kernel and
+//      its fold for steps of 32 frames or more; single frames defer their pair counts to
+//      64-frame blocks).  Each (ring, lag) bin has one owner per step: no atomics,
+//      deterministic for a given batching.
 #include <math.h>
 
 #include <algorithm>

@@ -594,9 +594,13 @@ cudaError_t launch_row_update_tc(const CUtensorMap& tmA, const CUtensorMap& tmW,
 // product of the hi pieces when the stream computes in f16).  The CTA is
 // persistent over its tiles and double-buffers the history rows and their r values, so a
 // tile's loads overlap the previous tile's epilogue; the frame's w rows are loaded once.
+// Where shared memory allows (two slices for f16 rows, one for bf16 hi | lo rows) the
+// producer also loads each tile's running sums (qg2 rings x 128 lags) into a slice as
+// soon as the slice is free, so the epilogue reads them without global-load latency.
 // Eight epilogue warps (TMEM lane quarter = warp mod 4, rings 18 h .. 18 h + 17 for
 // h = (warp - 2) / 4): the thread of lane c adds its lag's product to the running sum (f32
-// pair, TwoSum) of each ring in global memory, 32 consecutive lags per warp access.  Each (ring, lag) has one owner: no atomics, the additions of every step in
+// pair, TwoSum) of each ring and stores it to global memory, 32 consecutive lags per warp
+// access.  Each (ring, lag) has one owner: no atomics, the additions of every step in
 // stream order.  Every mbarrier wait is bounded.
 namespace {
 
