@@ -3,8 +3,9 @@
 The stream folds every pushed frame's two-time row into g2 sums over lags < W.  The
 reference is the FP64 oracle of the compressed two-time matrix of the same frames from
 the same FP64 basis, averaged along diagonals with lags >= W dropped.  The stream works in
-f32 (sparse encode, k-term dot products), so g2 agrees to 1e-4 of max|g2|; pair counts are
-exact.
+f32 (sparse encode, k-term dot products) with bf16x3 products, so g2 agrees to 1e-4 of
+max|g2|; a stream opened in f16 (one product of f16 rows) is held to 1e-3.  Pair counts are
+exact, including the counts that single-frame steps defer to 64-frame blocks.
 """
 import numpy as np
 import pytest
